@@ -1,0 +1,550 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle.
+
+Each test checks one part of the oracle against a closed form, a value the
+paper prints, a published known answer, a library routine, or brute force;
+chosen so that a dropped term, a wrong sign or index, or a transposed operand
+in that part fails here.  No GPU is needed.
+"""
+import dataclasses
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import orc
+from paper_2310_04957_gb300 import workloads as W
+from util import beam, field_only, grounded_box, rel_l2, with_particles
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EPS0 = 8.8541878128e-12
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the published known-answer vectors (Salmon et al. SC'11)."""
+    rows = []
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        rows.append([int(x, 16) for x in line.split()])
+    assert len(rows) == 3
+    for row in rows:
+        ctr, key, want = row[:4], row[4:6], row[6:]
+        assert list(orc.philox(ctr, key)) == want
+
+
+def test_philox_uniformity():
+    """Uniforms from consecutive counters pass a chi-square test of equidistribution."""
+    u = []
+    for c in range(4000):
+        x = orc.philox([c, 7, 1, 0x5EED], [12345, 0])
+        u.extend((int(v) >> 8) / 2**24 for v in x)
+    h, _ = np.histogram(u, bins=20, range=(0, 1))
+    exp = len(u) / 20
+    chi2 = ((h - exp) ** 2 / exp).sum()
+    assert chi2 < 45.0  # 19 dof, p ~ 1e-3
+
+
+# ---------------------------------------------------------------- cross sections
+def test_xs_lookup_matches_linear_interpolation():
+    """Between table nodes the lookup is linear interpolation (numpy.interp); clamped outside;
+    inelastic processes vanish below threshold."""
+    wl = W.small_cylinder(n_per_species=16)
+    o = orc.Oracle(with_particles(wl))
+    E_tab, S = wl.xs_energy, wl.xs_sigma
+    rng = np.random.default_rng(1)
+    Es = np.concatenate([10 ** rng.uniform(-3.5, 3.5, 400), E_tab[::97]])
+    for proc in range(5):
+        want = np.interp(Es, E_tab, S[proc])
+        if proc == 1:
+            want = np.where(Es < W.THR_EXC, 0.0, want)
+        if proc == 2:
+            want = np.where(Es < W.THR_ION, 0.0, want)
+        got = np.array([o.xs(proc, e) for e in Es])
+        np.testing.assert_allclose(got, want, rtol=1e-13, atol=0)
+
+
+def test_numax_bounds_every_energy():
+    """nu_max is an upper bound of n_g sigma_T(E) v(E) over the table range, and is attained
+    within the interpolation slack (at most the largest neighbouring-node ratio)."""
+    wl = W.small_cylinder(n_per_species=16)
+    o = orc.Oracle(with_particles(wl))
+    s = o.scalars()
+    E = np.logspace(-3, 3, 20001)
+    sig_e = sum(np.interp(E, wl.xs_energy, wl.xs_sigma[p]) * (E >= thr) for p, thr in ((0, 0), (1, W.THR_EXC), (2, W.THR_ION)))
+    nu_e = wl.n_gas * sig_e * np.sqrt(2 * E * W.ELEMENTARY_CHARGE / W.ELECTRON_MASS)
+    sig_i = np.interp(E, wl.xs_energy, wl.xs_sigma[3]) + np.interp(E, wl.xs_energy, wl.xs_sigma[4])
+    nu_i = wl.n_gas * sig_i * np.sqrt(2 * E * W.ELEMENTARY_CHARGE / W.ARGON_MASS)
+    assert nu_e.max() <= s["numax_e"] * (1 + 1e-12)
+    assert nu_i.max() <= s["numax_i"] * (1 + 1e-12)
+    assert nu_e.max() > 0.98 * s["numax_e"]
+    assert nu_i.max() > 0.98 * s["numax_i"]
+    assert s["pcoll_e"] == pytest.approx(1 - math.exp(-s["numax_e"] * wl.dt), rel=1e-14)
+
+
+# ---------------------------------------------------------------- kinematics primitives
+def test_scatter_cos_is_inverse_cdf():
+    """cos chi = (2 + E - 2(1+E)^R)/E is the inverse of R = ln(1 + E sin^2(chi/2)) / ln(1 + E)
+    (Vahedi & Surendra's screened angular distribution), with the limits R=0 -> forward,
+    R=1 -> backward, E->0 -> isotropic."""
+    rng = np.random.default_rng(2)
+    for _ in range(300):
+        E = 10 ** rng.uniform(-3, 3)
+        R = rng.uniform()
+        c = orc.scatter_cos(E, R)
+        s2 = (1 - c) / 2
+        assert math.log1p(E * s2) / math.log1p(E) == pytest.approx(R, abs=1e-9)
+    assert orc.scatter_cos(50.0, 0.0) == pytest.approx(1.0, abs=1e-15)
+    assert orc.scatter_cos(50.0, 1.0) == pytest.approx(-1.0, abs=1e-15)
+    assert orc.scatter_cos(1e-14, 0.25) == pytest.approx(0.5, abs=1e-15)
+
+
+def test_turn_rotates_by_the_given_angles():
+    """The turned vector is a unit vector at polar angle chi from the original; over uniform
+    azimuths it averages to cos(chi) times the original (no preferred side)."""
+    rng = np.random.default_rng(3)
+    for _ in range(100):
+        c = rng.normal(size=3)
+        c /= np.linalg.norm(c)
+        cc = rng.uniform(-1, 1)
+        phis = np.linspace(0, 2 * math.pi, 64, endpoint=False)
+        outs = np.array([orc.turn(c, cc, ph) for ph in phis])
+        np.testing.assert_allclose(np.linalg.norm(outs, axis=1), 1.0, atol=1e-13)
+        np.testing.assert_allclose(outs @ c, cc, atol=1e-13)
+        np.testing.assert_allclose(outs.mean(axis=0), cc * c, atol=1e-12)
+    # degenerate direction along z
+    for sgn in (1.0, -1.0):
+        out = orc.turn(np.array([0.0, 0.0, sgn]), 0.3, 1.1)
+        assert np.linalg.norm(out) == pytest.approx(1.0)
+        assert out[2] * sgn == pytest.approx(0.3)
+
+
+# ---------------------------------------------------------------- mover
+def _collisionless(wl):
+    return dataclasses.replace(wl, n_gas=0.0)
+
+
+def test_free_flight_is_a_straight_line():
+    """E = 0, no collisions: the r-z mover with cylindrical rotation reproduces straight-line
+    Cartesian motion r(t) = |(r0 + vr t, vt t)|, z = z0 + vz t, with r v_theta conserved,
+    including particles that pass through the axis."""
+    base = _collisionless(W.small_cylinder(n_per_species=16))
+    rng = np.random.default_rng(4)
+    n = 400
+    r0 = rng.uniform(0.005, 0.03, n)
+    z0 = rng.uniform(0.008, 0.017, n)
+    v = rng.normal(0, 2e4, (3, n))
+    v[0, :50] = -np.abs(v[0, :50]) * 5  # head for the axis
+    v[1, :50] *= 0.01
+    zeros = np.zeros(n)
+    P = W.Particles(r0, z0, v[0], v[1], v[2], zeros, zeros.copy(), zeros.copy(), np.arange(n, dtype=np.uint64))
+    wl = with_particles(base, electrons=P)
+    o = orc.Oracle(wl)
+    o.set_field("Er", np.zeros(o.n_nodes))
+    o.set_field("Ez", np.zeros(o.n_nodes))
+    nsteps = 12
+    for k in range(nsteps):
+        o.set_step(k)
+        o.particle_phase()
+    g = o.get_particles(0)
+    assert len(g["id"]) == n  # nothing reached a wall
+    idx = g["id"].astype(np.int64)
+    t = nsteps * wl.dt
+    X = r0[idx] + v[0, idx] * t
+    Y = v[1, idx] * t
+    np.testing.assert_allclose(g["r"], np.hypot(X, Y), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(g["z"], z0[idx] + v[2, idx] * t, rtol=1e-12)
+    np.testing.assert_allclose(g["r"] * g["vt"], r0[idx] * v[1, idx], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(g["vr"] ** 2 + g["vt"] ** 2, v[0, idx] ** 2 + v[1, idx] ** 2, rtol=1e-12)
+
+
+def test_uniform_field_d1_push_is_exact_parabola():
+    """Constant E_z, start-up state x~_0 = z0 - dt^2 a/2, v = v0 - 3/2 dt a, a-bar = a:
+    the D1 push gives z_n = z0 + v0 t + a t^2 / 2 exactly, so x~_{n+1} = z_{n+1} - dt^2 a/2."""
+    base = _collisionless(W.small_cylinder(n_per_species=16))
+    Ez = -2000.0
+    qm = base.q[0] / base.m[0]
+    a = qm * Ez
+    dt = base.dt
+    n = 50
+    rng = np.random.default_rng(5)
+    z0 = rng.uniform(0.004, 0.006, n)
+    v0 = rng.uniform(-1e5, 1e5, n)
+    r0 = rng.uniform(0.01, 0.02, n)
+    zeros = np.zeros(n)
+    P = W.Particles(r0, z0 - 0.5 * dt * dt * a, zeros.copy(), zeros.copy(), v0 - 1.5 * dt * a, zeros.copy(),
+                    zeros.copy(), a * np.ones(n), np.arange(n, dtype=np.uint64))
+    o = orc.Oracle(with_particles(base, electrons=P))
+    o.set_field("Er", np.zeros(o.n_nodes))
+    o.set_field("Ez", Ez * np.ones(o.n_nodes))
+    nsteps = 8
+    for k in range(nsteps):
+        o.set_step(k)
+        o.particle_phase()
+    g = o.get_particles(0)
+    idx = g["id"].astype(np.int64)
+    t1 = nsteps * dt  # x~ after nsteps phases predicts z at t_nsteps
+    want = z0[idx] + v0[idx] * t1 + 0.5 * a * t1 * t1 - 0.5 * dt * dt * a
+    np.testing.assert_allclose(g["z"], want, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(g["r"], r0[idx], rtol=1e-14)
+    # stored velocity after the last phase is v_{n-1/2} with n = nsteps - 1: v0 + a (n - 1/2) dt
+    np.testing.assert_allclose(g["vz"], v0[idx] + a * ((nsteps - 1.5) * dt), rtol=1e-10)
+
+
+# ---------------------------------------------------------------- weighting
+def test_area_weighting_moments():
+    """Deposited weights sum to one and reproduce r^2 and z linearly (the volume weighting's
+    defining moments); a uniform density is recovered exactly by the node volumes."""
+    base = W.small_cylinder(n_per_species=16)
+    rng = np.random.default_rng(6)
+    R, Z = base.nr * base.dr, base.nz * base.dz
+    for _ in range(20):
+        r, z = rng.uniform(0, R * 0.999), rng.uniform(0, Z * 0.999)
+        P = beam(1, r, z, (0, 0, 0))
+        o = orc.Oracle(with_particles(base, electrons=P))
+        o.deposit_only()
+        d = o.field("dep_e")
+        rr = (np.arange(base.nr + 1) * base.dr)[None, :]
+        zz = (np.arange(base.nz + 1) * base.dz)[:, None]
+        assert d.sum() == pytest.approx(1.0, abs=1e-14)
+        assert (d * rr**2).sum() == pytest.approx(r * r, rel=1e-12)
+        assert (d * zz).sum() == pytest.approx(z, rel=1e-12)
+        assert (d >= -1e-15).all()
+    # node volumes: sum equals the plasma volume; interior node volume 2 pi r dr dz
+    o = orc.Oracle(with_particles(base))
+    V = o.field("vnode")
+    assert V.sum() == pytest.approx(math.pi * R * R * Z, rel=1e-13)
+    i, j = 7, 5
+    assert V[j, i] == pytest.approx(2 * math.pi * i * base.dr * base.dr * base.dz, rel=1e-13)
+    assert V[j, 0] == pytest.approx(0.5 * math.pi * base.dr**2 * base.dz, rel=1e-13)
+
+
+# ---------------------------------------------------------------- field solve
+def test_manufactured_quadratic_is_exact():
+    """phi = (R^2 - r^2) z (L - z) solves the 5-point axisymmetric finite-volume form of Eq. 1
+    (eps uniform, chi = 0) exactly when the node charge is the source f = eps0 [4 z(L-z) +
+    2 (R^2 - r^2)] times the node's axial face area times dz; PCG reaches it to 1e-10."""
+    nr, nz, R, L = 24, 20, 0.05, 0.03
+    node, cell, eps = grounded_box(nr, nz, R, L)
+    wl = field_only(nr, nz, R, L, node, cell, eps)
+    o = orc.Oracle(wl)
+    o.assemble()
+    dr, dz = R / nr, L / nz
+    r = np.arange(nr + 1) * dr
+    z = np.arange(nz + 1) * dz
+    rh = np.minimum((np.arange(nr + 1) + 0.5) * dr, R)
+    rl = np.maximum((np.arange(nr + 1) - 0.5) * dr, 0)
+    area = math.pi * (rh**2 - rl**2)
+    f = EPS0 * (4 * (z * (L - z))[:, None] + 2 * (R * R - r * r)[None, :])
+    q = f * area[None, :] * dz
+    o.set_field("rho", q)
+    st, it, rel = o.solve_tol(1e-13)
+    assert st == 0
+    exact = (R * R - r * r)[None, :] * (z * (L - z))[:, None]
+    phi = o.field("phi")
+    assert rel_l2(phi, exact) < 1e-10
+    # E at interior nodes: central difference of a quadratic is exact for E_z
+    Ez = o.field("Ez")
+    assert np.abs(Ez[1:-1, 1:-1] - (-(R * R - r * r)[None, 1:-1] * (L - 2 * z)[1:-1, None])).max() < 1e-8 * np.abs(Ez).max()
+
+
+def test_layered_dielectric_capacitor():
+    """Plates at z = 0 (1 V) and z = L (0 V), Neumann outer wall, dielectric layer eps_r = 4
+    below row k: phi is piecewise linear with continuous D, and C_eq from the field energy
+    (Eqs. 6-7) equals eps0 pi R^2 / (d1/eps_r + d2) exactly; the Gauss-law charge agrees."""
+    nr, nz, R, L = 16, 24, 0.04, 0.024
+    k, er = 9, 4.0
+    node, cell, eps = grounded_box(nr, nz, R, L, neumann_wall=True, powered_bottom=True)
+    eps[:k, :] = er
+    cell[:k, :] = W.CELL_DIELECTRIC
+    wl = field_only(nr, nz, R, L, node, cell, eps, V=1.0, phase=math.pi / 2)
+    o = orc.Oracle(wl)
+    ceq, gauss = o.ceq()
+    d1, d2 = k * L / nz, (nz - k) * L / nz
+    want = EPS0 * math.pi * R * R / (d1 / er + d2)
+    assert ceq == pytest.approx(want, rel=1e-11)
+    assert gauss == pytest.approx(want, rel=1e-9)
+    o.init_fields()
+    phi = o.field("phi")
+    z = np.arange(nz + 1) * L / nz
+    Dn = 1.0 / (d1 / er + d2)  # D / eps0
+    exact = np.where(z <= d1, 1.0 - Dn * z / er, 1.0 - Dn * d1 / er - Dn * (z - d1))
+    np.testing.assert_allclose(phi, np.broadcast_to(exact[:, None], phi.shape), atol=1e-10)
+
+
+def test_parallel_plate_ceq_vacuum():
+    """Vacuum parallel plates with a Neumann outer wall: C_eq = eps0 pi R^2 / d on any grid."""
+    for nr, nz in ((8, 5), (20, 33)):
+        R, d = 0.051, 0.0254
+        node, cell, eps = grounded_box(nr, nz, R, d, neumann_wall=True, powered_bottom=True)
+        o = orc.Oracle(field_only(nr, nz, R, d, node, cell, eps))
+        c, g = o.ceq()
+        assert c == pytest.approx(EPS0 * math.pi * R * R / d, rel=1e-11)
+        assert g == pytest.approx(c, rel=1e-9)
+
+
+def test_pcg_matches_dense_solve():
+    """On small grids with dielectric, metal inserts and random charge, the PCG solution equals
+    a dense direct solve (numpy.linalg.solve) of the same conductance network."""
+    rng = np.random.default_rng(7)
+    for trial in range(3):
+        nr, nz = 9 + trial, 7 + 2 * trial
+        R, Z = 0.02, 0.015
+        node, cell, eps = grounded_box(nr, nz, R, Z, neumann_wall=(trial == 1), powered_bottom=True)
+        eps[: 2, 3:6] = 3.0
+        cell[: 2, 3:6] = W.CELL_DIELECTRIC
+        node[3:5, 6:8] = W.NODE_GROUNDED
+        cell[3:4, 6:7] = W.CELL_GROUNDED
+        wl = field_only(nr, nz, R, Z, node, cell, eps, V=37.0, phase=0.4)
+        o = orc.Oracle(wl)
+        o.init_fields()
+        q = rng.normal(0, 1e-12, (nz + 1, nr + 1)) * (node == W.NODE_FREE)
+        o.set_field("rho", q)
+        st, it, rel = o.solve_tol(1e-13)
+        assert st == 0
+        Gr, Gz = o.operator()
+        n = (nr + 1) * (nz + 1)
+        A = np.zeros((n, n))
+        idx = lambda i, j: j * (nr + 1) + i
+        for j in range(nz + 1):
+            for i in range(nr):
+                a, b, g = idx(i, j), idx(i + 1, j), Gr[j, i]
+                A[a, a] += g; A[b, b] += g; A[a, b] -= g; A[b, a] -= g
+        for j in range(nz):
+            for i in range(nr + 1):
+                a, b, g = idx(i, j), idx(i, j + 1), Gz[j, i]
+                A[a, a] += g; A[b, b] += g; A[a, b] -= g; A[b, a] -= g
+        U = 37.0 * math.sin(0.4)
+        fixed = node.ravel() != W.NODE_FREE
+        phid = np.where(node.ravel() == W.NODE_POWERED, U, 0.0)
+        free = ~fixed
+        rhs = q.ravel()[free] - A[np.ix_(free, fixed)] @ phid[fixed]
+        sol = np.linalg.solve(A[np.ix_(free, free)], rhs)
+        phi = o.field("phi").ravel()
+        assert rel_l2(phi[free], sol) < 1e-10
+        assert np.all(phi[fixed] == phid[fixed])
+
+
+# ---------------------------------------------------------------- circuit
+def _phasor_rlc(V, f, Rb, Lb, Cb, Ceq):
+    w = 2 * math.pi * f
+    Zb = Rb + 1j * w * Lb + 1 / (1j * w * Cb)
+    Zc = 1 / (1j * w * Ceq)
+    return V * Zc / (Zc + Zb)
+
+
+def _phasor_imn(V, f, Rs, Cm1, Lm, Cm2, Rm, Cst, Rst, Lst, Ceq):
+    w = 2 * math.pi * f
+    Zc = 1 / (1j * w * Ceq)
+    Zst = Rst + 1j * w * Lst + 1 / (1j * w * Cst)
+    Zload = Zc * Zst / (Zc + Zst)
+    Z2 = Rm + 1j * w * Lm + 1 / (1j * w * Cm2) + Zload
+    Z1 = 1 / (1j * w * Cm1)
+    Zin = Z1 * Z2 / (Z1 + Z2)
+    Uin = V * Zin / (Rs + Zin)
+    return Uin * Zload / Z2
+
+
+def _run_circuit(wl, ceq, periods):
+    o = orc.Oracle(wl)
+    o.set_ceq(ceq)
+    o.set_circuit_state(np.zeros(6))
+    o.set_conv_current(0.0)
+    o.set_step(0)
+    N = wl.steps_per_rf
+    U = o.circuit_run(periods * N)[-N:]
+    t = (np.arange((periods - 1) * N, periods * N) + 1) * wl.dt
+    c = 2 / N * np.sum(U * np.exp(-1j * 2 * math.pi * wl.f_src * t))
+    return c, U
+
+
+def test_circuit_rlc_matches_phasor():
+    """Circuit I (Eq. 9) with the electrode as C_eq (Eqs. 5, 8): periodic steady state of the
+    trapezoidal integrator equals the phasor solution of the series R-L-C_b-C_eq loop."""
+    wl = with_particles(W.small_cylinder(n_per_species=16))
+    wl = dataclasses.replace(wl, circuit=W.CIRCUIT_RLC, circ=(0.5, 0.01e-6, 5e-9) + (0.0,) * 5, steps_per_rf=200,
+                             dt=1 / W.F_RF / 200, V_src=100.0)
+    ceq = 7.35e-12
+    c, U = _run_circuit(wl, ceq, 40)
+    want = _phasor_rlc(100.0, W.F_RF, 0.5, 0.01e-6, 5e-9, ceq)
+    # phasor of sin(wt) is -j * amplitude in the e^{-j w t} DFT convention
+    assert abs(c) == pytest.approx(abs(want), rel=2e-5)
+    assert np.angle(c / (-1j * want)) == pytest.approx(0.0, abs=2e-4)
+
+
+def test_circuit_imn_reproduces_paper_vacuum_match():
+    """Circuit II (Eq. 10) with the paper's vacuum numbers (C_eq = 892.07 pF, matched C_m1, C_m2,
+    77 V source): the integrator's steady state equals the phasor solution, and the electrode
+    amplitude is the paper's ~100 V (Sec. 3)."""
+    g = {}
+    for line in open(os.path.join(GOLDEN, "paper_circuit2_vacuum.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v = line.split()
+        g[k] = float(v)
+    circ = (g["R_s"], g["C_m1"], g["L_m"], g["C_m2"], g["R_m"], g["C_stray"], g["R_stray"], g["L_stray"])
+    wl = with_particles(W.small_cylinder(n_per_species=16))
+    wl = dataclasses.replace(wl, circuit=W.CIRCUIT_IMN, circ=circ, steps_per_rf=200, dt=1 / g["f"] / 200,
+                             V_src=g["V_source"], f_src=g["f"])
+    c, U = _run_circuit(wl, g["C_eq"], 500)  # the matched network settles in ~400 periods
+    want = _phasor_imn(g["V_source"], g["f"], *circ, g["C_eq"])
+    assert abs(c) == pytest.approx(abs(want), rel=2e-6)
+    assert abs(want) == pytest.approx(g["U_electrode_amplitude"], rel=5e-3)
+    assert np.abs(U).max() == pytest.approx(g["U_electrode_amplitude"], rel=5e-3)
+
+
+# ---------------------------------------------------------------- MCC
+def _mcc_workload(n_gas, T_gas=300.0, zero_rows=()):
+    wl = W.small_cylinder(n_per_species=16)
+    sig = wl.xs_sigma.copy()
+    for r in zero_rows:
+        sig[r] = 0.0
+    return dataclasses.replace(wl, n_gas=n_gas, T_gas=T_gas, xs_sigma=sig)
+
+
+def _energy_eV(g, mass):
+    return 0.5 * mass * (g["vr"] ** 2 + g["vt"] ** 2 + g["vz"] ** 2) / W.ELEMENTARY_CHARGE
+
+
+def test_electron_collision_counts_match_rates():
+    """Monoenergetic electrons, no field: per process, the number of collisions in one step is
+    N P nu_k(E)/nu_max within 5 binomial standard deviations (null-collision method, Sec. 2)."""
+    for E in (5.0, 30.0, 120.0):
+        base = _mcc_workload(3.2e21)
+        speed = math.sqrt(2 * E * W.ELEMENTARY_CHARGE / W.ELECTRON_MASS)
+        n = 200_000
+        wl = with_particles(base, electrons=beam(n, 0.02, 0.0127, (0.0, 0.0, speed)))
+        o = orc.Oracle(wl)
+        o.set_field("Er", np.zeros(o.n_nodes))
+        o.set_field("Ez", np.zeros(o.n_nodes))
+        o.set_step(3)
+        o.particle_phase()
+        s = o.scalars()
+        P = s["pcoll_e"]
+        nus = [base.n_gas * np.interp(E, base.xs_energy, base.xs_sigma[p]) * speed * (E >= thr)
+               for p, thr in ((0, 0), (1, W.THR_EXC), (2, W.THR_ION))]
+        for nu, key in zip(nus, ("coll_e_el", "coll_e_ex", "coll_e_iz")):
+            p = P * nu / s["numax_e"]
+            mean, sd = n * p, math.sqrt(n * p * (1 - p))
+            assert abs(s[key] - mean) <= 5 * sd + 1, (E, key, s[key], mean)
+        assert s["born_e"] == s["coll_e_iz"] and s["born_i"] == s["coll_e_iz"]
+
+
+def test_ion_collision_counts_cold_gas():
+    """Ions in a (nearly) cold gas: relative speed = ion speed, so counts follow nu_k/nu_max."""
+    E = 8.0
+    base = _mcc_workload(3.2e21, T_gas=1e-9)
+    speed = math.sqrt(2 * E * W.ELEMENTARY_CHARGE / W.ARGON_MASS)
+    n = 200_000
+    wl = with_particles(base, ions=beam(n, 0.02, 0.0127, (speed, 0.0, 0.0)))
+    o = orc.Oracle(wl)
+    o.set_field("Er", np.zeros(o.n_nodes))
+    o.set_field("Ez", np.zeros(o.n_nodes))
+    o.set_step(9)
+    o.particle_phase()
+    s = o.scalars()
+    for proc, key in ((3, "coll_i_iso"), (4, "coll_i_cx")):
+        nu = base.n_gas * np.interp(E, base.xs_energy, base.xs_sigma[proc]) * speed
+        p = s["pcoll_i"] * nu / s["numax_i"]
+        mean, sd = n * p, math.sqrt(n * p * (1 - p))
+        assert abs(s[key] - mean) <= 5 * sd + 1, (key, s[key], mean)
+
+
+def test_ionization_and_excitation_energy_balance():
+    """With only ionization (or only excitation) enabled, the electrons' total kinetic energy
+    drops by exactly 15.76 eV (11.5 eV) per collision: E_in - 15.76 = E_scattered + E_ejected.
+    New Ar+ are Maxwellian at the gas temperature."""
+    E = 100.0
+    speed = math.sqrt(2 * E * W.ELEMENTARY_CHARGE / W.ELECTRON_MASS)
+    n = 100_000
+    for zero_rows, thr, key in (((0, 1), W.THR_ION, "coll_e_iz"), ((0, 2), W.THR_EXC, "coll_e_ex")):
+        base = _mcc_workload(3.0e22, zero_rows=zero_rows)
+        wl = with_particles(base, electrons=beam(n, 0.025, 0.0127, (0.3 * speed, 0.0, 0.9539392014169456 * speed)))
+        o = orc.Oracle(wl)
+        o.set_field("Er", np.zeros(o.n_nodes))
+        o.set_field("Ez", np.zeros(o.n_nodes))
+        o.set_step(1)
+        o.particle_phase()
+        s = o.scalars()
+        g = o.get_particles(0)
+        assert s[key] > 1000
+        total_in = n * 0.5 * W.ELECTRON_MASS * speed**2 / W.ELEMENTARY_CHARGE
+        total_out = _energy_eV(g, W.ELECTRON_MASS).sum()
+        assert total_out == pytest.approx(total_in - s[key] * thr, rel=1e-11)
+        if key == "coll_e_iz":
+            ions = o.get_particles(1)
+            assert len(ions["id"]) == s["coll_e_iz"]
+            sig2 = W.BOLTZMANN * base.T_gas / W.ARGON_MASS
+            for comp in ("vr", "vt", "vz"):
+                v = ions[comp]
+                m = len(v)
+                assert abs(v.mean()) < 5 * math.sqrt(sig2 / m)
+                assert v.var() == pytest.approx(sig2, rel=5 * math.sqrt(2 / m))
+            assert np.all(ions["id"] >= np.uint64(1 << 63))
+            assert len(np.unique(ions["id"])) == len(ions["id"])
+
+
+def test_ion_isotropic_and_charge_exchange_cold_gas():
+    """Cold gas (neutral at rest): charge exchange leaves the ion at rest; isotropic scattering in
+    the centre-of-mass frame of equal masses gives |v'|^2/|v|^2 = (1 + cos theta)/2, uniform on
+    [0, 1] (energy conservation in the CM frame)."""
+    E = 30.0
+    speed = math.sqrt(2 * E * W.ELEMENTARY_CHARGE / W.ARGON_MASS)
+    n = 100_000
+    for zero_row, key in ((4, "coll_i_iso"), (3, "coll_i_cx")):
+        base = _mcc_workload(3.0e23, T_gas=1e-12, zero_rows=(zero_row,))
+        wl = with_particles(base, ions=beam(n, 0.025, 0.0127, (0.0, 0.0, speed)))
+        o = orc.Oracle(wl)
+        o.set_field("Er", np.zeros(o.n_nodes))
+        o.set_field("Ez", np.zeros(o.n_nodes))
+        o.set_step(2)
+        o.particle_phase()
+        s = o.scalars()
+        g = o.get_particles(1)
+        ratio = (g["vr"] ** 2 + g["vt"] ** 2 + g["vz"] ** 2) / speed**2
+        moved = ratio < 1 - 1e-9
+        assert moved.sum() == pytest.approx(s[key], abs=2)
+        if key == "coll_i_cx":
+            assert np.all(ratio[moved] < 1e-15)  # neutral speed at 1e-12 K is ~1e-5 m/s
+        else:
+            x = np.sort(ratio[moved])
+            ks = np.abs(x - np.arange(1, len(x) + 1) / len(x)).max()
+            assert ks < 1.95 / math.sqrt(len(x))  # KS test vs uniform, p ~ 1e-3
+
+
+def test_elastic_energy_loss_bounds():
+    """Electron elastic scattering loses a fraction 2 m/M (1 - cos chi) in [0, 4 m/M] of E."""
+    E = 40.0
+    speed = math.sqrt(2 * E * W.ELEMENTARY_CHARGE / W.ELECTRON_MASS)
+    n = 50_000
+    base = _mcc_workload(3.0e22, zero_rows=(1, 2))
+    wl = with_particles(base, electrons=beam(n, 0.025, 0.0127, (0.0, 0.0, speed)))
+    o = orc.Oracle(wl)
+    o.set_field("Er", np.zeros(o.n_nodes))
+    o.set_field("Ez", np.zeros(o.n_nodes))
+    o.particle_phase()
+    g = o.get_particles(0)
+    frac = 1 - _energy_eV(g, W.ELECTRON_MASS) / E
+    assert (frac > -1e-12).all()
+    assert (frac < 4 * W.ELECTRON_MASS / W.ARGON_MASS + 1e-12).all()
+    assert (frac > 1e-9).sum() == pytest.approx(o.scalars()["coll_e_el"], abs=5)
+
+
+# ---------------------------------------------------------------- whole step
+def test_step_conserves_particles_and_charge():
+    """One full step of the small cylinder: deposited counts sum to the particle numbers, the
+    number balance old + born - absorbed = new holds, and the field residual meets 1e-10."""
+    wl = W.small_cylinder(n_per_species=20_000)
+    o = orc.Oracle(wl)
+    o.init_fields()
+    n0 = [o.count(0), o.count(1)]
+    o.step(1)
+    s = o.scalars()
+    for spc, tag in ((0, "e"), (1, "i")):
+        absn = sum(s[f"absn_{tag}_{k}"] for k in ("pow", "gnd", "surf"))
+        assert o.count(spc) == n0[spc] + s[f"born_{tag}"] - absn
+        assert o.field("dep_e" if spc == 0 else "dep_i").sum() == pytest.approx(o.count(spc), rel=1e-12)
+    assert s["pcg_relres"] <= 1e-10
+    g = o.get_particles(0)
+    assert np.all(np.diff(g["cell"]) >= 0)  # re-binned by cell
