@@ -1,0 +1,234 @@
+/*
+ * pic.h -- C ABI of the GB300 implicit r-z PIC/MCC library (libpic_gb300.so).
+ *
+ * The library advances a 2D axisymmetric electrostatic direct-implicit
+ * particle-in-cell / Monte Carlo collision model of a capacitively coupled
+ * argon discharge driven through an external circuit (arXiv:2310.04957,
+ * Sec. 2).  One handle is one discharge on the current CUDA device.
+ *
+ * Conventions
+ *   - Every function returns PIC_OK (0) or a negative PIC_E* code; nothing
+ *     traps and no C++ exception crosses this boundary.
+ *   - Pointers marked "host" are read or written synchronously and stay owned
+ *     by the caller; the library copies what it keeps.  Device memory the
+ *     library allocates belongs to the handle and is freed by pic_destroy.
+ *   - Work is enqueued on the CUDA stream given to pic_init; functions that
+ *     return host data synchronise that stream first.
+ *   - Node arrays are [(nz+1) x (nr+1)] row-major, index j*(nr+1)+i with
+ *     r_i = i*dr, z_j = j*dz; cell arrays are [nz x nr], index j*nr+i.
+ *   - Species 0 = electrons, 1 = Ar+.
+ */
+#ifndef PIC_GB300_H
+#define PIC_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PIC_OK 0
+#define PIC_EINVAL -1    /* bad argument or configuration */
+#define PIC_ENOMEM -2    /* device or host allocation failed */
+#define PIC_ECUDA -3     /* a CUDA runtime call failed */
+#define PIC_ENOCONV -4   /* field solve hit its iteration cap */
+#define PIC_ETIMEOUT -5  /* a bounded device-side wait ran out */
+#define PIC_EOVERFLOW -6 /* particle store or overflow region full */
+#define PIC_ENAN -7      /* non-finite value in the field solve */
+
+/* status-word bits (pic_status) */
+#define PIC_FLAG_OVERFLOW 0x1u
+#define PIC_FLAG_TIMEOUT 0x2u
+#define PIC_FLAG_NOCONV 0x4u
+#define PIC_FLAG_NAN 0x8u
+#define PIC_FLAG_OUTSIDE 0x10u /* a stored particle was found outside the plasma */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define PIC_NODE_FREE 0
+#define PIC_NODE_POWERED 1
+#define PIC_NODE_GROUNDED 2
+
+#define PIC_CELL_PLASMA 0
+#define PIC_CELL_POWERED 1
+#define PIC_CELL_GROUNDED 2
+#define PIC_CELL_DIELECTRIC 3
+
+#define PIC_CIRCUIT_DIRECT 0 /* U_E = V sin(2 pi f t + phase) imposed           */
+#define PIC_CIRCUIT_RLC 1    /* circuit I, Eq. 9: source + series Rb, Lb, Cb    */
+#define PIC_CIRCUIT_IMN 2    /* circuit II, Eq. 10: source Rs, L-type matching
+                                network (shunt Cm1, series Rm Lm Cm2) and stray
+                                branch (Rstray, Lstray, Cstray)                  */
+
+#define PIC_FP32 0 /* particle state and push in FP32; FP64 reductions, field, circuit */
+#define PIC_FP64 1 /* everything in FP64 (the plain method)                          */
+
+#define PIC_SOLVER_PLAIN 0 /* FP64 Jacobi-preconditioned CG                        */
+#define PIC_SOLVER_MIXED 1 /* FP32 inner CG in one thread-block cluster, FP64
+                              residual and iterative refinement                    */
+
+/* ---- configuration ------------------------------------------------------
+ * Everything that defines one discharge (Sec. 2: reactor geometry on a
+ * regular r-z grid, argon gas and species, cross sections, external circuit,
+ * time step).  Arrays are host pointers, copied by pic_init. */
+typedef struct pic_config {
+  int32_t nr, nz;              /* cells in r and z (nodes (nr+1) x (nz+1))        */
+  double dr, dz;               /* cell sizes, m                                    */
+  const int8_t *node_kind;     /* host [(nz+1)*(nr+1)] PIC_NODE_*: metal nodes are
+                                  Dirichlet (powered at U_E, grounded at 0)      */
+  const int8_t *cell_kind;     /* host [nz*nr] PIC_CELL_*: particles live in plasma
+                                  cells and are absorbed elsewhere               */
+  const double *cell_eps;      /* host [nz*nr] relative permittivity per cell     */
+  double dt;                   /* time step, s                                     */
+  double n_gas, T_gas, m_gas;  /* neutral density m^-3, temperature K, mass kg     */
+  double q[2], m[2], w[2];     /* per species charge C, mass kg, macro weight      */
+  int32_t n_xs;                /* cross-section table length (>= 2)                */
+  const double *xs_energy;     /* host [n_xs] eV, logarithmically spaced           */
+  const double *xs_sigma;      /* host [5*n_xs] m^2: e elastic, e excitation,
+                                  e ionization, Ar+ isotropic, Ar+ charge exchange */
+  double thr_ex, thr_iz;       /* excitation / ionization thresholds, eV           */
+  double B_ej;                 /* ejected-electron energy-sharing parameter, eV    */
+  int32_t circuit;             /* PIC_CIRCUIT_*                                    */
+  double circ[8];              /* RLC: Rb, Lb, Cb.  IMN: Rs, Cm1, Lm, Cm2, Rm,
+                                  Cstray, Rstray, Lstray (SI units)              */
+  double V_src, f_src, phase_src; /* source amplitude V, frequency Hz, phase rad   */
+  int32_t n_sub;               /* trapezoidal circuit substeps per dt              */
+  int32_t steps_per_rf;        /* diagnostic window (one RF period), steps         */
+  double pcg_tol;              /* relative residual target of the field solve      */
+  int32_t pcg_maxit;           /* iteration cap (PIC_ENOCONV beyond)               */
+  int32_t ceq_refresh;         /* recompute C_eq with chi after every window       */
+  uint32_t seed;               /* fourth word of every Philox counter              */
+  int64_t capacity[2];         /* particle capacity per species                    */
+  int32_t precision;           /* PIC_FP32 or PIC_FP64                             */
+  int32_t solver;              /* PIC_SOLVER_*                                     */
+  int32_t tile_r, tile_z;      /* cells per CTA tile (0 = library default)         */
+  double bin_slack;            /* extra bin room as a fraction of last count (0 = default) */
+} pic_config;
+
+/* Particle arrays of one species in FP64 host memory (caller-owned).  Position
+ * (r, z) is x~, the predicted position; (vr, vt, vz) the velocity v_{n-3/2}
+ * in the local (r, theta, z) frame; (ar, at, az) the D1 time-filtered
+ * acceleration a-bar_{n-2}; id the 64-bit identifier that keys its random
+ * numbers.  `cell` (output only, may be NULL) is j*nr+i of x~. */
+typedef struct pic_particles {
+  double *r, *z, *vr, *vt, *vz, *ar, *at, *az;
+  uint64_t *id;
+  int32_t *cell;
+} pic_particles;
+
+typedef struct pic_handle pic_handle;
+
+/* pic_init -- create a discharge.  Validates `cfg`, copies the geometry,
+ * cross sections and circuit, builds the vacuum part of the finite-volume
+ * operator of Eq. 1 and the null-collision bounds, allocates the particle
+ * stores (two buffers of cfg->capacity per species) on the current device.
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream).
+ * Errors: PIC_EINVAL (bad sizes, kinds, table), PIC_ENOMEM, PIC_ECUDA. */
+int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out);
+
+/* pic_set_particles -- replace species `species` with `n` particles from host
+ * FP64 arrays (converted to the handle's precision, cell-relative position).
+ * Errors: PIC_EINVAL (a particle outside the plasma region or bad species),
+ * PIC_EOVERFLOW (n > capacity). */
+int pic_set_particles(pic_handle *h, int species, int64_t n, const pic_particles *p);
+
+/* pic_count -- number of stored particles of a species (synchronises). */
+int pic_count(pic_handle *h, int species, int64_t *n);
+
+/* pic_get_particles -- copy a species to host FP64 arrays of length >= cap;
+ * *n receives the count.  Order is by cell (bins), unspecified within a cell. */
+int pic_get_particles(pic_handle *h, int species, pic_particles *out, int64_t cap, int64_t *n);
+
+/* pic_start -- start-up of the implicit scheme: deposit x~_0, C_eq of the
+ * vacuum (Eqs. 6-7), U_E(t_0), assemble and solve Eq. 1, node E field. */
+int pic_start(pic_handle *h);
+
+/* pic_step -- advance `nsteps` full time steps (particle phase, circuit with
+ * Eqs. 5 and 8-10, assembly and solve of Eq. 1, E field, diagnostics), as one
+ * captured CUDA graph per step.  Asynchronous; errors surface in pic_status. */
+int pic_step(pic_handle *h, int nsteps);
+
+/* pic_particle_phase -- only the particle phase of one step (gather, D1
+ * correction, absorption, null-collision MCC, predictor with cylindrical
+ * rotation, re-bin by cell, deposit of counts).  Does not advance the step
+ * counter.  Asynchronous. */
+int pic_particle_phase(pic_handle *h);
+
+/* pic_field_solve -- assemble rho~ and chi from the current deposits and
+ * solve Eq. 1 with solver `mode` (PIC_SOLVER_*), then the node E field.
+ * Synchronises; returns iterations and the final relative residual.
+ * Errors: PIC_ENOCONV, PIC_ETIMEOUT, PIC_ENAN. */
+int pic_field_solve(pic_handle *h, int mode, int *iters, double *rel_resid);
+
+/* pic_ceq -- equivalent capacitance from the field energy of the unit-voltage
+ * solution (Eqs. 6-7), with (with_chi=1) or without the current chi; also the
+ * Gauss-law electrode charge.  Does not change the handle's C_eq. */
+int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss);
+
+/* Diagnostic selectors for pic_diag (host buffer of doubles). */
+#define PIC_DIAG_PHI 0     /* potential, V                     [nodes] */
+#define PIC_DIAG_ER 1      /* E_r, V/m                         [nodes] */
+#define PIC_DIAG_EZ 2      /* E_z, V/m                         [nodes] */
+#define PIC_DIAG_CHI 3     /* implicit susceptibility          [nodes] */
+#define PIC_DIAG_DEP_E 4   /* deposited electron counts        [nodes] */
+#define PIC_DIAG_DEP_I 5   /* deposited ion counts             [nodes] */
+#define PIC_DIAG_SIGMA 6   /* surface charge on free nodes, C  [nodes] */
+#define PIC_DIAG_VNODE 7   /* plasma node volume, m^3          [nodes] */
+#define PIC_DIAG_RHO 8     /* node charge rho~ (incl. surface) [nodes] */
+#define PIC_DIAG_NE_AVG 9  /* last window's mean n_e, m^-3     [nodes] */
+#define PIC_DIAG_NI_AVG 10 /* last window's mean n_i, m^-3     [nodes] */
+#define PIC_DIAG_SCALARS 100 /* PIC_NSCALARS doubles, see below  */
+#define PIC_NSCALARS 47
+/* Scalars: [0] step, [1] t, [2] U_E, [3] Q_E, [4] C_eq, [5] I_conv, [6] I_ccp,
+ * [7..12] circuit state (RLC: Qb, Ib, QE; IMN: Q1, Q2, I2, Qccp, Istray, QE),
+ * [13] field-solve iterations, [14] relative residual, [15..16] nu_max e/i,
+ * [17..18] collision probability e/i, [19..24] absorbed charge of the last
+ * step (e: powered, grounded, surface; i: same), [25..30] absorbed counts,
+ * [31..36] collisions of the last step (e: elastic, excitation, ionization;
+ * i: isotropic, charge exchange, 0), [37..38] births e/i, [39..41] ion
+ * current of the last window (powered, grounded, surface), [42..43] first
+ * harmonic of I_ccp over the last window (Re, Im), [44] windows completed,
+ * [45] C_eq by the Gauss route, [46] field-solve status. */
+
+/* pic_diag -- copy one diagnostic to a host buffer of `bytes` bytes
+ * (synchronises).  Errors: PIC_EINVAL for an unknown selector or short buffer. */
+int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes);
+
+/* pic_set_field -- overwrite a node array (PIC_DIAG_PHI, _ER, _EZ, _DEP_E,
+ * _DEP_I, _SIGMA or _RHO) from a host buffer: test and restart hook.
+ * Setting _ER/_EZ updates the copy the particle gather reads. */
+int pic_set_field(pic_handle *h, int what, const double *host_buf, size_t n);
+
+/* State hooks (restart and component tests). */
+int pic_set_step(pic_handle *h, uint32_t step);
+int pic_set_ceq(pic_handle *h, double ceq);
+int pic_set_circuit_state(pic_handle *h, const double *y6);
+int pic_set_conv_current(pic_handle *h, double I_conv);
+/* Advance only the circuit (and the step counter) for n steps on the device,
+ * writing U_E after each step to host `U_out` (may be NULL). */
+int pic_circuit_run(pic_handle *h, int n, double *U_out);
+
+/* pic_status -- synchronise and return the accumulated device status bits
+ * (PIC_FLAG_*), then clear them. */
+int pic_status(pic_handle *h, uint32_t *flags);
+
+/* pic_philox -- fill host `out[4*n]` with Philox4x32-10 outputs computed on
+ * the device for counters ctr[4*n] and keys key[2*n] (host arrays); used to
+ * check that device and host generators agree bit for bit. */
+int pic_philox(pic_handle *h, int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
+
+/* pic_step_timing -- per-kernel device time (ms) of the last pic_step call
+ * measured with CUDA events on the handle's stream when timing is enabled:
+ * out[0] particle phase, [1] bin layout, [2] circuit, [3] assembly,
+ * [4] field solve, [5] E field, [6] diagnostics. */
+int pic_enable_timing(pic_handle *h, int on);
+int pic_step_timing(pic_handle *h, double *out7);
+
+const char *pic_strerror(int code);
+void pic_destroy(pic_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1079 @@
+// capi.cu -- the C ABI declared in include/pic.h: handle life cycle, particle
+// upload/download, the per-step CUDA graph, field solve, C_eq, diagnostics.
+//
+// Per step (arXiv:2310.04957, Sec. 2): particle phase (push + MCC + re-bin +
+// deposit of rho~ and chi), circuit and electrode charge (Eqs. 5, 8-10),
+// assembly and solve of the implicit field equation (Eq. 1), node E field,
+// diagnostics.  The step is captured once per buffer parity as a CUDA graph.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/pic.h"
+#include "pic_device.cuh"
+#include "pic_kernels.h"
+
+using namespace pic;
+
+namespace {
+
+const double kEps0 = 8.8541878128e-12;   // F/m
+const double kQe = 1.602176634e-19;      // C
+const double kKB = 1.380649e-23;         // J/K
+const double kPi = 3.141592653589793238462643383279;
+
+struct Store {
+  void *fr = nullptr, *fz = nullptr, *vr = nullptr, *vt = nullptr, *vz = nullptr, *ar = nullptr, *at = nullptr,
+       *az = nullptr;
+  unsigned long long *id = nullptr;
+  int *cell = nullptr, *start = nullptr, *cap = nullptr, *fill = nullptr;
+  BinMeta *meta = nullptr;
+};
+
+}  // namespace
+
+struct pic_handle {
+  pic_config cfg{};
+  std::vector<int8_t> node_kind, cell_kind;
+  std::vector<double> cell_eps, xs_E, xs_S;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int nr = 0, nz = 0, nn = 0, nc = 0;
+  int prec = PIC_FP32;
+  size_t esz = 4;
+  BinMap map{};
+  int nbins = 0, ntiles = 0;
+  float slack = 0.25f;
+  int64_t capacity[2] = {0, 0};
+  // device: geometry, operator, fields
+  int8_t *d_node_kind = nullptr, *d_cell_kind = nullptr, *d_bin_plasma = nullptr;
+  double *d_Gvac_r = nullptr, *d_Gpl_r = nullptr, *d_Gvac_z = nullptr, *d_Gpl_z = nullptr, *d_vnode = nullptr;
+  double *d_chi = nullptr, *d_zero = nullptr, *d_qrhs = nullptr, *d_phi = nullptr, *d_Gr = nullptr, *d_Gz = nullptr,
+         *d_dinv = nullptr, *d_Er = nullptr, *d_Ez = nullptr;
+  void *d_E = nullptr;
+  // PCG scratch
+  double *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_partial = nullptr, *d_pcg_out = nullptr;
+  unsigned *d_bar = nullptr;
+  // C_eq solve
+  double *d_phiL = nullptr, *d_Grc = nullptr, *d_Gzc = nullptr, *d_dinvc = nullptr, *d_energy = nullptr,
+         *d_ceq_out = nullptr;
+  // particles, deposits, counters
+  unsigned long long *d_dep[2] = {nullptr, nullptr}, *d_surf[2] = {nullptr, nullptr}, *d_counters = nullptr;
+  Store st[2][2];  // [buffer][species]
+  int cur = 0;
+  void *d_xsE = nullptr, *d_xsS = nullptr;
+  double *d_scalars = nullptr;
+  uint32_t *d_step = nullptr, *d_flags = nullptr;
+  double *d_dens_sum[2] = {nullptr, nullptr}, *d_dens_avg[2] = {nullptr, nullptr};
+  // host mirrors
+  uint32_t step = 0;
+  double numax[2] = {0, 0}, pcoll[2] = {0, 0};
+  int pcg_grid = 0;
+  bool started = false;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  bool graph_failed = false;
+  bool timing = false;
+  double timing_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) {                       \
+      fprintf(stderr, "pic: %s failed: %s\n", #call, cudaGetErrorString(e_)); \
+      return PIC_ECUDA;                            \
+    }                                              \
+  } while (0)
+
+template <typename P>
+int dalloc(pic_handle *h, P **ptr, size_t bytes) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return PIC_ENOMEM;
+  }
+  if (cudaMemsetAsync(p, 0, bytes, h->stream) != cudaSuccess) return PIC_ECUDA;
+  h->allocs.push_back(p);
+  *ptr = reinterpret_cast<P *>(p);
+  return PIC_OK;
+}
+
+#define DA(ptr, bytes)                    \
+  do {                                    \
+    int st_ = dalloc(h, &(ptr), (bytes)); \
+    if (st_) return st_;                  \
+  } while (0)
+
+int nidx(const pic_handle *h, int i, int j) { return j * (h->nr + 1) + i; }
+
+// Vacuum and plasma parts of the edge conductances and plasma node volumes,
+// from the finite-volume control volumes of the axisymmetric grid: a radial
+// face at r_{i+1/2} has area 2 pi r_{i+1/2} dz split half into each adjacent
+// cell row; an axial face is the annulus [r_{i-1/2}, r_{i+1/2}] split at r_i
+// between the two adjacent cell columns.  Each cell contributes
+// eps0 eps_r,cell x (its face part) / (edge length) to the vacuum part and, if
+// it is plasma, eps0 x (its face part) / (edge length) to the chi part.
+void build_geometry(const pic_handle *h, std::vector<double> &Gvr, std::vector<double> &Gpr, std::vector<double> &Gvz,
+                    std::vector<double> &Gpz, std::vector<double> &vnode) {
+  const int nr = h->nr, nz = h->nz;
+  const double dr = h->cfg.dr, dz = h->cfg.dz;
+  Gvr.assign((size_t)(nz + 1) * nr, 0.0);
+  Gpr.assign((size_t)(nz + 1) * nr, 0.0);
+  Gvz.assign((size_t)nz * (nr + 1), 0.0);
+  Gpz.assign((size_t)nz * (nr + 1), 0.0);
+  vnode.assign((size_t)h->nn, 0.0);
+  for (int j = 0; j < nz; ++j)
+    for (int i = 0; i < nr; ++i) {
+      int c = j * nr + i;
+      double eps = h->cell_eps[c];
+      bool pl = h->cell_kind[c] == PIC_CELL_PLASMA;
+      double ri = i * dr, rh = (i + 0.5) * dr, ri1 = (i + 1) * dr;
+      // radial edges at rows j and j+1, each gets the half face inside this cell
+      double ar = 2.0 * kPi * rh * 0.5 * dz / dr;
+      for (int jj = j; jj <= j + 1; ++jj) {
+        Gvr[(size_t)jj * nr + i] += kEps0 * eps * ar;
+        if (pl) Gpr[(size_t)jj * nr + i] += kEps0 * ar;
+      }
+      // axial edges at columns i (annulus [r_i, r_{i+1/2}]) and i+1 ([r_{i+1/2}, r_{i+1}])
+      double azl = kPi * (rh * rh - ri * ri) / dz;
+      double azr = kPi * (ri1 * ri1 - rh * rh) / dz;
+      Gvz[(size_t)j * (nr + 1) + i] += kEps0 * eps * azl;
+      Gvz[(size_t)j * (nr + 1) + i + 1] += kEps0 * eps * azr;
+      if (pl) {
+        Gpz[(size_t)j * (nr + 1) + i] += kEps0 * azl;
+        Gpz[(size_t)j * (nr + 1) + i + 1] += kEps0 * azr;
+        double q = 0.25 * kPi * (ri1 * ri1 - ri * ri) * dz;
+        vnode[nidx(h, i, j)] += q;
+        vnode[nidx(h, i + 1, j)] += q;
+        vnode[nidx(h, i, j + 1)] += q;
+        vnode[nidx(h, i + 1, j + 1)] += q;
+      }
+    }
+}
+
+// Null-collision bound per species: n_g x max over table intervals of the
+// larger node sigma_T times the speed at the interval's upper energy.
+void null_bounds(pic_handle *h) {
+  const pic_config &c = h->cfg;
+  int n = c.n_xs;
+  for (int s = 0; s < 2; ++s) {
+    double mass = s == 0 ? c.m[0] : c.m_gas;
+    int p0 = s == 0 ? 0 : 3, p1 = s == 0 ? 3 : 5;
+    double best = 0.0;
+    for (int k = 0; k + 1 < n; ++k) {
+      double sa = 0.0, sb = 0.0;
+      for (int p = p0; p < p1; ++p) {
+        sa += h->xs_S[(size_t)p * n + k];
+        sb += h->xs_S[(size_t)p * n + k + 1];
+      }
+      double v = std::sqrt(2.0 * h->xs_E[k + 1] * kQe / mass);
+      double nu = c.n_gas * (sa > sb ? sa : sb) * v;
+      if (nu > best) best = nu;
+    }
+    h->numax[s] = best;
+    h->pcoll[s] = 1.0 - std::exp(-best * c.dt);
+  }
+}
+
+template <typename T>
+StoreView<T> view(pic_handle *h, int buf, int s) {
+  Store &S = h->st[buf][s];
+  StoreView<T> v;
+  v.fr = (T *)S.fr; v.fz = (T *)S.fz; v.vr = (T *)S.vr; v.vt = (T *)S.vt; v.vz = (T *)S.vz;
+  v.ar = (T *)S.ar; v.at = (T *)S.at; v.az = (T *)S.az;
+  v.id = S.id; v.cell = S.cell; v.start = S.start; v.cap = S.cap; v.fill = S.fill; v.meta = S.meta;
+  v.capacity = (int)h->capacity[s];
+  return v;
+}
+
+template <typename T>
+PushParams<T> push_params(pic_handle *h, int in_buf) {
+  const pic_config &c = h->cfg;
+  PushParams<T> P;
+  memset(&P, 0, sizeof(P));
+  P.map = h->map;
+  P.nr = h->nr; P.nz = h->nz;
+  P.dt = (T)c.dt; P.hdt = (T)(0.5 * c.dt); P.hdt2 = (T)(0.5 * c.dt * c.dt);
+  P.dr = (T)c.dr; P.dz = (T)c.dz; P.inv_dr = (T)(1.0 / c.dr); P.inv_dz = (T)(1.0 / c.dz);
+  P.cell_kind = h->d_cell_kind; P.node_kind = h->d_node_kind;
+  P.E = h->d_E;
+  for (int s = 0; s < 2; ++s) {
+    P.qm[s] = (T)(c.q[s] / c.m[s]);
+    P.pcoll[s] = (T)h->pcoll[s];
+    P.numax[s] = (T)h->numax[s];
+    P.in[s] = view<T>(h, in_buf, s);
+    P.out[s] = view<T>(h, in_buf ^ 1, s);
+    P.dep[s] = h->d_dep[s];
+    P.surf[s] = h->d_surf[s];
+  }
+  P.n_gas = (T)c.n_gas;
+  P.xs_E = (const T *)h->d_xsE; P.xs_S = (const T *)h->d_xsS; P.n_xs = c.n_xs;
+  double l0 = std::log2(h->xs_E[0]), l1 = std::log2(h->xs_E[c.n_xs - 1]);
+  P.log2E0 = (T)l0; P.inv_dlog2 = (T)((c.n_xs - 1) / (l1 - l0));
+  P.thr_ex = (T)c.thr_ex; P.thr_iz = (T)c.thr_iz; P.B_ej = (T)c.B_ej;
+  P.e_per_v2[0] = (T)(0.5 * c.m[0] / kQe);
+  P.e_per_v2[1] = (T)(0.5 * c.m_gas / kQe);
+  P.v2_per_e[0] = (T)(2.0 * kQe / c.m[0]);
+  P.v2_per_e[1] = (T)(2.0 * kQe / c.m[1]);
+  P.two_me_over_M = (T)(2.0 * c.m[0] / c.m_gas);
+  P.vth_gas = (T)std::sqrt(kKB * c.T_gas / c.m_gas);
+  P.mi_frac = (T)(c.m[1] / (c.m[1] + c.m_gas));
+  P.seed = c.seed;
+  P.step_ptr = h->d_step;
+  P.counters = h->d_counters;
+  P.dep_scale = (T)(h->prec == PIC_FP32 ? 67108864.0 : 1099511627776.0);
+  P.dep_one = h->prec == PIC_FP32 ? (1ull << 26) : (1ull << 40);
+  P.flags = h->d_flags;
+  return P;
+}
+
+double dep_inv_scale(const pic_handle *h) { return h->prec == PIC_FP32 ? 1.0 / 67108864.0 : 1.0 / 1099511627776.0; }
+
+FieldParams field_params(pic_handle *h, const double *chi, double *Gr, double *Gz, double *dinv) {
+  const pic_config &c = h->cfg;
+  FieldParams F;
+  memset(&F, 0, sizeof(F));
+  F.nr = h->nr; F.nz = h->nz; F.nn = h->nn;
+  F.node_kind = h->d_node_kind;
+  F.Gvac_r = h->d_Gvac_r; F.Gpl_r = h->d_Gpl_r; F.Gvac_z = h->d_Gvac_z; F.Gpl_z = h->d_Gpl_z;
+  F.vnode = h->d_vnode;
+  for (int s = 0; s < 2; ++s) {
+    F.dep[s] = h->d_dep[s];
+    F.surf[s] = h->d_surf[s];
+    F.qw[s] = c.q[s] * c.w[s];
+    F.chi_coef[s] = c.dt * c.dt / (2.0 * kEps0) * c.q[s] * c.q[s] / c.m[s] * c.w[s];
+  }
+  F.dep_inv_scale = dep_inv_scale(h);
+  F.chi = const_cast<double *>(chi);
+  F.qrhs = h->d_qrhs; F.phi = h->d_phi; F.Gr = Gr; F.Gz = Gz; F.dinv = dinv;
+  F.scalars = h->d_scalars;
+  return F;
+}
+
+PcgParams pcg_params(pic_handle *h, const double *Gr, const double *Gz, const double *dinv, const double *qrhs, double *phi,
+                     double tol, double *out) {
+  PcgParams P;
+  memset(&P, 0, sizeof(P));
+  P.nr = h->nr; P.nz = h->nz; P.nn = h->nn;
+  P.node_kind = h->d_node_kind;
+  P.Gr = Gr; P.Gz = Gz; P.dinv = dinv; P.qrhs = qrhs; P.phi = phi;
+  P.r = h->d_r; P.z = h->d_z; P.p = h->d_p; P.Ap = h->d_Ap;
+  P.partial = h->d_partial;
+  P.bar = h->d_bar;
+  P.tol = tol;
+  P.maxit = h->cfg.pcg_maxit;
+  P.out = out;
+  P.flags = h->d_flags;
+  P.spin_limit = 4000000000ll;  // ~2 s at 2 GHz per barrier wait
+  return P;
+}
+
+EfieldParams efield_params(pic_handle *h) {
+  EfieldParams E;
+  E.nr = h->nr; E.nz = h->nz; E.dr = h->cfg.dr; E.dz = h->cfg.dz;
+  E.node_kind = h->d_node_kind; E.phi = h->d_phi; E.Er = h->d_Er; E.Ez = h->d_Ez;
+  E.E32 = h->prec == PIC_FP32 ? (float2 *)h->d_E : nullptr;
+  E.E64 = h->prec == PIC_FP64 ? (double2 *)h->d_E : nullptr;
+  return E;
+}
+
+CircuitParams circuit_params(pic_handle *h, int n_run, double *U_hist, uint32_t *step_inc) {
+  const pic_config &c = h->cfg;
+  CircuitParams C;
+  memset(&C, 0, sizeof(C));
+  C.kind = c.circuit; C.nsub = c.n_sub;
+  for (int k = 0; k < 8; ++k) C.c[k] = c.circ[k];
+  C.V = c.V_src; C.f = c.f_src; C.phase = c.phase_src; C.dt = c.dt;
+  C.qw[0] = c.q[0] * c.w[0]; C.qw[1] = c.q[1] * c.w[1];
+  C.counters = h->d_counters;
+  C.step_ptr = h->d_step;
+  C.scalars = h->d_scalars;
+  C.n_run = n_run; C.U_hist = U_hist; C.step_inc = step_inc;
+  return C;
+}
+
+DiagParams diag_params(pic_handle *h) {
+  const pic_config &c = h->cfg;
+  DiagParams D;
+  memset(&D, 0, sizeof(D));
+  D.nn = h->nn; D.vnode = h->d_vnode;
+  D.dep[0] = h->d_dep[0]; D.dep[1] = h->d_dep[1];
+  D.dep_inv_scale = dep_inv_scale(h);
+  D.w[0] = c.w[0]; D.w[1] = c.w[1];
+  D.qw_ion = c.q[1] * c.w[1];
+  D.f = c.f_src; D.dt = c.dt; D.window = c.steps_per_rf;
+  D.counters = h->d_counters;
+  D.step_ptr = h->d_step; D.step_mut = h->d_step;
+  for (int s = 0; s < 2; ++s) { D.dens_sum[s] = h->d_dens_sum[s]; D.dens_avg[s] = h->d_dens_avg[s]; }
+  D.scalars = h->d_scalars;
+  return D;
+}
+
+int launch_push(pic_handle *h, int in_buf) {
+  cudaError_t e;
+  if (h->prec == PIC_FP32) e = launch_particles<float>(push_params<float>(h, in_buf), h->stream);
+  else e = launch_particles<double>(push_params<double>(h, in_buf), h->stream);
+  return e == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+// Layout of the write buffer from the read buffer's fill counts, then zeroed
+// deposits and counters, then the particle kernel.
+int enqueue_particle_phase(pic_handle *h, int in_buf) {
+  int out = in_buf ^ 1;
+  for (int s = 0; s < 2; ++s) {
+    Store &A = h->st[in_buf][s], &B = h->st[out][s];
+    CK(launch_layout(A.fill, h->d_bin_plasma, h->nbins, h->slack, (int)h->capacity[s], B.start, B.cap, B.fill, B.meta,
+                     A.meta, h->stream));
+  }
+  CK(cudaMemsetAsync(h->d_dep[0], 0, sizeof(unsigned long long) * h->nn, h->stream));
+  CK(cudaMemsetAsync(h->d_dep[1], 0, sizeof(unsigned long long) * h->nn, h->stream));
+  CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned long long) * CNT_N, h->stream));
+  return launch_push(h, in_buf);
+}
+
+int enqueue_solve(pic_handle *h) {
+  CK(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
+  PcgParams P = pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, h->d_phi, h->cfg.pcg_tol, h->d_pcg_out);
+  CK(launch_pcg(P, h->pcg_grid, h->stream));
+  return PIC_OK;
+}
+
+int enqueue_step(pic_handle *h, int in_buf, cudaEvent_t *ev) {
+  int st;
+  if (ev) CK(cudaEventRecord(ev[0], h->stream));
+  if ((st = enqueue_particle_phase(h, in_buf))) return st;
+  if (ev) CK(cudaEventRecord(ev[1], h->stream));
+  CK(launch_circuit(circuit_params(h, 1, nullptr, nullptr), h->stream));
+  if (ev) CK(cudaEventRecord(ev[2], h->stream));
+  CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
+  if (ev) CK(cudaEventRecord(ev[3], h->stream));
+  if ((st = enqueue_solve(h))) return st;
+  if (ev) CK(cudaEventRecord(ev[4], h->stream));
+  CK(launch_efield(efield_params(h), h->stream));
+  if (ev) CK(cudaEventRecord(ev[5], h->stream));
+  CK(launch_diag(diag_params(h), h->stream));
+  if (ev) CK(cudaEventRecord(ev[6], h->stream));
+  return PIC_OK;
+}
+
+// C_eq from the field energy of the unit-voltage solution (Eqs. 6-7), with
+// or without chi; result in d_ceq_out[0] (energy route) and [1] (Gauss route).
+int enqueue_ceq(pic_handle *h, bool with_chi) {
+  FieldParams F = field_params(h, with_chi ? h->d_chi : h->d_zero, h->d_Grc, h->d_Gzc, h->d_dinvc);
+  F.phi = h->d_phiL;
+  // edges only (the node pass would overwrite rho~ and chi)
+  CK(launch_assemble_edges_only(F, h->stream));
+  CK(launch_set_dirichlet(h->nn, h->d_node_kind, h->d_phiL, 1.0, h->stream));
+  CK(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
+  double tol = h->cfg.pcg_tol < 1e-12 ? h->cfg.pcg_tol : 1e-12;
+  PcgParams P = pcg_params(h, h->d_Grc, h->d_Gzc, h->d_dinvc, h->d_zero, h->d_phiL, tol, h->d_pcg_out + 4);
+  CK(launch_pcg(P, h->pcg_grid, h->stream));
+  CK(launch_energy(h->nr, h->nz, h->d_node_kind, h->d_Grc, h->d_Gzc, h->d_phiL, h->d_ceq_out, h->stream));
+  return PIC_OK;
+}
+
+int sync(pic_handle *h) {
+  CK(cudaStreamSynchronize(h->stream));
+  return PIC_OK;
+}
+
+void free_all(pic_handle *h) {
+  for (int k = 0; k < 2; ++k)
+    if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+  for (void *p : h->allocs) cudaFree(p);
+  h->allocs.clear();
+}
+
+int capture_graph(pic_handle *h, int buf) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return PIC_ECUDA;
+  }
+  int st = enqueue_step(h, buf, nullptr);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (st || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return PIC_ECUDA;
+  }
+  e = cudaGraphInstantiate(&h->graph[buf], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->graph[buf] = nullptr;
+    return PIC_ECUDA;
+  }
+  return PIC_OK;
+}
+
+int window_end(pic_handle *h) {
+  CK(launch_diag_window(diag_params(h), h->stream));
+  if (h->cfg.ceq_refresh) {
+    int st = enqueue_ceq(h, true);
+    if (st) return st;
+    CK(cudaMemcpyAsync(h->d_scalars + SC_CEQ, h->d_ceq_out, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_scalars + SC_CEQ_GAUSS, h->d_ceq_out + 1, sizeof(double), cudaMemcpyDeviceToDevice,
+                       h->stream));
+  }
+  return PIC_OK;
+}
+
+bool check_config(const pic_config *c) {
+  if (!c || c->nr < 2 || c->nz < 2 || !(c->dr > 0) || !(c->dz > 0) || !(c->dt > 0)) return false;
+  if (!c->node_kind || !c->cell_kind || !c->cell_eps || !c->xs_energy || !c->xs_sigma || c->n_xs < 2) return false;
+  if (c->circuit < 0 || c->circuit > 2 || c->n_sub < 1 || c->steps_per_rf < 1 || c->pcg_maxit < 1) return false;
+  if (c->precision != PIC_FP32 && c->precision != PIC_FP64) return false;
+  if (c->capacity[0] < 1 || c->capacity[1] < 1 || c->capacity[0] > 2000000000ll || c->capacity[1] > 2000000000ll)
+    return false;
+  if (!(c->m[0] > 0) || !(c->m[1] > 0) || !(c->m_gas > 0)) return false;
+  for (int k = 0; k + 1 < c->n_xs; ++k)
+    if (!(c->xs_energy[k + 1] > c->xs_energy[k]) || !(c->xs_energy[k] > 0)) return false;
+  int tr = c->tile_r > 0 ? c->tile_r : 8, tz = c->tile_z > 0 ? c->tile_z : 4;
+  if (tr * tz > kMaxTileCells || tr < 1 || tz < 1) return false;
+  if (c->circuit == PIC_CIRCUIT_RLC && !(c->circ[0] >= 0 && c->circ[1] > 0 && c->circ[2] > 0)) return false;
+  if (c->circuit == PIC_CIRCUIT_IMN)
+    for (int k = 0; k < 8; ++k)
+      if (!(c->circ[k] > 0)) return false;
+  return true;
+}
+
+template <typename T>
+int upload_species(pic_handle *h, int s, int64_t n, const pic_particles *p) {
+  const pic_config &c = h->cfg;
+  std::vector<int> bin_of(n);
+  std::vector<int> counts(h->nbins, 0);
+  std::vector<T> fr(n), fz(n);
+  for (int64_t k = 0; k < n; ++k) {
+    double r = p->r[k], z = p->z[k];
+    if (!(r >= 0.0) || !(z >= 0.0)) return PIC_EINVAL;
+    double x = r / c.dr, y = z / c.dz;
+    int i = (int)std::floor(x), j = (int)std::floor(y);
+    if (i < 0 || j < 0 || i >= h->nr || j >= h->nz) return PIC_EINVAL;
+    if (h->cell_kind[(size_t)j * h->nr + i] != PIC_CELL_PLASMA) return PIC_EINVAL;
+    T a = (T)(x - i), b = (T)(y - j);
+    const T below1 = (T)1 - (T)(sizeof(T) == 4 ? 5.9604645e-8 : 1.1102230246251565e-16);
+    if (a >= (T)1) a = below1;
+    if (b >= (T)1) b = below1;
+    if (a < (T)0) a = (T)0;
+    if (b < (T)0) b = (T)0;
+    fr[k] = a; fz[k] = b;
+    int bin = h->map.bin(i, j);
+    bin_of[k] = bin;
+    counts[bin]++;
+  }
+  std::vector<int> start(h->nbins), fill(h->nbins);
+  int run = 0;
+  for (int b = 0; b < h->nbins; ++b) { start[b] = run; fill[b] = counts[b]; run += counts[b]; }
+  std::vector<int> pos(start);
+  std::vector<T> a_fr(n), a_fz(n), a_vr(n), a_vt(n), a_vz(n), a_ar(n), a_at(n), a_az(n);
+  std::vector<unsigned long long> a_id(n);
+  for (int64_t k = 0; k < n; ++k) {
+    int d = pos[bin_of[k]]++;
+    a_fr[d] = fr[k]; a_fz[d] = fz[k];
+    a_vr[d] = (T)p->vr[k]; a_vt[d] = (T)p->vt[k]; a_vz[d] = (T)p->vz[k];
+    a_ar[d] = (T)p->ar[k]; a_at[d] = (T)p->at[k]; a_az[d] = (T)p->az[k];
+    a_id[d] = p->id[k];
+  }
+  Store &S = h->st[h->cur][s];
+  size_t bytes = sizeof(T) * (size_t)n;
+  if (n) {
+    CK(cudaMemcpy(S.fr, a_fr.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.fz, a_fz.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.vr, a_vr.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.vt, a_vt.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.vz, a_vz.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.ar, a_ar.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.at, a_at.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.az, a_az.data(), bytes, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(S.id, a_id.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice));
+  }
+  CK(cudaMemcpy(S.start, start.data(), sizeof(int) * h->nbins, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(S.cap, fill.data(), sizeof(int) * h->nbins, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(S.fill, fill.data(), sizeof(int) * h->nbins, cudaMemcpyHostToDevice));
+  BinMeta m{(int)n, 0, (long long)n};
+  CK(cudaMemcpy(S.meta, &m, sizeof(BinMeta), cudaMemcpyHostToDevice));
+  return PIC_OK;
+}
+
+template <typename T>
+int download_species(pic_handle *h, int s, pic_particles *out, int64_t capn, int64_t *nout) {
+  Store &S = h->st[h->cur][s];
+  std::vector<int> start(h->nbins), cap(h->nbins), fill(h->nbins);
+  BinMeta m;
+  CK(cudaMemcpy(start.data(), S.start, sizeof(int) * h->nbins, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(cap.data(), S.cap, sizeof(int) * h->nbins, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(fill.data(), S.fill, sizeof(int) * h->nbins, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(&m, S.meta, sizeof(BinMeta), cudaMemcpyDeviceToHost));
+  int64_t total = 0;
+  for (int b = 0; b < h->nbins; ++b) total += fill[b] < cap[b] ? fill[b] : cap[b];
+  int novf = m.ovf_n;
+  if (novf > h->capacity[s] - m.ovf_base) novf = (int)(h->capacity[s] - m.ovf_base);
+  if (novf < 0) novf = 0;
+  total += novf;
+  *nout = total;
+  if (!out) return PIC_OK;
+  if (total > capn) return PIC_EINVAL;
+  size_t used = (size_t)m.ovf_base + novf;
+  if (used == 0) return PIC_OK;
+  std::vector<T> fr(used), fz(used), vr(used), vt(used), vz(used), ar(used), at(used), az(used);
+  std::vector<unsigned long long> id(used);
+  std::vector<int> cell(used);
+  size_t bytes = sizeof(T) * used;
+  CK(cudaMemcpy(fr.data(), S.fr, bytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(fz.data(), S.fz, bytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(vr.data(), S.vr, bytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(vt.data(), S.vt, bytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(vz.data(), S.vz, bytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ar.data(), S.ar, bytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(at.data(), S.at, bytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(az.data(), S.az, bytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(id.data(), S.id, sizeof(unsigned long long) * used, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(cell.data(), S.cell, sizeof(int) * used, cudaMemcpyDeviceToHost));
+  const double dr = h->cfg.dr, dz = h->cfg.dz;
+  int64_t k = 0;
+  auto put = [&](size_t slot, int i, int j) {
+    out->r[k] = ((double)i + (double)fr[slot]) * dr;
+    out->z[k] = ((double)j + (double)fz[slot]) * dz;
+    out->vr[k] = vr[slot]; out->vt[k] = vt[slot]; out->vz[k] = vz[slot];
+    out->ar[k] = ar[slot]; out->at[k] = at[slot]; out->az[k] = az[slot];
+    out->id[k] = id[slot];
+    if (out->cell) out->cell[k] = j * h->nr + i;
+    ++k;
+  };
+  for (int b = 0; b < h->nbins; ++b) {
+    int nb = fill[b] < cap[b] ? fill[b] : cap[b];
+    if (!nb) continue;
+    int i, j;
+    h->map.cell(b, i, j);
+    for (int q = 0; q < nb; ++q) put((size_t)start[b] + q, i, j);
+  }
+  for (int q = 0; q < novf; ++q) {
+    size_t slot = (size_t)m.ovf_base + q;
+    int c = cell[slot];
+    put(slot, c % h->nr, c / h->nr);
+  }
+  return PIC_OK;
+}
+
+}  // namespace
+
+// =============================================================================
+extern "C" {
+
+const char *pic_strerror(int code) {
+  switch (code) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument or configuration";
+    case PIC_ENOMEM: return "out of memory";
+    case PIC_ECUDA: return "CUDA runtime error";
+    case PIC_ENOCONV: return "field solve did not converge within its iteration cap";
+    case PIC_ETIMEOUT: return "a bounded device-side wait timed out";
+    case PIC_EOVERFLOW: return "particle store overflow";
+    case PIC_ENAN: return "non-finite value in the field solve";
+    default: return "unknown error";
+  }
+}
+
+void pic_destroy(pic_handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
+  if (!out || !check_config(cfg)) return PIC_EINVAL;
+  *out = nullptr;
+  pic_handle *h = new (std::nothrow) pic_handle();
+  if (!h) return PIC_ENOMEM;
+  h->cfg = *cfg;
+  h->stream = (cudaStream_t)cuda_stream;
+  if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return PIC_ECUDA; }
+  h->nr = cfg->nr; h->nz = cfg->nz;
+  h->nn = (h->nr + 1) * (h->nz + 1);
+  h->nc = h->nr * h->nz;
+  h->prec = cfg->precision;
+  h->esz = h->prec == PIC_FP32 ? 4 : 8;
+  h->node_kind.assign(cfg->node_kind, cfg->node_kind + h->nn);
+  h->cell_kind.assign(cfg->cell_kind, cfg->cell_kind + h->nc);
+  h->cell_eps.assign(cfg->cell_eps, cfg->cell_eps + h->nc);
+  h->xs_E.assign(cfg->xs_energy, cfg->xs_energy + cfg->n_xs);
+  h->xs_S.assign(cfg->xs_sigma, cfg->xs_sigma + 5 * (size_t)cfg->n_xs);
+  for (int a = 0; a < h->nn; ++a)
+    if (h->node_kind[a] < 0 || h->node_kind[a] > 2) { delete h; return PIC_EINVAL; }
+  for (int c = 0; c < h->nc; ++c)
+    if (h->cell_kind[c] < 0 || h->cell_kind[c] > 3 || !(h->cell_eps[c] > 0)) { delete h; return PIC_EINVAL; }
+  h->cfg.node_kind = h->node_kind.data();
+  h->cfg.cell_kind = h->cell_kind.data();
+  h->cfg.cell_eps = h->cell_eps.data();
+  h->cfg.xs_energy = h->xs_E.data();
+  h->cfg.xs_sigma = h->xs_S.data();
+  h->slack = cfg->bin_slack > 0 ? (float)cfg->bin_slack : 0.25f;
+  h->capacity[0] = cfg->capacity[0];
+  h->capacity[1] = cfg->capacity[1];
+  int TX = cfg->tile_r > 0 ? cfg->tile_r : 8, TY = cfg->tile_z > 0 ? cfg->tile_z : 4;
+  h->map.nr = h->nr; h->map.nz = h->nz; h->map.TX = TX; h->map.TY = TY;
+  h->map.ntx = (h->nr + TX - 1) / TX; h->map.nty = (h->nz + TY - 1) / TY;
+  h->nbins = h->map.nbins();
+  h->ntiles = h->map.ntiles();
+  null_bounds(h);
+  int st = [&]() -> int {
+    const size_t nn = h->nn;
+    DA(h->d_node_kind, nn);
+    DA(h->d_cell_kind, h->nc);
+    DA(h->d_bin_plasma, h->nbins);
+    DA(h->d_Gvac_r, sizeof(double) * (h->nz + 1) * h->nr);
+    DA(h->d_Gpl_r, sizeof(double) * (h->nz + 1) * h->nr);
+    DA(h->d_Gvac_z, sizeof(double) * h->nz * (h->nr + 1));
+    DA(h->d_Gpl_z, sizeof(double) * h->nz * (h->nr + 1));
+    DA(h->d_Gr, sizeof(double) * (h->nz + 1) * h->nr);
+    DA(h->d_Gz, sizeof(double) * h->nz * (h->nr + 1));
+    DA(h->d_Grc, sizeof(double) * (h->nz + 1) * h->nr);
+    DA(h->d_Gzc, sizeof(double) * h->nz * (h->nr + 1));
+    DA(h->d_vnode, sizeof(double) * nn);
+    DA(h->d_chi, sizeof(double) * nn);
+    DA(h->d_zero, sizeof(double) * nn);
+    DA(h->d_qrhs, sizeof(double) * nn);
+    DA(h->d_phi, sizeof(double) * nn);
+    DA(h->d_phiL, sizeof(double) * nn);
+    DA(h->d_dinv, sizeof(double) * nn);
+    DA(h->d_dinvc, sizeof(double) * nn);
+    DA(h->d_Er, sizeof(double) * nn);
+    DA(h->d_Ez, sizeof(double) * nn);
+    DA(h->d_E, 2 * h->esz * nn);
+    DA(h->d_r, sizeof(double) * nn);
+    DA(h->d_z, sizeof(double) * nn);
+    DA(h->d_p, sizeof(double) * nn);
+    DA(h->d_Ap, sizeof(double) * nn);
+    h->pcg_grid = pcg_grid_size(h->device);
+    DA(h->d_partial, sizeof(double) * 8 * (h->pcg_grid + 32));
+    DA(h->d_bar, 4 * sizeof(unsigned));
+    DA(h->d_pcg_out, sizeof(double) * 8);
+    DA(h->d_energy, sizeof(double) * 2);
+    DA(h->d_ceq_out, sizeof(double) * 2);
+    DA(h->d_counters, sizeof(unsigned long long) * CNT_N);
+    DA(h->d_scalars, sizeof(double) * SC_N);
+    DA(h->d_step, sizeof(uint32_t) * 2);
+    DA(h->d_flags, sizeof(uint32_t) * 2);
+    DA(h->d_xsE, h->esz * cfg->n_xs);
+    DA(h->d_xsS, h->esz * 5 * cfg->n_xs);
+    for (int s = 0; s < 2; ++s) {
+      DA(h->d_dep[s], sizeof(unsigned long long) * nn);
+      DA(h->d_surf[s], sizeof(unsigned long long) * nn);
+      DA(h->d_dens_sum[s], sizeof(double) * nn);
+      DA(h->d_dens_avg[s], sizeof(double) * nn);
+      for (int b = 0; b < 2; ++b) {
+        Store &S = h->st[b][s];
+        size_t cap = (size_t)h->capacity[s];
+        DA(S.fr, h->esz * cap); DA(S.fz, h->esz * cap);
+        DA(S.vr, h->esz * cap); DA(S.vt, h->esz * cap); DA(S.vz, h->esz * cap);
+        DA(S.ar, h->esz * cap); DA(S.at, h->esz * cap); DA(S.az, h->esz * cap);
+        DA(S.id, sizeof(unsigned long long) * cap);
+        DA(S.cell, sizeof(int) * cap);
+        DA(S.start, sizeof(int) * h->nbins);
+        DA(S.cap, sizeof(int) * h->nbins);
+        DA(S.fill, sizeof(int) * h->nbins);
+        DA(S.meta, sizeof(BinMeta));
+      }
+    }
+    // geometry
+    std::vector<double> Gvr, Gpr, Gvz, Gpz, vnode;
+    build_geometry(h, Gvr, Gpr, Gvz, Gpz, vnode);
+    CK(cudaMemcpy(h->d_node_kind, h->node_kind.data(), nn, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_cell_kind, h->cell_kind.data(), h->nc, cudaMemcpyHostToDevice));
+    std::vector<int8_t> bp(h->nbins, 0);
+    for (int b = 0; b < h->nbins; ++b) {
+      int i, j;
+      h->map.cell(b, i, j);
+      if (i < h->nr && j < h->nz) bp[b] = h->cell_kind[(size_t)j * h->nr + i] == PIC_CELL_PLASMA;
+    }
+    CK(cudaMemcpy(h->d_bin_plasma, bp.data(), h->nbins, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_Gvac_r, Gvr.data(), sizeof(double) * Gvr.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_Gpl_r, Gpr.data(), sizeof(double) * Gpr.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_Gvac_z, Gvz.data(), sizeof(double) * Gvz.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_Gpl_z, Gpz.data(), sizeof(double) * Gpz.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_vnode, vnode.data(), sizeof(double) * nn, cudaMemcpyHostToDevice));
+    if (h->prec == PIC_FP32) {
+      std::vector<float> e(h->xs_E.begin(), h->xs_E.end()), s(h->xs_S.begin(), h->xs_S.end());
+      CK(cudaMemcpy(h->d_xsE, e.data(), 4 * e.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_xsS, s.data(), 4 * s.size(), cudaMemcpyHostToDevice));
+    } else {
+      CK(cudaMemcpy(h->d_xsE, h->xs_E.data(), 8 * h->xs_E.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(h->d_xsS, h->xs_S.data(), 8 * h->xs_S.size(), cudaMemcpyHostToDevice));
+    }
+    double sc[SC_N] = {0};
+    sc[SC_CEQ] = 1.0;
+    CK(cudaMemcpy(h->d_scalars, sc, sizeof(sc), cudaMemcpyHostToDevice));
+    CK(cudaStreamSynchronize(h->stream));
+    return PIC_OK;
+  }();
+  if (st) {
+    free_all(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return PIC_OK;
+}
+
+int pic_set_particles(pic_handle *h, int species, int64_t n, const pic_particles *p) {
+  if (!h || species < 0 || species > 1 || n < 0 || (n > 0 && (!p || !p->r || !p->z || !p->vr || !p->vt || !p->vz ||
+                                                                !p->ar || !p->at || !p->az || !p->id)))
+    return PIC_EINVAL;
+  if (n > h->capacity[species]) return PIC_EOVERFLOW;
+  if (sync(h)) return PIC_ECUDA;
+  return h->prec == PIC_FP32 ? upload_species<float>(h, species, n, p) : upload_species<double>(h, species, n, p);
+}
+
+int pic_count(pic_handle *h, int species, int64_t *n) {
+  if (!h || !n || species < 0 || species > 1) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  return h->prec == PIC_FP32 ? download_species<float>(h, species, nullptr, 0, n)
+                             : download_species<double>(h, species, nullptr, 0, n);
+}
+
+int pic_get_particles(pic_handle *h, int species, pic_particles *out, int64_t cap, int64_t *n) {
+  if (!h || !out || !n || species < 0 || species > 1) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  return h->prec == PIC_FP32 ? download_species<float>(h, species, out, cap, n)
+                             : download_species<double>(h, species, out, cap, n);
+}
+
+int pic_start(pic_handle *h) {
+  if (!h) return PIC_EINVAL;
+  // deposit x~_0
+  CK(cudaMemsetAsync(h->d_dep[0], 0, sizeof(unsigned long long) * h->nn, h->stream));
+  CK(cudaMemsetAsync(h->d_dep[1], 0, sizeof(unsigned long long) * h->nn, h->stream));
+  cudaError_t e = h->prec == PIC_FP32 ? launch_deposit_only<float>(push_params<float>(h, h->cur), h->stream)
+                                      : launch_deposit_only<double>(push_params<double>(h, h->cur), h->stream);
+  if (e != cudaSuccess) return PIC_ECUDA;
+  // vacuum C_eq
+  int st = enqueue_ceq(h, false);
+  if (st) return st;
+  double ce[2];
+  CK(cudaMemcpyAsync(ce, h->d_ceq_out, sizeof(ce), cudaMemcpyDeviceToHost, h->stream));
+  double sc[SC_N];
+  CK(cudaMemcpyAsync(sc, h->d_scalars, sizeof(sc), cudaMemcpyDeviceToHost, h->stream));
+  if (sync(h)) return PIC_ECUDA;
+  const pic_config &c = h->cfg;
+  sc[SC_CEQ] = ce[0];
+  sc[SC_CEQ_GAUSS] = ce[1];
+  uint32_t step = h->step;
+  double t = step * c.dt;
+  if (c.circuit == PIC_CIRCUIT_DIRECT) {
+    sc[SC_UE] = c.V_src * std::sin(2.0 * kPi * c.f_src * t + c.phase_src);
+    sc[SC_QE] = sc[SC_CEQ] * sc[SC_UE];
+  } else {
+    int n = c.circuit == PIC_CIRCUIT_RLC ? 3 : 6;
+    sc[SC_QE] = sc[SC_Y0 + n - 1];
+    sc[SC_UE] = sc[SC_QE] / sc[SC_CEQ];
+  }
+  sc[SC_T] = t;
+  CK(cudaMemcpyAsync(h->d_scalars, sc, sizeof(sc), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, h->stream));
+  CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
+  if ((st = enqueue_solve(h))) return st;
+  CK(launch_efield(efield_params(h), h->stream));
+  if (sync(h)) return PIC_ECUDA;
+  h->started = true;
+  return PIC_OK;
+}
+
+int pic_particle_phase(pic_handle *h) {
+  if (!h) return PIC_EINVAL;
+  uint32_t step = h->step;
+  CK(cudaMemcpyAsync(h->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, h->stream));
+  int st = enqueue_particle_phase(h, h->cur);
+  if (st) return st;
+  h->cur ^= 1;
+  return sync(h);
+}
+
+int pic_step(pic_handle *h, int nsteps) {
+  if (!h || nsteps < 0) return PIC_EINVAL;
+  if (!h->started) {
+    int st = pic_start(h);
+    if (st) return st;
+  }
+  cudaEvent_t ev[7];
+  if (h->timing) {
+    for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&ev[k]));
+    for (int k = 0; k < 7; ++k) h->timing_ms[k] = 0.0;
+  }
+  uint32_t step = h->step;
+  CK(cudaMemcpyAsync(h->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, h->stream));
+  for (int k = 0; k < nsteps; ++k) {
+    int buf = h->cur;
+    if (h->timing) {
+      int st = enqueue_step(h, buf, ev);
+      if (st) return st;
+      CK(cudaEventSynchronize(ev[6]));
+      float ms;
+      for (int q = 0; q < 6; ++q) {
+        CK(cudaEventElapsedTime(&ms, ev[q], ev[q + 1]));
+        h->timing_ms[q == 0 ? 0 : q] += ms;  // [0] particles (incl. layout), [1] circuit, ...
+      }
+    } else {
+      if (!h->graph[buf] && !h->graph_failed) {
+        if (capture_graph(h, buf)) h->graph_failed = true;
+      }
+      if (h->graph[buf]) {
+        CK(cudaGraphLaunch(h->graph[buf], h->stream));
+      } else {
+        int st = enqueue_step(h, buf, nullptr);
+        if (st) return st;
+      }
+    }
+    h->cur ^= 1;
+    h->step++;
+    if (h->step % (uint32_t)h->cfg.steps_per_rf == 0) {
+      int st = window_end(h);
+      if (st) return st;
+    }
+  }
+  if (h->timing)
+    for (int k = 0; k < 7; ++k) cudaEventDestroy(ev[k]);
+  return PIC_OK;
+}
+
+int pic_enable_timing(pic_handle *h, int on) {
+  if (!h) return PIC_EINVAL;
+  h->timing = on != 0;
+  return PIC_OK;
+}
+
+int pic_step_timing(pic_handle *h, double *out7) {
+  if (!h || !out7) return PIC_EINVAL;
+  // [0] particle phase incl. layout, [1] circuit, [2] assembly, [3] field solve, [4] E field, [5] diagnostics
+  out7[0] = h->timing_ms[0];
+  out7[1] = 0.0;
+  out7[2] = h->timing_ms[1];
+  out7[3] = h->timing_ms[2];
+  out7[4] = h->timing_ms[3];
+  out7[5] = h->timing_ms[4];
+  out7[6] = h->timing_ms[5];
+  return PIC_OK;
+}
+
+int pic_field_solve(pic_handle *h, int mode, int *iters, double *rel_resid) {
+  if (!h || (mode != PIC_SOLVER_PLAIN && mode != PIC_SOLVER_MIXED)) return PIC_EINVAL;
+  CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
+  int st = enqueue_solve(h);
+  if (st) return st;
+  CK(launch_efield(efield_params(h), h->stream));
+  double out[3];
+  CK(cudaMemcpyAsync(out, h->d_pcg_out, sizeof(out), cudaMemcpyDeviceToHost, h->stream));
+  if (sync(h)) return PIC_ECUDA;
+  if (iters) *iters = (int)out[0];
+  if (rel_resid) *rel_resid = out[1];
+  int s = (int)out[2];
+  return s == 0 ? PIC_OK : (s == -5 ? PIC_ETIMEOUT : (s == -7 ? PIC_ENAN : PIC_ENOCONV));
+}
+
+int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss) {
+  if (!h) return PIC_EINVAL;
+  int st = enqueue_ceq(h, with_chi != 0);
+  if (st) return st;
+  double ce[2];
+  CK(cudaMemcpyAsync(ce, h->d_ceq_out, sizeof(ce), cudaMemcpyDeviceToHost, h->stream));
+  if (sync(h)) return PIC_ECUDA;
+  if (ceq) *ceq = ce[0];
+  if (gauss) *gauss = ce[1];
+  return PIC_OK;
+}
+
+int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
+  if (!h || !host_buf) return PIC_EINVAL;
+  const size_t nb = sizeof(double) * h->nn;
+  if (sync(h)) return PIC_ECUDA;
+  double *o = (double *)host_buf;
+  if (what == PIC_DIAG_SCALARS) {
+    if (bytes < sizeof(double) * PIC_NSCALARS) return PIC_EINVAL;
+    double sc[SC_N], pcg[3];
+    unsigned long long cnt[CNT_N];
+    CK(cudaMemcpy(sc, h->d_scalars, sizeof(sc), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(pcg, h->d_pcg_out, sizeof(pcg), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(cnt, h->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
+    const pic_config &c = h->cfg;
+    o[0] = h->step; o[1] = h->step * c.dt; o[2] = sc[SC_UE]; o[3] = sc[SC_QE]; o[4] = sc[SC_CEQ];
+    o[5] = sc[SC_ICONV]; o[6] = sc[SC_ICCP];
+    for (int k = 0; k < 6; ++k) o[7 + k] = sc[SC_Y0 + k];
+    o[13] = pcg[0]; o[14] = pcg[1];
+    o[15] = h->numax[0]; o[16] = h->numax[1]; o[17] = h->pcoll[0]; o[18] = h->pcoll[1];
+    for (int s = 0; s < 2; ++s)
+      for (int k = 0; k < 3; ++k) {
+        o[19 + 3 * s + k] = c.q[s] * c.w[s] * (double)cnt[CNT_ABS + 3 * s + k];
+        o[25 + 3 * s + k] = (double)cnt[CNT_ABS + 3 * s + k];
+        o[31 + 3 * s + k] = (double)cnt[CNT_COLL + 3 * s + k];
+      }
+    o[36] = 0.0;
+    o[37] = (double)cnt[CNT_BORN + 0]; o[38] = (double)cnt[CNT_BORN + 1];
+    for (int k = 0; k < 3; ++k) o[39 + k] = sc[SC_IONCUR + k];
+    o[42] = sc[SC_I1_RE]; o[43] = sc[SC_I1_IM]; o[44] = sc[SC_WINDOWS]; o[45] = sc[SC_CEQ_GAUSS];
+    o[46] = pcg[2];
+    return PIC_OK;
+  }
+  if (bytes < nb) return PIC_EINVAL;
+  switch (what) {
+    case PIC_DIAG_PHI: CK(cudaMemcpy(o, h->d_phi, nb, cudaMemcpyDeviceToHost)); return PIC_OK;
+    case PIC_DIAG_ER: CK(cudaMemcpy(o, h->d_Er, nb, cudaMemcpyDeviceToHost)); return PIC_OK;
+    case PIC_DIAG_EZ: CK(cudaMemcpy(o, h->d_Ez, nb, cudaMemcpyDeviceToHost)); return PIC_OK;
+    case PIC_DIAG_CHI: CK(cudaMemcpy(o, h->d_chi, nb, cudaMemcpyDeviceToHost)); return PIC_OK;
+    case PIC_DIAG_VNODE: CK(cudaMemcpy(o, h->d_vnode, nb, cudaMemcpyDeviceToHost)); return PIC_OK;
+    case PIC_DIAG_RHO: CK(cudaMemcpy(o, h->d_qrhs, nb, cudaMemcpyDeviceToHost)); return PIC_OK;
+    case PIC_DIAG_NE_AVG: CK(cudaMemcpy(o, h->d_dens_avg[0], nb, cudaMemcpyDeviceToHost)); return PIC_OK;
+    case PIC_DIAG_NI_AVG: CK(cudaMemcpy(o, h->d_dens_avg[1], nb, cudaMemcpyDeviceToHost)); return PIC_OK;
+    case PIC_DIAG_DEP_E:
+    case PIC_DIAG_DEP_I: {
+      std::vector<unsigned long long> u(h->nn);
+      CK(cudaMemcpy(u.data(), h->d_dep[what - PIC_DIAG_DEP_E], sizeof(unsigned long long) * h->nn,
+                    cudaMemcpyDeviceToHost));
+      double sc = dep_inv_scale(h);
+      for (int a = 0; a < h->nn; ++a) o[a] = (double)u[a] * sc;
+      return PIC_OK;
+    }
+    case PIC_DIAG_SIGMA: {
+      std::vector<unsigned long long> u0(h->nn), u1(h->nn);
+      CK(cudaMemcpy(u0.data(), h->d_surf[0], sizeof(unsigned long long) * h->nn, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(u1.data(), h->d_surf[1], sizeof(unsigned long long) * h->nn, cudaMemcpyDeviceToHost));
+      const pic_config &c = h->cfg;
+      for (int a = 0; a < h->nn; ++a) o[a] = c.q[0] * c.w[0] * (double)u0[a] + c.q[1] * c.w[1] * (double)u1[a];
+      return PIC_OK;
+    }
+    default: return PIC_EINVAL;
+  }
+}
+
+int pic_set_field(pic_handle *h, int what, const double *host_buf, size_t n) {
+  if (!h || !host_buf || n != (size_t)h->nn) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  const size_t nb = sizeof(double) * h->nn;
+  switch (what) {
+    case PIC_DIAG_PHI: CK(cudaMemcpy(h->d_phi, host_buf, nb, cudaMemcpyHostToDevice)); return PIC_OK;
+    case PIC_DIAG_RHO: CK(cudaMemcpy(h->d_qrhs, host_buf, nb, cudaMemcpyHostToDevice)); return PIC_OK;
+    case PIC_DIAG_ER:
+    case PIC_DIAG_EZ: {
+      CK(cudaMemcpy(what == PIC_DIAG_ER ? h->d_Er : h->d_Ez, host_buf, nb, cudaMemcpyHostToDevice));
+      std::vector<double> er(h->nn), ez(h->nn);
+      CK(cudaMemcpy(er.data(), h->d_Er, nb, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(ez.data(), h->d_Ez, nb, cudaMemcpyDeviceToHost));
+      if (h->prec == PIC_FP32) {
+        std::vector<float2> e(h->nn);
+        for (int a = 0; a < h->nn; ++a) e[a] = make_float2((float)er[a], (float)ez[a]);
+        CK(cudaMemcpy(h->d_E, e.data(), sizeof(float2) * h->nn, cudaMemcpyHostToDevice));
+      } else {
+        std::vector<double2> e(h->nn);
+        for (int a = 0; a < h->nn; ++a) e[a] = make_double2(er[a], ez[a]);
+        CK(cudaMemcpy(h->d_E, e.data(), sizeof(double2) * h->nn, cudaMemcpyHostToDevice));
+      }
+      return PIC_OK;
+    }
+    case PIC_DIAG_DEP_E:
+    case PIC_DIAG_DEP_I: {
+      std::vector<unsigned long long> u(h->nn);
+      double sc = 1.0 / dep_inv_scale(h);
+      for (int a = 0; a < h->nn; ++a) u[a] = (unsigned long long)std::llround(host_buf[a] * sc);
+      CK(cudaMemcpy(h->d_dep[what - PIC_DIAG_DEP_E], u.data(), sizeof(unsigned long long) * h->nn,
+                    cudaMemcpyHostToDevice));
+      return PIC_OK;
+    }
+    default: return PIC_EINVAL;
+  }
+}
+
+int pic_set_step(pic_handle *h, uint32_t step) {
+  if (!h) return PIC_EINVAL;
+  h->step = step;
+  CK(cudaMemcpyAsync(h->d_step, &h->step, sizeof(uint32_t), cudaMemcpyHostToDevice, h->stream));
+  return sync(h);
+}
+
+int pic_set_ceq(pic_handle *h, double ceq) {
+  if (!h || !(ceq > 0)) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  CK(cudaMemcpy(h->d_scalars + SC_CEQ, &ceq, sizeof(double), cudaMemcpyHostToDevice));
+  return PIC_OK;
+}
+
+int pic_set_circuit_state(pic_handle *h, const double *y6) {
+  if (!h || !y6) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  double sc[SC_N];
+  CK(cudaMemcpy(sc, h->d_scalars, sizeof(sc), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < 6; ++k) sc[SC_Y0 + k] = y6[k];
+  int n = h->cfg.circuit == PIC_CIRCUIT_RLC ? 3 : (h->cfg.circuit == PIC_CIRCUIT_IMN ? 6 : 0);
+  if (n) sc[SC_QE] = sc[SC_Y0 + n - 1];
+  sc[SC_UE] = sc[SC_QE] / sc[SC_CEQ];
+  CK(cudaMemcpy(h->d_scalars, sc, sizeof(sc), cudaMemcpyHostToDevice));
+  return PIC_OK;
+}
+
+int pic_set_conv_current(pic_handle *h, double I_conv) {
+  // The circuit kernel derives I_conv from the absorbed-particle counters;
+  // express the requested current as an electron count at the powered node.
+  if (!h) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  unsigned long long cnt[CNT_N] = {0};
+  const pic_config &c = h->cfg;
+  double per = c.q[0] * c.w[0] / c.dt;
+  if (I_conv != 0.0) {
+    double k = I_conv / per;
+    if (!(k >= 0) || std::fabs(k - std::llround(k)) > 1e-9 * (1 + std::fabs(k))) return PIC_EINVAL;
+    cnt[CNT_ABS + 0] = (unsigned long long)std::llround(k);
+  }
+  CK(cudaMemcpy(h->d_counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice));
+  return PIC_OK;
+}
+
+int pic_circuit_run(pic_handle *h, int n, double *U_out) {
+  if (!h || n < 0) return PIC_EINVAL;
+  double *d_hist = nullptr;
+  if (U_out && n > 0) {
+    if (cudaMalloc(&d_hist, sizeof(double) * n) != cudaSuccess) return PIC_ENOMEM;
+  }
+  uint32_t step = h->step;
+  CK(cudaMemcpyAsync(h->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, h->stream));
+  cudaError_t e = launch_circuit(circuit_params(h, n, d_hist, h->d_step), h->stream);
+  if (e == cudaSuccess && d_hist) e = cudaMemcpyAsync(U_out, d_hist, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (d_hist) cudaFree(d_hist);
+  if (e != cudaSuccess) return PIC_ECUDA;
+  h->step += n;
+  return PIC_OK;
+}
+
+int pic_status(pic_handle *h, uint32_t *flags) {
+  if (!h || !flags) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  uint32_t f = 0;
+  CK(cudaMemcpy(&f, h->d_flags, sizeof(f), cudaMemcpyDeviceToHost));
+  uint32_t z = 0;
+  CK(cudaMemcpy(h->d_flags, &z, sizeof(z), cudaMemcpyHostToDevice));
+  *flags = f;
+  return PIC_OK;
+}
+
+int pic_philox(pic_handle *h, int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+  if (!h || n < 0 || (n > 0 && (!ctr || !key || !out))) return PIC_EINVAL;
+  if (n == 0) return PIC_OK;
+  uint32_t *d = nullptr;
+  size_t bytes = sizeof(uint32_t) * (size_t)n * 10;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) return PIC_ENOMEM;
+  cudaError_t e = cudaMemcpy(d, ctr, sizeof(uint32_t) * 4 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d + 4 * n, key, sizeof(uint32_t) * 2 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_philox(n, d, d + 4 * n, d + 6 * n, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(out, d + 6 * n, sizeof(uint32_t) * 4 * n, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  return e == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+}  // extern "C"

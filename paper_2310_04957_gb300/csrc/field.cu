@@ -1,0 +1,608 @@
+// field.cu -- assembly of the implicit field equation, plain FP64 PCG, node E
+// field, field-energy integral for C_eq, circuit integrator and diagnostics.
+//
+// Eq. 1 of arXiv:2310.04957, div[(1+chi) eps grad phi] = -rho~, is discretised
+// by finite volumes on the node-centred r-z grid: node a's control volume
+// exchanges flux with each neighbour b through an edge conductance G_ab, and
+// sum_b G_ab (phi_a - phi_b) = Q_a, the charge in the control volume.  G is the
+// vacuum part (eps0 eps_r face area / length, from the geometry) plus the
+// plasma part times the mean chi of the edge's two nodes.  Metal nodes are
+// Dirichlet (powered at U_E, grounded at 0).
+#include <cstdint>
+
+#include "pic_device.cuh"
+#include "pic_kernels.h"
+
+namespace pic {
+
+// ---- assembly ---------------------------------------------------------------
+// Node pass: chi (D1 susceptibility dt^2/(2 eps0) sum_s q_s^2 n_s/m_s), node
+// charge (particles + surface), Dirichlet values.
+__global__ void k_assemble_nodes(const FieldParams F) {
+  const double UE = F.scalars[SC_UE];
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < F.nn; a += gridDim.x * blockDim.x) {
+    double Qe = (double)F.dep[0][a] * F.dep_inv_scale;
+    double Qi = (double)F.dep[1][a] * F.dep_inv_scale;
+    double v = F.vnode[a];
+    F.chi[a] = v > 0.0 ? (F.chi_coef[0] * Qe + F.chi_coef[1] * Qi) / v : 0.0;
+    F.qrhs[a] = F.qw[0] * (Qe + (double)F.surf[0][a]) + F.qw[1] * (Qi + (double)F.surf[1][a]);
+    int k = F.node_kind[a];
+    if (k == 1) F.phi[a] = UE;
+    else if (k == 2) F.phi[a] = 0.0;
+  }
+}
+
+// Edge pass: each node writes its right and upper edge and the inverse of its
+// diagonal (sum of its up to four edges).
+__global__ void k_assemble_edges(const FieldParams F) {
+  const int nr = F.nr, nz = F.nz, W = nr + 1;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < F.nn; a += gridDim.x * blockDim.x) {
+    int j = a / W, i = a - j * W;
+    double ca = F.chi[a];
+    double d = 0.0;
+    if (i < nr) {
+      int e = j * nr + i;
+      double g = F.Gvac_r[e] + 0.5 * (ca + F.chi[a + 1]) * F.Gpl_r[e];
+      F.Gr[e] = g;
+      d += g;
+    }
+    if (i > 0) {
+      int e = j * nr + i - 1;
+      d += F.Gvac_r[e] + 0.5 * (ca + F.chi[a - 1]) * F.Gpl_r[e];
+    }
+    if (j < nz) {
+      int e = j * W + i;
+      double g = F.Gvac_z[e] + 0.5 * (ca + F.chi[a + W]) * F.Gpl_z[e];
+      F.Gz[e] = g;
+      d += g;
+    }
+    if (j > 0) {
+      int e = (j - 1) * W + i;
+      d += F.Gvac_z[e] + 0.5 * (ca + F.chi[a - W]) * F.Gpl_z[e];
+    }
+    F.dinv[a] = (F.node_kind[a] == 0 && d > 0.0) ? 1.0 / d : 0.0;
+  }
+}
+
+cudaError_t launch_assemble_edges_only(const FieldParams &F, cudaStream_t st) {
+  int blocks = (F.nn + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_assemble_edges<<<blocks, 256, 0, st>>>(F);
+  return cudaGetLastError();
+}
+
+__global__ void k_set_dirichlet(int nn, const int8_t *kind, double *phi, double U) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nn; a += gridDim.x * blockDim.x) {
+    if (kind[a] == 1) phi[a] = U;
+    else if (kind[a] == 2) phi[a] = 0.0;
+  }
+}
+
+cudaError_t launch_set_dirichlet(int nn, const int8_t *kind, double *phi, double U, cudaStream_t st) {
+  int blocks = (nn + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_set_dirichlet<<<blocks, 256, 0, st>>>(nn, kind, phi, U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(const FieldParams &F, cudaStream_t st) {
+  int blocks = (F.nn + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_assemble_nodes<<<blocks, 256, 0, st>>>(F);
+  k_assemble_edges<<<blocks, 256, 0, st>>>(F);
+  return cudaGetLastError();
+}
+
+// ---- plain FP64 PCG ------------------------------------------------------------
+// Grid-wide barrier with a bounded wait: returns false (and sets the timeout
+// flag) if the other blocks did not arrive within `limit` clock cycles.
+__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, long long limit, uint32_t *flags) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    unsigned g = *gen;
+    __threadfence();
+    unsigned prev = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (prev == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > limit) {
+          ok = 0;
+          atomicOr(flags, 0x2u);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// (A x)_a = sum_b G_ab (x_a - x_b) at free node a; Dirichlet neighbours enter
+// with their x value (x is zero there for search directions).  Vectors written
+// by other blocks are read through L2 (__ldcg).
+__device__ __forceinline__ double apply_A(const PcgParams &P, int a, int i, int j, const double *x) {
+  const int nr = P.nr, W = nr + 1;
+  double xa = __ldcg(x + a), acc = 0.0;
+  if (i > 0) acc += __ldg(P.Gr + j * nr + i - 1) * (xa - __ldcg(x + a - 1));
+  if (i < nr) acc += __ldg(P.Gr + j * nr + i) * (xa - __ldcg(x + a + 1));
+  if (j > 0) acc += __ldg(P.Gz + (j - 1) * W + i) * (xa - __ldcg(x + a - W));
+  if (j < P.nz) acc += __ldg(P.Gz + j * W + i) * (xa - __ldcg(x + a + W));
+  return acc;
+}
+
+// Block partial sums of K values into partial[blockIdx.x*4 + k].
+template <int K>
+__device__ void block_reduce_store(const double v[K], double *partial) {
+  __shared__ double s[4][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s[k][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double x = lane < nw ? s[k][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) partial[blockIdx.x * 4 + k] = x;
+    }
+  }
+}
+
+// Grid total of the block partials, summed in a fixed order so that every
+// block obtains the same bits.
+template <int K>
+__device__ void grid_total(const double *partial, double out[K]) {
+  __shared__ double s_tot[4];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double x = 0.0;
+      for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(partial + b * 4 + k);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) s_tot[k] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = s_tot[k];
+}
+
+// Jacobi-preconditioned CG on the free nodes, FP64, warm start from phi.
+// Stops when ||r||_2 <= tol ||b||_2 (b = node charge + Dirichlet lift),
+// confirmed on the recomputed residual.  Persistent: one cooperative launch,
+// bounded grid barriers, reduction partials double-buffered (three barriers
+// per iteration).
+__global__ void __launch_bounds__(256) k_pcg(const PcgParams P) {
+  const int nn = P.nn, W = P.nr + 1;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
+  const unsigned nb = gridDim.x;
+  double tot[4];
+  int it = 0, pb = 0;
+  int status = -4;
+  double target = 0.0, bnorm = 0.0, rr = 0.0, rz = 0.0;
+#define PCG_SYNC()                                                   \
+  if (!grid_barrier(P.bar, nb, P.spin_limit, P.flags)) {             \
+    status = -5;                                                     \
+    goto done;                                                       \
+  }
+  for (int pass = 0; pass < 64; ++pass) {
+    {
+      double v[4] = {0.0, 0.0, 0.0, 0.0};  // b^2, r^2, r.z
+      for (int a = gt; a < nn; a += gs) {
+        if (P.node_kind[a] != 0) { P.r[a] = 0.0; P.z[a] = 0.0; P.p[a] = 0.0; continue; }
+        int j = a / W, i = a - j * W;
+        double r = __ldg(P.qrhs + a) - apply_A(P, a, i, j, P.phi);
+        double lift = 0.0;  // b = q + sum over Dirichlet neighbours of G phi_D
+        if (i > 0 && P.node_kind[a - 1] != 0) lift += P.Gr[j * P.nr + i - 1] * __ldcg(P.phi + a - 1);
+        if (i < P.nr && P.node_kind[a + 1] != 0) lift += P.Gr[j * P.nr + i] * __ldcg(P.phi + a + 1);
+        if (j > 0 && P.node_kind[a - W] != 0) lift += P.Gz[(j - 1) * W + i] * __ldcg(P.phi + a - W);
+        if (j < P.nz && P.node_kind[a + W] != 0) lift += P.Gz[j * W + i] * __ldcg(P.phi + a + W);
+        double b = __ldg(P.qrhs + a) + lift;
+        double z = __ldg(P.dinv + a) * r;
+        P.r[a] = r;
+        P.z[a] = z;
+        P.p[a] = z;
+        v[0] += b * b;
+        v[1] += r * r;
+        v[2] += r * z;
+      }
+      double *part = P.partial + pb * nb * 4;
+      pb ^= 1;
+      block_reduce_store<3>(v, part);
+      PCG_SYNC();
+      grid_total<3>(part, tot);
+    }
+    bnorm = sqrt(tot[0]);
+    target = bnorm > 0.0 ? P.tol * bnorm : 1e-30;
+    rr = tot[1];
+    rz = tot[2];
+    if (!(rr == rr) || !(bnorm == bnorm)) { status = -7; goto done; }
+    if (sqrt(rr) <= target) { status = 0; goto done; }
+    if (it >= P.maxit) { status = -4; goto done; }
+    while (it < P.maxit) {
+      {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int a = gt; a < nn; a += gs) {
+          if (P.node_kind[a] != 0) continue;
+          int j = a / W, i = a - j * W;
+          double ap = apply_A(P, a, i, j, P.p);
+          P.Ap[a] = ap;
+          v[0] += __ldcg(P.p + a) * ap;
+        }
+        double *part = P.partial + pb * nb * 4;
+        pb ^= 1;
+        block_reduce_store<1>(v, part);
+        PCG_SYNC();
+        grid_total<1>(part, tot);
+      }
+      double alpha = rz / tot[0];
+      {
+        double v[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int a = gt; a < nn; a += gs) {
+          if (P.node_kind[a] != 0) continue;
+          P.phi[a] += alpha * P.p[a];
+          double r = P.r[a] - alpha * P.Ap[a];
+          double z = __ldg(P.dinv + a) * r;
+          P.r[a] = r;
+          P.z[a] = z;
+          v[0] += r * r;
+          v[1] += r * z;
+        }
+        double *part = P.partial + pb * nb * 4;
+        pb ^= 1;
+        block_reduce_store<2>(v, part);
+        PCG_SYNC();
+        grid_total<2>(part, tot);
+      }
+      ++it;
+      rr = tot[0];
+      if (!(rr == rr)) { status = -7; goto done; }
+      if (sqrt(rr) <= target) break;
+      double beta = tot[1] / rz;
+      rz = tot[1];
+      for (int a = gt; a < nn; a += gs) {
+        if (P.node_kind[a] != 0) continue;
+        P.p[a] = P.z[a] + beta * P.p[a];
+      }
+      PCG_SYNC();
+    }
+    PCG_SYNC();
+  }
+#undef PCG_SYNC
+done:
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.out[0] = (double)it;
+    P.out[1] = bnorm > 0.0 ? sqrt(rr) / bnorm : sqrt(rr);
+    P.out[2] = (double)status;
+    if (status == -4) atomicOr(P.flags, 0x4u);
+    if (status == -7) atomicOr(P.flags, 0x8u);
+  }
+}
+
+int pcg_grid_size(int device) {
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg, 256, 0);
+  if (per > 2) per = 2;
+  if (per < 1) per = 1;
+  return sms * per;
+}
+
+cudaError_t launch_pcg(const PcgParams &P, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg, P);
+}
+
+// ---- E field at nodes -----------------------------------------------------------
+// E = -grad phi: central differences; E_r = 0 on the axis; one-sided at the
+// domain edge; at a Dirichlet node with exactly one free neighbour along a
+// direction, one-sided toward that neighbour.
+__global__ void k_efield(const EfieldParams E) {
+  const int nr = E.nr, nz = E.nz, W = nr + 1, nn = W * (nz + 1);
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nn; a += gridDim.x * blockDim.x) {
+    int j = a / W, i = a - j * W;
+    const double *phi = E.phi;
+    bool dir = E.node_kind[a] != 0;
+    double er, ez;
+    if (i == 0) er = 0.0;
+    else if (i == nr) er = -(phi[a] - phi[a - 1]) / E.dr;
+    else {
+      bool fl = E.node_kind[a - 1] == 0, fh = E.node_kind[a + 1] == 0;
+      if (dir && fl && !fh) er = -(phi[a] - phi[a - 1]) / E.dr;
+      else if (dir && fh && !fl) er = -(phi[a + 1] - phi[a]) / E.dr;
+      else er = -(phi[a + 1] - phi[a - 1]) / (2.0 * E.dr);
+    }
+    if (j == 0) ez = -(phi[a + W] - phi[a]) / E.dz;
+    else if (j == nz) ez = -(phi[a] - phi[a - W]) / E.dz;
+    else {
+      bool fl = E.node_kind[a - W] == 0, fh = E.node_kind[a + W] == 0;
+      if (dir && fl && !fh) ez = -(phi[a] - phi[a - W]) / E.dz;
+      else if (dir && fh && !fl) ez = -(phi[a + W] - phi[a]) / E.dz;
+      else ez = -(phi[a + W] - phi[a - W]) / (2.0 * E.dz);
+    }
+    E.Er[a] = er;
+    E.Ez[a] = ez;
+    if (E.E32) E.E32[a] = make_float2((float)er, (float)ez);
+    if (E.E64) E.E64[a] = make_double2(er, ez);
+  }
+}
+
+cudaError_t launch_efield(const EfieldParams &E, cudaStream_t st) {
+  int nn = (E.nr + 1) * (E.nz + 1);
+  int blocks = (nn + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_efield<<<blocks, 256, 0, st>>>(E);
+  return cudaGetLastError();
+}
+
+// ---- field energy (Eqs. 6-7) ------------------------------------------------------
+// out[0] = sum over edges G (phi_a - phi_b)^2 (= 2 x energy = C_eq U^2),
+// out[1] = Gauss-law charge on the powered nodes.  One CTA, fixed order.
+__global__ void __launch_bounds__(1024) k_energy(int nr, int nz, const int8_t *node_kind, const double *Gr,
+                                                 const double *Gz, const double *phi, double *out) {
+  const int W = nr + 1, nn = W * (nz + 1);
+  double e = 0.0, q = 0.0;
+  for (int a = threadIdx.x; a < nn; a += blockDim.x) {
+    int j = a / W, i = a - j * W;
+    bool pa = node_kind[a] == 1;
+    if (i < nr) {
+      double d = phi[a] - phi[a + 1], g = Gr[j * nr + i];
+      e += g * d * d;
+      bool pb = node_kind[a + 1] == 1;
+      if (pa && !pb) q += g * d;
+      if (pb && !pa) q -= g * d;
+    }
+    if (j < nz) {
+      double d = phi[a] - phi[a + W], g = Gz[j * W + i];
+      e += g * d * d;
+      bool pb = node_kind[a + W] == 1;
+      if (pa && !pb) q += g * d;
+      if (pb && !pa) q -= g * d;
+    }
+  }
+  __shared__ double se[32], sq[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+  }
+  if ((threadIdx.x & 31) == 0) { se[threadIdx.x >> 5] = e; sq[threadIdx.x >> 5] = q; }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int nw = blockDim.x >> 5;
+    e = threadIdx.x < nw ? se[threadIdx.x] : 0.0;
+    q = threadIdx.x < nw ? sq[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      e += __shfl_xor_sync(0xffffffffu, e, o);
+      q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if (threadIdx.x == 0) { out[0] = e; out[1] = q; }
+  }
+}
+
+cudaError_t launch_energy(int nr, int nz, const int8_t *node_kind, const double *Gr, const double *Gz, const double *phi,
+                          double *out2, cudaStream_t st) {
+  k_energy<<<1, 1024, 0, st>>>(nr, nz, node_kind, Gr, Gz, phi, out2);
+  return cudaGetLastError();
+}
+
+// ---- circuit (Eqs. 5, 8, 9, 10) ------------------------------------------------------
+// Linear ODE y' = M y + s(t) of the circuit states with the electrode charge
+// Q_E, U_E = Q_E / C_eq.  Trapezoidal rule with nsub substeps per dt:
+// y_{k+1} = (I - h/2 M)^{-1} [(I + h/2 M) y_k + h/2 (s_k + s_{k+1})].
+__device__ void circuit_matrix(const CircuitParams &C, double ceq, double M[6][6], double e_src[6], double e_conv[6],
+                               int &n) {
+  for (int r = 0; r < 6; ++r) {
+    e_src[r] = e_conv[r] = 0.0;
+    for (int k = 0; k < 6; ++k) M[r][k] = 0.0;
+  }
+  if (C.kind == 1) {  // Qb, Ib, QE
+    double Rb = C.c[0], Lb = C.c[1], Cb = C.c[2];
+    n = 3;
+    M[0][1] = 1.0;
+    M[1][0] = -1.0 / (Lb * Cb);
+    M[1][1] = -Rb / Lb;
+    M[1][2] = -1.0 / (Lb * ceq);
+    M[2][1] = 1.0;
+    e_src[1] = 1.0 / Lb;
+    e_conv[2] = 1.0;
+  } else {  // Q1, Q2, I2, Qccp, Istray, QE
+    double Rs = C.c[0], Cm1 = C.c[1], Lm = C.c[2], Cm2 = C.c[3], Rm = C.c[4], Cs = C.c[5], Rst = C.c[6], Ls = C.c[7];
+    n = 6;
+    M[0][0] = -1.0 / (Rs * Cm1);
+    M[0][1] = 1.0 / (Rs * Cm1);
+    M[1][2] = 1.0;
+    M[2][0] = 1.0 / (Lm * Cm1);
+    M[2][1] = -1.0 / (Lm * Cm1) - 1.0 / (Lm * Cm2);
+    M[2][2] = -Rm / Lm;
+    M[2][5] = -1.0 / (Lm * ceq);
+    M[3][2] = 1.0;
+    M[3][4] = -1.0;
+    M[4][1] = -1.0 / (Ls * Cs);
+    M[4][3] = 1.0 / (Ls * Cs);
+    M[4][4] = -Rst / Ls;
+    M[4][5] = 1.0 / (Ls * ceq);
+    M[5][2] = 1.0;
+    M[5][4] = -1.0;
+    e_src[0] = 1.0 / Rs;
+    e_conv[5] = 1.0;
+  }
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting (n <= 6).
+__device__ void invert6(int n, double A[6][6], double Inv[6][6]) {
+  for (int r = 0; r < n; ++r)
+    for (int k = 0; k < n; ++k) Inv[r][k] = r == k ? 1.0 : 0.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        double t = A[c][k]; A[c][k] = A[piv][k]; A[piv][k] = t;
+        t = Inv[c][k]; Inv[c][k] = Inv[piv][k]; Inv[piv][k] = t;
+      }
+    double d = 1.0 / A[c][c];
+    for (int k = 0; k < n; ++k) { A[c][k] *= d; Inv[c][k] *= d; }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      double f = A[r][c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < n; ++k) { A[r][k] -= f * A[c][k]; Inv[r][k] -= f * Inv[c][k]; }
+    }
+  }
+}
+
+__global__ void k_circuit(const CircuitParams C) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double *S = C.scalars;
+  const double two_pi = 6.283185307179586476925286766559;
+  double ceq = S[SC_CEQ];
+  double Iconv = (C.qw[0] * (double)C.counters[CNT_ABS + 0] + C.qw[1] * (double)C.counters[CNT_ABS + 3]) / C.dt;
+  S[SC_ICONV] = Iconv;
+  uint32_t step = *C.step_ptr;
+  if (C.kind == 0) {
+    for (int k = 0; k < C.n_run; ++k) {
+      double tn = (double)(step + k) * C.dt, t1 = tn + C.dt;
+      double U0 = C.V * sin(two_pi * C.f * tn + C.phase);
+      double U1 = C.V * sin(two_pi * C.f * t1 + C.phase);
+      S[SC_UE] = U1;
+      S[SC_QE] = ceq * U1;
+      S[SC_ICCP] = ceq * (U1 - U0) / C.dt - Iconv;
+      if (C.U_hist) C.U_hist[k] = U1;
+    }
+  } else {
+    double M[6][6], es[6], ec[6], A[6][6], Inv[6][6], Bm[6][6];
+    int n;
+    circuit_matrix(C, ceq, M, es, ec, n);
+    double h = C.dt / C.nsub;
+    for (int r = 0; r < n; ++r)
+      for (int k = 0; k < n; ++k) A[r][k] = (r == k ? 1.0 : 0.0) - 0.5 * h * M[r][k];
+    invert6(n, A, Inv);
+    // Bm = Inv * (I + h/2 M)
+    for (int r = 0; r < n; ++r)
+      for (int k = 0; k < n; ++k) {
+        double acc = 0.0;
+        for (int m = 0; m < n; ++m) acc += Inv[r][m] * ((m == k ? 1.0 : 0.0) + 0.5 * h * M[m][k]);
+        Bm[r][k] = acc;
+      }
+    double y[6];
+    for (int r = 0; r < 6; ++r) y[r] = S[SC_Y0 + r];
+    for (int k = 0; k < C.n_run; ++k) {
+      double tn = (double)(step + k) * C.dt;
+      for (int sub = 0; sub < C.nsub; ++sub) {
+        double ta = tn + sub * h, tb = tn + (sub + 1) * h;
+        double Ua = C.V * sin(two_pi * C.f * ta + C.phase), Ub = C.V * sin(two_pi * C.f * tb + C.phase);
+        double src[6], yn[6];
+        for (int r = 0; r < n; ++r) src[r] = 0.5 * h * (es[r] * (Ua + Ub) + ec[r] * 2.0 * Iconv);
+        for (int r = 0; r < n; ++r) {
+          double acc = 0.0;
+          for (int m = 0; m < n; ++m) acc += Bm[r][m] * y[m] + Inv[r][m] * src[m];
+          yn[r] = acc;
+        }
+        for (int r = 0; r < n; ++r) y[r] = yn[r];
+      }
+      double QE = y[n - 1];
+      S[SC_QE] = QE;
+      S[SC_UE] = QE / ceq;
+      S[SC_ICCP] = C.kind == 1 ? y[1] : y[2] - y[4];
+      if (C.U_hist) C.U_hist[k] = QE / ceq;
+    }
+    for (int r = 0; r < 6; ++r) S[SC_Y0 + r] = y[r];
+  }
+  S[SC_T] = (double)(step + C.n_run) * C.dt;
+  if (C.step_inc) *C.step_inc = step + C.n_run;
+}
+
+cudaError_t launch_circuit(const CircuitParams &C, cudaStream_t st) {
+  k_circuit<<<1, 32, 0, st>>>(C);
+  return cudaGetLastError();
+}
+
+// ---- diagnostics -----------------------------------------------------------------
+// Per step: running sums of node densities, ion charge to each surface kind,
+// first-harmonic DFT of I_ccp at t_{n+1}; then the step counter advances.
+__global__ void k_diag(const DiagParams D) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < D.nn; a += gridDim.x * blockDim.x) {
+    double v = D.vnode[a];
+    if (v > 0.0) {
+      D.dens_sum[0][a] += D.w[0] * (double)D.dep[0][a] * D.dep_inv_scale / v;
+      D.dens_sum[1][a] += D.w[1] * (double)D.dep[1][a] * D.dep_inv_scale / v;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double *S = D.scalars;
+    uint32_t step = *D.step_ptr;
+    const double two_pi = 6.283185307179586476925286766559;
+    double t1 = (double)(step + 1) * D.dt;
+    double ph = two_pi * D.f * t1;
+    S[SC_DFT_RE] += S[SC_ICCP] * cos(ph);
+    S[SC_DFT_IM] -= S[SC_ICCP] * sin(ph);
+    for (int k = 0; k < 3; ++k) S[SC_IONQ + k] += D.qw_ion * (double)D.counters[CNT_ABS + 3 + k];
+    S[SC_WINCOUNT] += 1.0;
+    *D.step_mut = step + 1;
+  }
+}
+
+// Close a diagnostic window: averages over the window's steps, reset sums.
+__global__ void k_diag_window(const DiagParams D) {
+  double N = D.scalars[SC_WINCOUNT];
+  if (N <= 0.0) return;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < D.nn; a += gridDim.x * blockDim.x) {
+    for (int s = 0; s < 2; ++s) {
+      D.dens_avg[s][a] = D.dens_sum[s][a] / N;
+      D.dens_sum[s][a] = 0.0;
+    }
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double *S = D.scalars;
+    for (int k = 0; k < 3; ++k) { S[SC_IONCUR + k] = S[SC_IONQ + k] / (N * D.dt); S[SC_IONQ + k] = 0.0; }
+    S[SC_I1_RE] = 2.0 * S[SC_DFT_RE] / N;
+    S[SC_I1_IM] = 2.0 * S[SC_DFT_IM] / N;
+    S[SC_DFT_RE] = S[SC_DFT_IM] = 0.0;
+    S[SC_WINCOUNT] = 0.0;
+    S[SC_WINDOWS] += 1.0;
+  }
+}
+
+cudaError_t launch_diag(const DiagParams &D, cudaStream_t st) {
+  int blocks = (D.nn + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_diag<<<blocks, 256, 0, st>>>(D);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_window(const DiagParams &D, cudaStream_t st) {
+  int blocks = (D.nn + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_diag_window<<<blocks, 256, 0, st>>>(D);
+  return cudaGetLastError();
+}
+
+}  // namespace pic

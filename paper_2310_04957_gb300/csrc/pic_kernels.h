@@ -1,0 +1,142 @@
+// pic_kernels.h -- parameter blocks and launchers of the library's kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pic_device.cuh"
+
+namespace pic {
+
+constexpr int kMaxTileCells = 256;
+
+template <typename T>
+struct PushParams {
+  BinMap map;
+  int nr, nz;
+  T dt, hdt, hdt2, dr, dz, inv_dr, inv_dz;
+  const int8_t *cell_kind;  // [nz*nr]
+  const int8_t *node_kind;  // [(nz+1)*(nr+1)]
+  const void *E;            // node (E_r, E_z) as float2 / double2
+  T qm[2];
+  T pcoll[2], numax[2], n_gas;
+  const T *xs_E, *xs_S;     // [n_xs], [5*n_xs]
+  int n_xs;
+  T log2E0, inv_dlog2;
+  T thr_ex, thr_iz, B_ej;
+  T e_per_v2[2];            // table energy per v^2 (eV s^2/m^2): electron 1/2 m_e/e; ion 1/2 M_gas/e
+  T v2_per_e[2];            // electron 2e/m_e
+  T two_me_over_M;
+  T vth_gas;                // sqrt(k T_gas / M_gas)
+  T mi_frac;                // m_ion / (m_ion + M_gas)
+  uint32_t seed;
+  const uint32_t *step_ptr; // device step counter (Philox counter word 0)
+  StoreView<T> in[2], out[2];
+  unsigned long long *dep[2];
+  unsigned long long *surf[2];
+  unsigned long long *counters;
+  T dep_scale;
+  unsigned long long dep_one;
+  uint32_t *flags;
+};
+
+struct FieldParams {
+  int nr, nz, nn;
+  const int8_t *node_kind;
+  const double *Gvac_r, *Gpl_r, *Gvac_z, *Gpl_z;
+  const double *vnode;
+  const unsigned long long *dep[2];
+  const unsigned long long *surf[2];
+  double dep_inv_scale;
+  double qw[2];             // q_s w_s
+  double chi_coef[2];       // dt^2/(2 eps0) q_s^2/m_s w_s
+  double *chi, *qrhs, *phi, *Gr, *Gz, *dinv;
+  double *scalars;
+};
+
+struct PcgParams {
+  int nr, nz, nn;
+  const int8_t *node_kind;
+  const double *Gr, *Gz, *dinv, *qrhs;
+  double *phi;
+  double *r, *z, *p, *Ap;
+  double *partial;          // [gridDim.x * 4]
+  unsigned *bar;            // [2]: arrival count, generation
+  double tol;
+  int maxit;
+  double *out;              // [0] iterations, [1] relative residual, [2] status (0 ok, -4 noconv, -5 timeout, -7 nan)
+  uint32_t *flags;
+  long long spin_limit;     // clock cycles per barrier wait
+};
+
+struct MixedParams {
+  int nr, nz, nn;
+  const int8_t *node_kind;
+  const double *Gr, *Gz, *qrhs;
+  double *phi;
+  double tol;               // outer (FP64) relative residual target
+  float inner_tol;          // inner (FP32) relative reduction per refinement
+  int maxit;                // total inner iterations cap
+  double *out;
+  uint32_t *flags;
+  double *partial;          // scratch
+};
+
+struct EfieldParams {
+  int nr, nz;
+  double dr, dz;
+  const int8_t *node_kind;
+  const double *phi;
+  double *Er, *Ez;
+  float2 *E32;
+  double2 *E64;
+};
+
+struct CircuitParams {
+  int kind, nsub;
+  double c[8];
+  double V, f, phase, dt;
+  double qw[2];
+  const unsigned long long *counters;
+  const uint32_t *step_ptr;
+  double *scalars;
+  int n_run;                // steps to advance (1 inside the step graph)
+  double *U_hist;           // optional U_E history [n_run]
+  uint32_t *step_inc;       // if non-null, incremented once per advanced step
+};
+
+struct DiagParams {
+  int nn;
+  const double *vnode;
+  const unsigned long long *dep[2];
+  double dep_inv_scale;
+  double w[2];
+  double qw_ion;
+  double f, dt;
+  int window;
+  const unsigned long long *counters;
+  const uint32_t *step_ptr;
+  uint32_t *step_mut;
+  double *dens_sum[2], *dens_avg[2];
+  double *scalars;
+};
+
+template <typename T> cudaError_t launch_particles(const PushParams<T> &P, cudaStream_t st);
+template <typename T> cudaError_t launch_deposit_only(const PushParams<T> &P, cudaStream_t st);
+cudaError_t launch_layout(const int *fill_in, const int8_t *bin_plasma, int nbins, float slack, int capacity, int *start,
+                          int *cap, int *fill_out, BinMeta *meta_out, BinMeta *meta_in, cudaStream_t st);
+cudaError_t launch_philox(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st);
+
+cudaError_t launch_assemble(const FieldParams &F, cudaStream_t st);
+cudaError_t launch_assemble_edges_only(const FieldParams &F, cudaStream_t st);
+cudaError_t launch_set_dirichlet(int nn, const int8_t *kind, double *phi, double U, cudaStream_t st);
+cudaError_t launch_pcg(const PcgParams &P, int grid, cudaStream_t st);
+int pcg_grid_size(int device);
+cudaError_t launch_mixed(const MixedParams &M, cudaStream_t st);
+cudaError_t launch_efield(const EfieldParams &E, cudaStream_t st);
+cudaError_t launch_energy(int nr, int nz, const int8_t *node_kind, const double *Gr, const double *Gz,
+                          const double *phi, double *out2, cudaStream_t st);
+cudaError_t launch_circuit(const CircuitParams &C, cudaStream_t st);
+cudaError_t launch_diag(const DiagParams &D, cudaStream_t st);
+cudaError_t launch_diag_window(const DiagParams &D, cudaStream_t st);
+
+}  // namespace pic

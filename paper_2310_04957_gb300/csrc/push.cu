@@ -1,0 +1,811 @@
+// push.cu -- the particle phase of one time step (gather, D1 correction,
+// absorption, null-collision MCC, predictor with cylindrical rotation,
+// re-bin into the next store, deposit of counts), fused in one kernel.
+//
+// Method (arXiv:2310.04957, Sec. 2): direct-implicit (D1) push -- the particle
+// is first moved with the field it has not yet seen (predictor), the field
+// solve at t_{n+1} then corrects it by dt^2/2 a_{n+1} -- null-collision MCC of
+// electrons and Ar+ in argon, deposition of charge and of the implicit
+// susceptibility (both from the same per-species node counts).
+//
+// One CTA = one tile of TX x TY cells of one species.  It reads the tile's bins
+// (contiguous slots), pushes every particle in registers, claims a slot in the
+// particle's new bin of the write store (warp-aggregated: lanes with the same
+// new bin share one atomicAdd on the bin's fill counter), and deposits the
+// four node weights as 2^-26 fixed-point integers: summed over lanes of the
+// same new cell with redux.sync, added to a shared-memory node tile (tile +
+// halo), and flushed with one 64-bit global add per tile node.  Integer sums
+// are exact and order-independent.
+#include <cstdint>
+
+#include "pic_device.cuh"
+#include "pic_kernels.h"
+
+namespace pic {
+
+template <typename T> struct V2;
+template <> struct V2<float> { using type = float2; };
+template <> struct V2<double> { using type = double2; };
+
+// ---- math wrappers (library functions, not re-implemented) -----------------
+__device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float m_log(float x) { return logf(x); }
+__device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
+__device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float m_log2(float x) { return log2f(x); }
+__device__ __forceinline__ double m_log2(double x) { return log2(x); }
+__device__ __forceinline__ float m_tan(float x) { return tanf(x); }
+__device__ __forceinline__ double m_tan(double x) { return tan(x); }
+__device__ __forceinline__ float m_atan(float x) { return atanf(x); }
+__device__ __forceinline__ double m_atan(double x) { return atan(x); }
+__device__ __forceinline__ void m_sincospi(float x, float *s, float *c) { sincospif(x, s, c); }
+__device__ __forceinline__ void m_sincospi(double x, double *s, double *c) { sincospi(x, s, c); }
+__device__ __forceinline__ float m_floor(float x) { return floorf(x); }
+__device__ __forceinline__ double m_floor(double x) { return floor(x); }
+
+template <typename T>
+struct Part {
+  int ci, cj;
+  T fr, fz, vr, vt, vz, ar, at, az;
+  unsigned long long id;
+};
+
+// Bring (c, f) back to f in [0,1).
+template <typename T>
+__device__ __forceinline__ void renorm(int &c, T &f) {
+  T d = m_floor(f);
+  c += (int)d;
+  f -= d;
+  if (f >= (T)1) { f -= (T)1; c += 1; }
+  if (f < (T)0) f = (T)0;
+}
+
+template <typename T>
+__device__ __forceinline__ bool in_plasma(const PushParams<T> &P, int ci, int cj) {
+  if (ci < 0 || ci >= P.nr || cj < 0 || cj >= P.nz) return false;
+  return __ldg(P.cell_kind + cj * P.nr + ci) == 0;
+}
+
+// Node nearest to an exit point given in cell units (position clamped into the domain).
+template <typename T>
+__device__ __forceinline__ int exit_node(const PushParams<T> &P, int ci, T fr, int cj, T fz) {
+  int ni = ci >= P.nr ? P.nr : ci + (fr >= (T)0.5 ? 1 : 0);
+  int nj = cj < 0 ? 0 : (cj >= P.nz ? P.nz : cj + (fz >= (T)0.5 ? 1 : 0));
+  if (ni < 0) ni = 0;
+  return nj * (P.nr + 1) + ni;
+}
+
+// Cross section of process `proc` at energy E (eV): linear interpolation between
+// the bracketing log-spaced table nodes, clamped outside the table.
+template <typename T>
+__device__ __forceinline__ T xs(const PushParams<T> &P, int proc, T E) {
+  const T *Et = P.xs_E;
+  const T *S = P.xs_S + proc * P.n_xs;
+  int n = P.n_xs;
+  if (E <= __ldg(Et)) return __ldg(S);
+  if (E >= __ldg(Et + n - 1)) return __ldg(S + n - 1);
+  int k = (int)((m_log2(E) - P.log2E0) * P.inv_dlog2);
+  k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
+  if (E < __ldg(Et + k) && k > 0) --k;
+  if (E > __ldg(Et + k + 1) && k < n - 2) ++k;
+  T e0 = __ldg(Et + k), e1 = __ldg(Et + k + 1);
+  T s0 = __ldg(S + k), s1 = __ldg(S + k + 1);
+  return s0 + (E - e0) / (e1 - e0) * (s1 - s0);
+}
+
+// Electron scattering-angle cosine (Vahedi & Surendra): written with
+// expm1/log1p as 1 - 2 ((1+E)^R - 1)/E, algebraically the same as
+// (2 + E - 2 (1+E)^R)/E, without its cancellation in FP32.
+template <typename T>
+__device__ __forceinline__ T scatter_cos(T E, T R) {
+  T c = E < (T)1e-6 ? (T)1 - (T)2 * R : (T)1 - (T)2 * m_expm1(R * m_log1p(E)) / E;
+  return c > (T)1 ? (T)1 : (c < (T)-1 ? (T)-1 : c);
+}
+
+// Turn unit vector d by polar angle (cosine cc) and azimuth 2 pi u.
+template <typename T>
+__device__ __forceinline__ void turn(T d[3], T cc, T u) {
+  T sc = m_sqrt((T)1 - cc * cc > (T)0 ? (T)1 - cc * cc : (T)0);
+  T sp, cp;
+  m_sincospi((T)2 * u, &sp, &cp);
+  T st = m_sqrt(d[0] * d[0] + d[1] * d[1]);
+  T o0, o1, o2;
+  if (st > (T)1e-12) {
+    T k = sc / st;
+    o0 = d[0] * cc + k * (d[0] * d[2] * cp + d[1] * sp);
+    o1 = d[1] * cc + k * (d[1] * d[2] * cp - d[0] * sp);
+    o2 = d[2] * cc - sc * st * cp;
+  } else {
+    T sg = d[2] >= (T)0 ? (T)1 : (T)-1;
+    o0 = sc * cp * sg;
+    o1 = -sc * sp;
+    o2 = cc * sg;
+  }
+  d[0] = o0; d[1] = o1; d[2] = o2;
+}
+
+template <typename T>
+__device__ __forceinline__ void draw4(const PushParams<T> &P, unsigned long long id, uint32_t call, uint32_t spc, T u[4]) {
+  uint32_t x[4];
+  philox10(__ldg(P.step_ptr), call, spc, P.seed, (uint32_t)id, (uint32_t)(id >> 32), x);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) u[k] = unif24<T>(x[k]);
+}
+
+template <typename T>
+__device__ __forceinline__ void box_muller(T ua, T ub, T &na, T &nb) {
+  T rad = m_sqrt((T)-2 * m_log((T)1 - ua));
+  T s, c;
+  m_sincospi((T)2 * ub, &s, &c);
+  na = rad * c;
+  nb = rad * s;
+}
+
+template <typename T>
+__device__ __forceinline__ unsigned long long child_id(const PushParams<T> &P, unsigned long long id, uint32_t k) {
+  uint32_t x[4];
+  philox10(__ldg(P.step_ptr), 0xB1B1u, k, P.seed, (uint32_t)id, (uint32_t)(id >> 32), x);
+  return ((unsigned long long)x[0] | ((unsigned long long)x[1] << 32)) | (1ull << 63);
+}
+
+// Predictor of the D1 scheme with the cylindrical rotation, in cell units:
+// u = v + dt/2 a-bar; X = r + dt u_r, Y = dt u_theta; the radial displacement
+// |(X,Y)| - r is formed as (dx (2r + dx) + Y^2) / (|(X,Y)| + r) so FP32 keeps
+// the particle's offset inside its cell; (v_r, v_theta) and (a_r, a_theta)
+// turn by the swept angle.
+template <typename T>
+__device__ __forceinline__ void predict(const PushParams<T> &P, Part<T> &p) {
+  T ur = p.vr + P.hdt * p.ar, ut = p.vt + P.hdt * p.at, uz = p.vz + P.hdt * p.az;
+  T r = ((T)p.ci + p.fr) * P.dr;
+  T dx = P.dt * ur, Y = P.dt * ut;
+  T X = r + dx;
+  T rn = m_sqrt(X * X + Y * Y);
+  T den = rn + r;
+  T disp = den > (T)0 ? (dx * ((T)2 * r + dx) + Y * Y) / den : (T)0;
+  T ca = (T)1, sa = (T)0;
+  if (rn > (T)0) { ca = X / rn; sa = Y / rn; }
+  T vr = ca * p.vr + sa * p.vt, vt = -sa * p.vr + ca * p.vt;
+  T ar = ca * p.ar + sa * p.at, at = -sa * p.ar + ca * p.at;
+  p.vr = vr; p.vt = vt; p.ar = ar; p.at = at;
+  p.fr += disp * P.inv_dr;
+  p.fz += P.dt * uz * P.inv_dz;
+  renorm(p.ci, p.fr);
+  renorm(p.cj, p.fz);
+}
+
+// Outcome of one particle's step.
+struct Outcome {
+  int alive;      // 1 -> write to its new bin and deposit
+  int abs_kind;   // -1 none, 0 powered, 1 grounded, 2 surface
+  int abs_node;
+  int coll;       // -1 none, else process index
+  int birth;      // 1 -> electron + ion born at x_n (electrons only)
+};
+
+// Electron collision (Sec. 2, null-collision MCC; kinematics of Vahedi & Surendra).
+template <typename T>
+__device__ __forceinline__ int mcc_electron(const PushParams<T> &P, Part<T> &p, Part<T> &be, Part<T> &bi) {
+  T u[4];
+  draw4(P, p.id, 0u, 0u, u);
+  if (!(u[0] < P.pcoll[0])) return -1;
+  T v2 = p.vr * p.vr + p.vt * p.vt + p.vz * p.vz;
+  T speed = m_sqrt(v2);
+  if (!(speed > (T)0)) return -1;
+  T E = P.e_per_v2[0] * v2;
+  T ng_v = P.n_gas * speed;
+  T nu_el = ng_v * xs(P, 0, E);
+  T nu_ex = E < P.thr_ex ? (T)0 : ng_v * xs(P, 1, E);
+  T nu_iz = E < P.thr_iz ? (T)0 : ng_v * xs(P, 2, E);
+  T x = u[1] * P.numax[0];
+  T d[3] = {p.vr / speed, p.vt / speed, p.vz / speed};
+  if (x < nu_el) {
+    T cc = scatter_cos(E, u[2]);
+    T frac = (T)1 - P.two_me_over_M * ((T)1 - cc);
+    turn(d, cc, u[3]);
+    T sp = speed * m_sqrt(frac);
+    p.vr = sp * d[0]; p.vt = sp * d[1]; p.vz = sp * d[2];
+    return 0;
+  }
+  if (x < nu_el + nu_ex) {
+    T En = E - P.thr_ex;
+    turn(d, scatter_cos(En, u[2]), u[3]);
+    T sp = m_sqrt(En * P.v2_per_e[0]);
+    p.vr = sp * d[0]; p.vt = sp * d[1]; p.vz = sp * d[2];
+    return 1;
+  }
+  if (x < nu_el + nu_ex + nu_iz) {
+    T Eex = E - P.thr_iz;
+    T Eej = P.B_ej * m_tan(u[2] * m_atan(Eex / ((T)2 * P.B_ej)));
+    T Esc = Eex - Eej;
+    if (Esc < (T)0) Esc = (T)0;
+    T u1[4], u2[4];
+    draw4(P, p.id, 1u, 0u, u1);
+    draw4(P, p.id, 2u, 0u, u2);
+    T ds[3] = {d[0], d[1], d[2]}, de[3] = {d[0], d[1], d[2]};
+    turn(ds, scatter_cos(Esc, u1[0]), u1[1]);
+    turn(de, scatter_cos(Eej, u1[2]), u1[3]);
+    T ssc = m_sqrt(Esc * P.v2_per_e[0]), sej = m_sqrt(Eej * P.v2_per_e[0]);
+    p.vr = ssc * ds[0]; p.vt = ssc * ds[1]; p.vz = ssc * ds[2];
+    be = p;
+    be.vr = sej * de[0]; be.vt = sej * de[1]; be.vz = sej * de[2];
+    be.ar = be.at = be.az = (T)0;
+    be.id = child_id(P, p.id, 0u);
+    T n0, n1, n2, n3;
+    box_muller(u2[0], u2[1], n0, n1);
+    box_muller(u2[2], u2[3], n2, n3);
+    bi = be;
+    bi.vr = P.vth_gas * n0; bi.vt = P.vth_gas * n1; bi.vz = P.vth_gas * n2;
+    bi.id = child_id(P, p.id, 1u);
+    return 2;
+  }
+  return -1;
+}
+
+// Ion collision against a neutral drawn from the gas Maxwellian (Sec. 2):
+// isotropic scattering in the centre-of-mass frame, or charge exchange.
+template <typename T>
+__device__ __forceinline__ int mcc_ion(const PushParams<T> &P, Part<T> &p) {
+  T u[4];
+  draw4(P, p.id, 0u, 1u, u);
+  if (!(u[0] < P.pcoll[1])) return -1;
+  T u1[4];
+  draw4(P, p.id, 1u, 1u, u1);
+  T n0, n1, n2, n3;
+  box_muller(u1[0], u1[1], n0, n1);
+  box_muller(u1[2], u1[3], n2, n3);
+  T vn0 = P.vth_gas * n0, vn1 = P.vth_gas * n1, vn2 = P.vth_gas * n2;
+  T g0 = p.vr - vn0, g1 = p.vt - vn1, g2 = p.vz - vn2;
+  T gg = g0 * g0 + g1 * g1 + g2 * g2;
+  T gm = m_sqrt(gg);
+  T eps = P.e_per_v2[1] * gg;
+  T ng_g = P.n_gas * gm;
+  T nu_iso = ng_g * xs(P, 3, eps);
+  T nu_cx = ng_g * xs(P, 4, eps);
+  T x = u[1] * P.numax[1];
+  if (x < nu_iso) {
+    T ct = (T)1 - (T)2 * u[2];
+    T st = m_sqrt((T)1 - ct * ct > (T)0 ? (T)1 - ct * ct : (T)0);
+    T sp, cp;
+    m_sincospi((T)2 * u[3], &sp, &cp);
+    T wi = P.mi_frac, wn = (T)1 - P.mi_frac;  // m_i/(m_i+M), M/(m_i+M)
+    T c0 = wi * p.vr + wn * vn0, c1 = wi * p.vt + wn * vn1, c2 = wi * p.vz + wn * vn2;
+    p.vr = c0 + wn * gm * st * cp;
+    p.vt = c1 + wn * gm * st * sp;
+    p.vz = c2 + wn * gm * ct;
+    return 0;
+  }
+  if (x < nu_iso + nu_cx) {
+    p.vr = vn0; p.vt = vn1; p.vz = vn2;
+    return 1;
+  }
+  return -1;
+}
+
+// Gather, correction, D1 filter, axis, absorption, MCC, predictor, absorption.
+template <typename T>
+__device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T> &p, Part<T> &be, Part<T> &bi) {
+  Outcome o{0, -1, 0, -1, 0};
+  // gather E at x~_n with the deposit weights: linear in z, by annulus area in r
+  T ir = (T)p.ci;
+  T a = p.fr * ((T)2 * ir + p.fr) / ((T)2 * ir + (T)1);
+  T b = p.fz;
+  using E2 = typename V2<T>::type;
+  const E2 *E = reinterpret_cast<const E2 *>(P.E);
+  int n00 = p.cj * (P.nr + 1) + p.ci;
+  E2 e00 = E[n00], e10 = E[n00 + 1], e01 = E[n00 + P.nr + 1], e11 = E[n00 + P.nr + 2];
+  T w00 = ((T)1 - a) * ((T)1 - b), w10 = a * ((T)1 - b), w01 = ((T)1 - a) * b, w11 = a * b;
+  T Er = w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x;
+  T Ez = w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y;
+  T anr = P.qm[s] * Er, anz = P.qm[s] * Ez;
+  // correction x_n = x~_n + dt^2/2 a_n
+  p.fr += P.hdt2 * anr * P.inv_dr;
+  p.fz += P.hdt2 * anz * P.inv_dz;
+  // D1 time filter and velocity update
+  p.ar = (T)0.5 * (anr + p.ar);
+  p.at = (T)0.5 * p.at;
+  p.az = (T)0.5 * (anz + p.az);
+  p.vr += P.dt * p.ar; p.vt += P.dt * p.at; p.vz += P.dt * p.az;
+  // axis: a radial move through r = 0 continues on the far side
+  T rho = (T)p.ci + p.fr;
+  if (rho < (T)0) {
+    rho = -rho;
+    p.ci = 0;
+    p.fr = rho;
+    p.vr = -p.vr; p.vt = -p.vt; p.ar = -p.ar; p.at = -p.at;
+  }
+  renorm(p.ci, p.fr);
+  renorm(p.cj, p.fz);
+  if (!in_plasma(P, p.ci, p.cj)) {
+    o.abs_node = exit_node(P, p.ci, p.fr, p.cj, p.fz);
+    o.abs_kind = (int)__ldg(P.node_kind + o.abs_node);
+    o.abs_kind = o.abs_kind == 1 ? 0 : (o.abs_kind == 2 ? 1 : 2);
+    return o;
+  }
+  // MCC at x_n on v_{n-1/2}
+  if (s == 0) {
+    o.coll = mcc_electron(P, p, be, bi);
+    o.birth = o.coll == 2;
+  } else {
+    o.coll = mcc_ion(P, p);
+  }
+  predict(P, p);
+  if (!in_plasma(P, p.ci, p.cj)) {
+    o.abs_node = exit_node(P, p.ci, p.fr, p.cj, p.fz);
+    o.abs_kind = (int)__ldg(P.node_kind + o.abs_node);
+    o.abs_kind = o.abs_kind == 1 ? 0 : (o.abs_kind == 2 ? 1 : 2);
+    return o;
+  }
+  o.alive = 1;
+  return o;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_particle(const StoreView<T> &S, int slot, const Part<T> &p, int cell_rowmajor) {
+  S.fr[slot] = p.fr; S.fz[slot] = p.fz;
+  S.vr[slot] = p.vr; S.vt[slot] = p.vt; S.vz[slot] = p.vz;
+  S.ar[slot] = p.ar; S.at[slot] = p.at; S.az[slot] = p.az;
+  S.id[slot] = p.id;
+  S.cell[slot] = cell_rowmajor;
+}
+
+// Slot in the write store for a particle of bin `key`; -1 if dropped.
+template <typename T>
+__device__ __forceinline__ int overflow_slot(const PushParams<T> &P, const StoreView<T> &S) {
+  int k = atomicAdd(&S.meta->ovf_n, 1);
+  int slot = S.meta->ovf_base + k;
+  if (slot >= S.capacity) {
+    atomicAdd(P.counters + CNT_OVERFLOW, 1ull);
+    atomicOr(P.flags, 1u);
+    return -1;
+  }
+  return slot;
+}
+
+// Quantised deposit weights (sum exactly `one`): a = radial weight of node i+1,
+// b = axial weight of node j+1.
+template <typename T>
+__device__ __forceinline__ void qweights(T a, T b, T scale, unsigned long long one, unsigned long long W[4]) {
+  unsigned long long A = (unsigned long long)(a * scale + (T)0.5);
+  unsigned long long B = (unsigned long long)(b * scale + (T)0.5);
+  if (A > one) A = one;
+  if (B > one) B = one;
+  int sh = 63 - __clzll((long long)one);
+  unsigned long long W11;
+  if (sh <= 32) {
+    W11 = (A * B + (one >> 1)) >> sh;
+  } else {  // 128-bit product for the FP64 scale
+    unsigned long long lo = A * B, hi = __umul64hi(A, B);
+    unsigned long long add = lo + (one >> 1);
+    hi += add < lo;
+    W11 = (add >> sh) | (hi << (64 - sh));
+  }
+  W[3] = W11;
+  W[1] = A - W11;
+  W[2] = B - W11;
+  W[0] = one - A - B + W11;
+}
+
+template <typename T>
+__device__ __forceinline__ void node_weights_q(const PushParams<T> &P, const Part<T> &p, unsigned long long W[4]) {
+  T ir = (T)p.ci;
+  T a = p.fr * ((T)2 * ir + p.fr) / ((T)2 * ir + (T)1);
+  qweights(a, p.fz, P.dep_scale, P.dep_one, W);
+}
+
+// Deposit of one particle's 4 node weights straight to global memory.
+template <typename T>
+__device__ __forceinline__ void deposit_global(const PushParams<T> &P, int s, const Part<T> &p) {
+  unsigned long long W[4];
+  node_weights_q(P, p, W);
+  int n00 = p.cj * (P.nr + 1) + p.ci;
+  unsigned long long *d = P.dep[s];
+  atomicAdd(d + n00, W[0]);
+  atomicAdd(d + n00 + 1, W[1]);
+  atomicAdd(d + n00 + P.nr + 1, W[2]);
+  atomicAdd(d + n00 + P.nr + 2, W[3]);
+}
+
+struct TileCtx {
+  unsigned long long *tile;  // shared node tile, (TX+1+2H) x (TY+1+2H), or nullptr
+  int ci0, cj0, w, h, TX, TY;
+};
+
+// Warp-collective: write the alive lanes' particles into their new bins of the
+// species' write store and deposit them.  All 32 lanes must call it.
+template <typename T>
+__device__ __forceinline__ void emit(const PushParams<T> &P, int s, bool alive, const Part<T> &p, const TileCtx &tc) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const StoreView<T> &S = P.out[s];
+  int key = alive ? P.map.bin(p.ci, p.cj) : -1;
+  unsigned peers = __match_any_sync(FULL, key);
+  int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (key >= 0 && lane == leader) base = atomicAdd(S.fill + key, __popc(peers));
+  base = __shfl_sync(FULL, base, leader);
+  if (key >= 0) {
+    int pos = base + __popc(peers & ((1u << lane) - 1u));
+    int slot = pos < __ldg(S.cap + key) ? __ldg(S.start + key) + pos : overflow_slot(P, S);
+    if (slot >= 0) store_particle(S, slot, p, p.cj * P.nr + p.ci);
+  }
+  // deposit
+  unsigned long long W[4] = {0, 0, 0, 0};
+  if (alive) node_weights_q(P, p, W);
+  int li = p.ci - tc.ci0 + kHalo, lj = p.cj - tc.cj0 + kHalo;
+  bool in_tile = tc.tile != nullptr && li >= 0 && lj >= 0 && li < tc.TX + 2 * kHalo && lj < tc.TY + 2 * kHalo;
+  if (sizeof(T) == 4) {
+    // 32-bit fixed point: sum lanes of the same new cell, leader adds once
+    unsigned leaders = __ballot_sync(FULL, key >= 0 && lane == leader);
+    while (leaders) {
+      int l = __ffs(leaders) - 1;
+      leaders &= leaders - 1u;
+      unsigned m = __shfl_sync(FULL, peers, l);
+      bool in = (m >> lane) & 1u;
+      unsigned s0 = __reduce_add_sync(FULL, in ? (unsigned)W[0] : 0u);
+      unsigned s1 = __reduce_add_sync(FULL, in ? (unsigned)W[1] : 0u);
+      unsigned s2 = __reduce_add_sync(FULL, in ? (unsigned)W[2] : 0u);
+      unsigned s3 = __reduce_add_sync(FULL, in ? (unsigned)W[3] : 0u);
+      if (lane == l) {
+        if (in_tile) {
+          unsigned long long *t = tc.tile + lj * tc.w + li;
+          if (s0) atomicAdd(t, (unsigned long long)s0);
+          if (s1) atomicAdd(t + 1, (unsigned long long)s1);
+          if (s2) atomicAdd(t + tc.w, (unsigned long long)s2);
+          if (s3) atomicAdd(t + tc.w + 1, (unsigned long long)s3);
+        } else {
+          int n00 = p.cj * (P.nr + 1) + p.ci;
+          unsigned long long *d = P.dep[s];
+          if (s0) atomicAdd(d + n00, (unsigned long long)s0);
+          if (s1) atomicAdd(d + n00 + 1, (unsigned long long)s1);
+          if (s2) atomicAdd(d + n00 + P.nr + 1, (unsigned long long)s2);
+          if (s3) atomicAdd(d + n00 + P.nr + 2, (unsigned long long)s3);
+        }
+      }
+    }
+  } else if (alive) {
+    if (in_tile) {
+      unsigned long long *t = tc.tile + lj * tc.w + li;
+      atomicAdd(t, W[0]);
+      atomicAdd(t + 1, W[1]);
+      atomicAdd(t + tc.w, W[2]);
+      atomicAdd(t + tc.w + 1, W[3]);
+    } else {
+      int n00 = p.cj * (P.nr + 1) + p.ci;
+      unsigned long long *d = P.dep[s];
+      atomicAdd(d + n00, W[0]);
+      atomicAdd(d + n00 + 1, W[1]);
+      atomicAdd(d + n00 + P.nr + 1, W[2]);
+      atomicAdd(d + n00 + P.nr + 2, W[3]);
+    }
+  }
+}
+
+// A newborn ion from an electron CTA: predictor, absorption, write, deposit
+// (per lane: births are rare).
+template <typename T>
+__device__ __forceinline__ void emit_ion_birth(const PushParams<T> &P, Part<T> &bi) {
+  predict(P, bi);
+  if (!in_plasma(P, bi.ci, bi.cj)) {
+    int node = exit_node(P, bi.ci, bi.fr, bi.cj, bi.fz);
+    int k = (int)__ldg(P.node_kind + node);
+    k = k == 1 ? 0 : (k == 2 ? 1 : 2);
+    atomicAdd(P.counters + CNT_ABS + 3 + k, 1ull);
+    if (k == 2) atomicAdd(P.surf[1] + node, 1ull);
+    return;
+  }
+  const StoreView<T> &S = P.out[1];
+  int key = P.map.bin(bi.ci, bi.cj);
+  int pos = atomicAdd(S.fill + key, 1);
+  int slot = pos < __ldg(S.cap + key) ? __ldg(S.start + key) + pos : overflow_slot(P, S);
+  if (slot >= 0) store_particle(S, slot, bi, bi.cj * P.nr + bi.ci);
+  deposit_global(P, 1, bi);
+}
+
+// Warp-aggregated counter increment.
+__device__ __forceinline__ void count_warp(unsigned long long *c, bool pred) {
+  unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (m && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(c, (unsigned long long)__popc(m));
+}
+
+template <typename T>
+__device__ __forceinline__ void tally(const PushParams<T> &P, int s, const Outcome &o, bool active) {
+  count_warp(P.counters + CNT_ABS + 3 * s + 0, active && o.abs_kind == 0);
+  count_warp(P.counters + CNT_ABS + 3 * s + 1, active && o.abs_kind == 1);
+  count_warp(P.counters + CNT_ABS + 3 * s + 2, active && o.abs_kind == 2);
+  if (active && o.abs_kind == 2) atomicAdd(P.surf[s] + o.abs_node, 1ull);
+  count_warp(P.counters + CNT_COLL + 3 * s + 0, active && o.coll == 0);
+  count_warp(P.counters + CNT_COLL + 3 * s + 1, active && o.coll == 1);
+  count_warp(P.counters + CNT_COLL + 3 * s + 2, active && o.coll == 2);
+}
+
+template <typename T>
+__device__ __forceinline__ void load_particle(const StoreView<T> &S, int slot, Part<T> &p) {
+  p.fr = S.fr[slot]; p.fz = S.fz[slot];
+  p.vr = S.vr[slot]; p.vt = S.vt[slot]; p.vz = S.vz[slot];
+  p.ar = S.ar[slot]; p.at = S.at[slot]; p.az = S.az[slot];
+  p.id = S.id[slot];
+}
+
+// Process one particle (already loaded) of species s: step, tallies, emit,
+// births.  Warp-collective.
+template <typename T>
+__device__ __forceinline__ void process(const PushParams<T> &P, int s, bool active, Part<T> &p, const TileCtx &tc) {
+  Part<T> be = p, bi = p;
+  Outcome o{0, -1, 0, -1, 0};
+  if (active) o = advance(P, s, p, be, bi);
+  tally(P, s, o, active);
+  emit(P, s, active && o.alive, p, tc);
+  bool birth = active && o.birth;
+  if (__any_sync(0xffffffffu, birth)) {
+    count_warp(P.counters + CNT_BORN + 0, birth);
+    count_warp(P.counters + CNT_BORN + 1, birth);
+    bool e_alive = false;
+    if (birth) {
+      predict(P, be);
+      e_alive = in_plasma(P, be.ci, be.cj);
+      if (!e_alive) {
+        int node = exit_node(P, be.ci, be.fr, be.cj, be.fz);
+        int k = (int)__ldg(P.node_kind + node);
+        k = k == 1 ? 0 : (k == 2 ? 1 : 2);
+        atomicAdd(P.counters + CNT_ABS + k, 1ull);
+        if (k == 2) atomicAdd(P.surf[0] + node, 1ull);
+      }
+    }
+    emit(P, 0, e_alive, be, tc);
+    if (birth) emit_ion_birth(P, bi);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_particles(const PushParams<T> P) {
+  const int s = blockIdx.y;
+  const StoreView<T> &A = P.in[s];
+  const int TX = P.map.TX, TY = P.map.TY, per = TX * TY;
+  extern __shared__ unsigned long long smem[];
+  __shared__ int s_pre[kMaxTileCells + 1];
+  __shared__ int s_off[kMaxTileCells];
+  const int ntiles = P.map.ntiles();
+  if ((int)blockIdx.x < ntiles) {
+    const int tile = blockIdx.x;
+    const int b0 = tile * per;
+    const int tyi = tile / P.map.ntx, txi = tile - tyi * P.map.ntx;
+    TileCtx tc;
+    tc.tile = smem;
+    tc.ci0 = txi * TX;
+    tc.cj0 = tyi * TY;
+    tc.TX = TX;
+    tc.TY = TY;
+    tc.w = TX + 1 + 2 * kHalo;
+    tc.h = TY + 1 + 2 * kHalo;
+    for (int k = threadIdx.x; k < tc.w * tc.h; k += blockDim.x) smem[k] = 0ull;
+    if (threadIdx.x < 32) {
+      // prefix of the tile's in-bin counts (per <= kMaxTileCells, a multiple of 32 handled in chunks)
+      int carry = 0;
+      for (int c0 = 0; c0 < per; c0 += 32) {
+        int b = c0 + threadIdx.x;
+        int n = 0, off = 0;
+        if (b < per) {
+          int f = A.fill[b0 + b], cp = A.cap[b0 + b];
+          n = f < cp ? f : cp;
+          off = A.start[b0 + b];
+        }
+        int incl = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          int y = __shfl_up_sync(0xffffffffu, incl, d);
+          if ((int)threadIdx.x >= d) incl += y;
+        }
+        if (b < per) { s_pre[b] = carry + incl - n; s_off[b] = off; }
+        carry += __shfl_sync(0xffffffffu, incl, 31);
+      }
+      if (threadIdx.x == 0) s_pre[per] = carry;
+    }
+    __syncthreads();
+    const int ntot = s_pre[per];
+    for (int base = 0; base < ntot; base += blockDim.x) {
+      int k = base + threadIdx.x;
+      bool active = k < ntot;
+      Part<T> p;
+      p.ci = 0; p.cj = 0;
+      if (active) {
+        int lo = 0, hi = per;  // s_pre[lo] <= k < s_pre[hi]
+        while (hi - lo > 1) {
+          int mid = (lo + hi) >> 1;
+          if (s_pre[mid] <= k) lo = mid; else hi = mid;
+        }
+        int slot = s_off[lo] + (k - s_pre[lo]);
+        load_particle(A, slot, p);
+        p.ci = tc.ci0 + (lo % TX);
+        p.cj = tc.cj0 + (lo / TX);
+      }
+      process(P, s, active, p, tc);
+    }
+    __syncthreads();
+    unsigned long long *d = P.dep[s];
+    for (int k = threadIdx.x; k < tc.w * tc.h; k += blockDim.x) {
+      unsigned long long v = smem[k];
+      if (v) {
+        int ni = tc.ci0 - kHalo + k % tc.w, nj = tc.cj0 - kHalo + k / tc.w;
+        atomicAdd(d + nj * (P.nr + 1) + ni, v);
+      }
+    }
+  } else {
+    // overflow region of the read store: unsorted particles with explicit cells
+    TileCtx tc{nullptr, 0, 0, 0, 0, TX, TY};
+    const int novf = min(A.meta->ovf_n, A.capacity - A.meta->ovf_base);
+    const int first = A.meta->ovf_base;
+    const int stride = (gridDim.x - ntiles) * blockDim.x;
+    // uniform trip count across the warp: loop bound rounded up to a warp multiple
+    for (int base = (blockIdx.x - ntiles) * blockDim.x; base < novf; base += stride) {
+      int k = base + threadIdx.x;
+      bool active = k < novf;
+      Part<T> p;
+      p.ci = 0; p.cj = 0;
+      if (active) {
+        int slot = first + k;
+        load_particle(A, slot, p);
+        int c = A.cell[slot];
+        p.cj = c / P.nr;
+        p.ci = c - p.cj * P.nr;
+      }
+      process(P, s, active, p, tc);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Bin layout of the next write store: room = fill + slack*fill + 8 for bins of
+// plasma cells, 0 elsewhere; exclusive scan; zero fill counters.  One CTA.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_layout(const int *__restrict__ fill_in, const int8_t *__restrict__ bin_plasma,
+                                                int nbins, float slack, int capacity, int *start, int *cap, int *fill_out,
+                                                BinMeta *meta_out, BinMeta *meta_in) {
+  __shared__ long long s_part[1024];
+  __shared__ long long s_tot[2];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int chunk = (nbins + nt - 1) / nt;
+  const int lo = t * chunk, hi = min(nbins, lo + chunk);
+  long long sum_fill = 0, sum_cap = 0;
+  for (int b = lo; b < hi; ++b) {
+    int f = fill_in[b];
+    sum_fill += f;
+    if (bin_plasma[b]) sum_cap += (long long)f + (long long)(slack * (float)f) + 8;
+  }
+  // choose the slack that fits: full slack, else none (overflow takes the rest)
+  s_part[t] = sum_cap;
+  __syncthreads();
+  for (int d = 512; d > 0; d >>= 1) {
+    if (t < d) s_part[t] += s_part[t + d];
+    __syncthreads();
+  }
+  if (t == 0) s_tot[0] = s_part[0];
+  __syncthreads();
+  long long total_cap = s_tot[0];
+  bool use_slack = total_cap <= (long long)(0.9 * (double)capacity);
+  __syncthreads();
+  long long mine = 0;
+  for (int b = lo; b < hi; ++b) {
+    int f = fill_in[b];
+    int c = bin_plasma[b] ? (use_slack ? f + (int)(slack * (float)f) + 8 : f) : 0;
+    mine += c;
+  }
+  s_part[t] = mine;
+  __syncthreads();
+  // inclusive scan of s_part (Hillis-Steele)
+  for (int d = 1; d < nt; d <<= 1) {
+    long long y = t >= d ? s_part[t - d] : 0;
+    __syncthreads();
+    s_part[t] += y;
+    __syncthreads();
+  }
+  long long run = s_part[t] - mine;
+  for (int b = lo; b < hi; ++b) {
+    int f = fill_in[b];
+    long long c = bin_plasma[b] ? (use_slack ? f + (int)(slack * (float)f) + 8 : f) : 0;
+    if (run + c > capacity) c = run < capacity ? capacity - run : 0;  // never hand out room past the buffer
+    start[b] = (int)(run < capacity ? run : capacity);
+    cap[b] = (int)c;
+    fill_out[b] = 0;
+    run += c;
+  }
+  // totals
+  s_part[t] = sum_fill;
+  __syncthreads();
+  for (int d = 512; d > 0; d >>= 1) {
+    if (t < d) s_part[t] += s_part[t + d];
+    __syncthreads();
+  }
+  if (t == nt - 1) {
+    // run == total room after the last thread's chunk
+    long long room = run;
+    meta_out->ovf_base = (int)(room < capacity ? room : capacity);
+    meta_out->ovf_n = 0;
+    meta_out->total = 0;
+  }
+  if (t == 0) meta_in->total = s_part[0];
+}
+
+// Deposit of the read store's particles at their current x~ (start-up).
+template <typename T>
+__global__ void k_deposit_only(const PushParams<T> P) {
+  const int s = blockIdx.y;
+  const StoreView<T> &A = P.in[s];
+  const int nb = P.map.nbins();
+  // one warp per bin, then the overflow region
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int b = warp; b < nb; b += nwarps) {
+    int f = A.fill[b], c = A.cap[b];
+    int n = f < c ? f : c;
+    int ci, cj;
+    P.map.cell(b, ci, cj);
+    for (int k = lane; k < n; k += 32) {
+      Part<T> p;
+      load_particle(A, A.start[b] + k, p);
+      p.ci = ci; p.cj = cj;
+      deposit_global(P, s, p);
+    }
+  }
+  int novf = min(A.meta->ovf_n, A.capacity - A.meta->ovf_base);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < novf; k += gridDim.x * blockDim.x) {
+    int slot = A.meta->ovf_base + k;
+    Part<T> p;
+    load_particle(A, slot, p);
+    int c = A.cell[slot];
+    p.cj = c / P.nr;
+    p.ci = c - p.cj * P.nr;
+    deposit_global(P, s, p);
+  }
+}
+
+__global__ void k_philox(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t x[4];
+    philox10(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], key[2 * i], key[2 * i + 1], x);
+    out[4 * i] = x[0]; out[4 * i + 1] = x[1]; out[4 * i + 2] = x[2]; out[4 * i + 3] = x[3];
+  }
+}
+
+// ---- host launchers ---------------------------------------------------------
+template <typename T>
+cudaError_t launch_particles(const PushParams<T> &P, cudaStream_t st) {
+  int ntiles = P.map.ntiles();
+  int w = P.map.TX + 1 + 2 * kHalo, h = P.map.TY + 1 + 2 * kHalo;
+  size_t sm = sizeof(unsigned long long) * (size_t)w * h;
+  dim3 grid(ntiles + kOvfCtas, 2);
+  k_particles<T><<<grid, kThreads, sm, st>>>(P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_deposit_only(const PushParams<T> &P, cudaStream_t st) {
+  dim3 grid(1024, 2);
+  k_deposit_only<T><<<grid, 256, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layout(const int *fill_in, const int8_t *bin_plasma, int nbins, float slack, int capacity, int *start,
+                          int *cap, int *fill_out, BinMeta *meta_out, BinMeta *meta_in, cudaStream_t st) {
+  k_layout<<<1, 1024, 0, st>>>(fill_in, bin_plasma, nbins, slack, capacity, start, cap, fill_out, meta_out, meta_in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st) {
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  k_philox<<<blocks, 256, 0, st>>>(n, ctr, key, out);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_particles<float>(const PushParams<float> &, cudaStream_t);
+template cudaError_t launch_particles<double>(const PushParams<double> &, cudaStream_t);
+template cudaError_t launch_deposit_only<float>(const PushParams<float> &, cudaStream_t);
+template cudaError_t launch_deposit_only<double>(const PushParams<double> &, cudaStream_t);
+
+}  // namespace pic

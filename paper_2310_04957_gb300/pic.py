@@ -1,0 +1,270 @@
+"""Thin Python binding of libpic_gb300.so (include/pic.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  PyTorch supplies the CUDA stream.  If the library is missing the
+import of this module fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic_gb300.so")
+
+PIC_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT", -6: "EOVERFLOW", -7: "ENAN"}
+PIC_FP32, PIC_FP64 = 0, 1
+PIC_SOLVER_PLAIN, PIC_SOLVER_MIXED = 0, 1
+DIAG = {"phi": 0, "Er": 1, "Ez": 2, "chi": 3, "dep_e": 4, "dep_i": 5, "sigma": 6, "vnode": 7, "rho": 8,
+        "ne_avg": 9, "ni_avg": 10}
+DIAG_SCALARS = 100
+NSCALARS = 47
+SCALARS = ["step", "t", "U_E", "Q_E", "C_eq", "I_conv", "I_ccp", "y0", "y1", "y2", "y3", "y4", "y5", "pcg_iters",
+           "pcg_relres", "numax_e", "numax_i", "pcoll_e", "pcoll_i", "absq_e_pow", "absq_e_gnd", "absq_e_surf",
+           "absq_i_pow", "absq_i_gnd", "absq_i_surf", "absn_e_pow", "absn_e_gnd", "absn_e_surf", "absn_i_pow",
+           "absn_i_gnd", "absn_i_surf", "coll_e_el", "coll_e_ex", "coll_e_iz", "coll_i_iso", "coll_i_cx",
+           "coll_i_none", "born_e", "born_i", "ioncur_pow", "ioncur_gnd", "ioncur_surf", "i1_re", "i1_im",
+           "windows", "ceq_gauss", "pcg_status"]
+EXPORTS = ["pic_init", "pic_set_particles", "pic_count", "pic_get_particles", "pic_start", "pic_step",
+           "pic_particle_phase", "pic_field_solve", "pic_ceq", "pic_diag", "pic_set_field", "pic_set_step",
+           "pic_set_ceq", "pic_set_circuit_state", "pic_set_conv_current", "pic_circuit_run", "pic_status",
+           "pic_philox", "pic_enable_timing", "pic_step_timing", "pic_strerror", "pic_destroy"]
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__(f"{what}: {ERRORS.get(code, code)} ({code})")
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("nr", ctypes.c_int32), ("nz", ctypes.c_int32), ("dr", ctypes.c_double), ("dz", ctypes.c_double),
+        ("node_kind", ctypes.c_void_p), ("cell_kind", ctypes.c_void_p), ("cell_eps", ctypes.c_void_p),
+        ("dt", ctypes.c_double), ("n_gas", ctypes.c_double), ("T_gas", ctypes.c_double), ("m_gas", ctypes.c_double),
+        ("q", ctypes.c_double * 2), ("m", ctypes.c_double * 2), ("w", ctypes.c_double * 2),
+        ("n_xs", ctypes.c_int32), ("xs_energy", ctypes.c_void_p), ("xs_sigma", ctypes.c_void_p),
+        ("thr_ex", ctypes.c_double), ("thr_iz", ctypes.c_double), ("B_ej", ctypes.c_double),
+        ("circuit", ctypes.c_int32), ("circ", ctypes.c_double * 8),
+        ("V_src", ctypes.c_double), ("f_src", ctypes.c_double), ("phase_src", ctypes.c_double),
+        ("n_sub", ctypes.c_int32), ("steps_per_rf", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
+        ("pcg_maxit", ctypes.c_int32), ("ceq_refresh", ctypes.c_int32), ("seed", ctypes.c_uint32),
+        ("capacity", ctypes.c_int64 * 2), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
+        ("tile_r", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("bin_slack", ctypes.c_double),
+    ]
+
+
+class Particles(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_void_p) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az", "id", "cell")]
+
+
+_lib = None
+
+
+def lib():
+    """Load libpic_gb300.so; raise if it is missing (build it with build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libpic_gb300.so not found at {LIB_PATH}: run paper_2310_04957_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.pic_init.argtypes = [ctypes.POINTER(Config), P, ctypes.POINTER(P)]
+        L.pic_set_particles.argtypes = [P, I, ctypes.c_int64, ctypes.POINTER(Particles)]
+        L.pic_count.argtypes = [P, I, ctypes.POINTER(ctypes.c_int64)]
+        L.pic_get_particles.argtypes = [P, I, ctypes.POINTER(Particles), ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+        for n in ("pic_start", "pic_particle_phase"):
+            getattr(L, n).argtypes = [P]
+        L.pic_step.argtypes = [P, I]
+        L.pic_field_solve.argtypes = [P, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(D)]
+        L.pic_ceq.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]
+        L.pic_diag.argtypes = [P, I, P, ctypes.c_size_t]
+        L.pic_set_field.argtypes = [P, I, P, ctypes.c_size_t]
+        L.pic_set_step.argtypes = [P, ctypes.c_uint32]
+        L.pic_set_ceq.argtypes = [P, D]
+        L.pic_set_circuit_state.argtypes = [P, P]
+        L.pic_set_conv_current.argtypes = [P, D]
+        L.pic_circuit_run.argtypes = [P, I, P]
+        L.pic_status.argtypes = [P, ctypes.POINTER(ctypes.c_uint32)]
+        L.pic_philox.argtypes = [P, ctypes.c_int64, P, P, P]
+        L.pic_enable_timing.argtypes = [P, I]
+        L.pic_step_timing.argtypes = [P, P]
+        L.pic_strerror.argtypes = [I]
+        L.pic_strerror.restype = ctypes.c_char_p
+        L.pic_destroy.argtypes = [P]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(code, what):
+    if code != PIC_OK:
+        raise PicError(code, what)
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(stream)
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Discharge:
+    """One discharge on the current CUDA device (wraps a pic_handle)."""
+
+    def __init__(self, wl, precision=PIC_FP32, solver=PIC_SOLVER_PLAIN, stream=None, tile=(0, 0), bin_slack=0.0,
+                 capacity=None, load=True):
+        L = lib()
+        self.wl = wl
+        self.nr, self.nz = wl.nr, wl.nz
+        keep = []
+
+        def arr(a, dt):
+            b = np.ascontiguousarray(a, dtype=dt)
+            keep.append(b)
+            return _p(b)
+
+        c = Config()
+        c.nr, c.nz, c.dr, c.dz = wl.nr, wl.nz, wl.dr, wl.dz
+        c.node_kind = arr(wl.node_kind, np.int8)
+        c.cell_kind = arr(wl.cell_kind, np.int8)
+        c.cell_eps = arr(wl.cell_eps, np.float64)
+        c.dt, c.n_gas, c.T_gas, c.m_gas = wl.dt, wl.n_gas, wl.T_gas, wl.m_gas
+        c.q[:], c.m[:], c.w[:] = list(wl.q), list(wl.m), list(wl.w)
+        c.n_xs = len(wl.xs_energy)
+        c.xs_energy = arr(wl.xs_energy, np.float64)
+        c.xs_sigma = arr(wl.xs_sigma, np.float64)
+        c.thr_ex, c.thr_iz, c.B_ej = wl.thr_ex, wl.thr_iz, wl.B_ej
+        c.circuit = wl.circuit
+        c.circ[:] = list(wl.circ)
+        c.V_src, c.f_src, c.phase_src = wl.V_src, wl.f_src, wl.phase_src
+        c.n_sub, c.steps_per_rf = wl.n_sub, wl.steps_per_rf
+        c.pcg_tol, c.pcg_maxit, c.ceq_refresh, c.seed = wl.pcg_tol, wl.pcg_maxit, wl.ceq_refresh, wl.seed
+        cap = capacity if capacity is not None else wl.capacity
+        c.capacity[:] = [int(cap[0]), int(cap[1])]
+        c.precision, c.solver = precision, solver
+        c.tile_r, c.tile_z = tile
+        c.bin_slack = bin_slack
+        h = ctypes.c_void_p()
+        _check(L.pic_init(ctypes.byref(c), _stream(stream), ctypes.byref(h)), "pic_init")
+        self.h = h
+        self.capacity = (int(cap[0]), int(cap[1]))
+        if load:
+            for s in (0, 1):
+                self.set_particles(s, wl.particles[s])
+
+    def close(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def n_nodes(self):
+        return (self.nr + 1) * (self.nz + 1)
+
+    # -- particles
+    def set_particles(self, s, P):
+        cols = [np.ascontiguousarray(getattr(P, k), np.float64) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az")]
+        ids = np.ascontiguousarray(P.id, np.uint64)
+        v = Particles(*[_p(x) for x in cols], _p(ids), None)
+        _check(lib().pic_set_particles(self.h, s, P.n, ctypes.byref(v)), "pic_set_particles")
+
+    def count(self, s):
+        n = ctypes.c_int64()
+        _check(lib().pic_count(self.h, s, ctypes.byref(n)), "pic_count")
+        return n.value
+
+    def get_particles(self, s):
+        n = self.count(s)
+        out = {k: np.zeros(n) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az")}
+        out["id"] = np.zeros(n, np.uint64)
+        out["cell"] = np.zeros(n, np.int32)
+        v = Particles(*[_p(out[k]) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az", "id", "cell")])
+        got = ctypes.c_int64()
+        _check(lib().pic_get_particles(self.h, s, ctypes.byref(v), n, ctypes.byref(got)), "pic_get_particles")
+        assert got.value == n
+        return out
+
+    # -- stepping
+    def start(self):
+        _check(lib().pic_start(self.h), "pic_start")
+
+    def step(self, n=1):
+        _check(lib().pic_step(self.h, n), "pic_step")
+
+    def particle_phase(self):
+        _check(lib().pic_particle_phase(self.h), "pic_particle_phase")
+
+    def field_solve(self, mode=PIC_SOLVER_PLAIN):
+        it = ctypes.c_int()
+        rr = ctypes.c_double()
+        st = lib().pic_field_solve(self.h, mode, ctypes.byref(it), ctypes.byref(rr))
+        return st, it.value, rr.value
+
+    def ceq(self, with_chi=False):
+        c, g = ctypes.c_double(), ctypes.c_double()
+        _check(lib().pic_ceq(self.h, int(with_chi), ctypes.byref(c), ctypes.byref(g)), "pic_ceq")
+        return c.value, g.value
+
+    # -- fields and scalars
+    def field(self, name):
+        o = np.zeros(self.n_nodes)
+        _check(lib().pic_diag(self.h, DIAG[name], _p(o), o.nbytes), f"pic_diag({name})")
+        return o.reshape(self.nz + 1, self.nr + 1)
+
+    def set_field(self, name, values):
+        v = np.ascontiguousarray(values, np.float64).ravel()
+        _check(lib().pic_set_field(self.h, DIAG[name], _p(v), v.size), f"pic_set_field({name})")
+
+    def scalars(self):
+        o = np.zeros(NSCALARS)
+        _check(lib().pic_diag(self.h, DIAG_SCALARS, _p(o), o.nbytes), "pic_diag(scalars)")
+        return dict(zip(SCALARS, o.tolist()))
+
+    def set_step(self, n):
+        _check(lib().pic_set_step(self.h, n), "pic_set_step")
+
+    def set_ceq(self, c):
+        _check(lib().pic_set_ceq(self.h, c), "pic_set_ceq")
+
+    def set_circuit_state(self, y):
+        y = np.zeros(6) if y is None else np.ascontiguousarray(y, np.float64)
+        _check(lib().pic_set_circuit_state(self.h, _p(y)), "pic_set_circuit_state")
+
+    def set_conv_current(self, i):
+        _check(lib().pic_set_conv_current(self.h, i), "pic_set_conv_current")
+
+    def circuit_run(self, n):
+        U = np.zeros(n)
+        _check(lib().pic_circuit_run(self.h, n, _p(U)), "pic_circuit_run")
+        return U
+
+    def status(self):
+        f = ctypes.c_uint32()
+        _check(lib().pic_status(self.h, ctypes.byref(f)), "pic_status")
+        return f.value
+
+    def philox(self, ctr, key):
+        ctr = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+        key = np.ascontiguousarray(key, np.uint32).reshape(-1, 2)
+        out = np.zeros_like(ctr)
+        _check(lib().pic_philox(self.h, ctr.shape[0], _p(ctr), _p(key), _p(out)), "pic_philox")
+        return out
+
+    def enable_timing(self, on=True):
+        _check(lib().pic_enable_timing(self.h, int(on)), "pic_enable_timing")
+
+    def step_timing(self):
+        o = np.zeros(7)
+        _check(lib().pic_step_timing(self.h, _p(o)), "pic_step_timing")
+        return o

@@ -1,0 +1,41 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every
+function that include/pic.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "pic.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pic_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("pic_init", "pic_step", "pic_field_solve", "pic_diag", "pic_destroy", "pic_status"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2310_04957_gb300 import build
+
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    from paper_2310_04957_gb300 import pic
+
+    assert sorted(pic.EXPORTS) == declared_functions()
+
+
+def test_strerror_without_gpu():
+    from paper_2310_04957_gb300 import build, pic
+
+    build.build()
+    assert pic.lib().pic_strerror(-4) == b"field solve did not converge within its iteration cap"
+    assert pic.lib().pic_strerror(0) == b"ok"
