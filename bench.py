@@ -1,0 +1,332 @@
+"""Benchmark of the implicit r-z PIC/MCC step on GB300.
+
+One step = the whole hot path: bin layout, fused particle kernel (gather, D1
+push, null-collision MCC, re-bin, deposit), circuit, assembly, field solve,
+E field, diagnostics.  Workload (default): the 256x128 GEC-like cell with
+4 M electrons + 4 M Ar+ (10 mTorr, 150 V through the L-network), synthetic
+seeded inputs.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload c2|c3|c1] [--solver plain|mixed] [--precision fp32|fp64]
+
+N > 1 (launched under torch.distributed.run): each rank runs an independent
+replica of the discharge (different seed); value = all ranks' particle-steps
+over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s (push+MCC+deposit); field-solve ms to 1e-10 residual, vs plain"
+BYTES_PER_PARTICLE_STEP = {"fp32": 80, "fp64": 144}  # state read once + written once
+KERNELS_PER_STEP = 9  # layout x2, particles, circuit, assemble x2, pcg, efield, diag
+KERNELS_PER_WINDOW = 5  # diag window, C_eq refresh (edges, dirichlet, pcg, energy)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--solver", default="plain", choices=["plain", "mixed"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic():
+    """DRAM bytes per particle-kernel launch from the committed ncu summary, scaled to
+    the bench's particle count, if the summary was taken on the current kernel source;
+    else None."""
+    p = os.path.join(ROOT, "profiles", "k_particles_gec256.md")
+    src = os.path.join(ROOT, "paper_2310_04957_gb300", "csrc", "push.cu")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        line = line.strip()
+        if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "particles_in_launch", "source_sha256"):
+            k, v = line.split(":", 1)
+            kv[k] = v.strip()
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    if kv.get("source_sha256") != sha:
+        return None
+    return {"bytes": float(kv["traffic_bytes_per_launch"]), "particles": float(kv["particles_in_launch"])}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(name, rank=0):
+    from paper_2310_04957_gb300 import workloads as W
+
+    wl = W.PRESETS[name]()
+    if rank:
+        import dataclasses
+
+        wl = dataclasses.replace(wl, seed=(wl.seed + 1000 * rank) & 0xFFFFFFFF)
+    return wl
+
+
+def make_workload_name(name):
+    return {"c1": "cylinder-32x32-100k", "c2": "gec-256x128-8M", "c3": "gec-512x256-64M"}[name]
+
+
+def cpu_baseline(wlname, seconds_target=12.0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample of the workload:
+    the same grid, gas, circuit and field solve with 1/10 of the particles."""
+    import dataclasses
+
+    from oracle import orc
+    from paper_2310_04957_gb300 import workloads as W
+
+    frac = 10 if wlname != "c1" else 1
+    full = W.PRESETS[wlname]
+    n_full = {"c1": 50_000, "c2": 4_000_000, "c3": 32_000_000}[wlname]
+    wl = full(n_per_species=n_full // frac)
+    o = orc.Oracle(wl)
+    o.init_fields()
+    o.step(1)
+    t0 = time.perf_counter()
+    steps = 0
+    ps = 0
+    while True:
+        n = o.count(0) + o.count(1)
+        o.step(1)
+        steps += 1
+        ps += n
+        if time.perf_counter() - t0 > seconds_target or steps >= 200:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": ps / dt, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"{wl.name}: same grid/gas/circuit/field solve, {n_full // frac} particles per species "
+                      f"(1/{frac} of the workload), {steps} full steps, FP64, single thread"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    base = cpu_baseline(args.workload, seconds_target=max(5.0, 2.0 * args.steps / 10))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "particle-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": make_workload_name(args.workload)}, "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2310_04957_gb300 import build
+
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2310_04957_gb300 import pic
+
+    prec = pic.PIC_FP32 if args.precision == "fp32" else pic.PIC_FP64
+    solver = pic.PIC_SOLVER_PLAIN if args.solver == "plain" else pic.PIC_SOLVER_MIXED
+    wl = make_workload(args.workload, rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        d = pic.Discharge(wl, precision=prec, solver=solver, stream=stream.cuda_stream)
+        d.start()
+        d.step(args.warmup)
+        torch.cuda.synchronize()
+        n0 = d.count(0) + d.count(1)
+        d.enable_timing(True)
+
+        def barrier():
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            d.step(args.steps)
+            e1.record(stream)
+            barrier()
+        ms_total = e0.elapsed_time(e1)
+        phases = d.step_timing()  # layout, particles, circuit, assembly, solve, efield, diag (ms, summed)
+        d.enable_timing(False)
+        n1 = d.count(0) + d.count(1)
+        flags = d.status()
+    n_avg = 0.5 * (n0 + n1)
+    particle_steps = n_avg * args.steps
+    # slowest rank's time; all ranks' work
+    t_max = ms_total
+    tot_ps = particle_steps
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        w = torch.tensor([particle_steps], device="cuda", dtype=torch.float64)
+        dist.all_reduce(w)
+        tot_ps = float(w.item())
+    value = tot_ps / (t_max * 1e-3)
+    k_ms = phases[1] / args.steps
+    bpp = BYTES_PER_PARTICLE_STEP[args.precision]
+    achieved = bpp * n_avg / (k_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = kernel_traffic()
+    windows = (args.warmup + args.steps) // wl.steps_per_rf - args.warmup // wl.steps_per_rf
+
+    # end to end through the public API with host buffers: upload the initial state from
+    # host arrays, then every step pic_step + a device->host read of the step's scalars
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+
+        with torch.cuda.stream(stream):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d2 = pic.Discharge(wl, precision=prec, solver=solver, stream=stream.cuda_stream)
+            d2.start()
+            for _ in range(args.steps):
+                d2.step(1)
+                sc = d2.scalars()
+            torch.cuda.synchronize()
+            t_e2e = time.perf_counter() - t0
+            h2d = sum(getattr(P, k).nbytes for P in wl.particles for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az", "id"))
+            e2e = {"value": n_avg * args.steps / t_e2e, "unit": "particle-steps/s",
+                   "h2d_bytes_per_step": int(h2d / args.steps + 4), "d2h_bytes_per_step": 8 * pic.NSCALARS,
+                   "includes": "pic_init + pic_set_particles from host FP64 arrays + pic_start + per step "
+                               "pic_step(1) and pic_diag(scalars)"}
+            d2.close()
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(args.workload)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "grid": [wl.nr, wl.nz], "particles": int(n_avg),
+                       "precision": args.precision, "solver": args.solver,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (particle store %.0f MB per buffer)" % (n_avg * bpp / 2 / 1e6)},
+            "roofline": {"bound": "hbm", "kernel": "k_particles", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": traffic["bytes"] / traffic["particles"] * n_avg if traffic else None,
+                         "bytes_per_particle_step": bpp},
+            "phases_ms": {"layout": phases[0] / args.steps, "particles": k_ms, "circuit": phases[2] / args.steps,
+                          "assembly": phases[3] / args.steps, "field_solve": phases[4] / args.steps,
+                          "efield": phases[5] / args.steps, "diag": phases[6] / args.steps},
+            "particle_phase": {"value": n_avg / ((phases[0] + phases[1]) / args.steps * 1e-3),
+                               "unit": "particle-steps/s"},
+            "field_solve": {"ms": phases[4] / args.steps, "solver": args.solver, "iters": sc["pcg_iters"] if e2e else None,
+                            "tol": wl.pcg_tol},
+            "gpu_launches": KERNELS_PER_STEP * args.steps + KERNELS_PER_WINDOW * windows,
+            "status_flags": flags,
+            "clocks": clk.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -218,10 +218,12 @@ int pic_status(pic_handle *h, uint32_t *flags);
  * check that device and host generators agree bit for bit. */
 int pic_philox(pic_handle *h, int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out);
 
-/* pic_step_timing -- per-kernel device time (ms) of the last pic_step call
- * measured with CUDA events on the handle's stream when timing is enabled:
- * out[0] particle phase, [1] bin layout, [2] circuit, [3] assembly,
- * [4] field solve, [5] E field, [6] diagnostics. */
+/* pic_enable_timing / pic_step_timing -- while timing is on, pic_step launches
+ * the step's kernels directly (no graph) with CUDA events on the handle's
+ * stream between phases.  pic_step_timing synchronises and returns the summed
+ * device time (ms) of every step since the last call: out[0] bin layout and
+ * zeroing, [1] particle kernel, [2] circuit, [3] assembly, [4] field solve,
+ * [5] E field, [6] diagnostics. */
 int pic_enable_timing(pic_handle *h, int on);
 int pic_step_timing(pic_handle *h, double *out7);
 

@@ -76,7 +76,8 @@ struct pic_handle {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   bool graph_failed = false;
   bool timing = false;
-  double timing_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+  double timing_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  std::vector<cudaEvent_t> tev;  // 8 events per timed step
   std::vector<void *> allocs;
 };
 
@@ -347,19 +348,29 @@ int enqueue_solve(pic_handle *h) {
 
 int enqueue_step(pic_handle *h, int in_buf, cudaEvent_t *ev) {
   int st;
+  int out = in_buf ^ 1;
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
-  if ((st = enqueue_particle_phase(h, in_buf))) return st;
+  for (int s = 0; s < 2; ++s) {
+    Store &A = h->st[in_buf][s], &B = h->st[out][s];
+    CK(launch_layout(A.fill, h->d_bin_plasma, h->nbins, h->slack, (int)h->capacity[s], B.start, B.cap, B.fill, B.meta,
+                     A.meta, h->stream));
+  }
+  CK(cudaMemsetAsync(h->d_dep[0], 0, sizeof(unsigned long long) * h->nn, h->stream));
+  CK(cudaMemsetAsync(h->d_dep[1], 0, sizeof(unsigned long long) * h->nn, h->stream));
+  CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned long long) * CNT_N, h->stream));
   if (ev) CK(cudaEventRecord(ev[1], h->stream));
-  CK(launch_circuit(circuit_params(h, 1, nullptr, nullptr), h->stream));
+  if ((st = launch_push(h, in_buf))) return st;
   if (ev) CK(cudaEventRecord(ev[2], h->stream));
-  CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
+  CK(launch_circuit(circuit_params(h, 1, nullptr, nullptr), h->stream));
   if (ev) CK(cudaEventRecord(ev[3], h->stream));
-  if ((st = enqueue_solve(h))) return st;
+  CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
   if (ev) CK(cudaEventRecord(ev[4], h->stream));
-  CK(launch_efield(efield_params(h), h->stream));
+  if ((st = enqueue_solve(h))) return st;
   if (ev) CK(cudaEventRecord(ev[5], h->stream));
-  CK(launch_diag(diag_params(h), h->stream));
+  CK(launch_efield(efield_params(h), h->stream));
   if (ev) CK(cudaEventRecord(ev[6], h->stream));
+  CK(launch_diag(diag_params(h), h->stream));
+  if (ev) CK(cudaEventRecord(ev[7], h->stream));
   return PIC_OK;
 }
 
@@ -387,6 +398,8 @@ int sync(pic_handle *h) {
 void free_all(pic_handle *h) {
   for (int k = 0; k < 2; ++k)
     if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+  for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+  h->tev.clear();
   for (void *p : h->allocs) cudaFree(p);
   h->allocs.clear();
 }
@@ -803,24 +816,18 @@ int pic_step(pic_handle *h, int nsteps) {
     int st = pic_start(h);
     if (st) return st;
   }
-  cudaEvent_t ev[7];
-  if (h->timing) {
-    for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&ev[k]));
-    for (int k = 0; k < 7; ++k) h->timing_ms[k] = 0.0;
-  }
   uint32_t step = h->step;
   CK(cudaMemcpyAsync(h->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, h->stream));
   for (int k = 0; k < nsteps; ++k) {
     int buf = h->cur;
     if (h->timing) {
+      cudaEvent_t ev[8];
+      for (int q = 0; q < 8; ++q) {
+        CK(cudaEventCreate(&ev[q]));
+        h->tev.push_back(ev[q]);
+      }
       int st = enqueue_step(h, buf, ev);
       if (st) return st;
-      CK(cudaEventSynchronize(ev[6]));
-      float ms;
-      for (int q = 0; q < 6; ++q) {
-        CK(cudaEventElapsedTime(&ms, ev[q], ev[q + 1]));
-        h->timing_ms[q == 0 ? 0 : q] += ms;  // [0] particles (incl. layout), [1] circuit, ...
-      }
     } else {
       if (!h->graph[buf] && !h->graph_failed) {
         if (capture_graph(h, buf)) h->graph_failed = true;
@@ -839,8 +846,6 @@ int pic_step(pic_handle *h, int nsteps) {
       if (st) return st;
     }
   }
-  if (h->timing)
-    for (int k = 0; k < 7; ++k) cudaEventDestroy(ev[k]);
   return PIC_OK;
 }
 
@@ -852,14 +857,17 @@ int pic_enable_timing(pic_handle *h, int on) {
 
 int pic_step_timing(pic_handle *h, double *out7) {
   if (!h || !out7) return PIC_EINVAL;
-  // [0] particle phase incl. layout, [1] circuit, [2] assembly, [3] field solve, [4] E field, [5] diagnostics
-  out7[0] = h->timing_ms[0];
-  out7[1] = 0.0;
-  out7[2] = h->timing_ms[1];
-  out7[3] = h->timing_ms[2];
-  out7[4] = h->timing_ms[3];
-  out7[5] = h->timing_ms[4];
-  out7[6] = h->timing_ms[5];
+  if (sync(h)) return PIC_ECUDA;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (size_t b = 0; b + 8 <= h->tev.size(); b += 8)
+    for (int q = 0; q < 7; ++q) {
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, h->tev[b + q], h->tev[b + q + 1]));
+      acc[q] += ms;
+    }
+  for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
+  h->tev.clear();
+  for (int q = 0; q < 7; ++q) out7[q] = acc[q];
   return PIC_OK;
 }
 
