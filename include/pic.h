@@ -227,6 +227,36 @@ int pic_philox(pic_handle *h, int64_t n, const uint32_t *ctr, const uint32_t *ke
 int pic_enable_timing(pic_handle *h, int on);
 int pic_step_timing(pic_handle *h, double *out7);
 
+/* pic_pcg_solve_static -- the paper has no counterpart to this entry point;
+ * it exists for callers that cannot allocate GPU memory when they need a
+ * field solve (an application that owns all device memory through its own
+ * pool, code running while a stream is captured into a CUDA graph, a plugin
+ * called from a loop that must not wait on the allocator).  It solves the
+ * same system as the plain solver of pic_field_solve -- Jacobi-preconditioned
+ * CG in FP64 on the free nodes of sum_b G_ab (phi_a - phi_b) = qrhs_a, warm
+ * start from phi, stop at ||r|| <= tol ||b|| -- on arrays the caller owns, and
+ * allocates nothing: its work vectors live in one fixed array inside the
+ * library, sized for PIC_STATIC_MAX_NODES nodes, which every GPU that loads
+ * the library keeps until the process exits.
+ *   nr, nz     grid cells (nodes (nr+1)*(nz+1) <= PIC_STATIC_MAX_NODES, else
+ *              PIC_EINVAL)
+ *   node_kind  device [(nz+1)*(nr+1)] PIC_NODE_* (Dirichlet where non-zero)
+ *   Gr, Gz     device edge conductances, [(nz+1)*nr] radial, [nz*(nr+1)] axial
+ *   qrhs       device node charge [(nz+1)*(nr+1)]
+ *   phi        device [(nz+1)*(nr+1)], in: Dirichlet values + initial guess,
+ *              out: solution
+ *   iters, rel_resid  host, may both be NULL: then the call returns once the
+ *              work is enqueued on cuda_stream; otherwise it synchronises the
+ *              stream and returns PIC_ENOCONV / PIC_ETIMEOUT / PIC_ENAN on failure.
+ * The first call on each device looks up the work array's device address;
+ * make that first call before any stream capture.  All calls share the work
+ * array: calls that can overlap on the GPU (other streams, other host threads
+ * on the same device) race on it and must be serialised by the caller. */
+#define PIC_STATIC_MAX_NODES 139264
+int pic_pcg_solve_static(int32_t nr, int32_t nz, const int8_t *node_kind, const double *Gr, const double *Gz,
+                         const double *qrhs, double *phi, double tol, int32_t maxit, void *cuda_stream,
+                         int32_t *iters, double *rel_resid);
+
 const char *pic_strerror(int code);
 void pic_destroy(pic_handle *h);
 

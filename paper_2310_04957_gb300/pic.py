@@ -31,7 +31,9 @@ SCALARS = ["step", "t", "U_E", "Q_E", "C_eq", "I_conv", "I_ccp", "y0", "y1", "y2
 EXPORTS = ["pic_init", "pic_set_particles", "pic_count", "pic_get_particles", "pic_start", "pic_step",
            "pic_particle_phase", "pic_field_solve", "pic_ceq", "pic_diag", "pic_set_field", "pic_set_step",
            "pic_set_ceq", "pic_set_circuit_state", "pic_set_conv_current", "pic_circuit_run", "pic_status",
-           "pic_philox", "pic_enable_timing", "pic_step_timing", "pic_strerror", "pic_destroy"]
+           "pic_philox", "pic_enable_timing", "pic_step_timing", "pic_strerror", "pic_destroy",
+           "pic_pcg_solve_static"]
+STATIC_MAX_NODES = 139264
 
 
 class PicError(RuntimeError):
@@ -95,6 +97,8 @@ def lib():
         L.pic_strerror.argtypes = [I]
         L.pic_strerror.restype = ctypes.c_char_p
         L.pic_destroy.argtypes = [P]
+        L.pic_pcg_solve_static.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, D, ctypes.c_int32, P,
+                                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(D)]
         _lib = L
     return _lib
 
@@ -268,3 +272,16 @@ class Discharge:
         o = np.zeros(7)
         _check(lib().pic_step_timing(self.h, _p(o)), "pic_step_timing")
         return o
+
+
+def pcg_solve_static(nr, nz, node_kind, Gr, Gz, qrhs, phi, tol, maxit, stream=None):
+    """Call pic_pcg_solve_static on caller-owned device arrays (raw device pointers as ints).
+
+    The library allocates nothing for this solve; it returns (status, iterations,
+    relative residual) after synchronising the stream."""
+    it = ctypes.c_int32()
+    rr = ctypes.c_double()
+    st = lib().pic_pcg_solve_static(nr, nz, ctypes.c_void_p(node_kind), ctypes.c_void_p(Gr), ctypes.c_void_p(Gz),
+                                    ctypes.c_void_p(qrhs), ctypes.c_void_p(phi), tol, maxit, _stream(stream),
+                                    ctypes.byref(it), ctypes.byref(rr))
+    return st, it.value, rr.value
