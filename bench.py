@@ -30,8 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s (push+MCC+deposit); field-solve ms to 1e-10 residual, vs plain"
 BYTES_PER_PARTICLE_STEP = {"fp32": 80, "fp64": 144}  # state read once + written once
-KERNELS_PER_STEP = 9  # layout x2, particles, circuit, assemble x2, pcg, efield, diag
-KERNELS_PER_WINDOW = 5  # diag window, C_eq refresh (edges, dirichlet, pcg, energy)
+KERNELS_PER_STEP = 10  # layout x3, particles, circuit, assemble x2, solve, efield, diag
+KERNELS_PER_WINDOW = 6  # diag window, C_eq refresh (edges, dirichlet, solve, energy), circuit propagator
 
 
 def parse():

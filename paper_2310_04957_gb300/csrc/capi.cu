@@ -55,7 +55,8 @@ struct pic_handle {
          *d_dinv = nullptr, *d_Er = nullptr, *d_Ez = nullptr;
   void *d_E = nullptr;
   // PCG scratch
-  double *d_r = nullptr, *d_z = nullptr, *d_p = nullptr, *d_Ap = nullptr, *d_partial = nullptr, *d_pcg_out = nullptr;
+  double *d_work = nullptr, *d_partial = nullptr, *d_pcg_out = nullptr;
+  float *d_work32 = nullptr;
   unsigned *d_bar = nullptr;
   // C_eq solve
   double *d_phiL = nullptr, *d_Grc = nullptr, *d_Gzc = nullptr, *d_dinvc = nullptr, *d_energy = nullptr,
@@ -65,7 +66,9 @@ struct pic_handle {
   Store st[2][2];  // [buffer][species]
   int cur = 0;
   void *d_xsE = nullptr, *d_xsS = nullptr;
-  double *d_scalars = nullptr;
+  double *d_scalars = nullptr, *d_prop = nullptr;
+  long long *d_lay_part = nullptr, *d_lay_boff = nullptr;
+  int *d_lay_use = nullptr;
   uint32_t *d_step = nullptr, *d_flags = nullptr;
   double *d_dens_sum[2] = {nullptr, nullptr}, *d_dens_avg[2] = {nullptr, nullptr};
   // host mirrors
@@ -265,8 +268,11 @@ PcgParams pcg_params(pic_handle *h, const double *Gr, const double *Gz, const do
   P.nr = h->nr; P.nz = h->nz; P.nn = h->nn;
   P.node_kind = h->d_node_kind;
   P.Gr = Gr; P.Gz = Gz; P.dinv = dinv; P.qrhs = qrhs; P.phi = phi;
-  P.r = h->d_r; P.z = h->d_z; P.p = h->d_p; P.Ap = h->d_Ap;
+  P.work = h->d_work;
+  P.work32 = h->d_work32;
   P.partial = h->d_partial;
+  P.inner_tol = 1e-4f;
+  P.gscale = 1.0 / (kEps0 * h->cfg.dr);
   P.bar = h->d_bar;
   P.tol = tol;
   P.maxit = h->cfg.pcg_maxit;
@@ -297,6 +303,7 @@ CircuitParams circuit_params(pic_handle *h, int n_run, double *U_hist, uint32_t 
   C.step_ptr = h->d_step;
   C.scalars = h->d_scalars;
   C.n_run = n_run; C.U_hist = U_hist; C.step_inc = step_inc;
+  C.prop = h->d_prop;
   return C;
 }
 
@@ -317,6 +324,26 @@ DiagParams diag_params(pic_handle *h) {
   return D;
 }
 
+LayoutParams layout_params(pic_handle *h, int in_buf) {
+  LayoutParams L;
+  memset(&L, 0, sizeof(L));
+  int out = in_buf ^ 1;
+  for (int s = 0; s < 2; ++s) {
+    Store &A = h->st[in_buf][s], &B = h->st[out][s];
+    L.fill_in[s] = A.fill;
+    L.capacity[s] = (int)h->capacity[s];
+    L.start[s] = B.start; L.cap[s] = B.cap; L.fill_out[s] = B.fill;
+    L.meta_out[s] = B.meta; L.meta_in[s] = A.meta;
+  }
+  L.bin_plasma = h->d_bin_plasma;
+  L.nbins = h->nbins;
+  L.slack = h->slack;
+  L.part = h->d_lay_part;
+  L.boff = h->d_lay_boff;
+  L.use_slack = h->d_lay_use;
+  return L;
+}
+
 int launch_push(pic_handle *h, int in_buf) {
   cudaError_t e;
   if (h->prec == PIC_FP32) e = launch_particles<float>(push_params<float>(h, in_buf), h->stream);
@@ -328,21 +355,18 @@ int launch_push(pic_handle *h, int in_buf) {
 // deposits and counters, then the particle kernel.
 int enqueue_particle_phase(pic_handle *h, int in_buf) {
   int out = in_buf ^ 1;
-  for (int s = 0; s < 2; ++s) {
-    Store &A = h->st[in_buf][s], &B = h->st[out][s];
-    CK(launch_layout(A.fill, h->d_bin_plasma, h->nbins, h->slack, (int)h->capacity[s], B.start, B.cap, B.fill, B.meta,
-                     A.meta, h->stream));
-  }
+  CK(launch_layout(layout_params(h, in_buf), h->stream));
   CK(cudaMemsetAsync(h->d_dep[0], 0, sizeof(unsigned long long) * h->nn, h->stream));
   CK(cudaMemsetAsync(h->d_dep[1], 0, sizeof(unsigned long long) * h->nn, h->stream));
   CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned long long) * CNT_N, h->stream));
   return launch_push(h, in_buf);
 }
 
-int enqueue_solve(pic_handle *h) {
+int enqueue_solve(pic_handle *h, int mode) {
   CK(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
   PcgParams P = pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, h->d_phi, h->cfg.pcg_tol, h->d_pcg_out);
-  CK(launch_pcg(P, h->pcg_grid, h->stream));
+  if (mode == PIC_SOLVER_MIXED) CK(launch_pcg_mixed(P, h->pcg_grid, h->stream));
+  else CK(launch_pcg(P, h->pcg_grid, h->stream));
   return PIC_OK;
 }
 
@@ -350,11 +374,7 @@ int enqueue_step(pic_handle *h, int in_buf, cudaEvent_t *ev) {
   int st;
   int out = in_buf ^ 1;
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
-  for (int s = 0; s < 2; ++s) {
-    Store &A = h->st[in_buf][s], &B = h->st[out][s];
-    CK(launch_layout(A.fill, h->d_bin_plasma, h->nbins, h->slack, (int)h->capacity[s], B.start, B.cap, B.fill, B.meta,
-                     A.meta, h->stream));
-  }
+  CK(launch_layout(layout_params(h, in_buf), h->stream));
   CK(cudaMemsetAsync(h->d_dep[0], 0, sizeof(unsigned long long) * h->nn, h->stream));
   CK(cudaMemsetAsync(h->d_dep[1], 0, sizeof(unsigned long long) * h->nn, h->stream));
   CK(cudaMemsetAsync(h->d_counters, 0, sizeof(unsigned long long) * CNT_N, h->stream));
@@ -365,7 +385,7 @@ int enqueue_step(pic_handle *h, int in_buf, cudaEvent_t *ev) {
   if (ev) CK(cudaEventRecord(ev[3], h->stream));
   CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
   if (ev) CK(cudaEventRecord(ev[4], h->stream));
-  if ((st = enqueue_solve(h))) return st;
+  if ((st = enqueue_solve(h, h->cfg.solver))) return st;
   if (ev) CK(cudaEventRecord(ev[5], h->stream));
   CK(launch_efield(efield_params(h), h->stream));
   if (ev) CK(cudaEventRecord(ev[6], h->stream));
@@ -435,6 +455,7 @@ int window_end(pic_handle *h) {
     CK(cudaMemcpyAsync(h->d_scalars + SC_CEQ, h->d_ceq_out, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
     CK(cudaMemcpyAsync(h->d_scalars + SC_CEQ_GAUSS, h->d_ceq_out + 1, sizeof(double), cudaMemcpyDeviceToDevice,
                        h->stream));
+    CK(launch_circuit_prepare(circuit_params(h, 1, nullptr, nullptr), h->stream));
   }
   return PIC_OK;
 }
@@ -444,6 +465,7 @@ bool check_config(const pic_config *c) {
   if (!c->node_kind || !c->cell_kind || !c->cell_eps || !c->xs_energy || !c->xs_sigma || c->n_xs < 2) return false;
   if (c->circuit < 0 || c->circuit > 2 || c->n_sub < 1 || c->steps_per_rf < 1 || c->pcg_maxit < 1) return false;
   if (c->precision != PIC_FP32 && c->precision != PIC_FP64) return false;
+  if (c->solver != PIC_SOLVER_PLAIN && c->solver != PIC_SOLVER_MIXED) return false;
   if (c->capacity[0] < 1 || c->capacity[1] < 1 || c->capacity[0] > 2000000000ll || c->capacity[1] > 2000000000ll)
     return false;
   if (!(c->m[0] > 0) || !(c->m[1] > 0) || !(c->m_gas > 0)) return false;
@@ -662,18 +684,24 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
     DA(h->d_Er, sizeof(double) * nn);
     DA(h->d_Ez, sizeof(double) * nn);
     DA(h->d_E, 2 * h->esz * nn);
-    DA(h->d_r, sizeof(double) * nn);
-    DA(h->d_z, sizeof(double) * nn);
-    DA(h->d_p, sizeof(double) * nn);
-    DA(h->d_Ap, sizeof(double) * nn);
+    DA(h->d_work, sizeof(double) * 8 * nn);
+    DA(h->d_work32, sizeof(float) * 12 * nn);
     h->pcg_grid = pcg_grid_size(h->device);
-    DA(h->d_partial, sizeof(double) * 8 * (h->pcg_grid + 32));
+    DA(h->d_partial, sizeof(double) * 16 * (h->pcg_grid + 32));
     DA(h->d_bar, 4 * sizeof(unsigned));
     DA(h->d_pcg_out, sizeof(double) * 8);
     DA(h->d_energy, sizeof(double) * 2);
     DA(h->d_ceq_out, sizeof(double) * 2);
     DA(h->d_counters, sizeof(unsigned long long) * CNT_N);
     DA(h->d_scalars, sizeof(double) * SC_N);
+    DA(h->d_prop, sizeof(double) * 64);
+    {
+      int nblk = (h->nbins + 1023) / 1024;
+      if (nblk > 1024) return PIC_EINVAL;
+      DA(h->d_lay_part, sizeof(long long) * 2 * 4 * nblk);
+      DA(h->d_lay_boff, sizeof(long long) * 2 * nblk);
+      DA(h->d_lay_use, sizeof(int) * 2);
+    }
     DA(h->d_step, sizeof(uint32_t) * 2);
     DA(h->d_flags, sizeof(uint32_t) * 2);
     DA(h->d_xsE, h->esz * cfg->n_xs);
@@ -792,8 +820,9 @@ int pic_start(pic_handle *h) {
   sc[SC_T] = t;
   CK(cudaMemcpyAsync(h->d_scalars, sc, sizeof(sc), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, h->stream));
+  CK(launch_circuit_prepare(circuit_params(h, 1, nullptr, nullptr), h->stream));
   CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
-  if ((st = enqueue_solve(h))) return st;
+  if ((st = enqueue_solve(h, h->cfg.solver))) return st;
   CK(launch_efield(efield_params(h), h->stream));
   if (sync(h)) return PIC_ECUDA;
   h->started = true;
@@ -874,7 +903,7 @@ int pic_step_timing(pic_handle *h, double *out7) {
 int pic_field_solve(pic_handle *h, int mode, int *iters, double *rel_resid) {
   if (!h || (mode != PIC_SOLVER_PLAIN && mode != PIC_SOLVER_MIXED)) return PIC_EINVAL;
   CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
-  int st = enqueue_solve(h);
+  int st = enqueue_solve(h, mode);
   if (st) return st;
   CK(launch_efield(efield_params(h), h->stream));
   double out[3];
@@ -1008,7 +1037,8 @@ int pic_set_ceq(pic_handle *h, double ceq) {
   if (!h || !(ceq > 0)) return PIC_EINVAL;
   if (sync(h)) return PIC_ECUDA;
   CK(cudaMemcpy(h->d_scalars + SC_CEQ, &ceq, sizeof(double), cudaMemcpyHostToDevice));
-  return PIC_OK;
+  CK(launch_circuit_prepare(circuit_params(h, 1, nullptr, nullptr), h->stream));
+  return sync(h);
 }
 
 int pic_set_circuit_state(pic_handle *h, const double *y6) {

@@ -93,232 +93,6 @@ cudaError_t launch_assemble(const FieldParams &F, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// ---- plain FP64 PCG ------------------------------------------------------------
-// Grid-wide barrier with a bounded wait: returns false (and sets the timeout
-// flag) if the other blocks did not arrive within `limit` clock cycles.
-__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, long long limit, uint32_t *flags) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *gen = bar + 1;
-    unsigned g = *gen;
-    __threadfence();
-    unsigned prev = atomicAdd(bar, 1u);
-    int ok = 1;
-    if (prev == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long t0 = clock64();
-      while (*gen == g) {
-        if (clock64() - t0 > limit) {
-          ok = 0;
-          atomicOr(flags, 0x2u);
-          break;
-        }
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
-// (A x)_a = sum_b G_ab (x_a - x_b) at free node a; Dirichlet neighbours enter
-// with their x value (x is zero there for search directions).  Vectors written
-// by other blocks are read through L2 (__ldcg).
-__device__ __forceinline__ double apply_A(const PcgParams &P, int a, int i, int j, const double *x) {
-  const int nr = P.nr, W = nr + 1;
-  double xa = __ldcg(x + a), acc = 0.0;
-  if (i > 0) acc += __ldg(P.Gr + j * nr + i - 1) * (xa - __ldcg(x + a - 1));
-  if (i < nr) acc += __ldg(P.Gr + j * nr + i) * (xa - __ldcg(x + a + 1));
-  if (j > 0) acc += __ldg(P.Gz + (j - 1) * W + i) * (xa - __ldcg(x + a - W));
-  if (j < P.nz) acc += __ldg(P.Gz + j * W + i) * (xa - __ldcg(x + a + W));
-  return acc;
-}
-
-// Block partial sums of K values into partial[blockIdx.x*4 + k].
-template <int K>
-__device__ void block_reduce_store(const double v[K], double *partial) {
-  __shared__ double s[4][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) s[k][wid] = x;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    int nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double x = lane < nw ? s[k][lane] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) partial[blockIdx.x * 4 + k] = x;
-    }
-  }
-}
-
-// Grid total of the block partials, summed in a fixed order so that every
-// block obtains the same bits.
-template <int K>
-__device__ void grid_total(const double *partial, double out[K]) {
-  __shared__ double s_tot[4];
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      double x = 0.0;
-      for (int b = lane; b < (int)gridDim.x; b += 32) x += __ldcg(partial + b * 4 + k);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) s_tot[k] = x;
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k) out[k] = s_tot[k];
-}
-
-// Jacobi-preconditioned CG on the free nodes, FP64, warm start from phi.
-// Stops when ||r||_2 <= tol ||b||_2 (b = node charge + Dirichlet lift),
-// confirmed on the recomputed residual.  Persistent: one cooperative launch,
-// bounded grid barriers, reduction partials double-buffered (three barriers
-// per iteration).
-__global__ void __launch_bounds__(256) k_pcg(const PcgParams P) {
-  const int nn = P.nn, W = P.nr + 1;
-  const int gt = blockIdx.x * blockDim.x + threadIdx.x, gs = gridDim.x * blockDim.x;
-  const unsigned nb = gridDim.x;
-  double tot[4];
-  int it = 0, pb = 0;
-  int status = -4;
-  double target = 0.0, bnorm = 0.0, rr = 0.0, rz = 0.0;
-#define PCG_SYNC()                                                   \
-  if (!grid_barrier(P.bar, nb, P.spin_limit, P.flags)) {             \
-    status = -5;                                                     \
-    goto done;                                                       \
-  }
-  for (int pass = 0; pass < 64; ++pass) {
-    {
-      double v[4] = {0.0, 0.0, 0.0, 0.0};  // b^2, r^2, r.z
-      for (int a = gt; a < nn; a += gs) {
-        if (P.node_kind[a] != 0) { P.r[a] = 0.0; P.z[a] = 0.0; P.p[a] = 0.0; continue; }
-        int j = a / W, i = a - j * W;
-        double r = __ldg(P.qrhs + a) - apply_A(P, a, i, j, P.phi);
-        double lift = 0.0;  // b = q + sum over Dirichlet neighbours of G phi_D
-        if (i > 0 && P.node_kind[a - 1] != 0) lift += P.Gr[j * P.nr + i - 1] * __ldcg(P.phi + a - 1);
-        if (i < P.nr && P.node_kind[a + 1] != 0) lift += P.Gr[j * P.nr + i] * __ldcg(P.phi + a + 1);
-        if (j > 0 && P.node_kind[a - W] != 0) lift += P.Gz[(j - 1) * W + i] * __ldcg(P.phi + a - W);
-        if (j < P.nz && P.node_kind[a + W] != 0) lift += P.Gz[j * W + i] * __ldcg(P.phi + a + W);
-        double b = __ldg(P.qrhs + a) + lift;
-        double z = __ldg(P.dinv + a) * r;
-        P.r[a] = r;
-        P.z[a] = z;
-        P.p[a] = z;
-        v[0] += b * b;
-        v[1] += r * r;
-        v[2] += r * z;
-      }
-      double *part = P.partial + pb * nb * 4;
-      pb ^= 1;
-      block_reduce_store<3>(v, part);
-      PCG_SYNC();
-      grid_total<3>(part, tot);
-    }
-    bnorm = sqrt(tot[0]);
-    target = bnorm > 0.0 ? P.tol * bnorm : 1e-30;
-    rr = tot[1];
-    rz = tot[2];
-    if (!(rr == rr) || !(bnorm == bnorm)) { status = -7; goto done; }
-    if (sqrt(rr) <= target) { status = 0; goto done; }
-    if (it >= P.maxit) { status = -4; goto done; }
-    while (it < P.maxit) {
-      {
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int a = gt; a < nn; a += gs) {
-          if (P.node_kind[a] != 0) continue;
-          int j = a / W, i = a - j * W;
-          double ap = apply_A(P, a, i, j, P.p);
-          P.Ap[a] = ap;
-          v[0] += __ldcg(P.p + a) * ap;
-        }
-        double *part = P.partial + pb * nb * 4;
-        pb ^= 1;
-        block_reduce_store<1>(v, part);
-        PCG_SYNC();
-        grid_total<1>(part, tot);
-      }
-      double alpha = rz / tot[0];
-      {
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int a = gt; a < nn; a += gs) {
-          if (P.node_kind[a] != 0) continue;
-          P.phi[a] += alpha * P.p[a];
-          double r = P.r[a] - alpha * P.Ap[a];
-          double z = __ldg(P.dinv + a) * r;
-          P.r[a] = r;
-          P.z[a] = z;
-          v[0] += r * r;
-          v[1] += r * z;
-        }
-        double *part = P.partial + pb * nb * 4;
-        pb ^= 1;
-        block_reduce_store<2>(v, part);
-        PCG_SYNC();
-        grid_total<2>(part, tot);
-      }
-      ++it;
-      rr = tot[0];
-      if (!(rr == rr)) { status = -7; goto done; }
-      if (sqrt(rr) <= target) break;
-      double beta = tot[1] / rz;
-      rz = tot[1];
-      for (int a = gt; a < nn; a += gs) {
-        if (P.node_kind[a] != 0) continue;
-        P.p[a] = P.z[a] + beta * P.p[a];
-      }
-      PCG_SYNC();
-    }
-    PCG_SYNC();
-  }
-#undef PCG_SYNC
-done:
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    P.out[0] = (double)it;
-    P.out[1] = bnorm > 0.0 ? sqrt(rr) / bnorm : sqrt(rr);
-    P.out[2] = (double)status;
-    if (status == -4) atomicOr(P.flags, 0x4u);
-    if (status == -7) atomicOr(P.flags, 0x8u);
-  }
-}
-
-int pcg_grid_size(int device) {
-  int sms = 0, per = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg, 256, 0);
-  if (per > 2) per = 2;
-  if (per < 1) per = 1;
-  return sms * per;
-}
-
-cudaError_t launch_pcg(const PcgParams &P, int grid, cudaStream_t st) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_pcg, P);
-}
-
 // ---- E field at nodes -----------------------------------------------------------
 // E = -grad phi: central differences; E_r = 0 on the axis; one-sided at the
 // domain edge; at a Dirichlet node with exactly one free neighbour along a
@@ -478,6 +252,71 @@ __device__ void invert6(int n, double A[6][6], double Inv[6][6]) {
   }
 }
 
+// Propagator of one time step: the n_sub trapezoidal substeps compose, for a
+// fixed C_eq, into y_{n+1} = Phi y_n + Im(exp(i(w t_n + phase)) c) + g I_conv,
+// with B = (I - h/2 M)^-1 (I + h/2 M), Phi = B^n_sub, and c, g the sums of
+// the propagated source terms (the source is V sin(w t + phase)).  Rebuilt
+// whenever C_eq changes.  prop layout: Phi[36], c_re[6], c_im[6], g[6], n.
+__global__ void k_circuit_prepare(const CircuitParams C) {
+  if (threadIdx.x != 0 || blockIdx.x != 0 || C.kind == 0) return;
+  double *S = C.scalars;
+  const double two_pi = 6.283185307179586476925286766559;
+  double ceq = S[SC_CEQ];
+  double M[6][6], es[6], ec[6], A[6][6], Inv[6][6], B[6][6], Phi[6][6], T[6][6];
+  int n;
+  circuit_matrix(C, ceq, M, es, ec, n);
+  double h = C.dt / C.nsub;
+  for (int r = 0; r < n; ++r)
+    for (int k = 0; k < n; ++k) A[r][k] = (r == k ? 1.0 : 0.0) - 0.5 * h * M[r][k];
+  invert6(n, A, Inv);
+  for (int r = 0; r < n; ++r)
+    for (int k = 0; k < n; ++k) {
+      double acc = 0.0;
+      for (int m = 0; m < n; ++m) acc += Inv[r][m] * ((m == k ? 1.0 : 0.0) + 0.5 * h * M[m][k]);
+      B[r][k] = acc;
+      Phi[r][k] = r == k ? 1.0 : 0.0;
+    }
+  double cre[6] = {0, 0, 0, 0, 0, 0}, cim[6] = {0, 0, 0, 0, 0, 0}, g[6] = {0, 0, 0, 0, 0, 0};
+  double srcv[6], srcg[6];
+  for (int r = 0; r < n; ++r) {
+    double a = 0.0, b = 0.0;
+    for (int m = 0; m < n; ++m) { a += Inv[r][m] * es[m]; b += Inv[r][m] * ec[m]; }
+    srcv[r] = 0.5 * h * C.V * a;  // Inv (h/2) e_src V
+    srcg[r] = h * b;              // Inv h e_conv
+  }
+  for (int k = 0; k < C.nsub; ++k) {
+    // acc <- B acc + term_k
+    double nre[6], nim[6], ng[6];
+    double ph0 = two_pi * C.f * k * h, ph1 = two_pi * C.f * (k + 1) * h;
+    double er = cos(ph0) + cos(ph1), ei = sin(ph0) + sin(ph1);
+    for (int r = 0; r < n; ++r) {
+      double a = 0.0, b = 0.0, c = 0.0;
+      for (int m = 0; m < n; ++m) { a += B[r][m] * cre[m]; b += B[r][m] * cim[m]; c += B[r][m] * g[m]; }
+      nre[r] = a + srcv[r] * er;
+      nim[r] = b + srcv[r] * ei;
+      ng[r] = c + srcg[r];
+    }
+    for (int r = 0; r < n; ++r) { cre[r] = nre[r]; cim[r] = nim[r]; g[r] = ng[r]; }
+    for (int r = 0; r < n; ++r)
+      for (int q = 0; q < n; ++q) {
+        double acc = 0.0;
+        for (int m = 0; m < n; ++m) acc += B[r][m] * Phi[m][q];
+        T[r][q] = acc;
+      }
+    for (int r = 0; r < n; ++r)
+      for (int q = 0; q < n; ++q) Phi[r][q] = T[r][q];
+  }
+  double *o = C.prop;
+  for (int r = 0; r < 6; ++r)
+    for (int q = 0; q < 6; ++q) o[r * 6 + q] = (r < n && q < n) ? Phi[r][q] : 0.0;
+  for (int r = 0; r < 6; ++r) {
+    o[36 + r] = r < n ? cre[r] : 0.0;
+    o[42 + r] = r < n ? cim[r] : 0.0;
+    o[48 + r] = r < n ? g[r] : 0.0;
+  }
+  o[54] = n;
+}
+
 __global__ void k_circuit(const CircuitParams C) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double *S = C.scalars;
@@ -497,36 +336,22 @@ __global__ void k_circuit(const CircuitParams C) {
       if (C.U_hist) C.U_hist[k] = U1;
     }
   } else {
-    double M[6][6], es[6], ec[6], A[6][6], Inv[6][6], Bm[6][6];
-    int n;
-    circuit_matrix(C, ceq, M, es, ec, n);
-    double h = C.dt / C.nsub;
-    for (int r = 0; r < n; ++r)
-      for (int k = 0; k < n; ++k) A[r][k] = (r == k ? 1.0 : 0.0) - 0.5 * h * M[r][k];
-    invert6(n, A, Inv);
-    // Bm = Inv * (I + h/2 M)
-    for (int r = 0; r < n; ++r)
-      for (int k = 0; k < n; ++k) {
-        double acc = 0.0;
-        for (int m = 0; m < n; ++m) acc += Inv[r][m] * ((m == k ? 1.0 : 0.0) + 0.5 * h * M[m][k]);
-        Bm[r][k] = acc;
-      }
+    const double *pr = C.prop;
+    const int n = (int)pr[54];
     double y[6];
     for (int r = 0; r < 6; ++r) y[r] = S[SC_Y0 + r];
     for (int k = 0; k < C.n_run; ++k) {
       double tn = (double)(step + k) * C.dt;
-      for (int sub = 0; sub < C.nsub; ++sub) {
-        double ta = tn + sub * h, tb = tn + (sub + 1) * h;
-        double Ua = C.V * sin(two_pi * C.f * ta + C.phase), Ub = C.V * sin(two_pi * C.f * tb + C.phase);
-        double src[6], yn[6];
-        for (int r = 0; r < n; ++r) src[r] = 0.5 * h * (es[r] * (Ua + Ub) + ec[r] * 2.0 * Iconv);
-        for (int r = 0; r < n; ++r) {
-          double acc = 0.0;
-          for (int m = 0; m < n; ++m) acc += Bm[r][m] * y[m] + Inv[r][m] * src[m];
-          yn[r] = acc;
-        }
-        for (int r = 0; r < n; ++r) y[r] = yn[r];
+      double sn, cs;
+      sincos(two_pi * C.f * tn + C.phase, &sn, &cs);
+      double yn[6];
+      for (int r = 0; r < n; ++r) {
+        double acc = 0.0;
+        for (int m = 0; m < n; ++m) acc += pr[r * 6 + m] * y[m];
+        // Im((cs + i sn)(c_re + i c_im)) = sn c_re + cs c_im
+        yn[r] = acc + sn * pr[36 + r] + cs * pr[42 + r] + pr[48 + r] * Iconv;
       }
+      for (int r = 0; r < n; ++r) y[r] = yn[r];
       double QE = y[n - 1];
       S[SC_QE] = QE;
       S[SC_UE] = QE / ceq;
@@ -537,6 +362,11 @@ __global__ void k_circuit(const CircuitParams C) {
   }
   S[SC_T] = (double)(step + C.n_run) * C.dt;
   if (C.step_inc) *C.step_inc = step + C.n_run;
+}
+
+cudaError_t launch_circuit_prepare(const CircuitParams &C, cudaStream_t st) {
+  k_circuit_prepare<<<1, 32, 0, st>>>(C);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_circuit(const CircuitParams &C, cudaStream_t st) {

@@ -53,32 +53,25 @@ struct FieldParams {
   double *scalars;
 };
 
+// Field solve on the free nodes of sum_b G_ab (phi_a - phi_b) = qrhs_a.
+// work: [8*nn] doubles (plain) -- r[2], w[2], s[2], p, spare;
+// work32: [11*nn] floats (mixed) -- r[2], w[2], s[2], p, x, Gr, Gz, dinv.
 struct PcgParams {
   int nr, nz, nn;
   const int8_t *node_kind;
   const double *Gr, *Gz, *dinv, *qrhs;
   double *phi;
-  double *r, *z, *p, *Ap;
-  double *partial;          // [gridDim.x * 4]
+  double *work;
+  float *work32;
+  double *partial;          // [16 * gridDim.x]: FP64 partials, then FP32 partials (mixed)
   unsigned *bar;            // [2]: arrival count, generation
-  double tol;
-  int maxit;
-  double *out;              // [0] iterations, [1] relative residual, [2] status (0 ok, -4 noconv, -5 timeout, -7 nan)
+  double tol;               // relative residual target ||b - A phi|| <= tol ||b||
+  float inner_tol;          // mixed: relative reduction of each FP32 inner solve
+  double gscale;            // mixed: scale making the FP32 operator entries O(1)
+  int maxit;                // iteration cap (total inner iterations for mixed)
+  double *out;              // [0] iterations, [1] relative residual, [2] status, [3] outer steps
   uint32_t *flags;
   long long spin_limit;     // clock cycles per barrier wait
-};
-
-struct MixedParams {
-  int nr, nz, nn;
-  const int8_t *node_kind;
-  const double *Gr, *Gz, *qrhs;
-  double *phi;
-  double tol;               // outer (FP64) relative residual target
-  float inner_tol;          // inner (FP32) relative reduction per refinement
-  int maxit;                // total inner iterations cap
-  double *out;
-  uint32_t *flags;
-  double *partial;          // scratch
 };
 
 struct EfieldParams {
@@ -102,6 +95,7 @@ struct CircuitParams {
   int n_run;                // steps to advance (1 inside the step graph)
   double *U_hist;           // optional U_E history [n_run]
   uint32_t *step_inc;       // if non-null, incremented once per advanced step
+  double *prop;             // [64] step propagator (k_circuit_prepare)
 };
 
 struct DiagParams {
@@ -122,20 +116,33 @@ struct DiagParams {
 
 template <typename T> cudaError_t launch_particles(const PushParams<T> &P, cudaStream_t st);
 template <typename T> cudaError_t launch_deposit_only(const PushParams<T> &P, cudaStream_t st);
-cudaError_t launch_layout(const int *fill_in, const int8_t *bin_plasma, int nbins, float slack, int capacity, int *start,
-                          int *cap, int *fill_out, BinMeta *meta_out, BinMeta *meta_in, cudaStream_t st);
+struct LayoutParams {
+  const int *fill_in[2];
+  const int8_t *bin_plasma;
+  int nbins;
+  float slack;
+  int capacity[2];
+  int *start[2], *cap[2], *fill_out[2];
+  BinMeta *meta_out[2], *meta_in[2];
+  long long *part;          // [2 * nblk * 4]
+  long long *boff;          // [2 * nblk]
+  int *use_slack;           // [2]
+};
+cudaError_t launch_layout(const LayoutParams &L, cudaStream_t st);
 cudaError_t launch_philox(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st);
 
 cudaError_t launch_assemble(const FieldParams &F, cudaStream_t st);
 cudaError_t launch_assemble_edges_only(const FieldParams &F, cudaStream_t st);
 cudaError_t launch_set_dirichlet(int nn, const int8_t *kind, double *phi, double U, cudaStream_t st);
 cudaError_t launch_pcg(const PcgParams &P, int grid, cudaStream_t st);
+cudaError_t launch_pcg_mixed(const PcgParams &P, int grid, cudaStream_t st);
 int pcg_grid_size(int device);
-cudaError_t launch_mixed(const MixedParams &M, cudaStream_t st);
+constexpr int kPcgThreads = 256;
 cudaError_t launch_efield(const EfieldParams &E, cudaStream_t st);
 cudaError_t launch_energy(int nr, int nz, const int8_t *node_kind, const double *Gr, const double *Gz,
                           const double *phi, double *out2, cudaStream_t st);
 cudaError_t launch_circuit(const CircuitParams &C, cudaStream_t st);
+cudaError_t launch_circuit_prepare(const CircuitParams &C, cudaStream_t st);
 cudaError_t launch_diag(const DiagParams &D, cudaStream_t st);
 cudaError_t launch_diag_window(const DiagParams &D, cudaStream_t st);
 

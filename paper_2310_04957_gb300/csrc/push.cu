@@ -658,75 +658,131 @@ __global__ void __launch_bounds__(kThreads) k_particles(const PushParams<T> P) {
 }
 
 // ---------------------------------------------------------------------------
-// Bin layout of the next write store: room = fill + slack*fill + 8 for bins of
-// plasma cells, 0 elsewhere; exclusive scan; zero fill counters.  One CTA.
+// Bin layout of the next write store, both species at once: room of a bin =
+// fill + slack*fill + 8 for bins of plasma cells (0 elsewhere), or exactly the
+// fill if that does not fit in 90 % of the capacity; start = exclusive scan of
+// the rooms (clamped to the capacity); fill counters of the write store zeroed.
+// Three launches: block sums, one scan of the block sums, block scans + writes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) k_layout(const int *__restrict__ fill_in, const int8_t *__restrict__ bin_plasma,
-                                                int nbins, float slack, int capacity, int *start, int *cap, int *fill_out,
-                                                BinMeta *meta_out, BinMeta *meta_in) {
-  __shared__ long long s_part[1024];
-  __shared__ long long s_tot[2];
-  const int t = threadIdx.x, nt = blockDim.x;
-  const int chunk = (nbins + nt - 1) / nt;
-  const int lo = t * chunk, hi = min(nbins, lo + chunk);
-  long long sum_fill = 0, sum_cap = 0;
-  for (int b = lo; b < hi; ++b) {
-    int f = fill_in[b];
-    sum_fill += f;
-    if (bin_plasma[b]) sum_cap += (long long)f + (long long)(slack * (float)f) + 8;
+__device__ __forceinline__ long long room_of(int f, int plasma, int use_slack, float slack) {
+  if (!plasma) return 0;
+  return use_slack ? (long long)f + (long long)(slack * (float)f) + 8 : (long long)f;
+}
+
+template <int K>
+__device__ __forceinline__ void block_sum_ll(long long v[K], long long *sh /* [K][32] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    long long x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[k * 32 + wid] = x;
   }
-  // choose the slack that fits: full slack, else none (overflow takes the rest)
-  s_part[t] = sum_cap;
   __syncthreads();
-  for (int d = 512; d > 0; d >>= 1) {
-    if (t < d) s_part[t] += s_part[t + d];
-    __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      long long x = lane < (int)(blockDim.x >> 5) ? sh[k * 32 + lane] : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) sh[k * 32] = x;
+    }
   }
-  if (t == 0) s_tot[0] = s_part[0];
   __syncthreads();
-  long long total_cap = s_tot[0];
-  bool use_slack = total_cap <= (long long)(0.9 * (double)capacity);
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = sh[k * 32];
+}
+
+// Exclusive scan over the block (blockDim.x = 1024); returns the block total.
+__device__ __forceinline__ long long block_exscan_ll(long long v, long long &excl, long long *sh /* [32] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long long x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) sh[wid] = x;
   __syncthreads();
-  long long mine = 0;
-  for (int b = lo; b < hi; ++b) {
-    int f = fill_in[b];
-    int c = bin_plasma[b] ? (use_slack ? f + (int)(slack * (float)f) + 8 : f) : 0;
-    mine += c;
+  if (wid == 0) {
+    long long t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, t, d);
+      if (lane >= d) t += y;
+    }
+    sh[lane] = t;  // inclusive warp totals
   }
-  s_part[t] = mine;
   __syncthreads();
-  // inclusive scan of s_part (Hillis-Steele)
-  for (int d = 1; d < nt; d <<= 1) {
-    long long y = t >= d ? s_part[t - d] : 0;
-    __syncthreads();
-    s_part[t] += y;
-    __syncthreads();
-  }
-  long long run = s_part[t] - mine;
-  for (int b = lo; b < hi; ++b) {
-    int f = fill_in[b];
-    long long c = bin_plasma[b] ? (use_slack ? f + (int)(slack * (float)f) + 8 : f) : 0;
-    if (run + c > capacity) c = run < capacity ? capacity - run : 0;  // never hand out room past the buffer
-    start[b] = (int)(run < capacity ? run : capacity);
-    cap[b] = (int)c;
-    fill_out[b] = 0;
-    run += c;
-  }
-  // totals
-  s_part[t] = sum_fill;
+  long long before = wid > 0 ? sh[wid - 1] : 0;
+  excl = before + x - v;
+  long long total = sh[(blockDim.x >> 5) - 1];
   __syncthreads();
-  for (int d = 512; d > 0; d >>= 1) {
-    if (t < d) s_part[t] += s_part[t + d];
-    __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(1024) k_layout_sums(const LayoutParams L) {
+  __shared__ long long sh[3 * 32];
+  const int s = blockIdx.y;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  long long v[3] = {0, 0, 0};
+  if (b < L.nbins) {
+    int f = L.fill_in[s][b], pl = L.bin_plasma[b];
+    v[0] = room_of(f, pl, 1, L.slack);
+    v[1] = room_of(f, pl, 0, L.slack);
+    v[2] = f;
   }
-  if (t == nt - 1) {
-    // run == total room after the last thread's chunk
-    long long room = run;
-    meta_out->ovf_base = (int)(room < capacity ? room : capacity);
-    meta_out->ovf_n = 0;
-    meta_out->total = 0;
+  block_sum_ll<3>(v, sh);
+  if (threadIdx.x < 3) L.part[((size_t)s * gridDim.x + blockIdx.x) * 4 + threadIdx.x] = v[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(1024) k_layout_scan(const LayoutParams L, int nblk) {
+  __shared__ long long sh[3 * 32];
+  __shared__ int s_use;
+  const int s = blockIdx.x;
+  const long long *part = L.part + (size_t)s * nblk * 4;
+  long long v[3] = {0, 0, 0};
+  if ((int)threadIdx.x < nblk) {
+    v[0] = part[threadIdx.x * 4 + 0];
+    v[1] = part[threadIdx.x * 4 + 1];
+    v[2] = part[threadIdx.x * 4 + 2];
   }
-  if (t == 0) meta_in->total = s_part[0];
+  long long tot[3] = {v[0], v[1], v[2]};
+  block_sum_ll<3>(tot, sh);
+  if (threadIdx.x == 0) s_use = tot[0] <= (long long)(0.9 * (double)L.capacity[s]) ? 1 : 0;
+  __syncthreads();
+  int use = s_use;
+  long long mine = use ? v[0] : v[1];
+  long long excl;
+  long long total = block_exscan_ll(mine, excl, sh);
+  if ((int)threadIdx.x < nblk) L.boff[(size_t)s * nblk + threadIdx.x] = excl;
+  if (threadIdx.x == 0) {
+    L.use_slack[s] = use;
+    L.meta_out[s]->ovf_base = (int)(total < L.capacity[s] ? total : L.capacity[s]);
+    L.meta_out[s]->ovf_n = 0;
+    L.meta_out[s]->total = 0;
+    L.meta_in[s]->total = tot[2];
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_layout_write(const LayoutParams L) {
+  __shared__ long long sh[32];
+  const int s = blockIdx.y;
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int use = L.use_slack[s];
+  long long c = 0;
+  if (b < L.nbins) c = room_of(L.fill_in[s][b], L.bin_plasma[b], use, L.slack);
+  long long excl;
+  block_exscan_ll(c, excl, sh);
+  if (b < L.nbins) {
+    long long run = L.boff[(size_t)s * gridDim.x + blockIdx.x] + excl;
+    long long cap = L.capacity[s];
+    if (run + c > cap) c = run < cap ? cap - run : 0;  // never hand out room past the buffer
+    L.start[s][b] = (int)(run < cap ? run : cap);
+    L.cap[s][b] = (int)c;
+    L.fill_out[s][b] = 0;
+  }
 }
 
 // Deposit of the read store's particles at their current x~ (start-up).
@@ -789,9 +845,12 @@ cudaError_t launch_deposit_only(const PushParams<T> &P, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_layout(const int *fill_in, const int8_t *bin_plasma, int nbins, float slack, int capacity, int *start,
-                          int *cap, int *fill_out, BinMeta *meta_out, BinMeta *meta_in, cudaStream_t st) {
-  k_layout<<<1, 1024, 0, st>>>(fill_in, bin_plasma, nbins, slack, capacity, start, cap, fill_out, meta_out, meta_in);
+cudaError_t launch_layout(const LayoutParams &L, cudaStream_t st) {
+  int nblk = (L.nbins + 1023) / 1024;
+  if (nblk > 1024) return cudaErrorInvalidValue;
+  k_layout_sums<<<dim3(nblk, 2), 1024, 0, st>>>(L);
+  k_layout_scan<<<2, 1024, 0, st>>>(L, nblk);
+  k_layout_write<<<dim3(nblk, 2), 1024, 0, st>>>(L);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,431 @@
+// solve.cu -- field solve of the finite-volume implicit Poisson system
+// sum_b G_ab (phi_a - phi_b) = qrhs_a on the free nodes (Eq. 1 of
+// arXiv:2310.04957), Dirichlet metal nodes held fixed.
+//
+// Both solvers are Jacobi-preconditioned conjugate gradients in the
+// Chronopoulos-Gear arrangement: the inner products of an iteration are
+// formed together, so each iteration needs one grid-wide reduction and one
+// barrier.  That barrier also publishes the vectors the next matrix-vector
+// product reads at neighbouring nodes; r, w and s are double-buffered so a
+// block rebuilds its neighbours' next preconditioned residual
+// u = M^-1 (r - alpha (w + beta s)) on the fly without a second barrier.
+//
+//   plain: FP64 throughout, warm start from phi, stop at ||r|| <= tol ||b||
+//          (b = node charge + Dirichlet lift), confirmed on the recomputed
+//          residual.
+//   mixed: FP64 residual and iterative refinement around FP32 inner solves of
+//          the normalised residual equation (all inner arithmetic, products and
+//          reductions in FP32).
+//
+// GB300 executes FP64 at 1/58 of the FP32 rate (one FP64 warp instruction
+// holds a sub-partition for ~68 cycles), so the FP64 work is kept to the
+// per-node arithmetic: nodes are spread evenly over all SMs, the scalar
+// recurrences run in one thread per block, convergence is tested on squared
+// norms.  One persistent cooperative launch; bounded barrier waits.
+#include <cstdint>
+
+#include "pic_device.cuh"
+#include "pic_kernels.h"
+
+namespace pic {
+
+__device__ bool grid_barrier(unsigned *bar, unsigned nblocks, long long limit, uint32_t *flags) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *gen = bar + 1;
+    unsigned g = *gen;
+    __threadfence();
+    unsigned prev = atomicAdd(bar, 1u);
+    int ok = 1;
+    if (prev == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > limit) {
+          ok = 0;
+          atomicOr(flags, 0x2u);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Sum K per-thread values of type A over the block; result returned to all threads.
+template <typename A, int K>
+__device__ __forceinline__ void block_sum(A v[K]) {
+  __shared__ A s[K][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    A x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s[k][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      A x = lane < nw ? s[k][lane] : (A)0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) s[k][0] = x;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = s[k][0];
+  __syncthreads();
+}
+
+// Grid reduction: block partials -> barrier -> every block sums all partials
+// in the same order (bit-identical totals in every block).  Partials are
+// double-buffered by parity so one barrier suffices.
+template <typename A, int K>
+__device__ __forceinline__ bool grid_sum(A v[K], A *partial, int parity, const PcgParams &P) {
+  block_sum<A, K>(v);
+  A *part = partial + parity * 4 * gridDim.x;
+  if (threadIdx.x < K) part[blockIdx.x * 4 + threadIdx.x] = v[threadIdx.x];
+  if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) return false;
+  A w[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) w[k] = (A)0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] += __ldcg(part + b * 4 + k);
+  }
+  block_sum<A, K>(w);
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = w[k];
+  return true;
+}
+
+// Contiguous chunk of nodes owned by this block.
+struct Range {
+  int lo, hi;
+};
+__device__ __forceinline__ Range block_range(int nn) {
+  int chunk = (nn + gridDim.x - 1) / gridDim.x;
+  int lo = blockIdx.x * chunk;
+  int hi = min(nn, lo + chunk);
+  return {lo, hi};
+}
+
+template <typename T>
+struct CgView {
+  T *r[2], *w[2], *s[2], *p, *x;
+  const T *Gr, *Gz, *dinv;
+};
+
+// u_{i+1} at node b from the buffers of iteration i (parity q).
+template <typename T>
+__device__ __forceinline__ T u_next(const CgView<T> &V, int q, int b, T alpha, T beta) {
+  T sv = __ldcg(V.w[q] + b) + beta * __ldcg(V.s[q] + b);
+  T rv = __ldcg(V.r[q] + b) - alpha * sv;
+  return __ldcg(V.dinv + b) * rv;
+}
+
+// One Chronopoulos-Gear iteration at this block's free nodes, reading parity q
+// and writing parity q^1; accumulates gamma = r.u, delta = w.u, rho = r.r.
+template <typename T>
+__device__ __forceinline__ void cg_iteration(const PcgParams &P, const CgView<T> &V, int q, T alpha, T beta,
+                                             T acc[3]) {
+  const int nr = P.nr, W = nr + 1;
+  const Range R = block_range(P.nn);
+  for (int a = R.lo + threadIdx.x; a < R.hi; a += blockDim.x) {
+    if (P.node_kind[a] != 0) continue;
+    int j = a / W, i = a - j * W;
+    T ra = __ldcg(V.r[q] + a), wa = __ldcg(V.w[q] + a), sa = __ldcg(V.s[q] + a), da = __ldcg(V.dinv + a);
+    T pa = da * ra + beta * __ldcg(V.p + a);
+    T snew = wa + beta * sa;
+    T rnew = ra - alpha * snew;
+    T unew = da * rnew;
+    T wnew = (T)0;
+    if (i > 0) wnew += __ldcg(V.Gr + j * nr + i - 1) * (unew - u_next(V, q, a - 1, alpha, beta));
+    if (i < nr) wnew += __ldcg(V.Gr + j * nr + i) * (unew - u_next(V, q, a + 1, alpha, beta));
+    if (j > 0) wnew += __ldcg(V.Gz + (j - 1) * W + i) * (unew - u_next(V, q, a - W, alpha, beta));
+    if (j < P.nz) wnew += __ldcg(V.Gz + j * W + i) * (unew - u_next(V, q, a + W, alpha, beta));
+    V.x[a] = V.x[a] + alpha * pa;
+    V.p[a] = pa;
+    V.r[q ^ 1][a] = rnew;
+    V.w[q ^ 1][a] = wnew;
+    V.s[q ^ 1][a] = snew;
+    acc[0] += rnew * unew;
+    acc[1] += wnew * unew;
+    acc[2] += rnew * rnew;
+  }
+}
+
+// w_0 = A M^-1 r_0 from buffer 0 (r_0 complete), plus the first products.
+template <typename T>
+__device__ __forceinline__ void cg_start(const PcgParams &P, const CgView<T> &V, T acc[3]) {
+  const int nr = P.nr, W = nr + 1;
+  const Range R = block_range(P.nn);
+  for (int a = R.lo + threadIdx.x; a < R.hi; a += blockDim.x) {
+    if (P.node_kind[a] != 0) continue;
+    int j = a / W, i = a - j * W;
+    T ra = __ldcg(V.r[0] + a);
+    T ua = __ldcg(V.dinv + a) * ra;
+    T w = (T)0;
+    if (i > 0) w += __ldcg(V.Gr + j * nr + i - 1) * (ua - __ldcg(V.dinv + a - 1) * __ldcg(V.r[0] + a - 1));
+    if (i < nr) w += __ldcg(V.Gr + j * nr + i) * (ua - __ldcg(V.dinv + a + 1) * __ldcg(V.r[0] + a + 1));
+    if (j > 0) w += __ldcg(V.Gz + (j - 1) * W + i) * (ua - __ldcg(V.dinv + a - W) * __ldcg(V.r[0] + a - W));
+    if (j < P.nz) w += __ldcg(V.Gz + j * W + i) * (ua - __ldcg(V.dinv + a + W) * __ldcg(V.r[0] + a + W));
+    V.w[0][a] = w;
+    acc[0] += ra * ua;
+    acc[1] += w * ua;
+    acc[2] += ra * ra;
+  }
+}
+
+// FP64 residual r = qrhs - A phi at this block's free nodes, with ||b||^2 and
+// ||r||^2 (b = qrhs + Dirichlet lift).
+__device__ __forceinline__ void residual64(const PcgParams &P, double *r64, double acc[2]) {
+  const int nr = P.nr, W = nr + 1;
+  const Range R = block_range(P.nn);
+  for (int a = R.lo + threadIdx.x; a < R.hi; a += blockDim.x) {
+    if (P.node_kind[a] != 0) continue;
+    int j = a / W, i = a - j * W;
+    double pa = __ldcg(P.phi + a), ax = 0.0, lift = 0.0;
+    if (i > 0) {
+      double g = __ldg(P.Gr + j * nr + i - 1), pb = __ldcg(P.phi + a - 1);
+      ax += g * (pa - pb);
+      if (P.node_kind[a - 1] != 0) lift += g * pb;
+    }
+    if (i < nr) {
+      double g = __ldg(P.Gr + j * nr + i), pb = __ldcg(P.phi + a + 1);
+      ax += g * (pa - pb);
+      if (P.node_kind[a + 1] != 0) lift += g * pb;
+    }
+    if (j > 0) {
+      double g = __ldg(P.Gz + (j - 1) * W + i), pb = __ldcg(P.phi + a - W);
+      ax += g * (pa - pb);
+      if (P.node_kind[a - W] != 0) lift += g * pb;
+    }
+    if (j < P.nz) {
+      double g = __ldg(P.Gz + j * W + i), pb = __ldcg(P.phi + a + W);
+      ax += g * (pa - pb);
+      if (P.node_kind[a + W] != 0) lift += g * pb;
+    }
+    double q = __ldg(P.qrhs + a);
+    double r = q - ax, b = q + lift;
+    r64[a] = r;
+    acc[0] += b * b;
+    acc[1] += r * r;
+  }
+}
+
+__device__ __forceinline__ bool finite(double x) { return isfinite(x); }
+__device__ __forceinline__ bool finite(float x) { return isfinite(x); }
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+
+// Inner CG loop.  Entry: parity-0 buffers hold r_0, w_0 (s = p = 0) and tot =
+// (gamma_0, delta_0, rho_0).  Runs until rho <= stop2 or *it reaches cap.
+// The scalar recurrence runs in thread 0 and is broadcast through shared
+// memory.  Returns 0 ok, -5 timeout, -7 non-finite, 1 stopped at the cap.
+template <typename T>
+__device__ int cg_loop(const PcgParams &P, const CgView<T> &V, T *partial, T tot[3], T stop2, int cap, int *it,
+                       int *parity) {
+  __shared__ T s_ab[2];
+  __shared__ int s_state;
+  T gamma = tot[0], delta = tot[1], rho = tot[2];
+  T gamma_prev = (T)1, alpha_prev = (T)1;
+  int q = 0, k = 0;
+  while (true) {
+    if (threadIdx.x == 0) {
+      int state = 0;
+      if (!finite(rho) || !finite(gamma) || !finite(delta)) state = -7;
+      else if (rho <= stop2) state = 2;
+      else if (*it >= cap) state = 1;
+      else {
+        T beta = k == 0 ? (T)0 : gamma * recip(gamma_prev);
+        T den = k == 0 ? delta : delta - beta * gamma * recip(alpha_prev);
+        T alpha = gamma * recip(den);
+        s_ab[0] = alpha;
+        s_ab[1] = beta;
+      }
+      s_state = state;
+    }
+    __syncthreads();
+    int state = s_state;
+    if (state == 2) return 0;
+    if (state != 0) return state;
+    T alpha = s_ab[0], beta = s_ab[1];
+    T acc[3] = {(T)0, (T)0, (T)0};
+    cg_iteration<T>(P, V, q, alpha, beta, acc);
+    if (!grid_sum<T, 3>(acc, partial, *parity, P)) return -5;
+    *parity ^= 1;
+    q ^= 1;
+    ++k;
+    ++*it;
+    gamma_prev = gamma;
+    alpha_prev = alpha;
+    gamma = acc[0];
+    delta = acc[1];
+    rho = acc[2];
+  }
+}
+
+// ---- plain FP64 ------------------------------------------------------------------
+__global__ void __launch_bounds__(kPcgThreads) k_pcg(const PcgParams P) {
+  const int nn = P.nn;
+  CgView<double> V;
+  for (int k = 0; k < 2; ++k) {
+    V.r[k] = P.work + (size_t)k * nn;
+    V.w[k] = P.work + (size_t)(2 + k) * nn;
+    V.s[k] = P.work + (size_t)(4 + k) * nn;
+  }
+  V.p = P.work + (size_t)6 * nn;
+  V.x = P.phi;
+  V.Gr = P.Gr;
+  V.Gz = P.Gz;
+  V.dinv = P.dinv;
+  const Range R = block_range(nn);
+  int it = 0, parity = 0, status = -4;
+  double b2 = 0.0, r2 = 0.0;
+  for (int pass = 0; pass < 32; ++pass) {
+    for (int a = R.lo + threadIdx.x; a < R.hi; a += blockDim.x) {
+      for (int k = 0; k < 2; ++k) { V.r[k][a] = 0.0; V.w[k][a] = 0.0; V.s[k][a] = 0.0; }
+      V.p[a] = 0.0;
+    }
+    if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { status = -5; break; }
+    double acc2[2] = {0.0, 0.0};
+    residual64(P, V.r[0], acc2);
+    if (!grid_sum<double, 2>(acc2, P.partial, parity, P)) { status = -5; break; }
+    parity ^= 1;
+    b2 = acc2[0];
+    r2 = acc2[1];
+    double target2 = b2 > 0.0 ? P.tol * P.tol * b2 : 1e-60;
+    if (!isfinite(r2)) { status = -7; break; }
+    if (r2 <= target2) { status = 0; break; }
+    if (it >= P.maxit) { status = -4; break; }
+    double tot[3] = {0.0, 0.0, 0.0};
+    cg_start<double>(P, V, tot);
+    if (!grid_sum<double, 3>(tot, P.partial, parity, P)) { status = -5; break; }
+    parity ^= 1;
+    int st = cg_loop<double>(P, V, P.partial, tot, target2, P.maxit, &it, &parity);
+    if (st == -5 || st == -7) { status = st; break; }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.out[0] = (double)it;
+    P.out[1] = b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
+    P.out[2] = (double)status;
+    P.out[3] = 0.0;
+    if (status == -4) atomicOr(P.flags, 0x4u);
+    if (status == -7) atomicOr(P.flags, 0x8u);
+  }
+}
+
+// ---- mixed: FP64 refinement around FP32 inner CG ---------------------------------------
+__global__ void __launch_bounds__(kPcgThreads) k_pcg_mixed(const PcgParams P) {
+  const int nn = P.nn, nr = P.nr, W = nr + 1;
+  float *f = P.work32;
+  CgView<float> V;
+  for (int k = 0; k < 2; ++k) {
+    V.r[k] = f + (size_t)k * nn;
+    V.w[k] = f + (size_t)(2 + k) * nn;
+    V.s[k] = f + (size_t)(4 + k) * nn;
+  }
+  V.p = f + (size_t)6 * nn;
+  V.x = f + (size_t)7 * nn;
+  float *gr32 = f + (size_t)8 * nn, *gz32 = f + (size_t)9 * nn, *dinv32 = f + (size_t)10 * nn;
+  float *part32 = reinterpret_cast<float *>(P.partial + 8 * gridDim.x);  // FP32 partials after the FP64 ones
+  V.Gr = gr32;
+  V.Gz = gz32;
+  V.dinv = dinv32;
+  double *r64 = P.work;
+  const Range R = block_range(nn);
+  // FP32 operator, scaled by the largest diagonal so its entries are O(1)
+  for (int a = R.lo + threadIdx.x; a < R.hi; a += blockDim.x) {
+    int j = a / W, i = a - j * W;
+    if (i < nr) gr32[j * nr + i] = (float)(__ldg(P.Gr + j * nr + i) * P.gscale);
+    if (j < P.nz) gz32[j * W + i] = (float)(__ldg(P.Gz + j * W + i) * P.gscale);
+    dinv32[a] = (float)(__ldg(P.dinv + a) / P.gscale);
+  }
+  int it = 0, parity = 0, status = -4, outer = 0;
+  double b2 = 0.0, r2 = 0.0;
+  for (outer = 0; outer < 64; ++outer) {
+    for (int a = R.lo + threadIdx.x; a < R.hi; a += blockDim.x) {
+      for (int k = 0; k < 2; ++k) { V.r[k][a] = 0.0f; V.w[k][a] = 0.0f; V.s[k][a] = 0.0f; }
+      V.p[a] = 0.0f;
+      V.x[a] = 0.0f;
+    }
+    if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { status = -5; break; }
+    double acc2[2] = {0.0, 0.0};
+    residual64(P, r64, acc2);
+    if (!grid_sum<double, 2>(acc2, P.partial, parity, P)) { status = -5; break; }
+    parity ^= 1;
+    b2 = acc2[0];
+    r2 = acc2[1];
+    double target2 = b2 > 0.0 ? P.tol * P.tol * b2 : 1e-60;
+    if (!isfinite(r2)) { status = -7; break; }
+    if (r2 <= target2) { status = 0; break; }
+    if (it >= P.maxit) { status = -4; break; }
+    // inner right-hand side = residual / ||residual|| (unit 2-norm, FP32-safe)
+    double inv = rsqrt(r2);
+    for (int a = R.lo + threadIdx.x; a < R.hi; a += blockDim.x)
+      if (P.node_kind[a] == 0) V.r[0][a] = (float)(r64[a] * inv);
+    if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { status = -5; break; }
+    float tot[3] = {0.0f, 0.0f, 0.0f};
+    cg_start<float>(P, V, tot);
+    if (!grid_sum<float, 3>(tot, part32, parity, P)) { status = -5; break; }
+    parity ^= 1;
+    // inner reduction: inner_tol, or just what the outer target still needs
+    float stop = P.inner_tol;
+    float need = (float)sqrt(target2 / r2);
+    if (need > stop) stop = need;
+    int st = cg_loop<float>(P, V, part32, tot, stop * stop, P.maxit, &it, &parity);
+    if (st == -5 || st == -7) { status = st; break; }
+    // phi += ||residual|| x (the operator was scaled by gscale, so x carries 1/gscale)
+    double back = sqrt(r2) * P.gscale;
+    for (int a = R.lo + threadIdx.x; a < R.hi; a += blockDim.x)
+      if (P.node_kind[a] == 0) P.phi[a] += (double)V.x[a] * back;
+    if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { status = -5; break; }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.out[0] = (double)it;
+    P.out[1] = b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
+    P.out[2] = (double)status;
+    P.out[3] = (double)outer;
+    if (status == -4) atomicOr(P.flags, 0x4u);
+    if (status == -7) atomicOr(P.flags, 0x8u);
+  }
+}
+
+int pcg_grid_size(int device) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  return sms;  // one block per SM (kPcgThreads threads)
+}
+
+static cudaError_t launch_coop(void (*kern)(PcgParams), const PcgParams &P, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kPcgThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, P);
+}
+
+cudaError_t launch_pcg(const PcgParams &P, int grid, cudaStream_t st) { return launch_coop(k_pcg, P, grid, st); }
+
+cudaError_t launch_pcg_mixed(const PcgParams &P, int grid, cudaStream_t st) {
+  return launch_coop(k_pcg_mixed, P, grid, st);
+}
+
+}  // namespace pic

@@ -19,7 +19,7 @@
 namespace {
 
 constexpr int kMaxPcgBlocks = 1024;
-constexpr size_t kVecs = 5;  // r, z, p, Ap, diagonal inverse
+constexpr size_t kVecs = 9;  // 8 solver work vectors + the diagonal inverse
 constexpr size_t kPartial = 8 * (kMaxPcgBlocks + 32);
 constexpr size_t kStaticDoubles = kVecs * PIC_STATIC_MAX_NODES + kPartial + 8 + 8;
 
@@ -77,8 +77,8 @@ extern "C" int pic_pcg_solve_static(int32_t nr, int32_t nz, const int8_t *node_k
   int grid = pic::pcg_grid_size(dev);
   if (grid > kMaxPcgBlocks) grid = kMaxPcgBlocks;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  double *r = base, *z = r + PIC_STATIC_MAX_NODES, *p = z + PIC_STATIC_MAX_NODES, *Ap = p + PIC_STATIC_MAX_NODES;
-  double *dinv = Ap + PIC_STATIC_MAX_NODES, *partial = dinv + PIC_STATIC_MAX_NODES, *out = partial + kPartial;
+  double *work = base, *dinv = work + 8 * (size_t)PIC_STATIC_MAX_NODES;
+  double *partial = dinv + PIC_STATIC_MAX_NODES, *out = partial + kPartial;
   unsigned *bar = reinterpret_cast<unsigned *>(out + 8);
   // what must start at zero: the grid-barrier counter and the result slots
   if (cudaMemsetAsync(out, 0, 16 * sizeof(double), s) != cudaSuccess) return PIC_ECUDA;
@@ -90,11 +90,13 @@ extern "C" int pic_pcg_solve_static(int32_t nr, int32_t nz, const int8_t *node_k
   P.nr = nr; P.nz = nz; P.nn = (int)nn;
   P.node_kind = node_kind;
   P.Gr = Gr; P.Gz = Gz; P.dinv = dinv; P.qrhs = qrhs; P.phi = phi;
-  P.r = r; P.z = z; P.p = p; P.Ap = Ap;
+  P.work = work;
+  P.work32 = nullptr;
   P.partial = partial;
   P.bar = bar;
   P.tol = tol;
   P.maxit = maxit;
+  P.gscale = 1.0;
   P.out = out;
   P.flags = reinterpret_cast<uint32_t *>(bar + 2);
   P.spin_limit = 4000000000ll;
