@@ -471,8 +471,8 @@ bool check_config(const pic_config *c) {
   if (!(c->m[0] > 0) || !(c->m[1] > 0) || !(c->m_gas > 0)) return false;
   for (int k = 0; k + 1 < c->n_xs; ++k)
     if (!(c->xs_energy[k + 1] > c->xs_energy[k]) || !(c->xs_energy[k] > 0)) return false;
-  int tr = c->tile_r > 0 ? c->tile_r : 8, tz = c->tile_z > 0 ? c->tile_z : 4;
-  if (tr * tz > kMaxTileCells || tr < 1 || tz < 1) return false;
+  int tr = c->tile_r > 0 ? c->tile_r : 4, tz = c->tile_z > 0 ? c->tile_z : 4;
+  if (!tile_supported(tr, tz)) return false;
   if (c->circuit == PIC_CIRCUIT_RLC && !(c->circ[0] >= 0 && c->circ[1] > 0 && c->circ[2] > 0)) return false;
   if (c->circuit == PIC_CIRCUIT_IMN)
     for (int k = 0; k < 8; ++k)
@@ -654,7 +654,7 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
   h->slack = cfg->bin_slack > 0 ? (float)cfg->bin_slack : 0.25f;
   h->capacity[0] = cfg->capacity[0];
   h->capacity[1] = cfg->capacity[1];
-  int TX = cfg->tile_r > 0 ? cfg->tile_r : 8, TY = cfg->tile_z > 0 ? cfg->tile_z : 4;
+  int TX = cfg->tile_r > 0 ? cfg->tile_r : 4, TY = cfg->tile_z > 0 ? cfg->tile_z : 4;
   h->map.nr = h->nr; h->map.nz = h->nz; h->map.TX = TX; h->map.TY = TY;
   h->map.ntx = (h->nr + TX - 1) / TX; h->map.nty = (h->nz + TY - 1) / TY;
   h->nbins = h->map.nbins();

@@ -115,6 +115,7 @@ struct DiagParams {
 };
 
 template <typename T> cudaError_t launch_particles(const PushParams<T> &P, cudaStream_t st);
+bool tile_supported(int tx, int ty);
 template <typename T> cudaError_t launch_deposit_only(const PushParams<T> &P, cudaStream_t st);
 struct LayoutParams {
   const int *fill_in[2];

@@ -46,6 +46,23 @@ __device__ __forceinline__ void m_sincospi(float x, float *s, float *c) { sincos
 __device__ __forceinline__ void m_sincospi(double x, double *s, double *c) { sincospi(x, s, c); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
+// Reciprocal and reciprocal square root: FP32 uses the correctly rounded
+// reciprocal and one Newton step on the hardware rsqrt estimate (error ~1 ulp,
+// unbiased); FP64 keeps IEEE division and square root.
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rsq(float q) {
+  float y = rsqrtf(q);
+  return y * (1.5f - 0.5f * q * y * y);
+}
+__device__ __forceinline__ double rsq(double q) { return 1.0 / sqrt(q); }
+
+// Bin of cell (i, j) for compile-time tile sizes (powers of two).
+template <int TX, int TY>
+__device__ __forceinline__ int bin_key(int i, int j, int ntx) {
+  int tx = i / TX, ty = j / TY;
+  return ((ty * ntx + tx) * TY + (j & (TY - 1))) * TX + (i & (TX - 1));
+}
 
 template <typename T>
 struct Part {
@@ -163,11 +180,16 @@ __device__ __forceinline__ void predict(const PushParams<T> &P, Part<T> &p) {
   T r = ((T)p.ci + p.fr) * P.dr;
   T dx = P.dt * ur, Y = P.dt * ut;
   T X = r + dx;
-  T rn = m_sqrt(X * X + Y * Y);
+  T q = X * X + Y * Y;
+  T ca = (T)1, sa = (T)0, rn = (T)0;
+  if (q > (T)0) {
+    T inv = rsq(q);
+    rn = q * inv;
+    ca = X * inv;
+    sa = Y * inv;
+  }
   T den = rn + r;
-  T disp = den > (T)0 ? (dx * ((T)2 * r + dx) + Y * Y) / den : (T)0;
-  T ca = (T)1, sa = (T)0;
-  if (rn > (T)0) { ca = X / rn; sa = Y / rn; }
+  T disp = den > (T)0 ? (dx * ((T)2 * r + dx) + Y * Y) * rcp(den) : (T)0;
   T vr = ca * p.vr + sa * p.vt, vt = -sa * p.vr + ca * p.vt;
   T ar = ca * p.ar + sa * p.at, at = -sa * p.ar + ca * p.at;
   p.vr = vr; p.vt = vt; p.ar = ar; p.at = at;
@@ -291,7 +313,7 @@ __device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T
   Outcome o{0, -1, 0, -1, 0};
   // gather E at x~_n with the deposit weights: linear in z, by annulus area in r
   T ir = (T)p.ci;
-  T a = p.fr * ((T)2 * ir + p.fr) / ((T)2 * ir + (T)1);
+  T a = p.fr * ((T)2 * ir + p.fr) * rcp((T)2 * ir + (T)1);
   T b = p.fz;
   using E2 = typename V2<T>::type;
   const E2 *E = reinterpret_cast<const E2 *>(P.E);
@@ -343,13 +365,16 @@ __device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T
   return o;
 }
 
+// Store a particle; its cell is implied by the bin except in the overflow
+// region (ovf = true), where it is stored explicitly.
 template <typename T>
-__device__ __forceinline__ void store_particle(const StoreView<T> &S, int slot, const Part<T> &p, int cell_rowmajor) {
+__device__ __forceinline__ void store_particle(const StoreView<T> &S, int slot, const Part<T> &p, int cell_rowmajor,
+                                               bool ovf) {
   S.fr[slot] = p.fr; S.fz[slot] = p.fz;
   S.vr[slot] = p.vr; S.vt[slot] = p.vt; S.vz[slot] = p.vz;
   S.ar[slot] = p.ar; S.at[slot] = p.at; S.az[slot] = p.az;
   S.id[slot] = p.id;
-  S.cell[slot] = cell_rowmajor;
+  if (ovf) S.cell[slot] = cell_rowmajor;
 }
 
 // Slot in the write store for a particle of bin `key`; -1 if dropped.
@@ -389,10 +414,30 @@ __device__ __forceinline__ void qweights(T a, T b, T scale, unsigned long long o
   W[0] = one - A - B + W11;
 }
 
-template <typename T>
-__device__ __forceinline__ void node_weights_q(const PushParams<T> &P, const Part<T> &p, unsigned long long W[4]) {
-  T ir = (T)p.ci;
-  T a = p.fr * ((T)2 * ir + p.fr) / ((T)2 * ir + (T)1);
+// FP32 path: 2^26 fixed point with 32-bit conversions and one 32x32->64
+// product (the four weights still sum to exactly 2^26).
+__device__ __forceinline__ void qweights32(float a, float b, unsigned long long W[4]) {
+  const unsigned one = 1u << 26;
+  unsigned A = __float2uint_rn(a * 67108864.0f), B = __float2uint_rn(b * 67108864.0f);
+  A = A > one ? one : A;
+  B = B > one ? one : B;
+  unsigned W11 = (unsigned)(((unsigned long long)A * B + (1ull << 25)) >> 26);
+  W[3] = W11;
+  W[1] = A - W11;
+  W[2] = B - W11;
+  W[0] = one - A - B + W11;
+}
+
+__device__ __forceinline__ void node_weights_q(const PushParams<float> &P, const Part<float> &p, unsigned long long W[4]) {
+  float ir = (float)p.ci;
+  float a = p.fr * (2.0f * ir + p.fr) * rcp(2.0f * ir + 1.0f);
+  qweights32(a, p.fz, W);
+}
+
+__device__ __forceinline__ void node_weights_q(const PushParams<double> &P, const Part<double> &p,
+                                               unsigned long long W[4]) {
+  double ir = (double)p.ci;
+  double a = p.fr * (2.0 * ir + p.fr) * rcp(2.0 * ir + 1.0);
   qweights(a, p.fz, P.dep_scale, P.dep_one, W);
 }
 
@@ -411,17 +456,26 @@ __device__ __forceinline__ void deposit_global(const PushParams<T> &P, int s, co
 
 struct TileCtx {
   unsigned long long *tile;  // shared node tile, (TX+1+2H) x (TY+1+2H), or nullptr
-  int ci0, cj0, w, h, TX, TY;
+  int ci0, cj0;
 };
+
+// 64-bit shared accumulator updated with 32-bit atomics (faster than 64-bit
+// shared atomics): add to the low word, carry into the high word on wrap.
+__device__ __forceinline__ void add_shared64(unsigned long long *t, unsigned v) {
+  unsigned *w = reinterpret_cast<unsigned *>(t);
+  unsigned old = atomicAdd(w, v);
+  if (old + v < old) atomicAdd(w + 1, 1u);
+}
 
 // Warp-collective: write the alive lanes' particles into their new bins of the
 // species' write store and deposit them.  All 32 lanes must call it.
-template <typename T>
+template <typename T, int TX, int TY>
 __device__ __forceinline__ void emit(const PushParams<T> &P, int s, bool alive, const Part<T> &p, const TileCtx &tc) {
+  constexpr int TW = TX + 1 + 2 * kHalo;
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const StoreView<T> &S = P.out[s];
-  int key = alive ? P.map.bin(p.ci, p.cj) : -1;
+  int key = alive ? bin_key<TX, TY>(p.ci, p.cj, P.map.ntx) : -1;
   unsigned peers = __match_any_sync(FULL, key);
   int leader = __ffs(peers) - 1;
   int base = 0;
@@ -429,50 +483,40 @@ __device__ __forceinline__ void emit(const PushParams<T> &P, int s, bool alive, 
   base = __shfl_sync(FULL, base, leader);
   if (key >= 0) {
     int pos = base + __popc(peers & ((1u << lane) - 1u));
-    int slot = pos < __ldg(S.cap + key) ? __ldg(S.start + key) + pos : overflow_slot(P, S);
-    if (slot >= 0) store_particle(S, slot, p, p.cj * P.nr + p.ci);
+    bool ovf = !(pos < __ldg(S.cap + key));
+    int slot = ovf ? overflow_slot(P, S) : __ldg(S.start + key) + pos;
+    if (slot >= 0) store_particle(S, slot, p, p.cj * P.nr + p.ci, ovf);
   }
   // deposit
   unsigned long long W[4] = {0, 0, 0, 0};
   if (alive) node_weights_q(P, p, W);
   int li = p.ci - tc.ci0 + kHalo, lj = p.cj - tc.cj0 + kHalo;
-  bool in_tile = tc.tile != nullptr && li >= 0 && lj >= 0 && li < tc.TX + 2 * kHalo && lj < tc.TY + 2 * kHalo;
+  bool in_tile = tc.tile != nullptr && li >= 0 && lj >= 0 && li < TX + 2 * kHalo && lj < TY + 2 * kHalo;
   if (sizeof(T) == 4) {
-    // 32-bit fixed point: sum lanes of the same new cell, leader adds once
-    unsigned leaders = __ballot_sync(FULL, key >= 0 && lane == leader);
-    while (leaders) {
-      int l = __ffs(leaders) - 1;
-      leaders &= leaders - 1u;
-      unsigned m = __shfl_sync(FULL, peers, l);
-      bool in = (m >> lane) & 1u;
-      unsigned s0 = __reduce_add_sync(FULL, in ? (unsigned)W[0] : 0u);
-      unsigned s1 = __reduce_add_sync(FULL, in ? (unsigned)W[1] : 0u);
-      unsigned s2 = __reduce_add_sync(FULL, in ? (unsigned)W[2] : 0u);
-      unsigned s3 = __reduce_add_sync(FULL, in ? (unsigned)W[3] : 0u);
-      if (lane == l) {
-        if (in_tile) {
-          unsigned long long *t = tc.tile + lj * tc.w + li;
-          if (s0) atomicAdd(t, (unsigned long long)s0);
-          if (s1) atomicAdd(t + 1, (unsigned long long)s1);
-          if (s2) atomicAdd(t + tc.w, (unsigned long long)s2);
-          if (s3) atomicAdd(t + tc.w + 1, (unsigned long long)s3);
-        } else {
-          int n00 = p.cj * (P.nr + 1) + p.ci;
-          unsigned long long *d = P.dep[s];
-          if (s0) atomicAdd(d + n00, (unsigned long long)s0);
-          if (s1) atomicAdd(d + n00 + 1, (unsigned long long)s1);
-          if (s2) atomicAdd(d + n00 + P.nr + 1, (unsigned long long)s2);
-          if (s3) atomicAdd(d + n00 + P.nr + 2, (unsigned long long)s3);
-        }
+    // 32-bit fixed point: each group of lanes with the same new cell (disjoint
+    // masks from match_any) reduces its four node weights with one redux.sync
+    // per node; the group's lanes then share the four atomic adds by rank.
+    unsigned s4[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s4[k] = __reduce_add_sync(peers, (unsigned)W[k]);
+    if (key >= 0) {
+      const int rank = __popc(peers & ((1u << lane) - 1u)), size = __popc(peers);
+      const int n00 = p.cj * (P.nr + 1) + p.ci;
+      for (int n = rank; n < 4; n += size) {
+        unsigned v = n == 0 ? s4[0] : (n == 1 ? s4[1] : (n == 2 ? s4[2] : s4[3]));
+        if (!v) continue;
+        int dx = n & 1, dy = n >> 1;
+        if (in_tile) add_shared64(tc.tile + (lj + dy) * TW + li + dx, v);
+        else atomicAdd(P.dep[s] + n00 + dy * (P.nr + 1) + dx, (unsigned long long)v);
       }
     }
   } else if (alive) {
     if (in_tile) {
-      unsigned long long *t = tc.tile + lj * tc.w + li;
+      unsigned long long *t = tc.tile + lj * TW + li;
       atomicAdd(t, W[0]);
       atomicAdd(t + 1, W[1]);
-      atomicAdd(t + tc.w, W[2]);
-      atomicAdd(t + tc.w + 1, W[3]);
+      atomicAdd(t + TW, W[2]);
+      atomicAdd(t + TW + 1, W[3]);
     } else {
       int n00 = p.cj * (P.nr + 1) + p.ci;
       unsigned long long *d = P.dep[s];
@@ -486,7 +530,7 @@ __device__ __forceinline__ void emit(const PushParams<T> &P, int s, bool alive, 
 
 // A newborn ion from an electron CTA: predictor, absorption, write, deposit
 // (per lane: births are rare).
-template <typename T>
+template <typename T, int TX, int TY>
 __device__ __forceinline__ void emit_ion_birth(const PushParams<T> &P, Part<T> &bi) {
   predict(P, bi);
   if (!in_plasma(P, bi.ci, bi.cj)) {
@@ -498,10 +542,11 @@ __device__ __forceinline__ void emit_ion_birth(const PushParams<T> &P, Part<T> &
     return;
   }
   const StoreView<T> &S = P.out[1];
-  int key = P.map.bin(bi.ci, bi.cj);
+  int key = bin_key<TX, TY>(bi.ci, bi.cj, P.map.ntx);
   int pos = atomicAdd(S.fill + key, 1);
-  int slot = pos < __ldg(S.cap + key) ? __ldg(S.start + key) + pos : overflow_slot(P, S);
-  if (slot >= 0) store_particle(S, slot, bi, bi.cj * P.nr + bi.ci);
+  bool ovf = !(pos < __ldg(S.cap + key));
+  int slot = ovf ? overflow_slot(P, S) : __ldg(S.start + key) + pos;
+  if (slot >= 0) store_particle(S, slot, bi, bi.cj * P.nr + bi.ci, ovf);
   deposit_global(P, 1, bi);
 }
 
@@ -513,6 +558,7 @@ __device__ __forceinline__ void count_warp(unsigned long long *c, bool pred) {
 
 template <typename T>
 __device__ __forceinline__ void tally(const PushParams<T> &P, int s, const Outcome &o, bool active) {
+  if (!__any_sync(0xffffffffu, active && (o.abs_kind >= 0 || o.coll >= 0))) return;
   count_warp(P.counters + CNT_ABS + 3 * s + 0, active && o.abs_kind == 0);
   count_warp(P.counters + CNT_ABS + 3 * s + 1, active && o.abs_kind == 1);
   count_warp(P.counters + CNT_ABS + 3 * s + 2, active && o.abs_kind == 2);
@@ -532,13 +578,13 @@ __device__ __forceinline__ void load_particle(const StoreView<T> &S, int slot, P
 
 // Process one particle (already loaded) of species s: step, tallies, emit,
 // births.  Warp-collective.
-template <typename T>
+template <typename T, int TX, int TY>
 __device__ __forceinline__ void process(const PushParams<T> &P, int s, bool active, Part<T> &p, const TileCtx &tc) {
   Part<T> be = p, bi = p;
   Outcome o{0, -1, 0, -1, 0};
   if (active) o = advance(P, s, p, be, bi);
   tally(P, s, o, active);
-  emit(P, s, active && o.alive, p, tc);
+  emit<T, TX, TY>(P, s, active && o.alive, p, tc);
   bool birth = active && o.birth;
   if (__any_sync(0xffffffffu, birth)) {
     count_warp(P.counters + CNT_BORN + 0, birth);
@@ -555,19 +601,20 @@ __device__ __forceinline__ void process(const PushParams<T> &P, int s, bool acti
         if (k == 2) atomicAdd(P.surf[0] + node, 1ull);
       }
     }
-    emit(P, 0, e_alive, be, tc);
-    if (birth) emit_ion_birth(P, bi);
+    emit<T, TX, TY>(P, 0, e_alive, be, tc);
+    if (birth) emit_ion_birth<T, TX, TY>(P, bi);
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kThreads) k_particles(const PushParams<T> P) {
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_particles(const PushParams<T> P) {
+  constexpr int per = TX * TY;
+  constexpr int TW = TX + 1 + 2 * kHalo, TH = TY + 1 + 2 * kHalo;
   const int s = blockIdx.y;
   const StoreView<T> &A = P.in[s];
-  const int TX = P.map.TX, TY = P.map.TY, per = TX * TY;
-  extern __shared__ unsigned long long smem[];
-  __shared__ int s_pre[kMaxTileCells + 1];
-  __shared__ int s_off[kMaxTileCells];
+  __shared__ unsigned long long smem[TW * TH];
+  __shared__ int s_pre[per + 1];
+  __shared__ int s_off[per];
   const int ntiles = P.map.ntiles();
   if ((int)blockIdx.x < ntiles) {
     const int tile = blockIdx.x;
@@ -577,14 +624,11 @@ __global__ void __launch_bounds__(kThreads) k_particles(const PushParams<T> P) {
     tc.tile = smem;
     tc.ci0 = txi * TX;
     tc.cj0 = tyi * TY;
-    tc.TX = TX;
-    tc.TY = TY;
-    tc.w = TX + 1 + 2 * kHalo;
-    tc.h = TY + 1 + 2 * kHalo;
-    for (int k = threadIdx.x; k < tc.w * tc.h; k += blockDim.x) smem[k] = 0ull;
+    for (int k = threadIdx.x; k < TW * TH; k += blockDim.x) smem[k] = 0ull;
     if (threadIdx.x < 32) {
-      // prefix of the tile's in-bin counts (per <= kMaxTileCells, a multiple of 32 handled in chunks)
+      // prefix of the tile's in-bin counts
       int carry = 0;
+#pragma unroll
       for (int c0 = 0; c0 < per; c0 += 32) {
         int b = c0 + threadIdx.x;
         int n = 0, off = 0;
@@ -612,34 +656,32 @@ __global__ void __launch_bounds__(kThreads) k_particles(const PushParams<T> P) {
       Part<T> p;
       p.ci = 0; p.cj = 0;
       if (active) {
-        int lo = 0, hi = per;  // s_pre[lo] <= k < s_pre[hi]
-        while (hi - lo > 1) {
-          int mid = (lo + hi) >> 1;
-          if (s_pre[mid] <= k) lo = mid; else hi = mid;
-        }
+        int lo = 0;  // largest bin with s_pre[lo] <= k
+#pragma unroll
+        for (int step = per / 2; step >= 1; step >>= 1)
+          if (lo + step < per && s_pre[lo + step] <= k) lo += step;
         int slot = s_off[lo] + (k - s_pre[lo]);
         load_particle(A, slot, p);
-        p.ci = tc.ci0 + (lo % TX);
+        p.ci = tc.ci0 + (lo & (TX - 1));
         p.cj = tc.cj0 + (lo / TX);
       }
-      process(P, s, active, p, tc);
+      process<T, TX, TY>(P, s, active, p, tc);
     }
     __syncthreads();
     unsigned long long *d = P.dep[s];
-    for (int k = threadIdx.x; k < tc.w * tc.h; k += blockDim.x) {
+    for (int k = threadIdx.x; k < TW * TH; k += blockDim.x) {
       unsigned long long v = smem[k];
       if (v) {
-        int ni = tc.ci0 - kHalo + k % tc.w, nj = tc.cj0 - kHalo + k / tc.w;
+        int ni = tc.ci0 - kHalo + k % TW, nj = tc.cj0 - kHalo + k / TW;
         atomicAdd(d + nj * (P.nr + 1) + ni, v);
       }
     }
   } else {
     // overflow region of the read store: unsorted particles with explicit cells
-    TileCtx tc{nullptr, 0, 0, 0, 0, TX, TY};
+    TileCtx tc{nullptr, 0, 0};
     const int novf = min(A.meta->ovf_n, A.capacity - A.meta->ovf_base);
     const int first = A.meta->ovf_base;
     const int stride = (gridDim.x - ntiles) * blockDim.x;
-    // uniform trip count across the warp: loop bound rounded up to a warp multiple
     for (int base = (blockIdx.x - ntiles) * blockDim.x; base < novf; base += stride) {
       int k = base + threadIdx.x;
       bool active = k < novf;
@@ -652,7 +694,7 @@ __global__ void __launch_bounds__(kThreads) k_particles(const PushParams<T> P) {
         p.cj = c / P.nr;
         p.ci = c - p.cj * P.nr;
       }
-      process(P, s, active, p, tc);
+      process<T, TX, TY>(P, s, active, p, tc);
     }
   }
 }
@@ -828,14 +870,35 @@ __global__ void k_philox(int64_t n, const uint32_t *ctr, const uint32_t *key, ui
 }
 
 // ---- host launchers ---------------------------------------------------------
+template <typename T, int TX, int TY>
+static cudaError_t launch_tiles(const PushParams<T> &P, cudaStream_t st) {
+  dim3 grid(P.map.ntiles() + kOvfCtas, 2);
+  k_particles<T, TX, TY><<<grid, kThreads, 0, st>>>(P);
+  return cudaGetLastError();
+}
+
+// Tile shapes compiled in (cells in r x z); others are rejected at pic_init.
+bool tile_supported(int tx, int ty) {
+  return (tx == 2 && ty == 2) || (tx == 4 && ty == 2) || (tx == 2 && ty == 4) || (tx == 4 && ty == 4) ||
+         (tx == 8 && ty == 4) || (tx == 8 && ty == 8) || (tx == 16 && ty == 4) || (tx == 16 && ty == 8) ||
+         (tx == 32 && ty == 4) || (tx == 4 && ty == 8) || (tx == 8 && ty == 2);
+}
+
 template <typename T>
 cudaError_t launch_particles(const PushParams<T> &P, cudaStream_t st) {
-  int ntiles = P.map.ntiles();
-  int w = P.map.TX + 1 + 2 * kHalo, h = P.map.TY + 1 + 2 * kHalo;
-  size_t sm = sizeof(unsigned long long) * (size_t)w * h;
-  dim3 grid(ntiles + kOvfCtas, 2);
-  k_particles<T><<<grid, kThreads, sm, st>>>(P);
-  return cudaGetLastError();
+  const int tx = P.map.TX, ty = P.map.TY;
+  if (tx == 2 && ty == 2) return launch_tiles<T, 2, 2>(P, st);
+  if (tx == 4 && ty == 2) return launch_tiles<T, 4, 2>(P, st);
+  if (tx == 2 && ty == 4) return launch_tiles<T, 2, 4>(P, st);
+  if (tx == 8 && ty == 2) return launch_tiles<T, 8, 2>(P, st);
+  if (tx == 4 && ty == 4) return launch_tiles<T, 4, 4>(P, st);
+  if (tx == 8 && ty == 4) return launch_tiles<T, 8, 4>(P, st);
+  if (tx == 8 && ty == 8) return launch_tiles<T, 8, 8>(P, st);
+  if (tx == 16 && ty == 4) return launch_tiles<T, 16, 4>(P, st);
+  if (tx == 16 && ty == 8) return launch_tiles<T, 16, 8>(P, st);
+  if (tx == 32 && ty == 4) return launch_tiles<T, 32, 4>(P, st);
+  if (tx == 4 && ty == 8) return launch_tiles<T, 4, 8>(P, st);
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>
