@@ -548,3 +548,37 @@ def test_step_conserves_particles_and_charge():
     assert s["pcg_relres"] <= 1e-10
     g = o.get_particles(0)
     assert np.all(np.diff(g["cell"]) >= 0)  # re-binned by cell
+
+
+def test_efield_rules_on_a_linear_potential():
+    """Between plates with a Neumann wall phi is linear in z (slope -D/eps in each layer): the
+    node field is exact with central differences inside each layer, one-sided at the plates,
+    and E_r = 0 everywhere (axis rule and no radial variation)."""
+    nr, nz, R, L = 10, 12, 0.03, 0.024
+    node, cell, eps = grounded_box(nr, nz, R, L, neumann_wall=True, powered_bottom=True)
+    o = orc.Oracle(field_only(nr, nz, R, L, node, cell, eps, V=3.0, phase=math.pi / 2))
+    o.init_fields()
+    Ez, Er = o.field("Ez"), o.field("Er")
+    np.testing.assert_allclose(Ez, 3.0 / L, rtol=1e-8)  # PCG tolerance; a wrong one-sided rule is off by 2x
+    assert np.abs(Er).max() < 1e-9 * 3.0 / L
+
+
+def test_first_harmonic_of_direct_drive_current():
+    """Direct drive, no particles: I_ccp(t_{n+1}) = C_eq (U(t_{n+1}) - U(t_n)) / dt, whose
+    first Fourier coefficient over one RF period is C_eq V (2 sin(w dt/2)/dt) exp(-i w dt/2)
+    (the diagnostic's DFT, Eq. 11's fundamental)."""
+    base = W.small_cylinder(n_per_species=16)
+    wl = dataclasses.replace(with_particles(base), V_src=80.0, phase_src=0.3, ceq_refresh=0)
+    o = orc.Oracle(wl)
+    o.init_fields()
+    o.step(wl.steps_per_rf)
+    s = o.scalars()
+    assert s["windows"] == 1
+    w, dt = 2 * math.pi * wl.f_src, wl.dt
+    amp = s["C_eq"] * 80.0 * 2 * math.sin(w * dt / 2) / dt
+    # I_ccp(t_{n+1}) = C V (sin(w t_{n+1}+ph) - sin(w t_n+ph))/dt = amp cos(w t_{n+1} + ph - w dt/2)
+    # -> coefficient of exp(i w t): amp/2 exp(i(ph - w dt/2)); the DFT returns 2 x conj-coefficient
+    want = amp * complex(math.cos(0.3 - w * dt / 2), math.sin(0.3 - w * dt / 2))
+    got = complex(s["i1_re"], s["i1_im"])
+    assert abs(got - want) <= 1e-9 * abs(want)
+    assert np.abs(o.field("ne_avg")).max() == 0.0
