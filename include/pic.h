@@ -257,6 +257,42 @@ int pic_pcg_solve_static(int32_t nr, int32_t nz, const int8_t *node_kind, const 
                          const double *qrhs, double *phi, double tol, int32_t maxit, void *cuda_stream,
                          int32_t *iters, double *rel_resid);
 
+/* ---- learned field-solve preconditioner (U-Net) -------------------------
+ * A 4-level U-Net (32 base channels, BF16 weights and activations, FP32
+ * accumulation on the tensor cores) mapping (rho~, chi, boundary-voltage
+ * mask) on an H x W node grid to phi; used as the initial guess and the
+ * preconditioner of the field solve.  H, W multiples of 8, H*W <= 2^24.
+ * Tensors passed in are device FP32 arrays in the caller's memory; the
+ * network owns its weights, activations and gradient buffers. */
+typedef struct pic_unet pic_unet;
+int pic_unet_create(int H, int W, void *cuda_stream, pic_unet **out);
+void pic_unet_destroy(pic_unet *u);
+/* number of parameters; order: per conv (14) W[cout][9][cin] then bias[cout],
+ * then the 1x1 output conv's 32 weights and its bias */
+int pic_unet_param_count(const pic_unet *u, int64_t *n);
+int pic_unet_set_params(pic_unet *u, const float *host, int64_t n);
+int pic_unet_get_params(pic_unet *u, float *host, int64_t n);
+/* accumulated parameter gradients, same order as the parameters */
+int pic_unet_get_grads(pic_unet *u, float *host, int64_t n);
+int pic_unet_zero_grads(pic_unet *u);
+/* in: device [3][H*W] (rho~, chi, mask, channel-major); out: device [H*W] */
+int pic_unet_forward(pic_unet *u, const float *in, float *out);
+/* backward of the last forward for dLoss/dout (device [H*W]); adds to the gradients */
+int pic_unet_backward(pic_unet *u, const float *gout);
+/* one Adam step (t = step number from 1) on the accumulated gradients */
+int pic_unet_adam(pic_unet *u, float lr, float beta1, float beta2, float eps, int t);
+/* synchronise; *err = 1 if a bounded tensor-core wait timed out since the last call */
+int pic_unet_status(pic_unet *u, int *err);
+/* One tensor-core convolution on caller-owned device tensors (dense NHWC BF16,
+ * H x W pixels, Cin and Cout multiples of 16, Cout <= 256), for kernel tests:
+ *   op 0: out = FP32 [H*W][Cout] conv3x3(in, w), w = BF16 [Cout][9][Cin]
+ *   op 1: out = BF16 [H*W][Cout] ReLU(conv3x3(in, w) + bias)
+ *   op 2: out = FP32 [9*Cin][Cout] weight gradient: sum_p in[p + off(tap)][cin] w[p][cout]
+ *         (here `w` is the output gradient, BF16 [H*W][Cout])
+ * Synchronises the stream.  Errors: PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ETIMEOUT. */
+int pic_conv3x3_op(int op, int H, int W, const void *in, int Cin, const void *w, const float *bias, void *out,
+                   int Cout, void *cuda_stream);
+
 const char *pic_strerror(int code);
 void pic_destroy(pic_handle *h);
 

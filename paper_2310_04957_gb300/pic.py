@@ -32,7 +32,9 @@ EXPORTS = ["pic_init", "pic_set_particles", "pic_count", "pic_get_particles", "p
            "pic_particle_phase", "pic_field_solve", "pic_ceq", "pic_diag", "pic_set_field", "pic_set_step",
            "pic_set_ceq", "pic_set_circuit_state", "pic_set_conv_current", "pic_circuit_run", "pic_status",
            "pic_philox", "pic_enable_timing", "pic_step_timing", "pic_strerror", "pic_destroy",
-           "pic_pcg_solve_static"]
+           "pic_pcg_solve_static", "pic_unet_create", "pic_unet_destroy", "pic_unet_param_count",
+           "pic_unet_set_params", "pic_unet_get_params", "pic_unet_get_grads", "pic_unet_zero_grads",
+           "pic_unet_forward", "pic_unet_backward", "pic_unet_adam", "pic_unet_status", "pic_conv3x3_op"]
 STATIC_MAX_NODES = 139264
 
 
@@ -285,3 +287,74 @@ def pcg_solve_static(nr, nz, node_kind, Gr, Gz, qrhs, phi, tol, maxit, stream=No
                                     ctypes.c_void_p(qrhs), ctypes.c_void_p(phi), tol, maxit, _stream(stream),
                                     ctypes.byref(it), ctypes.byref(rr))
     return st, it.value, rr.value
+
+
+class UNet:
+    """The learned preconditioner's network on the current device (wraps pic_unet)."""
+
+    def __init__(self, H, W, stream=None):
+        L = lib()
+        P = ctypes.c_void_p
+        for name, args in (("pic_unet_create", [ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)]),
+                           ("pic_unet_destroy", [P]), ("pic_unet_param_count", [P, ctypes.POINTER(ctypes.c_int64)]),
+                           ("pic_unet_set_params", [P, P, ctypes.c_int64]), ("pic_unet_get_params", [P, P, ctypes.c_int64]),
+                           ("pic_unet_get_grads", [P, P, ctypes.c_int64]), ("pic_unet_zero_grads", [P]),
+                           ("pic_unet_forward", [P, P, P]), ("pic_unet_backward", [P, P]),
+                           ("pic_unet_adam", [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int]),
+                           ("pic_unet_status", [P, ctypes.POINTER(ctypes.c_int)])):
+            getattr(L, name).argtypes = args
+        h = ctypes.c_void_p()
+        _check(L.pic_unet_create(H, W, _stream(stream), ctypes.byref(h)), "pic_unet_create")
+        self.h, self.H, self.W = h, H, W
+        n = ctypes.c_int64()
+        _check(L.pic_unet_param_count(h, ctypes.byref(n)), "pic_unet_param_count")
+        self.nparams = n.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.pic_unet_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(lib().pic_unet_set_params(self.h, _p(p), p.size), "pic_unet_set_params")
+
+    def get_params(self):
+        o = np.zeros(self.nparams, np.float32)
+        _check(lib().pic_unet_get_params(self.h, _p(o), o.size), "pic_unet_get_params")
+        return o
+
+    def get_grads(self):
+        o = np.zeros(self.nparams, np.float32)
+        _check(lib().pic_unet_get_grads(self.h, _p(o), o.size), "pic_unet_get_grads")
+        return o
+
+    def zero_grads(self):
+        _check(lib().pic_unet_zero_grads(self.h), "pic_unet_zero_grads")
+
+    def forward(self, inp_ptr, out_ptr):
+        """inp_ptr: device FP32 [3][H*W]; out_ptr: device FP32 [H*W] (raw pointers)."""
+        _check(lib().pic_unet_forward(self.h, ctypes.c_void_p(inp_ptr), ctypes.c_void_p(out_ptr)), "pic_unet_forward")
+
+    def backward(self, gout_ptr):
+        _check(lib().pic_unet_backward(self.h, ctypes.c_void_p(gout_ptr)), "pic_unet_backward")
+
+    def adam(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().pic_unet_adam(self.h, lr, beta1, beta2, eps, t), "pic_unet_adam")
+
+    def status(self):
+        e = ctypes.c_int()
+        _check(lib().pic_unet_status(self.h, ctypes.byref(e)), "pic_unet_status")
+        return e.value
+
+
+def conv3x3_op(op, H, W, inp_ptr, Cin, w_ptr, bias_ptr, out_ptr, Cout, stream=None):
+    """Call pic_conv3x3_op on raw device pointers; returns the status code."""
+    L = lib()
+    P = ctypes.c_void_p
+    L.pic_conv3x3_op.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P, P, ctypes.c_int, P]
+    return L.pic_conv3x3_op(op, H, W, P(inp_ptr), Cin, P(w_ptr), P(bias_ptr) if bias_ptr else None, P(out_ptr), Cout,
+                            _stream(stream))
