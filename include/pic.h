@@ -284,14 +284,22 @@ int pic_unet_adam(pic_unet *u, float lr, float beta1, float beta2, float eps, in
 /* synchronise; *err = 1 if a bounded tensor-core wait timed out since the last call */
 int pic_unet_status(pic_unet *u, int *err);
 /* One tensor-core convolution on caller-owned device tensors (dense NHWC BF16,
- * H x W pixels, Cin and Cout multiples of 16, Cout <= 256), for kernel tests:
+ * H x W pixels, Cin and Cout multiples of 16), for kernel tests:
  *   op 0: out = FP32 [H*W][Cout] conv3x3(in, w), w = BF16 [Cout][9][Cin]
  *   op 1: out = BF16 [H*W][Cout] ReLU(conv3x3(in, w) + bias)
  *   op 2: out = FP32 [9*Cin][Cout] weight gradient: sum_p in[p + off(tap)][cin] w[p][cout]
- *         (here `w` is the output gradient, BF16 [H*W][Cout])
+ *         (here `w` is the output gradient, BF16 [H*W][Cout]; Cout <= 256)
+ * Ops 0 and 1 run the TMA-fed kernel when W is a multiple of 8 and some tiling
+ * fits, else the cp.async gather kernel (Cout <= 256).
  * Synchronises the stream.  Errors: PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ETIMEOUT. */
 int pic_conv3x3_op(int op, int H, int W, const void *in, int Cin, const void *w, const float *bias, void *out,
                    int Cout, void *cuda_stream);
+/* As pic_conv3x3_op with a chosen tiling for ops 0 and 1: tile_n = output
+ * channels per CTA (32, 64, 128, 256; must divide Cout), tile_mma = 128-pixel
+ * accumulators per CTA (1, 2, 4, 8); 0 = automatic; tile_n = -1 forces the
+ * gather kernel.  PIC_EINVAL if the forced tiling does not fit. */
+int pic_conv3x3_op_ex(int op, int H, int W, const void *in, int Cin, const void *w, const float *bias, void *out,
+                      int Cout, int tile_n, int tile_mma, void *cuda_stream);
 
 const char *pic_strerror(int code);
 void pic_destroy(pic_handle *h);

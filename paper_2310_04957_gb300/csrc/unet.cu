@@ -53,6 +53,13 @@ struct pic_unet {
   __nv_bfloat16 *dpre = nullptr;
   int *err = nullptr;
   size_t nparams = 0;
+  // TMA tilings, input tensor maps and packed weights of each forward conv (f)
+  // and input-gradient conv (g); use_* false -> the cp.async gather kernel
+  ConvGeom geo_f[kNConv], geo_g[kNConv];
+  CUtensorMap map_f[kNConv], map_g[kNConv];
+  bool use_f[kNConv] = {}, use_g[kNConv] = {};
+  __nv_bfloat16 *wpk[kNConv], *wtpk[kNConv];
+  bool tuning = false;  // set while pic_unet_create times the candidate tilings
 };
 
 namespace {
@@ -100,24 +107,37 @@ __global__ void k_pack_input(const float *src, int HW, __nv_bfloat16 *dst) {
 }
 
 // 2x2 average pool: src (h x w, channels [off, off+C) of cs) -> dst (h/2 x w/2 x C).
+// One thread per 8 channels of an output pixel (16-byte loads and stores).
 __global__ void k_pool(const __nv_bfloat16 *src, int cs, int off, int C, int h, int w, __nv_bfloat16 *dst) {
-  int ho = h / 2, wo = w / 2;
-  int n = ho * wo * C;
+  const int ho = h / 2, wo = w / 2, C8 = C / 8;
+  const int n = ho * wo * C8;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int c = i % C, q = i / C, y = q / wo, x = q - y * wo;
-    float s = 0.0f;
+    const int c = (i % C8) * 8, q = i / C8, y = q / wo, x = q - y * wo;
+    float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int dy = 0; dy < 2; ++dy)
-      for (int dx = 0; dx < 2; ++dx) s += __bfloat162float(src[((size_t)(2 * y + dy) * w + 2 * x + dx) * cs + off + c]);
-    dst[i] = __float2bfloat16(0.25f * s);
+      for (int dx = 0; dx < 2; ++dx) {
+        __align__(16) __nv_bfloat16 v[8];
+        *reinterpret_cast<uint4 *>(v) =
+            *reinterpret_cast<const uint4 *>(src + ((size_t)(2 * y + dy) * w + 2 * x + dx) * cs + off + c);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(v[k]);
+      }
+    __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = __float2bfloat16(0.25f * s[k]);
+    *reinterpret_cast<uint4 *>(dst + (size_t)q * C + c) = *reinterpret_cast<const uint4 *>(o);
   }
 }
 
 // Nearest 2x upsample of src (h x w x C) into channels [0, C) of dst (2h x 2w, cs).
+// One thread per 8 channels of an output pixel.
 __global__ void k_upsample(const __nv_bfloat16 *src, int C, int h, int w, __nv_bfloat16 *dst, int cs) {
-  int n = 4 * h * w * C;
+  const int C8 = C / 8, W2 = 2 * w;
+  const int n = 4 * h * w * C8;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int c = i % C, q = i / C, W2 = 2 * w, y = q / W2, x = q - y * W2;
-    dst[(size_t)q * cs + c] = src[((size_t)(y / 2) * w + x / 2) * C + c];
+    const int c = (i % C8) * 8, q = i / C8, y = q / W2, x = q - y * W2;
+    *reinterpret_cast<uint4 *>(dst + (size_t)q * cs + c) =
+        *reinterpret_cast<const uint4 *>(src + ((size_t)(y / 2) * w + x / 2) * C + c);
   }
 }
 
@@ -147,18 +167,33 @@ __global__ void k_pool_bwd(const float *gp, int C, int h, int w, float *g, const
   }
 }
 
-// Gradient (FP32 slice) -> BF16 dense pre-activation gradient, with the bias gradient.
+// Gradient (FP32 slice) -> BF16 dense pre-activation gradient, with the bias
+// gradient.  One thread per 8 channels; the grid stride is a multiple of C/8,
+// so each thread keeps one channel group and sums it in registers.
 __global__ void k_to_bf16_bias(const float *g, int cs, int off, int C, int HW, __nv_bfloat16 *dst, float *gb) {
   extern __shared__ float sb[];
   for (int c = threadIdx.x; c < C; c += blockDim.x) sb[c] = 0.0f;
   __syncthreads();
-  int n = HW * C;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    int c = i % C, p = i / C;
-    float v = g[(size_t)p * cs + off + c];
-    __nv_bfloat16 h = __float2bfloat16(v);
-    dst[i] = h;
-    atomicAdd(&sb[c], __bfloat162float(h));
+  const int C8 = C / 8, n = HW * C8;
+  float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int i = i0; i < n; i += gridDim.x * blockDim.x) {
+    const int c = (i % C8) * 8, p = i / C8;
+    const float4 *src = reinterpret_cast<const float4 *>(g + (size_t)p * cs + off + c);
+    const float4 a = src[0], b = src[1];
+    const float v[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      h[k] = __float2bfloat16(v[k]);
+      acc[k] += __bfloat162float(h[k]);
+    }
+    *reinterpret_cast<uint4 *>(dst + (size_t)p * C + c) = *reinterpret_cast<const uint4 *>(h);
+  }
+  if (i0 < n) {
+    const int c = (i0 % C8) * 8;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) atomicAdd(&sb[c + k], acc[k]);
   }
   __syncthreads();
   for (int c = threadIdx.x; c < C; c += blockDim.x) atomicAdd(&gb[c], sb[c]);
@@ -166,9 +201,19 @@ __global__ void k_to_bf16_bias(const float *g, int cs, int off, int C, int HW, _
 
 // 1x1 output conv: out[p] = b + sum_c w[c] d0[p][c].
 __global__ void k_out_fwd(const __nv_bfloat16 *d0, int HW, const float *w, const float *b, float *out) {
+  __shared__ float sw[33];
+  if (threadIdx.x < 33) sw[threadIdx.x] = w[threadIdx.x];  // w[32] is the bias
+  __syncthreads();
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
-    float s = b[0];
-    for (int c = 0; c < 32; ++c) s += w[c] * __bfloat162float(d0[(size_t)p * 32 + c]);
+    float s = sw[32];
+    const uint4 *src = reinterpret_cast<const uint4 *>(d0 + (size_t)p * 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __align__(16) __nv_bfloat16 v[8];
+      *reinterpret_cast<uint4 *>(v) = src[q];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s += sw[8 * q + k] * __bfloat162float(v[k]);
+    }
     out[p] = s;
   }
 }
@@ -176,16 +221,38 @@ __global__ void k_out_fwd(const __nv_bfloat16 *d0, int HW, const float *w, const
 // 1x1 backward: g_d0[p][c] = gout[p] w[c] (d0 > 0); gw[c] += sum gout d0; gw[32] += sum gout.
 __global__ void k_out_bwd(const float *gout, const __nv_bfloat16 *d0, int HW, const float *w, float *g_d0, float *gw) {
   __shared__ float s[33];
+  __shared__ float sw[32];
   if (threadIdx.x < 33) s[threadIdx.x] = 0.0f;
+  if (threadIdx.x < 32) sw[threadIdx.x] = w[threadIdx.x];
   __syncthreads();
+  float acc[33];
+#pragma unroll
+  for (int c = 0; c < 33; ++c) acc[c] = 0.0f;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
-    float go = gout[p];
-    for (int c = 0; c < 32; ++c) {
-      float a = __bfloat162float(d0[(size_t)p * 32 + c]);
-      g_d0[(size_t)p * 32 + c] = a > 0.0f ? go * w[c] : 0.0f;
-      atomicAdd(&s[c], go * a);
+    const float go = gout[p];
+    const uint4 *src = reinterpret_cast<const uint4 *>(d0 + (size_t)p * 32);
+    float4 *dst = reinterpret_cast<float4 *>(g_d0 + (size_t)p * 32);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      __align__(16) __nv_bfloat16 v[8];
+      *reinterpret_cast<uint4 *>(v) = src[q];
+      float o[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float a = __bfloat162float(v[k]);
+        o[k] = a > 0.0f ? go * sw[8 * q + k] : 0.0f;
+        acc[8 * q + k] += go * a;
+      }
+      dst[2 * q] = make_float4(o[0], o[1], o[2], o[3]);
+      dst[2 * q + 1] = make_float4(o[4], o[5], o[6], o[7]);
     }
-    atomicAdd(&s[32], go);
+    acc[32] += go;
+  }
+#pragma unroll
+  for (int c = 0; c < 33; ++c) {
+    float v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s[c], v);
   }
   __syncthreads();
   if (threadIdx.x < 33) atomicAdd(&gw[threadIdx.x], s[threadIdx.x]);
@@ -240,6 +307,40 @@ ConvArgs conv_args(pic_unet *u, const Tensor &in, int in_off, int Cin, int level
   return a;
 }
 
+// Autotuner: times every TMA tiling of one convolution (two warm-up and five
+// timed launches on the network's own buffers) and keeps the fastest.
+template <class Launch>
+int tune_conv(pic_unet *u, int h, int w, int Cin, int Cout, const __nv_bfloat16 *inp, int in_cs, ConvGeom *geo,
+              CUtensorMap *map, Launch launch) {
+  cudaEvent_t e0, e1;
+  UK(cudaEventCreate(&e0));
+  UK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  const int ns[4] = {32, 64, 128, 256};
+  for (int ni = 0; ni < 4; ++ni)
+    for (int m = 1; m <= 8; m *= 2) {
+      ConvGeom g;
+      CUtensorMap mp;
+      if (!plan_conv(h, w, Cin, Cout, ns[ni], m, &g)) continue;
+      if (make_input_map(&mp, inp, in_cs, h, w, g) != cudaSuccess) continue;
+      for (int r = 0; r < 2; ++r) UK(launch(mp, g));
+      UK(cudaEventRecord(e0, u->stream));
+      for (int r = 0; r < 5; ++r) UK(launch(mp, g));
+      UK(cudaEventRecord(e1, u->stream));
+      UK(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      UK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        *geo = g;
+        *map = mp;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return PIC_OK;
+}
+
 int conv_fwd(pic_unet *u, int l, const Tensor &in, int in_off, const Tensor &out, int out_off) {
   ConvArgs a = conv_args(u, in, in_off, kCin[l], kLevel[l]);
   a.out_bf = out.p;
@@ -249,7 +350,15 @@ int conv_fwd(pic_unet *u, int l, const Tensor &in, int in_off, const Tensor &out
   a.w = u->w[l];
   a.bias = u->b[l];
   a.relu = 1;
-  UK(launch_conv3x3(a, u->stream));
+  if (u->use_f[l] && u->tuning) {
+    int st = tune_conv(u, a.H, a.W, a.Cin, a.Cout, in.p, in.cs, &u->geo_f[l], &u->map_f[l],
+                       [&](const CUtensorMap &m, const ConvGeom &g) { return launch_conv_tma(m, a, g, u->wpk[l], u->stream); });
+    if (st) return st;
+  }
+  if (u->use_f[l])
+    UK(launch_conv_tma(u->map_f[l], a, u->geo_f[l], u->wpk[l], u->stream));
+  else
+    UK(launch_conv3x3(a, u->stream));
   return PIC_OK;
 }
 
@@ -259,7 +368,7 @@ int conv_fwd(pic_unet *u, int l, const Tensor &in, int in_off, const Tensor &out
 int conv_bwd(pic_unet *u, int l, const Tensor &in, int in_off, const float *g_out, int g_cs, int g_off, float *g_in,
              int g_in_cs, int g_in_off, bool mask_in, bool accumulate) {
   const int level = kLevel[l], HW = pixels(u, level), Cin = kCin[l], Cout = kCout[l];
-  k_to_bf16_bias<<<grid_for((long long)HW * Cout), 256, Cout * sizeof(float), u->stream>>>(g_out, g_cs, g_off, Cout, HW,
+  k_to_bf16_bias<<<grid_for((long long)HW * Cout / 8), 256, Cout * sizeof(float), u->stream>>>(g_out, g_cs, g_off, Cout, HW,
                                                                                          u->dpre, u->gb[l]);
   UK(cudaGetLastError());
   WgradArgs wa;
@@ -278,9 +387,27 @@ int conv_bwd(pic_unet *u, int l, const Tensor &in, int in_off, const float *g_ou
   wa.pix_per_cta = HW >= 65536 ? 1024 : (HW >= 8192 ? 512 : 256);
   wa.err = u->err;
   UK(launch_wgrad(wa, u->stream));
-  if (g_in) {
-    // input gradient = conv with the flipped transposed weights Wt[cin][9][cout],
-    // in output-channel chunks of at most 256 (the accumulator width)
+  if (g_in && u->use_g[l]) {
+    // input gradient = conv with the flipped transposed weights Wt[cin][9][cout]
+    Tensor dp{u->dpre, Cout};
+    ConvArgs a = conv_args(u, dp, 0, Cout, level);
+    a.out_f = g_in;
+    a.out_cs = g_in_cs;
+    a.out_off = g_in_off;
+    a.Cout = Cin;
+    a.w = u->wt[l];
+    a.mask = mask_in ? in.p : nullptr;
+    a.mask_cs = in.cs;
+    a.mask_off = in_off;
+    a.accumulate = accumulate ? 1 : 0;
+    if (u->tuning) {
+      int st = tune_conv(u, a.H, a.W, a.Cin, a.Cout, u->dpre, Cout, &u->geo_g[l], &u->map_g[l],
+                         [&](const CUtensorMap &m, const ConvGeom &g) { return launch_conv_tma(m, a, g, u->wtpk[l], u->stream); });
+      if (st) return st;
+    }
+    UK(launch_conv_tma(u->map_g[l], a, u->geo_g[l], u->wtpk[l], u->stream));
+  } else if (g_in) {
+    // gather kernel, in output-channel chunks of at most 256 (the accumulator width)
     Tensor dp{u->dpre, Cout};
     for (int c0 = 0; c0 < Cin; c0 += 256) {
       const int nc = Cin - c0 < 256 ? Cin - c0 : 256;
@@ -307,6 +434,8 @@ int refresh_weights(pic_unet *u, float lr, float b1, float b2, float eps, int t)
     k_adam_conv<<<grid_for(n), 256, 0, u->stream>>>(kCin[l], kCout[l], u->wm[l], u->gw[l], u->mw[l], u->vw[l], u->w[l],
                                                      u->wt[l], lr, b1, b2, eps, c1, c2);
     UK(cudaGetLastError());
+    if (u->use_f[l]) UK(pack_weights(u->w[l], kCin[l], kCout[l], u->geo_f[l].N, u->wpk[l], u->stream));
+    if (u->use_g[l]) UK(pack_weights(u->wt[l], kCout[l], kCin[l], u->geo_g[l].N, u->wtpk[l], u->stream));
     if (lr > 0) {
       k_adam_vec<<<1, 256, 0, u->stream>>>(kCout[l], u->b[l], u->gb[l], u->mb[l], u->vb[l], lr, b1, b2, eps, c1, c2);
       UK(cudaGetLastError());
@@ -374,8 +503,38 @@ int pic_unet_create(int H, int W, void *cuda_stream, pic_unet **out) {
     UA(u->g_a0, p0 * 32 * 4);
     UA(u->dpre, p0 * 64 * 2);  // largest Cout x pixels among the layers
     UA(u->err, 16);
+    // TMA tilings and tensor maps (input buffers are fixed for the network's life)
+    const Tensor *fin[kNConv] = {&u->in0, &u->a0, &u->pool0, &u->a1, &u->pool1, &u->a2, &u->pool2,
+                                 &u->b1, &u->cat2, &u->d2a, &u->cat1, &u->d1a, &u->cat0, &u->d0a};
+    for (int l = 0; l < kNConv; ++l) {
+      const int h = H >> kLevel[l], w = W >> kLevel[l];
+      size_t n = (size_t)kCout[l] * 9 * kCin[l];
+      if (plan_conv(h, w, kCin[l], kCout[l], 0, 0, &u->geo_f[l]) &&
+          make_input_map(&u->map_f[l], fin[l]->p, fin[l]->cs, h, w, u->geo_f[l]) == cudaSuccess) {
+        u->use_f[l] = true;
+        UA(u->wpk[l], n * 2);
+      }
+      if (l > 0 && plan_conv(h, w, kCout[l], kCin[l], 0, 0, &u->geo_g[l]) &&
+          make_input_map(&u->map_g[l], u->dpre, kCout[l], h, w, u->geo_g[l]) == cudaSuccess) {
+        u->use_g[l] = true;
+        UA(u->wtpk[l], n * 2);
+      }
+    }
     if (cudaStreamSynchronize(u->stream) != cudaSuccess) return PIC_ECUDA;
-    return PIC_OK;
+    // choose each convolution's tiling by timing (all weights and inputs are zero here)
+    float *zero = nullptr;
+    if (cudaMalloc(&zero, (size_t)p0 * 3 * 4) != cudaSuccess) return PIC_ENOMEM;
+    cudaMemsetAsync(zero, 0, (size_t)p0 * 3 * 4, u->stream);
+    u->tuning = true;
+    int t = pic_unet_forward(u, zero, nullptr);
+    if (!t) t = pic_unet_backward(u, zero);
+    u->tuning = false;
+    if (cudaStreamSynchronize(u->stream) != cudaSuccess) t = PIC_ECUDA;
+    cudaFree(zero);
+    if (!t) t = pic_unet_zero_grads(u);
+    if (!t && cudaMemsetAsync(u->err, 0, 16, u->stream) != cudaSuccess) t = PIC_ECUDA;
+    if (!t && cudaStreamSynchronize(u->stream) != cudaSuccess) t = PIC_ECUDA;
+    return t;
   }();
   if (st) {
     for (void *p : u->allocs) cudaFree(p);
@@ -467,22 +626,22 @@ int pic_unet_forward(pic_unet *u, const float *in, float *out) {
   int st = 0;
   st |= conv_fwd(u, 0, u->in0, 0, u->a0, 0);
   st |= conv_fwd(u, 1, u->a0, 0, u->cat0, 64);
-  k_pool<<<grid_for((long long)pixels(u, 1) * 32), 256, 0, s>>>(u->cat0.p, 96, 64, 32, H, W, u->pool0.p);
+  k_pool<<<grid_for((long long)pixels(u, 1) * 4), 256, 0, s>>>(u->cat0.p, 96, 64, 32, H, W, u->pool0.p);
   st |= conv_fwd(u, 2, u->pool0, 0, u->a1, 0);
   st |= conv_fwd(u, 3, u->a1, 0, u->cat1, 128);
-  k_pool<<<grid_for((long long)pixels(u, 2) * 64), 256, 0, s>>>(u->cat1.p, 192, 128, 64, H >> 1, W >> 1, u->pool1.p);
+  k_pool<<<grid_for((long long)pixels(u, 2) * 8), 256, 0, s>>>(u->cat1.p, 192, 128, 64, H >> 1, W >> 1, u->pool1.p);
   st |= conv_fwd(u, 4, u->pool1, 0, u->a2, 0);
   st |= conv_fwd(u, 5, u->a2, 0, u->cat2, 256);
-  k_pool<<<grid_for((long long)pixels(u, 3) * 128), 256, 0, s>>>(u->cat2.p, 384, 256, 128, H >> 2, W >> 2, u->pool2.p);
+  k_pool<<<grid_for((long long)pixels(u, 3) * 16), 256, 0, s>>>(u->cat2.p, 384, 256, 128, H >> 2, W >> 2, u->pool2.p);
   st |= conv_fwd(u, 6, u->pool2, 0, u->b1, 0);
   st |= conv_fwd(u, 7, u->b1, 0, u->b2, 0);
-  k_upsample<<<grid_for((long long)pixels(u, 2) * 256), 256, 0, s>>>(u->b2.p, 256, H >> 3, W >> 3, u->cat2.p, 384);
+  k_upsample<<<grid_for((long long)pixels(u, 2) * 32), 256, 0, s>>>(u->b2.p, 256, H >> 3, W >> 3, u->cat2.p, 384);
   st |= conv_fwd(u, 8, u->cat2, 0, u->d2a, 0);
   st |= conv_fwd(u, 9, u->d2a, 0, u->d2, 0);
-  k_upsample<<<grid_for((long long)pixels(u, 1) * 128), 256, 0, s>>>(u->d2.p, 128, H >> 2, W >> 2, u->cat1.p, 192);
+  k_upsample<<<grid_for((long long)pixels(u, 1) * 16), 256, 0, s>>>(u->d2.p, 128, H >> 2, W >> 2, u->cat1.p, 192);
   st |= conv_fwd(u, 10, u->cat1, 0, u->d1a, 0);
   st |= conv_fwd(u, 11, u->d1a, 0, u->d1, 0);
-  k_upsample<<<grid_for((long long)pixels(u, 0) * 64), 256, 0, s>>>(u->d1.p, 64, H >> 1, W >> 1, u->cat0.p, 96);
+  k_upsample<<<grid_for((long long)pixels(u, 0) * 8), 256, 0, s>>>(u->d1.p, 64, H >> 1, W >> 1, u->cat0.p, 96);
   st |= conv_fwd(u, 12, u->cat0, 0, u->d0a, 0);
   st |= conv_fwd(u, 13, u->d0a, 0, u->d0, 0);
   k_out_fwd<<<grid_for(H * W), 256, 0, s>>>(u->d0.p, H * W, u->w_out, u->b_out, out ? out : u->out);
@@ -537,12 +696,25 @@ int pic_unet_adam(pic_unet *u, float lr, float beta1, float beta2, float eps, in
 //   op 1: out_bf16[H*W][Cout] = bf16(ReLU(conv3x3(in, w) + bias))
 //   op 2: out_f32[9*Cin][Cout] = weight gradient sum_p in[p+off][cin] dy[p][cout]
 //         (in = x [H*W][Cin], w = dy [H*W][Cout] for this op)
-int pic_conv3x3_op(int op, int H, int W, const void *in, int Cin, const void *w, const float *bias, void *out, int Cout,
-                   void *cuda_stream) {
-  if (H < 1 || W < 1 || !in || !w || !out || Cin % 16 || Cout % 16 || Cout > 256 || op < 0 || op > 2) return PIC_EINVAL;
+// tile_n / tile_mma choose the tiling of ops 0 and 1 (0 = automatic; tile_n = -1
+// = the cp.async gather kernel).
+int pic_conv3x3_op_ex(int op, int H, int W, const void *in, int Cin, const void *w, const float *bias, void *out,
+                      int Cout, int tile_n, int tile_mma, void *cuda_stream) {
+  if (H < 1 || W < 1 || !in || !w || !out || Cin % 16 || Cout % 16 || op < 0 || op > 2) return PIC_EINVAL;
+  if (tile_n != 0 && tile_n != -1 && tile_n != 32 && tile_n != 64 && tile_n != 128 && tile_n != 256) return PIC_EINVAL;
+  if (tile_mma != 0 && tile_mma != 1 && tile_mma != 2 && tile_mma != 4 && tile_mma != 8) return PIC_EINVAL;
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  ConvGeom geo;
+  const bool tma = op < 2 && tile_n != -1 && plan_conv(H, W, Cin, Cout, tile_n > 0 ? tile_n : 0, tile_mma, &geo);
+  if (op < 2 && !tma && (tile_n > 0 || tile_mma > 0)) return PIC_EINVAL;  // forced tiling not possible
+  if (!tma && Cout > 256) return PIC_EINVAL;
   int *err = nullptr;
+  __nv_bfloat16 *wpk = nullptr;
   if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return PIC_ENOMEM;
+  if (tma && cudaMalloc(&wpk, (size_t)Cout * 9 * Cin * 2) != cudaSuccess) {
+    cudaFree(err);
+    return PIC_ENOMEM;
+  }
   cudaMemsetAsync(err, 0, sizeof(int), s);
   cudaError_t e;
   if (op < 2) {
@@ -564,7 +736,14 @@ int pic_conv3x3_op(int op, int H, int W, const void *in, int Cin, const void *w,
       a.bias = bias;
       a.relu = 1;
     }
-    e = launch_conv3x3(a, s);
+    if (tma) {
+      CUtensorMap map;
+      e = make_input_map(&map, a.in, Cin, H, W, geo);
+      if (e == cudaSuccess) e = pack_weights(a.w, Cin, Cout, geo.N, wpk, s);
+      if (e == cudaSuccess) e = launch_conv_tma(map, a, geo, wpk, s);
+    } else {
+      e = launch_conv3x3(a, s);
+    }
   } else {
     WgradArgs a;
     memset(&a, 0, sizeof(a));
@@ -585,9 +764,16 @@ int pic_conv3x3_op(int op, int H, int W, const void *in, int Cin, const void *w,
   int herr = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  else cudaStreamSynchronize(s);
   cudaFree(err);
+  if (wpk) cudaFree(wpk);
   if (e != cudaSuccess) return PIC_ECUDA;
   return herr ? PIC_ETIMEOUT : PIC_OK;
+}
+
+int pic_conv3x3_op(int op, int H, int W, const void *in, int Cin, const void *w, const float *bias, void *out, int Cout,
+                   void *cuda_stream) {
+  return pic_conv3x3_op_ex(op, H, W, in, Cin, w, bias, out, Cout, 0, 0, cuda_stream);
 }
 
 int pic_unet_status(pic_unet *u, int *err) {

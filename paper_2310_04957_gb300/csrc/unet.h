@@ -1,6 +1,7 @@
 // unet.h -- internal interface of the learned preconditioner's kernels.
 #pragma once
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -38,6 +39,37 @@ struct WgradArgs {
   int *err;
 };
 
+// Tiling of the TMA-fed convolution.  A CTA computes `nmma` accumulators of
+// 128 pixels x N output channels; each accumulator covers q = 128 / Wt image
+// rows of a Wt-pixel-wide column strip, so a CTA covers R = nmma * q rows.
+//   halo mode (nvar = 1, Wt = 128): one box of Bx = 130 pixels x By = R + 2 rows
+//     per 8-channel group; tap (dy, dx) is the same box shifted by dy rows and
+//     dx pixels (the MMA reads 128 contiguous pixels of one row).
+//   column-copy mode (nvar = 3, Wt <= 64): three boxes of Bx = Wt pixels, read at
+//     x0 - 1, x0, x0 + 1, so that tap (dy, dx) is box dx shifted by whole rows.
+struct ConvGeom {
+  int N, nmma, Wt, q, R, nvar, Bx, By;
+  int slot;         // shared-memory bytes per box (128-byte multiple)
+  int a_bytes;      // A bytes per stage: 2 groups x nvar boxes
+  int stage_bytes;  // A + B (B = 2 groups x 9 taps x N rows x 16 bytes)
+  int tx_bytes;     // bytes the TMA delivers per stage
+  int S;            // pipeline stages
+  int tiles_x, tiles_y, nsplit;
+  int tcols, smem;
+};
+
+// Chooses a tiling for an H x W convolution with Cin -> Cout channels.  tile_n
+// and tile_mma force N and nmma when nonzero.  Returns false when the shape has
+// no TMA tiling (W not a multiple of 8, Cin or Cout not multiples of 16/32).
+bool plan_conv(int H, int W, int Cin, int Cout, int tile_n, int tile_mma, ConvGeom *g);
+// Tensor map of the BF16 NHWC input (cs channels per pixel) for tiling g.
+cudaError_t make_input_map(CUtensorMap *m, const __nv_bfloat16 *base, int cs, int H, int W, const ConvGeom &g);
+// w [Cout][9][Cin] -> packed [Cout/N][Cin/16][2][9][N][8], the per-stage shared-memory image.
+cudaError_t pack_weights(const __nv_bfloat16 *w, int Cin, int Cout, int N, __nv_bfloat16 *dst, cudaStream_t st);
+cudaError_t launch_conv_tma(const CUtensorMap &tin, const ConvArgs &a, const ConvGeom &g,
+                            const __nv_bfloat16 *wpk, cudaStream_t st);
+
+// cp.async gather kernel (any W; Cin multiple of 16, Cout <= 256).
 cudaError_t launch_conv3x3(const ConvArgs &a, cudaStream_t st);
 cudaError_t launch_wgrad(const WgradArgs &a, cudaStream_t st);
 

@@ -34,7 +34,8 @@ EXPORTS = ["pic_init", "pic_set_particles", "pic_count", "pic_get_particles", "p
            "pic_philox", "pic_enable_timing", "pic_step_timing", "pic_strerror", "pic_destroy",
            "pic_pcg_solve_static", "pic_unet_create", "pic_unet_destroy", "pic_unet_param_count",
            "pic_unet_set_params", "pic_unet_get_params", "pic_unet_get_grads", "pic_unet_zero_grads",
-           "pic_unet_forward", "pic_unet_backward", "pic_unet_adam", "pic_unet_status", "pic_conv3x3_op"]
+           "pic_unet_forward", "pic_unet_backward", "pic_unet_adam", "pic_unet_status", "pic_conv3x3_op",
+           "pic_conv3x3_op_ex"]
 STATIC_MAX_NODES = 139264
 
 
@@ -351,10 +352,12 @@ class UNet:
         return e.value
 
 
-def conv3x3_op(op, H, W, inp_ptr, Cin, w_ptr, bias_ptr, out_ptr, Cout, stream=None):
-    """Call pic_conv3x3_op on raw device pointers; returns the status code."""
+def conv3x3_op(op, H, W, inp_ptr, Cin, w_ptr, bias_ptr, out_ptr, Cout, stream=None, tile_n=0, tile_mma=0):
+    """Call pic_conv3x3_op_ex on raw device pointers; returns the status code.
+    tile_n / tile_mma force a tiling (0 = automatic, tile_n = -1 = gather kernel)."""
     L = lib()
     P = ctypes.c_void_p
-    L.pic_conv3x3_op.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P, P, ctypes.c_int, P]
-    return L.pic_conv3x3_op(op, H, W, P(inp_ptr), Cin, P(w_ptr), P(bias_ptr) if bias_ptr else None, P(out_ptr), Cout,
-                            _stream(stream))
+    I = ctypes.c_int
+    L.pic_conv3x3_op_ex.argtypes = [I, I, I, P, I, P, P, P, I, I, I, P]
+    return L.pic_conv3x3_op_ex(op, H, W, P(inp_ptr), Cin, P(w_ptr), P(bias_ptr) if bias_ptr else None, P(out_ptr),
+                               Cout, tile_n, tile_mma, _stream(stream))

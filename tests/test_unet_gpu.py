@@ -94,3 +94,55 @@ def test_unet_forward_and_gradients_match_oracle(H, W):
     assert rel_l2(g_gpu[offs[14]:], g_ref[offs[14]:]) <= max(3 * sp, 1e-3)
     # parameters round-trip
     np.testing.assert_array_equal(net.get_params(), params.astype(np.float32))
+
+
+@pytest.mark.parametrize("Cin,Cout,H,W,tile_n,tile_mma", [
+    (32, 64, 44, 256, 32, 8),    # one-row accumulators (128-pixel rows), ragged last row block
+    (64, 64, 40, 128, 64, 4),
+    (384, 128, 6, 128, 128, 2),  # 24 channel steps through a ring of fewer stages
+    (256, 256, 30, 64, 256, 1),  # two image rows per accumulator
+    (128, 256, 30, 64, 64, 2),   # four rows per CTA, ragged
+    (64, 96, 20, 32, 32, 2),     # four rows per accumulator
+    (16, 32, 40, 72, 32, 1),     # eight-pixel-wide strips
+    (96, 32, 16, 40, -1, 0),     # the gather kernel
+])
+def test_conv_tilings_match_float64(Cin, Cout, H, W, tile_n, tile_mma):
+    """Every tiling of the TMA-fed convolution (halo boxes for 128-pixel rows,
+    shifted column copies for narrower strips, channel splits, several
+    accumulators per CTA) gives the float64 sums of the same BF16 operands to
+    FP32 accumulation accuracy."""
+    torch = pytest.importorskip("torch")
+    import torch.nn.functional as F
+
+    P = pic()
+    g = torch.Generator().manual_seed(Cin * 13 + Cout + H)
+    x = torch.randn(H * W, Cin, generator=g).to(torch.bfloat16)
+    w = (torch.randn(Cout, 9, Cin, generator=g) / (3 * Cin ** 0.5)).to(torch.bfloat16)
+    bias = torch.randn(Cout, generator=g).float()
+    xd, wd, bd = x.cuda(), w.cuda(), bias.cuda()
+    ref = F.conv2d(x.double().T.reshape(1, Cin, H, W), w.double().reshape(Cout, 3, 3, Cin).permute(0, 3, 1, 2),
+                   padding=1)[0].reshape(Cout, -1).T
+    out = torch.full((H * W, Cout), float("nan"), device="cuda")
+    assert P.conv3x3_op(0, H, W, xd.data_ptr(), Cin, wd.data_ptr(), 0, out.data_ptr(), Cout,
+                        tile_n=tile_n, tile_mma=tile_mma) == 0
+    o = out.cpu().double().numpy()
+    assert np.isfinite(o).all()
+    assert rel_l2(o, ref.numpy()) <= 1e-5
+    assert np.abs(o - ref.numpy()).max() <= 1e-5 * np.abs(ref.numpy()).max()
+    outb = torch.zeros(H * W, Cout, dtype=torch.bfloat16, device="cuda")
+    assert P.conv3x3_op(1, H, W, xd.data_ptr(), Cin, wd.data_ptr(), bd.data_ptr(), outb.data_ptr(), Cout,
+                        tile_n=tile_n, tile_mma=tile_mma) == 0
+    refb = torch.relu(ref + bias.double()).to(torch.bfloat16).double()
+    pre = (ref + bias.double()).abs().max().item()
+    assert ((outb.cpu().double() - refb).abs() <= 2.0 ** -7 * refb.abs() + 1e-5 * pre).all()
+
+
+def test_conv_forced_tiling_that_does_not_fit_is_rejected():
+    torch = pytest.importorskip("torch")
+    P = pic()
+    x = torch.zeros(16 * 20, 32, dtype=torch.bfloat16, device="cuda")
+    w = torch.zeros(64, 9, 32, dtype=torch.bfloat16, device="cuda")
+    out = torch.zeros(16 * 20, 64, device="cuda")
+    # W = 20 has no 8-pixel strip; 48 output channels are not a multiple of 32
+    assert P.conv3x3_op(0, 16, 20, x.data_ptr(), 32, w.data_ptr(), 0, out.data_ptr(), 64, tile_n=64) != 0
+    assert P.conv3x3_op(0, 16, 24, x.data_ptr(), 32, w.data_ptr(), 0, out.data_ptr(), 48, tile_n=32) != 0
