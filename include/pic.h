@@ -67,6 +67,10 @@ extern "C" {
 #define PIC_SOLVER_PLAIN 0 /* FP64 Jacobi-preconditioned CG                        */
 #define PIC_SOLVER_MIXED 1 /* FP32 inner CG in one thread-block cluster, FP64
                               residual and iterative refinement                    */
+#define PIC_SOLVER_LEARNED 2 /* flexible CG preconditioned by the attached U-Net
+                              (pic_attach_unet), FP64 recurrences; the plain or
+                              mixed PCG then confirms the residual and finishes
+                              the solve if the learned loop stopped short     */
 
 /* ---- configuration ------------------------------------------------------
  * Everything that defines one discharge (Sec. 2: reactor geometry on a
@@ -178,6 +182,8 @@ int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss);
 #define PIC_DIAG_RHO 8     /* node charge rho~ (incl. surface) [nodes] */
 #define PIC_DIAG_NE_AVG 9  /* last window's mean n_e, m^-3     [nodes] */
 #define PIC_DIAG_NI_AVG 10 /* last window's mean n_i, m^-3     [nodes] */
+#define PIC_DIAG_PHI_WARM 11 /* warm start of the last solve, V (kept by
+                                pic_keep_warm or the learned solver) [nodes] */
 #define PIC_DIAG_SCALARS 100 /* PIC_NSCALARS doubles, see below  */
 #define PIC_NSCALARS 47
 /* Scalars: [0] step, [1] t, [2] U_E, [3] Q_E, [4] C_eq, [5] I_conv, [6] I_ccp,
@@ -279,6 +285,11 @@ int pic_unet_zero_grads(pic_unet *u);
 int pic_unet_forward(pic_unet *u, const float *in, float *out);
 /* backward of the last forward for dLoss/dout (device [H*W]); adds to the gradients */
 int pic_unet_backward(pic_unet *u, const float *gout);
+/* Relative L2 loss of the last forward's output o against target t (device
+ * FP32 [H*W]) over the pixels where in3's channel 2 (the Dirichlet mask) is 0:
+ * L = sum (o - t)^2 / sum t^2.  Adds dL/do's backward to the gradients and L
+ * to *loss (device FP32, may be NULL).  Asynchronous. */
+int pic_unet_loss_backward(pic_unet *u, const float *in3, const float *target, float *loss);
 /* one Adam step (t = step number from 1) on the accumulated gradients */
 int pic_unet_adam(pic_unet *u, float lr, float beta1, float beta2, float eps, int t);
 /* synchronise; *err = 1 if a bounded tensor-core wait timed out since the last call */
@@ -300,6 +311,41 @@ int pic_conv3x3_op(int op, int H, int W, const void *in, int Cin, const void *w,
  * gather kernel.  PIC_EINVAL if the forced tiling does not fit. */
 int pic_conv3x3_op_ex(int op, int H, int W, const void *in, int Cin, const void *w, const float *bias, void *out,
                       int Cout, int tile_n, int tile_mma, void *cuda_stream);
+
+/* ---- learned field solve -------------------------------------------------
+ * pic_attach_unet -- use network u (created with H = nz, W = nr; it covers
+ * nodes i < nr, j < nz) as the preconditioner of PIC_SOLVER_LEARNED solves:
+ * z = s U(D^-1 r / s, chi, Dirichlet mask) with D the operator diagonal and s
+ * the rms of D^-1 r over the covered free nodes, followed by `smooth` (0..8)
+ * damped Jacobi steps z += (2/3) D^-1 (r - A z); flexible CG with one stored
+ * direction, at most `maxit` network applications per solve, then the solver
+ * `finish` (PIC_SOLVER_PLAIN or PIC_SOLVER_MIXED) confirms the FP64 residual
+ * and finishes the solve from the learned iterate when needed.  The first
+ * application on the warm start's residual is the learned initial-guess
+ * correction.  u = NULL detaches.  The handle does not own u; keep it alive
+ * while attached.  Builds one CUDA graph with a device-side loop.
+ * Errors: PIC_EINVAL (grid mismatch), PIC_ENOMEM, PIC_ECUDA. */
+int pic_attach_unet(pic_handle *h, pic_unet *u, int maxit, int smooth, int finish);
+/* pic_keep_warm -- keep a copy of each solve's warm start (needed by
+ * pic_learned_pair with the plain and mixed solvers). */
+int pic_keep_warm(pic_handle *h, int on);
+/* pic_learned_snapshot -- in later learned solves, keep the iterate after k
+ * network applications (k = 0: off) for pic_learned_pair(source 1). */
+int pic_learned_snapshot(pic_handle *h, int k);
+/* pic_learned_pair -- a training pair of the last solve, from a start
+ * phi_w (source 0: the solve's warm start; source 1: the learned iterate kept by
+ * pic_learned_snapshot, valid when that solve made at least k applications) and
+ * the solution phi: r0 = b - A phi_w, delta = phi - phi_w = A^-1 r0, and with
+ * s = rms of D^-1 r0 over the covered free nodes:
+ *   in3    (device FP32 [3][nz*nr]) = D^-1 r0 / s, chi, Dirichlet mask,
+ *   target (device FP32 [nz*nr])    = delta / s  (0 at Dirichlet nodes);
+ * *scale = s.  Synchronises. */
+int pic_learned_pair(pic_handle *h, int source, float *in3, float *target, double *scale);
+/* pic_learned_stats -- last learned solve: [0] network applications,
+ * [1] its final relative residual, [2] its status (0 converged, -4 hit maxit,
+ * -7 non-finite: restarted from the warm start), [3] iterations the plain PCG
+ * added afterwards (0 when the learned solve met the tolerance). */
+int pic_learned_stats(pic_handle *h, double *out4);
 
 const char *pic_strerror(int code);
 void pic_destroy(pic_handle *h);

@@ -13,8 +13,10 @@
 #include <vector>
 
 #include "../../include/pic.h"
+#include "learned.h"
 #include "pic_device.cuh"
 #include "pic_kernels.h"
+#include "unet.h"
 
 using namespace pic;
 
@@ -82,6 +84,16 @@ struct pic_handle {
   double timing_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> tev;  // 8 events per timed step
   std::vector<void *> allocs;
+  // learned preconditioner (PIC_SOLVER_LEARNED)
+  pic_unet *net = nullptr;
+  cudaGraphExec_t fcg_exec = nullptr;
+  cudaStream_t side = nullptr;
+  learned::FcgParams fcg{};
+  int fcg_nblk = 0;
+  double *d_phi_warm = nullptr, *d_lstats = nullptr, *d_pair_s2 = nullptr;
+  bool keep_warm = false;
+  int learned_finish = PIC_SOLVER_PLAIN;  // solver that confirms / finishes a learned solve
+  std::vector<void *> lallocs;  // learned-solver buffers (freed on re-attach)
 };
 
 namespace {
@@ -362,12 +374,47 @@ int enqueue_particle_phase(pic_handle *h, int in_buf) {
   return launch_push(h, in_buf);
 }
 
+// If the learned solve ended on a non-finite value, restart from the warm start.
+__global__ void k_restore_warm(int nn, const int8_t *kind, const double *stats, const double *warm, double *phi) {
+  if (stats[2] != -7.0) return;
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nn; a += gridDim.x * blockDim.x)
+    if (kind[a] == 0) phi[a] = warm[a];
+}
+
 int enqueue_solve(pic_handle *h, int mode) {
+  if (h->keep_warm || mode == PIC_SOLVER_LEARNED)
+    CK(cudaMemcpyAsync(h->d_phi_warm, h->d_phi, sizeof(double) * h->nn, cudaMemcpyDeviceToDevice, h->stream));
+  if (mode == PIC_SOLVER_LEARNED) {
+    // flexible CG with the network; the plain PCG below then confirms the
+    // residual in FP64 (zero iterations when it holds) or finishes the solve
+    if (!h->fcg_exec) return PIC_EINVAL;
+    CK(cudaGraphLaunch(h->fcg_exec, h->stream));
+    k_restore_warm<<<h->fcg_nblk, 256, 0, h->stream>>>(h->nn, h->d_node_kind, h->d_lstats, h->d_phi_warm, h->d_phi);
+    CK(cudaGetLastError());
+  }
   CK(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
   PcgParams P = pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, h->d_phi, h->cfg.pcg_tol, h->d_pcg_out);
-  if (mode == PIC_SOLVER_MIXED) CK(launch_pcg_mixed(P, h->pcg_grid, h->stream));
+  const int finisher = mode == PIC_SOLVER_LEARNED ? h->learned_finish : mode;
+  if (finisher == PIC_SOLVER_MIXED) CK(launch_pcg_mixed(P, h->pcg_grid, h->stream));
   else CK(launch_pcg(P, h->pcg_grid, h->stream));
   return PIC_OK;
+}
+
+// Parameters of the learned solve / training pairs (network grid nz x nr).
+learned::FcgParams fcg_params(pic_handle *h) {
+  learned::FcgParams F;
+  memset(&F, 0, sizeof(F));
+  F.nr = h->nr; F.nz = h->nz; F.nn = h->nn;
+  F.H = h->nz; F.W = h->nr;
+  int n = 0;
+  for (int j = 0; j < h->nz; ++j)
+    for (int i = 0; i < h->nr; ++i) n += h->node_kind[nidx(h, i, j)] == 0;
+  F.n_cov = n;
+  F.node_kind = h->d_node_kind;
+  F.Gr = h->d_Gr; F.Gz = h->d_Gz; F.dinv = h->d_dinv; F.qrhs = h->d_qrhs; F.chi = h->d_chi;
+  F.phi = h->d_phi;
+  F.tol = h->cfg.pcg_tol;
+  return F;
 }
 
 int enqueue_step(pic_handle *h, int in_buf, cudaEvent_t *ev) {
@@ -415,7 +462,18 @@ int sync(pic_handle *h) {
   return PIC_OK;
 }
 
+void free_learned(pic_handle *h) {
+  if (h->fcg_exec) cudaGraphExecDestroy(h->fcg_exec);
+  h->fcg_exec = nullptr;
+  for (void *p : h->lallocs) cudaFree(p);
+  h->lallocs.clear();
+  h->net = nullptr;
+}
+
 void free_all(pic_handle *h) {
+  free_learned(h);
+  if (h->side) cudaStreamDestroy(h->side);
+  h->side = nullptr;
   for (int k = 0; k < 2; ++k)
     if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
   for (cudaEvent_t e : h->tev) cudaEventDestroy(e);
@@ -465,7 +523,7 @@ bool check_config(const pic_config *c) {
   if (!c->node_kind || !c->cell_kind || !c->cell_eps || !c->xs_energy || !c->xs_sigma || c->n_xs < 2) return false;
   if (c->circuit < 0 || c->circuit > 2 || c->n_sub < 1 || c->steps_per_rf < 1 || c->pcg_maxit < 1) return false;
   if (c->precision != PIC_FP32 && c->precision != PIC_FP64) return false;
-  if (c->solver != PIC_SOLVER_PLAIN && c->solver != PIC_SOLVER_MIXED) return false;
+  if (c->solver != PIC_SOLVER_PLAIN && c->solver != PIC_SOLVER_MIXED && c->solver != PIC_SOLVER_LEARNED) return false;
   if (c->capacity[0] < 1 || c->capacity[1] < 1 || c->capacity[0] > 2000000000ll || c->capacity[1] > 2000000000ll)
     return false;
   if (!(c->m[0] > 0) || !(c->m[1] > 0) || !(c->m_gas > 0)) return false;
@@ -690,6 +748,9 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
     DA(h->d_partial, sizeof(double) * 16 * (h->pcg_grid + 32));
     DA(h->d_bar, 4 * sizeof(unsigned));
     DA(h->d_pcg_out, sizeof(double) * 8);
+    DA(h->d_phi_warm, sizeof(double) * nn);
+    DA(h->d_lstats, sizeof(double) * 4);
+    DA(h->d_pair_s2, sizeof(double) * 2);
     DA(h->d_energy, sizeof(double) * 2);
     DA(h->d_ceq_out, sizeof(double) * 2);
     DA(h->d_counters, sizeof(unsigned long long) * CNT_N);
@@ -858,7 +919,8 @@ int pic_step(pic_handle *h, int nsteps) {
       int st = enqueue_step(h, buf, ev);
       if (st) return st;
     } else {
-      if (!h->graph[buf] && !h->graph_failed) {
+      if (h->cfg.solver == PIC_SOLVER_LEARNED && !h->fcg_exec) return PIC_EINVAL;
+      if (!h->graph[buf] && !h->graph_failed && h->cfg.solver != PIC_SOLVER_LEARNED) {
         if (capture_graph(h, buf)) h->graph_failed = true;
       }
       if (h->graph[buf]) {
@@ -901,7 +963,8 @@ int pic_step_timing(pic_handle *h, double *out7) {
 }
 
 int pic_field_solve(pic_handle *h, int mode, int *iters, double *rel_resid) {
-  if (!h || (mode != PIC_SOLVER_PLAIN && mode != PIC_SOLVER_MIXED)) return PIC_EINVAL;
+  if (!h || (mode != PIC_SOLVER_PLAIN && mode != PIC_SOLVER_MIXED && mode != PIC_SOLVER_LEARNED)) return PIC_EINVAL;
+  if (mode == PIC_SOLVER_LEARNED && !h->fcg_exec) return PIC_EINVAL;
   CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
   int st = enqueue_solve(h, mode);
   if (st) return st;
@@ -913,6 +976,107 @@ int pic_field_solve(pic_handle *h, int mode, int *iters, double *rel_resid) {
   if (rel_resid) *rel_resid = out[1];
   int s = (int)out[2];
   return s == 0 ? PIC_OK : (s == -5 ? PIC_ETIMEOUT : (s == -7 ? PIC_ENAN : PIC_ENOCONV));
+}
+
+int pic_attach_unet(pic_handle *h, pic_unet *u, int maxit, int smooth, int finish) {
+  if (!h || maxit < 1 || smooth < 0 || smooth > 8) return PIC_EINVAL;
+  if (finish != PIC_SOLVER_PLAIN && finish != PIC_SOLVER_MIXED) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  free_learned(h);
+  if (!u) return PIC_OK;
+  int H = 0, W = 0;
+  unet::net_dims(u, &H, &W);
+  if (H != h->nz || W != h->nr) return PIC_EINVAL;
+  if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  learned::FcgParams F = fcg_params(h);
+  if (F.n_cov == 0) return PIC_EINVAL;
+  const int nblk = learned::node_blocks(h->device);
+  const size_t nn = h->nn;
+  auto la = [&](void **p, size_t bytes) -> int {
+    if (cudaMalloc(p, bytes) != cudaSuccess) { cudaGetLastError(); return PIC_ENOMEM; }
+    h->lallocs.push_back(*p);
+    return cudaMemsetAsync(*p, 0, bytes, h->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+  };
+  int st = 0;
+  void *v = nullptr;
+  st |= la(&v, sizeof(double) * 7 * nn);
+  if (st) { free_learned(h); return PIC_ENOMEM; }
+  double *d = (double *)v;
+  F.r = d; F.z = d + nn; F.p[0] = d + 2 * nn; F.p[1] = d + 3 * nn; F.q[0] = d + 4 * nn; F.q[1] = d + 5 * nn;
+  F.z2 = d + 6 * nn;
+  F.smooth = smooth;
+  F.omega = 2.0 / 3.0;
+  st |= la(&v, sizeof(double) * 4 * 4 * nblk); F.part = (double *)v;
+  st |= la(&v, sizeof(double) * 8); F.sc = (double *)v;
+  st |= la(&v, sizeof(double) * nn); F.snap = (double *)v;
+  st |= la(&v, sizeof(float) * 3 * (size_t)H * W); F.in3 = (float *)v;
+  st |= la(&v, sizeof(float) * (size_t)H * W); F.out_net = (float *)v;
+  if (st) { free_learned(h); return PIC_ENOMEM; }
+  F.maxit = maxit;
+  F.stats = h->d_lstats;
+  if (sync(h)) { free_learned(h); return PIC_ECUDA; }
+  cudaError_t e = learned::build_fcg_graph(F, nblk, u, h->side, &h->fcg_exec);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "pic: learned solver graph: %s\n", cudaGetErrorString(e));
+    h->fcg_exec = nullptr;
+    free_learned(h);
+    return PIC_ECUDA;
+  }
+  h->fcg = F;
+  h->fcg_nblk = nblk;
+  h->net = u;
+  h->learned_finish = finish;
+  return PIC_OK;
+}
+
+int pic_keep_warm(pic_handle *h, int on) {
+  if (!h) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  if (h->keep_warm != (on != 0)) {
+    // the step graphs hold the solve sequence: capture them again
+    for (int k = 0; k < 2; ++k)
+      if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    h->graph[0] = h->graph[1] = nullptr;
+    h->graph_failed = false;
+  }
+  h->keep_warm = on != 0;
+  return PIC_OK;
+}
+
+int pic_learned_snapshot(pic_handle *h, int k) {
+  if (!h || k < 0 || !h->fcg_exec) return PIC_EINVAL;
+  double v = (double)k;
+  CK(cudaMemcpyAsync(h->fcg.sc + 6, &v, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  return sync(h);
+}
+
+int pic_learned_pair(pic_handle *h, int source, float *in3, float *target, double *scale) {
+  if (!h || !in3 || !target || source < 0 || source > 1) return PIC_EINVAL;
+  if (source == 0 && !h->keep_warm && !h->fcg_exec) return PIC_EINVAL;
+  if (source == 1 && !h->fcg_exec) return PIC_EINVAL;
+  learned::FcgParams F = fcg_params(h);
+  if (F.n_cov == 0) return PIC_EINVAL;
+  F.in3 = in3;
+  const double *from = source == 0 ? h->d_phi_warm : h->fcg.snap;
+  CK(learned::launch_pair(F, learned::node_blocks(h->device), from, target, h->d_pair_s2, h->stream));
+  double s2 = 0.0;
+  CK(cudaMemcpyAsync(&s2, h->d_pair_s2, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  if (sync(h)) return PIC_ECUDA;
+  if (scale) *scale = std::sqrt(s2 / (double)F.n_cov);
+  return PIC_OK;
+}
+
+int pic_learned_stats(pic_handle *h, double *out4) {
+  if (!h || !out4) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  double ls[4], ps[3];
+  CK(cudaMemcpy(ls, h->d_lstats, sizeof(ls), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(ps, h->d_pcg_out, sizeof(ps), cudaMemcpyDeviceToHost));
+  out4[0] = ls[0];
+  out4[1] = ls[1];
+  out4[2] = ls[2];
+  out4[3] = ps[0];
+  return PIC_OK;
 }
 
 int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss) {
@@ -968,6 +1132,7 @@ int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
     case PIC_DIAG_RHO: CK(cudaMemcpy(o, h->d_qrhs, nb, cudaMemcpyDeviceToHost)); return PIC_OK;
     case PIC_DIAG_NE_AVG: CK(cudaMemcpy(o, h->d_dens_avg[0], nb, cudaMemcpyDeviceToHost)); return PIC_OK;
     case PIC_DIAG_NI_AVG: CK(cudaMemcpy(o, h->d_dens_avg[1], nb, cudaMemcpyDeviceToHost)); return PIC_OK;
+    case PIC_DIAG_PHI_WARM: CK(cudaMemcpy(o, h->d_phi_warm, nb, cudaMemcpyDeviceToHost)); return PIC_OK;
     case PIC_DIAG_DEP_E:
     case PIC_DIAG_DEP_I: {
       std::vector<unsigned long long> u(h->nn);

@@ -60,6 +60,9 @@ struct pic_unet {
   bool use_f[kNConv] = {}, use_g[kNConv] = {};
   __nv_bfloat16 *wpk[kNConv], *wtpk[kNConv];
   bool tuning = false;  // set while pic_unet_create times the candidate tilings
+  const float *last_out = nullptr;  // output of the last forward
+  float *gout = nullptr;            // loss gradient scratch [H*W]
+  double *loss_sums = nullptr;      // [2]
 };
 
 namespace {
@@ -256,6 +259,35 @@ __global__ void k_out_bwd(const float *gout, const __nv_bfloat16 *d0, int HW, co
   }
   __syncthreads();
   if (threadIdx.x < 33) atomicAdd(&gw[threadIdx.x], s[threadIdx.x]);
+}
+
+// Relative L2 loss over free pixels (mask channel == 0): sums t^2 and (o-t)^2.
+__global__ void k_loss_sums(const float *o, const float *t, const float *mask, int HW, double *sums) {
+  double a = 0.0, b = 0.0;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x) {
+    if (mask[p] != 0.0f) continue;
+    const double tv = t[p], d = (double)o[p] - tv;
+    a += tv * tv;
+    b += d * d;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[0], a);
+    atomicAdd(&sums[1], b);
+  }
+}
+
+// dL/do = 2 (o - t) / sum t^2 on free pixels; adds L to *loss.
+__global__ void k_loss_grad(const float *o, const float *t, const float *mask, int HW, const double *sums, float *g,
+                            float *loss) {
+  const double t2 = sums[0] > 0.0 ? sums[0] : 1.0;
+  const float sc = (float)(2.0 / t2);
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < HW; p += gridDim.x * blockDim.x)
+    g[p] = mask[p] != 0.0f ? 0.0f : sc * (o[p] - t[p]);
+  if (loss && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(loss, (float)(sums[1] / t2));
 }
 
 // Adam on one conv layer: master W [cout][9][cin] from gradient gWt [(tap*cin+ci)*cout+co];
@@ -502,6 +534,8 @@ int pic_unet_create(int H, int W, void *cuda_stream, pic_unet **out) {
     UA(u->g_a2, p2 * 128 * 4); UA(u->g_pool1, p2 * 64 * 4); UA(u->g_a1, p1 * 64 * 4); UA(u->g_pool0, p1 * 32 * 4);
     UA(u->g_a0, p0 * 32 * 4);
     UA(u->dpre, p0 * 64 * 2);  // largest Cout x pixels among the layers
+    UA(u->gout, p0 * 4);
+    UA(u->loss_sums, 2 * sizeof(double));
     UA(u->err, 16);
     // TMA tilings and tensor maps (input buffers are fixed for the network's life)
     const Tensor *fin[kNConv] = {&u->in0, &u->a0, &u->pool0, &u->a1, &u->pool1, &u->a2, &u->pool2,
@@ -646,6 +680,7 @@ int pic_unet_forward(pic_unet *u, const float *in, float *out) {
   st |= conv_fwd(u, 13, u->d0a, 0, u->d0, 0);
   k_out_fwd<<<grid_for(H * W), 256, 0, s>>>(u->d0.p, H * W, u->w_out, u->b_out, out ? out : u->out);
   UK(cudaGetLastError());
+  u->last_out = out ? out : u->out;
   return st ? PIC_ECUDA : PIC_OK;
 }
 
@@ -684,6 +719,38 @@ int pic_unet_backward(pic_unet *u, const float *gout) {
   (void)p0;
   UK(cudaGetLastError());
   return st ? PIC_ECUDA : PIC_OK;
+}
+
+}  // extern "C"
+
+namespace pic {
+namespace unet {
+int forward_on_stream(pic_unet *u, const float *in, float *out, cudaStream_t s) {
+  if (!u) return PIC_EINVAL;
+  cudaStream_t keep = u->stream;
+  u->stream = s;
+  int st = pic_unet_forward(u, in, out);
+  u->stream = keep;
+  return st;
+}
+void net_dims(const pic_unet *u, int *H, int *W) {
+  *H = u ? u->H : 0;
+  *W = u ? u->W : 0;
+}
+}  // namespace unet
+}  // namespace pic
+
+extern "C" {
+
+int pic_unet_loss_backward(pic_unet *u, const float *in3, const float *target, float *loss) {
+  if (!u || !in3 || !target || !u->last_out) return PIC_EINVAL;
+  const int HW = u->H * u->W;
+  const float *mask = in3 + 2 * (size_t)HW;
+  UK(cudaMemsetAsync(u->loss_sums, 0, 2 * sizeof(double), u->stream));
+  k_loss_sums<<<grid_for(HW), 256, 0, u->stream>>>(u->last_out, target, mask, HW, u->loss_sums);
+  k_loss_grad<<<grid_for(HW), 256, 0, u->stream>>>(u->last_out, target, mask, HW, u->loss_sums, u->gout, loss);
+  UK(cudaGetLastError());
+  return pic_unet_backward(u, u->gout);
 }
 
 int pic_unet_adam(pic_unet *u, float lr, float beta1, float beta2, float eps, int t) {

@@ -5,6 +5,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include "../../include/pic.h"
+
 namespace pic {
 namespace unet {
 
@@ -68,6 +70,12 @@ cudaError_t make_input_map(CUtensorMap *m, const __nv_bfloat16 *base, int cs, in
 cudaError_t pack_weights(const __nv_bfloat16 *w, int Cin, int Cout, int N, __nv_bfloat16 *dst, cudaStream_t st);
 cudaError_t launch_conv_tma(const CUtensorMap &tin, const ConvArgs &a, const ConvGeom &g,
                             const __nv_bfloat16 *wpk, cudaStream_t st);
+
+// Network forward (as pic_unet_forward) enqueued on stream s instead of the
+// network's own stream (used to capture it into the solver's graph).
+int forward_on_stream(pic_unet *u, const float *in, float *out, cudaStream_t s);
+// Grid of the network.
+void net_dims(const pic_unet *u, int *H, int *W);
 
 // cp.async gather kernel (any W; Cin multiple of 16, Cout <= 256).
 cudaError_t launch_conv3x3(const ConvArgs &a, cudaStream_t st);

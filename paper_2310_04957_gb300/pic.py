@@ -17,9 +17,9 @@ LIB_PATH = os.path.join(_HERE, "libpic_gb300.so")
 PIC_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT", -6: "EOVERFLOW", -7: "ENAN"}
 PIC_FP32, PIC_FP64 = 0, 1
-PIC_SOLVER_PLAIN, PIC_SOLVER_MIXED = 0, 1
+PIC_SOLVER_PLAIN, PIC_SOLVER_MIXED, PIC_SOLVER_LEARNED = 0, 1, 2
 DIAG = {"phi": 0, "Er": 1, "Ez": 2, "chi": 3, "dep_e": 4, "dep_i": 5, "sigma": 6, "vnode": 7, "rho": 8,
-        "ne_avg": 9, "ni_avg": 10}
+        "ne_avg": 9, "ni_avg": 10, "phi_warm": 11}
 DIAG_SCALARS = 100
 NSCALARS = 47
 SCALARS = ["step", "t", "U_E", "Q_E", "C_eq", "I_conv", "I_ccp", "y0", "y1", "y2", "y3", "y4", "y5", "pcg_iters",
@@ -35,7 +35,8 @@ EXPORTS = ["pic_init", "pic_set_particles", "pic_count", "pic_get_particles", "p
            "pic_pcg_solve_static", "pic_unet_create", "pic_unet_destroy", "pic_unet_param_count",
            "pic_unet_set_params", "pic_unet_get_params", "pic_unet_get_grads", "pic_unet_zero_grads",
            "pic_unet_forward", "pic_unet_backward", "pic_unet_adam", "pic_unet_status", "pic_conv3x3_op",
-           "pic_conv3x3_op_ex"]
+           "pic_conv3x3_op_ex", "pic_attach_unet", "pic_keep_warm", "pic_learned_pair", "pic_learned_stats",
+           "pic_unet_loss_backward", "pic_learned_snapshot"]
 STATIC_MAX_NODES = 139264
 
 
@@ -276,6 +277,37 @@ class Discharge:
         _check(lib().pic_step_timing(self.h, _p(o)), "pic_step_timing")
         return o
 
+    # -- learned field solve
+    def attach_unet(self, net, maxit=200, smooth=0, finish=PIC_SOLVER_PLAIN):
+        """Use `net` (a UNet of H = nz, W = nr) in PIC_SOLVER_LEARNED solves: at most
+        maxit network applications, then `finish` confirms / completes the solve."""
+        L = lib()
+        L.pic_attach_unet.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        _check(L.pic_attach_unet(self.h, net.h if net is not None else None, maxit, smooth, finish),
+               "pic_attach_unet")
+        self._net = net
+
+    def keep_warm(self, on=True):
+        _check(lib().pic_keep_warm(self.h, int(on)), "pic_keep_warm")
+
+    def learned_pair(self, in3_ptr, target_ptr, source=0):
+        """Training pair of the last solve into device FP32 buffers; returns the scale s.
+        source 0: from the warm start; 1: from the kept learned iterate."""
+        L = lib()
+        L.pic_learned_pair.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+        s = ctypes.c_double()
+        _check(L.pic_learned_pair(self.h, source, in3_ptr, target_ptr, ctypes.byref(s)), "pic_learned_pair")
+        return s.value
+
+    def learned_snapshot(self, k):
+        _check(lib().pic_learned_snapshot(self.h, k), "pic_learned_snapshot")
+
+    def learned_stats(self):
+        o = np.zeros(4)
+        _check(lib().pic_learned_stats(self.h, _p(o)), "pic_learned_stats")
+        return o
+
 
 def pcg_solve_static(nr, nz, node_kind, Gr, Gz, qrhs, phi, tol, maxit, stream=None):
     """Call pic_pcg_solve_static on caller-owned device arrays (raw device pointers as ints).
@@ -342,6 +374,14 @@ class UNet:
 
     def backward(self, gout_ptr):
         _check(lib().pic_unet_backward(self.h, ctypes.c_void_p(gout_ptr)), "pic_unet_backward")
+
+    def loss_backward(self, in3_ptr, target_ptr, loss_ptr=0):
+        """Relative L2 loss of the last forward against the target over free pixels;
+        backpropagates it and adds it to the device float at loss_ptr (if nonzero)."""
+        L = lib()
+        L.pic_unet_loss_backward.argtypes = [ctypes.c_void_p] * 4
+        _check(L.pic_unet_loss_backward(self.h, ctypes.c_void_p(in3_ptr), ctypes.c_void_p(target_ptr),
+                                        ctypes.c_void_p(loss_ptr) if loss_ptr else None), "pic_unet_loss_backward")
 
     def adam(self, lr, t, beta1=0.9, beta2=0.999, eps=1e-8):
         _check(lib().pic_unet_adam(self.h, lr, beta1, beta2, eps, t), "pic_unet_adam")

@@ -280,4 +280,14 @@ def gec_512(n_per_species=32_000_000, **kw):
                  CIRCUIT_IMN, IMN_GEC, 150.0, 2, n_particles_override=n_per_species, **kw)
 
 
+def gec_case(nr, nz, pressure_mtorr, V_src, cm2=200e-12, n_per_species=1_000_000, seed_index=16, name=None):
+    """GEC-like cell on an nr x nz grid at a given pressure, source amplitude and
+    series matching capacitor (the L-network of IMN_GEC otherwise)."""
+    circ = list(IMN_GEC)
+    circ[3] = cm2
+    nm = name or f"gec-{nr}x{nz}-{pressure_mtorr:g}mT-{V_src:g}V"
+    return _make(nm, nr, nz, 0.10, 0.06, "gec", pressure_mtorr, n_per_species, 200, CIRCUIT_IMN, tuple(circ), V_src,
+                 seed_index, n_particles_override=n_per_species)
+
+
 PRESETS = {"c1": small_cylinder, "c2": gec_256, "c3": gec_512}
