@@ -40,10 +40,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
     ap.add_argument("--solver", default="plain", choices=["plain", "mixed"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -200,10 +201,110 @@ def run_reference(args):
     return 0
 
 
+def field_solve_comparison(wl, steps=5):
+    """Field solve to 1e-10 relative residual from the same warm starts: plain FP64
+    PCG, mixed PCG, and the learned solve (network trained here, on this workload's
+    own run, by the library's kernels: up to 3 network applications, then the mixed
+    PCG finishes).  Medians over `steps` consecutive steps of ms per
+    pic_field_solve call (assembly + solve + E field + one scalar read)."""
+    import statistics
+
+    from paper_2310_04957_gb300 import learned as Lr
+    from paper_2310_04957_gb300 import pic
+
+    net, d, info = Lr.train_on_discharge(wl)
+    d.keep_warm(True)
+    d.attach_unet(net, maxit=3, finish=pic.PIC_SOLVER_MIXED)
+    rows = {0: [], 1: [], 2: []}
+    for _ in range(steps):
+        d.step(1)
+        r = Lr.compare_solvers(d, repeats=2)
+        for m in rows:
+            rows[m].append(r[m])
+    med = lambda m, k: statistics.median(x[k] for x in rows[m])
+    out = {"tol": wl.pcg_tol, "steps": steps,
+           "plain": {"ms": med(0, 3), "iters": med(0, 1)},
+           "mixed": {"ms": med(1, 3), "inner_iters": med(1, 1)},
+           "learned_mixed": {"ms": med(2, 3), "network_applications": statistics.median(x[4][0] for x in rows[2]),
+                             "finisher_inner_iters": med(2, 1),
+                             "max_rel_residual": max(x[2] for x in rows[2])},
+           "training": info}
+    out["learned_vs_plain"] = out["plain"]["ms"] / out["learned_mixed"]["ms"]
+    out["learned_vs_mixed"] = out["mixed"]["ms"] / out["learned_mixed"]["ms"]
+    d.close()
+    net.close()
+    return out
+
+
+def run_sweep(args):
+    """64 discharges of the seeded Latin-hypercube sweep (uneven grids and
+    particle counts): autotuned particle tiles, then each discharge stepped alone
+    (the sum of their times) against all of them stepped by one batch graph per
+    step.  Host-timed with the device synchronised on both sides."""
+    import torch
+
+    from paper_2310_04957_gb300 import build
+
+    build.build()
+    from paper_2310_04957_gb300 import pic, sweep
+
+    torch.cuda.set_device(0)
+    t_setup = time.perf_counter()
+    pts = sweep.design(64, seed=4)
+    wls = sweep.workloads(pts)
+    choice, timings = sweep.autotune_tiles(wls)
+    ds = [pic.Discharge(wl, solver=pic.PIC_SOLVER_MIXED, tile=choice[sweep.tile_class(wl)]) for wl in wls]
+    for d in ds:
+        d.start()
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t_setup
+    K, Wm = args.steps, args.warmup
+    seq_s, ps = 0.0, 0.0
+    for d in ds:
+        d.step(Wm)
+        torch.cuda.synchronize()
+        n = d.count(0) + d.count(1)
+        t0 = time.perf_counter()
+        d.step(K)
+        torch.cuda.synchronize()
+        seq_s += time.perf_counter() - t0
+        ps += n * K
+    b = pic.Batch(ds)
+    b.step(Wm)
+    b.sync()
+    n = sum(d.count(0) + d.count(1) for d in ds)
+    with ClockSampler(0) as clk:
+        t0 = time.perf_counter()
+        b.step(K)
+        b.sync()
+        t_b = time.perf_counter() - t0
+    flags = 0
+    for d in ds:
+        flags |= d.status()
+    value = n * K / t_b
+    line = {"metric": "aggregate particle-steps/s, 64-discharge batch vs sequential", "value": value,
+            "unit": "particle-steps/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": 1e3 * t_b / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sweep-64-gec-lhs", "discharges": len(ds), "particles": int(n),
+                       "grids": sorted({f"{w.nr}x{w.nz}" for w in wls}), "solver": "batched mixed (one CTA per discharge)",
+                       "parallelism": "single", "l2": "inputs larger than L2"},
+            "sequential": {"value": ps / seq_s, "ms_per_step": 1e3 * seq_s / K, "solver": "mixed, one discharge at a time"},
+            "speedup_vs_sequential": (n * K / t_b) / (ps / seq_s),
+            "autotuned_tiles": {f"{c[0]}x{c[1]}": list(t) for c, t in choice.items()},
+            "autotune_ms": {f"{c[0]}x{c[1]}": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in tv.items()}
+                            for c, tv in timings.items()},
+            "setup_s": t_setup, "status_flags": flags, "clocks": clk.summary(),
+            "gpu_launches": None, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_sweep(args)
     rank, world, local = dist_env()
     import torch
 
@@ -292,6 +393,9 @@ def main():
                    "includes": "pic_init + pic_set_particles from host FP64 arrays + pic_start + per step "
                                "pic_step(1) and pic_diag(scalars)"}
             d2.close()
+    learned_cmp = None
+    if rank == 0 and not args.no_learned and args.workload in ("c2", "c3"):
+        learned_cmp = field_solve_comparison(wl)
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args.workload)
@@ -314,7 +418,7 @@ def main():
             "particle_phase": {"value": n_avg / ((phases[0] + phases[1]) / args.steps * 1e-3),
                                "unit": "particle-steps/s"},
             "field_solve": {"ms": phases[4] / args.steps, "solver": args.solver, "iters": sc["pcg_iters"] if e2e else None,
-                            "tol": wl.pcg_tol},
+                            "tol": wl.pcg_tol, "comparison": learned_cmp},
             "gpu_launches": KERNELS_PER_STEP * args.steps + KERNELS_PER_WINDOW * windows,
             "status_flags": flags,
             "clocks": clk.summary(),

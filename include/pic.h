@@ -326,6 +326,9 @@ int pic_conv3x3_op_ex(int op, int H, int W, const void *in, int Cin, const void 
  * while attached.  Builds one CUDA graph with a device-side loop.
  * Errors: PIC_EINVAL (grid mismatch), PIC_ENOMEM, PIC_ECUDA. */
 int pic_attach_unet(pic_handle *h, pic_unet *u, int maxit, int smooth, int finish);
+/* pic_set_solver -- change the solver of later steps (PIC_SOLVER_*; LEARNED
+ * needs an attached network when the step runs). */
+int pic_set_solver(pic_handle *h, int solver);
 /* pic_keep_warm -- keep a copy of each solve's warm start (needed by
  * pic_learned_pair with the plain and mixed solvers). */
 int pic_keep_warm(pic_handle *h, int on);
@@ -346,6 +349,26 @@ int pic_learned_pair(pic_handle *h, int source, float *in3, float *target, doubl
  * -7 non-finite: restarted from the warm start), [3] iterations the plain PCG
  * added afterwards (0 when the learned solve met the tolerance). */
 int pic_learned_stats(pic_handle *h, double *out4);
+
+/* ---- batched sweep ----------------------------------------------------------
+ * pic_batch_create -- step n independent discharges (a parameter sweep with
+ * uneven grids and particle counts) together.  Each step is one CUDA graph
+ * launch holding one independent chain per discharge: particle phase, circuit
+ * and assembly, then its field solve in one thread-block cluster of 1-8 CTAs
+ * by grid size (FP32 Jacobi CG inside FP64 residual refinement to the
+ * discharge's pcg_tol, whatever its cfg.solver; no grid-wide barrier, so the
+ * chains never wait on one another),
+ * then its E field and diagnostics.  The handles must share a device and be at the same buffer
+ * parity (stepped the same number of times); they stay owned by the caller and
+ * must outlive the batch.  Unstarted handles are started.
+ * pic_batch_step advances all of them by nsteps (asynchronous, except at RF
+ * window ends, which run per handle as in pic_step); pic_batch_sync waits.
+ * Errors: PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA. */
+typedef struct pic_batch pic_batch;
+int pic_batch_create(pic_handle *const *hs, int n, pic_batch **out);
+int pic_batch_step(pic_batch *b, int nsteps);
+int pic_batch_sync(pic_batch *b);
+void pic_batch_destroy(pic_batch *b);
 
 const char *pic_strerror(int code);
 void pic_destroy(pic_handle *h);

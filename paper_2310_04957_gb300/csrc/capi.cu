@@ -96,6 +96,14 @@ struct pic_handle {
   std::vector<void *> lallocs;  // learned-solver buffers (freed on re-attach)
 };
 
+// A sweep of independent discharges stepped together (see pic_batch_create).
+struct pic_batch {
+  std::vector<pic_handle *> hs;
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  PcgParams *d_params = nullptr;
+};
+
 namespace {
 
 #define CK(call)                                   \
@@ -417,9 +425,9 @@ learned::FcgParams fcg_params(pic_handle *h) {
   return F;
 }
 
-int enqueue_step(pic_handle *h, int in_buf, cudaEvent_t *ev) {
+// Step before the field solve: layout, particle phase, circuit, assembly.
+int enqueue_step_pre(pic_handle *h, int in_buf, cudaEvent_t *ev) {
   int st;
-  int out = in_buf ^ 1;
   if (ev) CK(cudaEventRecord(ev[0], h->stream));
   CK(launch_layout(layout_params(h, in_buf), h->stream));
   CK(cudaMemsetAsync(h->d_dep[0], 0, sizeof(unsigned long long) * h->nn, h->stream));
@@ -432,13 +440,24 @@ int enqueue_step(pic_handle *h, int in_buf, cudaEvent_t *ev) {
   if (ev) CK(cudaEventRecord(ev[3], h->stream));
   CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
   if (ev) CK(cudaEventRecord(ev[4], h->stream));
-  if ((st = enqueue_solve(h, h->cfg.solver))) return st;
-  if (ev) CK(cudaEventRecord(ev[5], h->stream));
+  return PIC_OK;
+}
+
+// Step after the field solve: node E field and diagnostics (advances the device step).
+int enqueue_step_post(pic_handle *h, cudaEvent_t *ev) {
   CK(launch_efield(efield_params(h), h->stream));
   if (ev) CK(cudaEventRecord(ev[6], h->stream));
   CK(launch_diag(diag_params(h), h->stream));
   if (ev) CK(cudaEventRecord(ev[7], h->stream));
   return PIC_OK;
+}
+
+int enqueue_step(pic_handle *h, int in_buf, cudaEvent_t *ev) {
+  int st;
+  if ((st = enqueue_step_pre(h, in_buf, ev))) return st;
+  if ((st = enqueue_solve(h, h->cfg.solver))) return st;
+  if (ev) CK(cudaEventRecord(ev[5], h->stream));
+  return enqueue_step_post(h, ev);
 }
 
 // C_eq from the field energy of the unit-voltage solution (Eqs. 6-7), with
@@ -654,6 +673,63 @@ int download_species(pic_handle *h, int s, pic_particles *out, int64_t capn, int
     put(slot, c % h->nr, c / h->nr);
   }
   return PIC_OK;
+}
+
+// ---- batched sweep -----------------------------------------------------------------
+void batch_free(pic_batch *b) {
+  for (int k = 0; k < 2; ++k)
+    if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+  if (b->d_params) cudaFree(b->d_params);
+  if (b->stream) cudaStreamDestroy(b->stream);
+}
+
+// Captures what `enqueue` puts on handle h's stream into a child graph node of G.
+template <class F>
+cudaError_t add_child(cudaGraph_t G, pic_handle *h, cudaStream_t cap, const cudaGraphNode_t *deps, size_t nd,
+                             cudaGraphNode_t *node, F enqueue) {
+  cudaStream_t keep = h->stream;
+  h->stream = cap;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { h->stream = keep; return e; }
+  const int st = enqueue(h);
+  e = cudaStreamEndCapture(cap, &g);
+  h->stream = keep;
+  if (st != PIC_OK && e == cudaSuccess) e = cudaErrorUnknown;
+  if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(node, G, deps, nd, g);
+  if (g) cudaGraphDestroy(g);
+  return e;
+}
+
+// One step of every discharge: per discharge the chain [layout, particles,
+// circuit, assembly] -> [field solve: one thread-block cluster] -> [E field,
+// diagnostics]; the chains are independent branches of one graph, so one
+// discharge's solve overlaps another's particle phase.
+cudaError_t batch_build(pic_batch *b, int parity) {
+  cudaGraph_t G = nullptr;
+  cudaError_t e = cudaGraphCreate(&G, 0);
+  if (e != cudaSuccess) return e;
+  const size_t n = b->hs.size();
+  std::vector<cudaGraphNode_t> pre(n), solve(n), post(n);
+  for (size_t i = 0; i < n && e == cudaSuccess; ++i) {
+    e = add_child(G, b->hs[i], b->stream, nullptr, 0, &pre[i],
+                  [&](pic_handle *h) { return enqueue_step_pre(h, parity, nullptr); });
+    if (e != cudaSuccess) break;
+    const PcgParams *params = b->d_params + i;
+    e = add_child(G, b->hs[i], b->stream, &pre[i], 1, &solve[i], [&](pic_handle *h) {
+      return launch_pcg_batch(params, 1, batch_cluster_size(h->nn), h->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+    });
+    if (e != cudaSuccess) break;
+    e = add_child(G, b->hs[i], b->stream, &solve[i], 1, &post[i],
+                  [&](pic_handle *h) { return enqueue_step_post(h, nullptr); });
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph[parity], G, 0);
+  cudaGraphDestroy(G);
+  if (e != cudaSuccess) {
+    b->graph[parity] = nullptr;
+    cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace
@@ -978,6 +1054,90 @@ int pic_field_solve(pic_handle *h, int mode, int *iters, double *rel_resid) {
   return s == 0 ? PIC_OK : (s == -5 ? PIC_ETIMEOUT : (s == -7 ? PIC_ENAN : PIC_ENOCONV));
 }
 
+int pic_batch_create(pic_handle *const *hs, int n, pic_batch **out) {
+  if (!hs || n < 1 || !out) return PIC_EINVAL;
+  *out = nullptr;
+  pic_batch *b = new (std::nothrow) pic_batch();
+  if (!b) return PIC_ENOMEM;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i] || hs[i]->device != hs[0]->device || hs[i]->cur != hs[0]->cur) { delete b; return PIC_EINVAL; }
+    for (int k = 0; k < i; ++k)
+      if (hs[k] == hs[i]) { delete b; return PIC_EINVAL; }
+    b->hs.push_back(hs[i]);
+  }
+  for (pic_handle *h : b->hs) {
+    if (!h->started) {
+      int st = pic_start(h);
+      if (st) { delete b; return st; }
+    }
+    if (sync(h)) { delete b; return PIC_ECUDA; }
+  }
+  std::vector<PcgParams> P(n);
+  for (int i = 0; i < n; ++i) {
+    pic_handle *h = b->hs[i];
+    P[i] = pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, h->d_phi, h->cfg.pcg_tol, h->d_pcg_out);
+  }
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaMalloc(&b->d_params, sizeof(PcgParams) * n) != cudaSuccess ||
+      cudaMemcpy(b->d_params, P.data(), sizeof(PcgParams) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaGetLastError();
+    batch_free(b);
+    delete b;
+    return PIC_ECUDA;
+  }
+  *out = b;
+  return PIC_OK;
+}
+
+int pic_batch_step(pic_batch *b, int nsteps) {
+  if (!b || nsteps < 0) return PIC_EINVAL;
+  for (pic_handle *h : b->hs) {
+    if (h->cur != b->hs[0]->cur) return PIC_EINVAL;
+    if (sync(h)) return PIC_ECUDA;
+    uint32_t step = h->step;
+    CK(cudaMemcpy(h->d_step, &step, sizeof(step), cudaMemcpyHostToDevice));
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    const int parity = b->hs[0]->cur;
+    if (!b->graph[parity]) {
+      cudaError_t e = batch_build(b, parity);
+      if (e != cudaSuccess) {
+        fprintf(stderr, "pic: batch graph: %s\n", cudaGetErrorString(e));
+        return PIC_ECUDA;
+      }
+    }
+    CK(cudaGraphLaunch(b->graph[parity], b->stream));
+    bool window = false;
+    for (pic_handle *h : b->hs) {
+      h->cur ^= 1;
+      h->step++;
+      window |= h->step % (uint32_t)h->cfg.steps_per_rf == 0;
+    }
+    if (window) {
+      CK(cudaStreamSynchronize(b->stream));
+      for (pic_handle *h : b->hs)
+        if (h->step % (uint32_t)h->cfg.steps_per_rf == 0) {
+          int st = window_end(h);
+          if (st) return st;
+        }
+    }
+  }
+  return PIC_OK;
+}
+
+int pic_batch_sync(pic_batch *b) {
+  if (!b) return PIC_EINVAL;
+  CK(cudaStreamSynchronize(b->stream));
+  return PIC_OK;
+}
+
+void pic_batch_destroy(pic_batch *b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  delete b;
+}
+
 int pic_attach_unet(pic_handle *h, pic_unet *u, int maxit, int smooth, int finish) {
   if (!h || maxit < 1 || smooth < 0 || smooth > 8) return PIC_EINVAL;
   if (finish != PIC_SOLVER_PLAIN && finish != PIC_SOLVER_MIXED) return PIC_EINVAL;
@@ -1026,6 +1186,19 @@ int pic_attach_unet(pic_handle *h, pic_unet *u, int maxit, int smooth, int finis
   h->fcg_nblk = nblk;
   h->net = u;
   h->learned_finish = finish;
+  return PIC_OK;
+}
+
+int pic_set_solver(pic_handle *h, int solver) {
+  if (!h || (solver != PIC_SOLVER_PLAIN && solver != PIC_SOLVER_MIXED && solver != PIC_SOLVER_LEARNED)) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  if (h->cfg.solver != solver) {
+    for (int k = 0; k < 2; ++k)
+      if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    h->graph[0] = h->graph[1] = nullptr;
+    h->graph_failed = false;
+  }
+  h->cfg.solver = solver;
   return PIC_OK;
 }
 

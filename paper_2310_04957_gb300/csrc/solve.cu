@@ -22,10 +22,13 @@
 // per-node arithmetic: nodes are spread evenly over all SMs, the scalar
 // recurrences run in one thread per block, convergence is tested on squared
 // norms.  One persistent cooperative launch; bounded barrier waits.
+#include <cooperative_groups.h>
 #include <cstdint>
 
 #include "pic_device.cuh"
 #include "pic_kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace pic {
 
@@ -400,6 +403,215 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_mixed(const PcgParams P) {
     P.out[3] = (double)outer;
     if (status == -4) atomicOr(P.flags, 0x4u);
     if (status == -7) atomicOr(P.flags, 0x8u);
+  }
+}
+
+// ---- batched: one thread-block cluster per discharge, mixed precision ------------------
+// Many independent small systems (the discharges of a sweep), each solved by
+// its own cluster of CL CTAs (1..8, by grid size): no grid-wide barrier, so
+// the solves of different discharges never wait on one another.  FP64
+// residual and refinement as in k_pcg_mixed around FP32 Jacobi-preconditioned
+// CG (standard two-reduction form).  Block sums are combined across the
+// cluster through distributed shared memory; the hardware cluster barrier
+// orders the neighbour reads of the matrix-vector product.
+template <typename T, int K>
+__device__ __forceinline__ void cta_sum(T v[K]) {
+  __shared__ T s[K][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    T x = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) s[k][wid] = x;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    T x = (T)0;
+    for (int w = 0; w < nw; ++w) x += s[k][w];
+    v[k] = x;
+  }
+  __syncthreads();
+}
+
+// Cluster-wide sum (every thread of every CTA gets the same total: the CTA
+// partials are added in rank order).  slots: this CTA's [2][4] doubles, used
+// by alternating parity so one cluster barrier per sum suffices.
+template <int CL, typename T, int K>
+__device__ __forceinline__ void cluster_sum(T v[K], double (*slots)[4], double *bcast, int &par) {
+  cta_sum<T, K>(v);
+  if (CL == 1) return;
+  cg::cluster_group cl = cg::this_cluster();
+  if (threadIdx.x < K) slots[par][threadIdx.x] = (double)v[threadIdx.x];
+  cl.sync();
+  // K threads gather the CL partials (rank order) and broadcast through shared memory
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int r = 0; r < CL; ++r) t += cl.map_shared_rank(&slots[par][0], r)[threadIdx.x];
+    bcast[threadIdx.x] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = (T)bcast[k];
+  par ^= 1;
+}
+
+template <int CL>
+__device__ __forceinline__ void cluster_barrier() {
+  if (CL == 1) __syncthreads();
+  else cg::this_cluster().sync();
+}
+
+template <int CL>
+__global__ void __launch_bounds__(kBatchThreads, 1) k_pcg_cluster(const PcgParams *__restrict__ Ps) {
+  __shared__ double slots[2][4];
+  __shared__ double bcast[4];
+  const PcgParams &P = Ps[blockIdx.x / CL];
+  const int rank = CL == 1 ? 0 : (int)cg::this_cluster().block_rank();
+  const int nn = P.nn, nr = P.nr, W = nr + 1, nz = P.nz, nt = blockDim.x;
+  const int chunk = (nn + CL - 1) / CL, lo = rank * chunk, hi = min(nn, lo + chunk);
+  const int a0 = lo + threadIdx.x;
+  float *f = P.work32;
+  float *r = f, *z = f + nn, *p = f + 2 * (size_t)nn, *q = f + 3 * (size_t)nn, *x = f + 4 * (size_t)nn;
+  float *gr = f + 8 * (size_t)nn, *gz = f + 9 * (size_t)nn, *dv = f + 10 * (size_t)nn;
+  double *r64 = P.work;
+  const int8_t *kind = P.node_kind;
+  int par = 0;
+  for (int a = a0; a < hi; a += nt) {
+    const int j = a / W, i = a - j * W;
+    if (i < nr) gr[j * nr + i] = (float)(P.Gr[j * nr + i] * P.gscale);
+    if (j < nz) gz[j * W + i] = (float)(P.Gz[j * W + i] * P.gscale);
+    dv[a] = (float)(P.dinv[a] / P.gscale);
+  }
+  cluster_barrier<CL>();
+  int it = 0, status = -4, outer = 0;
+  double b2 = 0.0, r2 = 0.0;
+  for (outer = 0; outer < 64; ++outer) {
+    double acc[2] = {0.0, 0.0};
+    for (int a = a0; a < hi; a += nt) {
+      if (kind[a] != 0) continue;
+      const int j = a / W, i = a - j * W;
+      const double pa = P.phi[a];
+      double ax = 0.0, lift = 0.0;
+      if (i > 0) { const double g = P.Gr[j * nr + i - 1], pb = P.phi[a - 1]; ax += g * (pa - pb); if (kind[a - 1]) lift += g * pb; }
+      if (i < nr) { const double g = P.Gr[j * nr + i], pb = P.phi[a + 1]; ax += g * (pa - pb); if (kind[a + 1]) lift += g * pb; }
+      if (j > 0) { const double g = P.Gz[(j - 1) * W + i], pb = P.phi[a - W]; ax += g * (pa - pb); if (kind[a - W]) lift += g * pb; }
+      if (j < nz) { const double g = P.Gz[j * W + i], pb = P.phi[a + W]; ax += g * (pa - pb); if (kind[a + W]) lift += g * pb; }
+      const double qa = P.qrhs[a], ra = qa - ax, ba = qa + lift;
+      r64[a] = ra;
+      acc[0] += ba * ba;
+      acc[1] += ra * ra;
+    }
+    cluster_sum<CL, double, 2>(acc, slots, bcast, par);
+    b2 = acc[0];
+    r2 = acc[1];
+    const double target2 = b2 > 0.0 ? P.tol * P.tol * b2 : 1e-60;
+    if (!isfinite(r2)) { status = -7; break; }
+    if (r2 <= target2) { status = 0; break; }
+    if (it >= P.maxit) { status = -4; break; }
+    const double inv = rsqrt(r2);
+    float rz[1] = {0.0f};
+    for (int a = a0; a < hi; a += nt) {
+      const float ra = kind[a] == 0 ? (float)(r64[a] * inv) : 0.0f;
+      const float za = dv[a] * ra;
+      r[a] = ra;
+      z[a] = za;
+      p[a] = kind[a] == 0 ? za : 0.0f;
+      x[a] = 0.0f;
+      rz[0] += ra * za;
+    }
+    cluster_sum<CL, float, 1>(rz, slots, bcast, par);  // its barrier also publishes p
+    float rho = rz[0];
+    float stop = P.inner_tol;
+    const float need = (float)sqrt(target2 / r2);
+    if (need > stop) stop = need;
+    const float stop2 = stop * stop;
+    bool bad = false;
+    while (it < P.maxit) {
+      float pq[1] = {0.0f};
+      for (int a = a0; a < hi; a += nt) {
+        if (kind[a] != 0) continue;
+        const int j = a / W, i = a - j * W;
+        const float pa = p[a];
+        float qa = 0.0f;
+        if (i > 0) qa += gr[j * nr + i - 1] * (pa - p[a - 1]);
+        if (i < nr) qa += gr[j * nr + i] * (pa - p[a + 1]);
+        if (j > 0) qa += gz[(j - 1) * W + i] * (pa - p[a - W]);
+        if (j < nz) qa += gz[j * W + i] * (pa - p[a + W]);
+        q[a] = qa;
+        pq[0] += pa * qa;
+      }
+      cluster_sum<CL, float, 1>(pq, slots, bcast, par);
+      const float alpha = rho / pq[0];
+      float red[2] = {0.0f, 0.0f};
+      for (int a = a0; a < hi; a += nt) {
+        if (kind[a] != 0) continue;
+        x[a] += alpha * p[a];
+        const float ra = r[a] - alpha * q[a];
+        const float za = dv[a] * ra;
+        r[a] = ra;
+        z[a] = za;
+        red[0] += ra * za;
+        red[1] += ra * ra;
+      }
+      cluster_sum<CL, float, 2>(red, slots, bcast, par);
+      ++it;
+      if (!isfinite(red[0]) || !isfinite(red[1])) { bad = true; break; }
+      if (red[1] <= stop2) break;
+      const float beta = red[0] / rho;
+      rho = red[0];
+      for (int a = a0; a < hi; a += nt)
+        if (kind[a] == 0) p[a] = z[a] + beta * p[a];
+      cluster_barrier<CL>();
+    }
+    if (bad) { status = -7; break; }
+    const double back = sqrt(r2) * P.gscale;
+    for (int a = a0; a < hi; a += nt)
+      if (kind[a] == 0) P.phi[a] += (double)x[a] * back;
+    cluster_barrier<CL>();
+  }
+  if (rank == 0 && threadIdx.x == 0) {
+    P.out[0] = (double)it;
+    P.out[1] = b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
+    P.out[2] = (double)status;
+    P.out[3] = (double)outer;
+    if (status == -4) atomicOr(P.flags, 0x4u);
+    if (status == -7) atomicOr(P.flags, 0x8u);
+  }
+  // no CTA may leave while others still read its shared-memory partials
+  cluster_barrier<CL>();
+}
+
+int batch_cluster_size(int nn) {
+  int cl = 1;
+  while (cl < 8 && nn > 4096 * cl) cl *= 2;
+  return cl;
+}
+
+template <int CL>
+static cudaError_t launch_cluster(const PcgParams *d_params, int n, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n * CL);
+  cfg.blockDim = dim3(kBatchThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg_cluster<CL>, d_params);
+}
+
+cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, cudaStream_t st) {
+  switch (cluster) {
+    case 1: return launch_cluster<1>(d_params, n, st);
+    case 2: return launch_cluster<2>(d_params, n, st);
+    case 4: return launch_cluster<4>(d_params, n, st);
+    case 8: return launch_cluster<8>(d_params, n, st);
+    default: return cudaErrorInvalidValue;
   }
 }
 

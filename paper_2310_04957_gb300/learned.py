@@ -24,6 +24,25 @@ import numpy as np
 from . import pic
 
 
+# Layer widths of the library's U-Net (the parameter layout of pic_unet_set_params).
+CONV_IN = (16, 32, 32, 64, 64, 128, 128, 256, 384, 128, 192, 64, 96, 32)
+CONV_OUT = (32, 32, 64, 64, 128, 128, 256, 256, 128, 128, 64, 64, 32, 32)
+
+
+def init_params(seed):
+    """He-normal weights (fan-in 9 x live input channels; the first layer has 3
+    live channels of 16), zero biases, 1x1 output weights N(0, 1/32)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in zip(CONV_IN, CONV_OUT):
+        fan = 9 * (3 if ci == 16 else ci)
+        parts.append(rng.normal(0.0, math.sqrt(2.0 / fan), 9 * ci * co))
+        parts.append(np.zeros(co))
+    parts.append(rng.normal(0.0, math.sqrt(1.0 / 32), 32))
+    parts.append(np.zeros(1))
+    return np.concatenate(parts).astype(np.float32)
+
+
 class PairStore:
     """Device-resident training pairs: inputs [n][3][H*W] and targets [n][H*W] (FP32)."""
 
@@ -131,3 +150,32 @@ def compare_solvers(d, modes=(pic.PIC_SOLVER_PLAIN, pic.PIC_SOLVER_MIXED, pic.PI
                 best = (st, it, rr, ms, ls)
         out[m] = best
     return out
+
+
+def train_on_discharge(wl, warm_pairs=300, iterate_pairs=200, steps=1500, seed=0, settle=10, net=None):
+    """Train a network for workload wl from scratch on pairs its own run
+    generates: warm-start pairs from mixed-solver steps, a first training pass,
+    then pairs from iterates of learned solves with that network, and a second
+    pass on both.  Returns (net, discharge, info); the discharge has the network
+    attached."""
+    import time
+
+    t0 = time.perf_counter()
+    d = pic.Discharge(wl, solver=pic.PIC_SOLVER_MIXED)
+    d.step(settle)
+    store = PairStore(warm_pairs + iterate_pairs, wl.nz, wl.nr)
+    collect_warm_pairs(d, store, warm_pairs, 0)
+    if net is None:
+        net = pic.UNet(wl.nz, wl.nr)
+        net.set_params(init_params(seed))
+    h1 = train(net, store, np.arange(store.n), steps, lr=1e-3, batch=4, seed=seed, log_every=steps)
+    n0 = store.n
+    d.set_solver(pic.PIC_SOLVER_LEARNED)
+    d.attach_unet(net, maxit=60)
+    collect_iterate_pairs(d, store, iterate_pairs, 1, seed=seed)
+    h2 = train(net, store, np.arange(store.n), steps, lr=5e-4, batch=4, seed=seed + 1, log_every=steps)
+    d.set_solver(pic.PIC_SOLVER_MIXED)
+    info = {"warm_pairs": n0, "iterate_pairs": store.n - n0, "adam_steps": 2 * steps, "batch": 4,
+            "loss_pass1": h1[-1], "loss_pass2": h2[-1], "seconds": time.perf_counter() - t0}
+    del store
+    return net, d, info

@@ -36,7 +36,8 @@ EXPORTS = ["pic_init", "pic_set_particles", "pic_count", "pic_get_particles", "p
            "pic_unet_set_params", "pic_unet_get_params", "pic_unet_get_grads", "pic_unet_zero_grads",
            "pic_unet_forward", "pic_unet_backward", "pic_unet_adam", "pic_unet_status", "pic_conv3x3_op",
            "pic_conv3x3_op_ex", "pic_attach_unet", "pic_keep_warm", "pic_learned_pair", "pic_learned_stats",
-           "pic_unet_loss_backward", "pic_learned_snapshot"]
+           "pic_unet_loss_backward", "pic_learned_snapshot", "pic_batch_create", "pic_batch_step", "pic_batch_sync",
+           "pic_batch_destroy", "pic_set_solver"]
 STATIC_MAX_NODES = 139264
 
 
@@ -287,6 +288,9 @@ class Discharge:
                "pic_attach_unet")
         self._net = net
 
+    def set_solver(self, solver):
+        _check(lib().pic_set_solver(self.h, solver), "pic_set_solver")
+
     def keep_warm(self, on=True):
         _check(lib().pic_keep_warm(self.h, int(on)), "pic_keep_warm")
 
@@ -401,3 +405,33 @@ def conv3x3_op(op, H, W, inp_ptr, Cin, w_ptr, bias_ptr, out_ptr, Cout, stream=No
     L.pic_conv3x3_op_ex.argtypes = [I, I, I, P, I, P, P, P, I, I, I, P]
     return L.pic_conv3x3_op_ex(op, H, W, P(inp_ptr), Cin, P(w_ptr), P(bias_ptr) if bias_ptr else None, P(out_ptr),
                                Cout, tile_n, tile_mma, _stream(stream))
+
+
+class Batch:
+    """Independent discharges stepped together in one graph per step (wraps pic_batch)."""
+
+    def __init__(self, discharges):
+        L = lib()
+        L.pic_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(ctypes.c_void_p)]
+        L.pic_batch_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.pic_batch_sync.argtypes = [ctypes.c_void_p]
+        L.pic_batch_destroy.argtypes = [ctypes.c_void_p]
+        self.discharges = list(discharges)
+        arr = (ctypes.c_void_p * len(self.discharges))(*[d.h.value for d in self.discharges])
+        h = ctypes.c_void_p()
+        _check(L.pic_batch_create(arr, len(self.discharges), ctypes.byref(h)), "pic_batch_create")
+        self.h = h
+
+    def step(self, n=1):
+        _check(lib().pic_batch_step(self.h, n), "pic_batch_step")
+
+    def sync(self):
+        _check(lib().pic_batch_sync(self.h), "pic_batch_sync")
+
+    def close(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            _lib.pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

@@ -1,0 +1,79 @@
+"""The batched sweep (independent discharges stepped by one graph per step with
+one field-solve launch for all of them) against the same discharges stepped
+one at a time, through the C ABI."""
+import numpy as np
+import pytest
+
+from gpu_common import compare_particles, pic
+from paper_2310_04957_gb300 import sweep
+from paper_2310_04957_gb300 import workloads as W
+from util import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+MIXED = 1
+
+
+def _cases():
+    return [W.gec_case(64, 32, 20.0, 120.0, cm2=150e-12, n_per_species=30_000, seed_index=70),
+            W.gec_case(96, 48, 60.0, 250.0, cm2=350e-12, n_per_species=60_000, seed_index=71),
+            W.gec_case(128, 64, 8.0, 80.0, n_per_species=20_000, seed_index=72),
+            W.gec_case(256, 128, 30.0, 150.0, n_per_species=40_000, seed_index=76)]
+
+
+def test_batch_matches_discharges_stepped_alone():
+    """Uneven grids and particle counts (field solves on clusters of 1, 2, 4 and 8
+    CTAs): after each of 3 steps every discharge's potential agrees with its solo
+    run within 1e-8 relative L2 (both solves meet 1e-10 relative residual, by
+    different CG arrangements), and its particles within 1e-5."""
+    P = pic()
+    wls = _cases()
+    solo = [P.Discharge(wl, solver=MIXED) for wl in wls]
+    both = [P.Discharge(wl, solver=MIXED, tile=(8, 4)) for wl in wls]
+    b = P.Batch(both)
+    for _ in range(3):
+        for d in solo:
+            d.step(1)
+        b.step(1)
+        b.sync()
+        for d, e, wl in zip(both, solo, wls):
+            sc = d.scalars()
+            assert sc["pcg_relres"] <= wl.pcg_tol
+            assert rel_l2(d.field("phi"), e.field("phi")) <= 1e-8
+    for d, e in zip(both, solo):
+        for s in (0, 1):
+            c = compare_particles(d.get_particles(s), e.get_particles(s), 1e-5)
+            assert c["only_dev"] == 0 and c["only_orc"] == 0
+            assert c["bad"] <= max(2, 1e-4 * c["common"]), c
+        assert d.status() == 0
+        assert d.scalars()["step"] == e.scalars()["step"] == 3
+
+
+def test_batch_crosses_an_rf_window():
+    """Stepping the batch past the end of an RF period runs each discharge's
+    window bookkeeping (C_eq refresh, averages) like pic_step does."""
+    P = pic()
+    wls = [W.gec_case(64, 32, 20.0, 120.0, n_per_species=5_000, seed_index=73),
+           W.gec_case(96, 48, 40.0, 200.0, n_per_species=5_000, seed_index=74)]
+    ds = [P.Discharge(wl, solver=MIXED) for wl in wls]
+    b = P.Batch(ds)
+    for k in range(wls[0].steps_per_rf + 2):
+        b.step(1)
+        b.sync()
+        for i, d in enumerate(ds):
+            assert d.status() == 0, (k, i, d.scalars())
+    for d in ds:
+        sc = d.scalars()
+        assert sc["windows"] >= 1
+        assert sc["step"] == wls[0].steps_per_rf + 2
+        assert np.isfinite(d.field("ne_avg")).all() and d.field("ne_avg").max() > 0
+        assert d.status() == 0
+
+
+def test_autotuner_picks_a_measured_tile():
+    P = pic()
+    wls = [W.gec_case(64, 32, 20.0, 120.0, n_per_species=20_000, seed_index=75)]
+    choice, t = sweep.autotune_tiles(wls, candidates=((2, 2), (4, 4), (8, 8)), reps=2)
+    cls = sweep.tile_class(wls[0])
+    assert choice[cls] in ((2, 2), (4, 4), (8, 8))
+    assert t[cls][choice[cls]] == min(t[cls].values())
