@@ -57,6 +57,20 @@ __device__ __forceinline__ float rsq(float q) {
 }
 __device__ __forceinline__ double rsq(double q) { return 1.0 / sqrt(q); }
 
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // Bin of cell (i, j) for compile-time tile sizes (powers of two).
 template <int TX, int TY>
 __device__ __forceinline__ int bin_key(int i, int j, int ntx) {
@@ -308,17 +322,28 @@ __device__ __forceinline__ int mcc_ion(const PushParams<T> &P, Part<T> &p) {
 }
 
 // Gather, correction, D1 filter, axis, absorption, MCC, predictor, absorption.
+// E at the four nodes of cell (ci, cj): 00, 10, 01, 11.
 template <typename T>
-__device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T> &p, Part<T> &be, Part<T> &bi) {
+__device__ __forceinline__ void gather_nodes(const PushParams<T> &P, int ci, int cj, typename V2<T>::type e[4]) {
+  using E2 = typename V2<T>::type;
+  const E2 *E = reinterpret_cast<const E2 *>(P.E);
+  int n00 = cj * (P.nr + 1) + ci;
+  e[0] = E[n00];
+  e[1] = E[n00 + 1];
+  e[2] = E[n00 + P.nr + 1];
+  e[3] = E[n00 + P.nr + 2];
+}
+
+template <typename T>
+__device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T> &p, Part<T> &be, Part<T> &bi,
+                                           const typename V2<T>::type en[4]) {
   Outcome o{0, -1, 0, -1, 0};
   // gather E at x~_n with the deposit weights: linear in z, by annulus area in r
   T ir = (T)p.ci;
   T a = p.fr * ((T)2 * ir + p.fr) * rcp((T)2 * ir + (T)1);
   T b = p.fz;
   using E2 = typename V2<T>::type;
-  const E2 *E = reinterpret_cast<const E2 *>(P.E);
-  int n00 = p.cj * (P.nr + 1) + p.ci;
-  E2 e00 = E[n00], e10 = E[n00 + 1], e01 = E[n00 + P.nr + 1], e11 = E[n00 + P.nr + 2];
+  const E2 e00 = en[0], e10 = en[1], e01 = en[2], e11 = en[3];
   T w00 = ((T)1 - a) * ((T)1 - b), w10 = a * ((T)1 - b), w01 = ((T)1 - a) * b, w11 = a * b;
   T Er = w00 * e00.x + w10 * e10.x + w01 * e01.x + w11 * e11.x;
   T Ez = w00 * e00.y + w10 * e10.y + w01 * e01.y + w11 * e11.y;
@@ -579,10 +604,11 @@ __device__ __forceinline__ void load_particle(const StoreView<T> &S, int slot, P
 // Process one particle (already loaded) of species s: step, tallies, emit,
 // births.  Warp-collective.
 template <typename T, int TX, int TY>
-__device__ __forceinline__ void process(const PushParams<T> &P, int s, bool active, Part<T> &p, const TileCtx &tc) {
+__device__ __forceinline__ void process(const PushParams<T> &P, int s, bool active, Part<T> &p, const TileCtx &tc,
+                                        const typename V2<T>::type en[4]) {
   Part<T> be = p, bi = p;
   Outcome o{0, -1, 0, -1, 0};
-  if (active) o = advance(P, s, p, be, bi);
+  if (active) o = advance(P, s, p, be, bi, en);
   tally(P, s, o, active);
   emit<T, TX, TY>(P, s, active && o.alive, p, tc);
   bool birth = active && o.birth;
@@ -650,22 +676,84 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_particles(
     }
     __syncthreads();
     const int ntot = s_pre[per];
-    for (int base = 0; base < ntot; base += blockDim.x) {
-      int k = base + threadIdx.x;
-      bool active = k < ntot;
-      Part<T> p;
-      p.ci = 0; p.cj = 0;
-      if (active) {
-        int lo = 0;  // largest bin with s_pre[lo] <= k
+    if constexpr (sizeof(T) == 4) {
+      // Software pipeline: while a round of blockDim.x particles is processed,
+      // the state of each thread's particle of the next round streams from HBM
+      // into shared memory with cp.async.  A thread only reads back what it
+      // fetched itself, so no block barrier is needed.  (The E field at the
+      // cell's nodes is read directly: it is small and L1-resident, and staging
+      // it as well measured slower.)
+      __shared__ float pf[2][8][kThreads];
+      __shared__ unsigned long long pid[2][kThreads];
+      __shared__ int plo[2][kThreads];
+      const int tid = threadIdx.x;
+      auto issue = [&](int base, int b) {
+        const int k = base + tid;
+        if (k < ntot) {
+          int lo = 0;  // largest bin with s_pre[lo] <= k
 #pragma unroll
-        for (int step = per / 2; step >= 1; step >>= 1)
-          if (lo + step < per && s_pre[lo + step] <= k) lo += step;
-        int slot = s_off[lo] + (k - s_pre[lo]);
-        load_particle(A, slot, p);
-        p.ci = tc.ci0 + (lo & (TX - 1));
-        p.cj = tc.cj0 + (lo / TX);
+          for (int step = per / 2; step >= 1; step >>= 1)
+            if (lo + step < per && s_pre[lo + step] <= k) lo += step;
+          const int slot = s_off[lo] + (k - s_pre[lo]);
+          cp_async4(&pf[b][0][tid], A.fr + slot);
+          cp_async4(&pf[b][1][tid], A.fz + slot);
+          cp_async4(&pf[b][2][tid], A.vr + slot);
+          cp_async4(&pf[b][3][tid], A.vt + slot);
+          cp_async4(&pf[b][4][tid], A.vz + slot);
+          cp_async4(&pf[b][5][tid], A.ar + slot);
+          cp_async4(&pf[b][6][tid], A.at + slot);
+          cp_async4(&pf[b][7][tid], A.az + slot);
+          cp_async8(&pid[b][tid], A.id + slot);
+          plo[b][tid] = lo;
+        }
+        cp_async_commit_group();
+      };
+      issue(0, 0);
+      for (int base = 0, it = 0; base < ntot; base += blockDim.x, ++it) {
+        const int b = it & 1;
+        if (base + (int)blockDim.x < ntot) {
+          issue(base + blockDim.x, b ^ 1);
+          cp_async_wait_group<1>();
+        } else {
+          cp_async_wait_group<0>();
+        }
+        const int k = base + tid;
+        const bool active = k < ntot;
+        Part<T> p;
+        p.ci = 0; p.cj = 0;
+        float2 en[4];
+        if (active) {
+          p.fr = pf[b][0][tid]; p.fz = pf[b][1][tid];
+          p.vr = pf[b][2][tid]; p.vt = pf[b][3][tid]; p.vz = pf[b][4][tid];
+          p.ar = pf[b][5][tid]; p.at = pf[b][6][tid]; p.az = pf[b][7][tid];
+          p.id = pid[b][tid];
+          const int lo = plo[b][tid];
+          p.ci = tc.ci0 + (lo & (TX - 1));
+          p.cj = tc.cj0 + (lo / TX);
+          gather_nodes(P, p.ci, p.cj, en);  // E is small and L1/L2-resident
+        }
+        process<T, TX, TY>(P, s, active, p, tc, en);
       }
-      process<T, TX, TY>(P, s, active, p, tc);
+    } else {
+      for (int base = 0; base < ntot; base += blockDim.x) {
+        int k = base + threadIdx.x;
+        bool active = k < ntot;
+        Part<T> p;
+        p.ci = 0; p.cj = 0;
+        typename V2<T>::type en[4];
+        if (active) {
+          int lo = 0;  // largest bin with s_pre[lo] <= k
+#pragma unroll
+          for (int step = per / 2; step >= 1; step >>= 1)
+            if (lo + step < per && s_pre[lo + step] <= k) lo += step;
+          int slot = s_off[lo] + (k - s_pre[lo]);
+          load_particle(A, slot, p);
+          p.ci = tc.ci0 + (lo & (TX - 1));
+          p.cj = tc.cj0 + (lo / TX);
+          gather_nodes(P, p.ci, p.cj, en);
+        }
+        process<T, TX, TY>(P, s, active, p, tc, en);
+      }
     }
     __syncthreads();
     unsigned long long *d = P.dep[s];
@@ -687,14 +775,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_particles(
       bool active = k < novf;
       Part<T> p;
       p.ci = 0; p.cj = 0;
+      typename V2<T>::type en[4];
       if (active) {
         int slot = first + k;
         load_particle(A, slot, p);
         int c = A.cell[slot];
         p.cj = c / P.nr;
         p.ci = c - p.cj * P.nr;
+        gather_nodes(P, p.ci, p.cj, en);
       }
-      process<T, TX, TY>(P, s, active, p, tc);
+      process<T, TX, TY>(P, s, active, p, tc, en);
     }
   }
 }
@@ -926,6 +1016,7 @@ cudaError_t launch_philox(int64_t n, const uint32_t *ctr, const uint32_t *key, u
 }
 
 template cudaError_t launch_particles<float>(const PushParams<float> &, cudaStream_t);
+
 template cudaError_t launch_particles<double>(const PushParams<double> &, cudaStream_t);
 template cudaError_t launch_deposit_only<float>(const PushParams<float> &, cudaStream_t);
 template cudaError_t launch_deposit_only<double>(const PushParams<double> &, cudaStream_t);
