@@ -286,7 +286,7 @@ def run_sweep(args):
             "unit": "particle-steps/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": 1e3 * t_b / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "sweep-64-gec-lhs", "discharges": len(ds), "particles": int(n),
-                       "grids": sorted({f"{w.nr}x{w.nz}" for w in wls}), "solver": "batched mixed (one CTA per discharge)",
+                       "grids": sorted({f"{w.nr}x{w.nz}" for w in wls}), "solver": "batched mixed (one thread-block cluster per discharge, CG state in shared memory)",
                        "parallelism": "single", "l2": "inputs larger than L2"},
             "sequential": {"value": ps / seq_s, "ms_per_step": 1e3 * seq_s / K, "solver": "mixed, one discharge at a time"},
             "speedup_vs_sequential": (n * K / t_b) / (ps / seq_s),

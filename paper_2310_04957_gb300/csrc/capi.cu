@@ -717,7 +717,9 @@ cudaError_t batch_build(pic_batch *b, int parity) {
     if (e != cudaSuccess) break;
     const PcgParams *params = b->d_params + i;
     e = add_child(G, b->hs[i], b->stream, &pre[i], 1, &solve[i], [&](pic_handle *h) {
-      return launch_pcg_batch(params, 1, batch_cluster_size(h->nn), h->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+      return launch_pcg_batch(params, 1, batch_cluster_size(h->nr, h->nz), h->nr, h->nz, h->stream) == cudaSuccess
+                 ? PIC_OK
+                 : PIC_ECUDA;
     });
     if (e != cudaSuccess) break;
     e = add_child(G, b->hs[i], b->stream, &solve[i], 1, &post[i],
@@ -1061,6 +1063,7 @@ int pic_batch_create(pic_handle *const *hs, int n, pic_batch **out) {
   if (!b) return PIC_ENOMEM;
   for (int i = 0; i < n; ++i) {
     if (!hs[i] || hs[i]->device != hs[0]->device || hs[i]->cur != hs[0]->cur) { delete b; return PIC_EINVAL; }
+    if (batch_cluster_size(hs[i]->nr, hs[i]->nz) == 0) { delete b; return PIC_EINVAL; }
     for (int k = 0; k < i; ++k)
       if (hs[k] == hs[i]) { delete b; return PIC_EINVAL; }
     b->hs.push_back(hs[i]);

@@ -137,11 +137,12 @@ cudaError_t launch_assemble_edges_only(const FieldParams &F, cudaStream_t st);
 cudaError_t launch_set_dirichlet(int nn, const int8_t *kind, double *phi, double U, cudaStream_t st);
 cudaError_t launch_pcg(const PcgParams &P, int grid, cudaStream_t st);
 cudaError_t launch_pcg_mixed(const PcgParams &P, int grid, cudaStream_t st);
-// n independent systems (device array of parameters), one cluster of `cluster`
-// CTAs (1, 2, 4, 8) each, mixed precision.
+// n independent systems of one grid size (device array of parameters), one
+// cluster of `cluster` CTAs (1, 2, 4, 8) each, mixed precision with the CG
+// state resident in the cluster's shared memory.
 constexpr int kBatchThreads = 1024;
-int batch_cluster_size(int nn);
-cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, cudaStream_t st);
+int batch_cluster_size(int nr, int nz);  // 0: the grid does not fit an 8-CTA cluster
+cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, int nr, int nz, cudaStream_t st);
 int pcg_grid_size(int device);
 constexpr int kPcgThreads = 256;
 cudaError_t launch_efield(const EfieldParams &E, cudaStream_t st);

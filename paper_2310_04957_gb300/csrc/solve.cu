@@ -409,11 +409,9 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_mixed(const PcgParams P) {
 // ---- batched: one thread-block cluster per discharge, mixed precision ------------------
 // Many independent small systems (the discharges of a sweep), each solved by
 // its own cluster of CL CTAs (1..8, by grid size): no grid-wide barrier, so
-// the solves of different discharges never wait on one another.  FP64
-// residual and refinement as in k_pcg_mixed around FP32 Jacobi-preconditioned
-// CG (standard two-reduction form).  Block sums are combined across the
-// cluster through distributed shared memory; the hardware cluster barrier
-// orders the neighbour reads of the matrix-vector product.
+// the solves of different discharges never wait on one another.  Block sums
+// are combined across the cluster through distributed shared memory; the
+// hardware cluster barrier orders the neighbour reads.
 template <typename T, int K>
 __device__ __forceinline__ void cta_sum(T v[K]) {
   __shared__ T s[K][32];
@@ -463,43 +461,72 @@ __device__ __forceinline__ void cluster_barrier() {
   else cg::this_cluster().sync();
 }
 
+// Shared-memory-resident version: the nodes are split by rows over the CL
+// CTAs of the cluster; each CTA keeps the FP32 operator (scaled) and the CG
+// vectors of its rows in shared memory and reads its neighbours' rows through
+// distributed shared memory.  Inner CG in the Chronopoulos-Gear arrangement
+// of cg_iteration (one cluster-wide reduction per iteration; r, w, s
+// double-buffered so the neighbours' next preconditioned residual is rebuilt
+// on the fly); FP64 residual and refinement in global memory around it.
+constexpr int kSmemFloats = 12;  // per node: gr gzu gzd dinv x p r[2] w[2] s[2]
+
 template <int CL>
-__global__ void __launch_bounds__(kBatchThreads, 1) k_pcg_cluster(const PcgParams *__restrict__ Ps) {
+__global__ void __launch_bounds__(kBatchThreads, 1) k_pcg_cluster(const PcgParams *__restrict__ Ps, int cap) {
+  extern __shared__ __align__(16) float sm[];
   __shared__ double slots[2][4];
   __shared__ double bcast[4];
   const PcgParams &P = Ps[blockIdx.x / CL];
   const int rank = CL == 1 ? 0 : (int)cg::this_cluster().block_rank();
-  const int nn = P.nn, nr = P.nr, W = nr + 1, nz = P.nz, nt = blockDim.x;
-  const int chunk = (nn + CL - 1) / CL, lo = rank * chunk, hi = min(nn, lo + chunk);
-  const int a0 = lo + threadIdx.x;
-  float *f = P.work32;
-  float *r = f, *z = f + nn, *p = f + 2 * (size_t)nn, *q = f + 3 * (size_t)nn, *x = f + 4 * (size_t)nn;
-  float *gr = f + 8 * (size_t)nn, *gz = f + 9 * (size_t)nn, *dv = f + 10 * (size_t)nn;
-  double *r64 = P.work;
+  const int nr = P.nr, nz = P.nz, W1 = nr + 1, tid = threadIdx.x, nt = blockDim.x;
+  const int R = (nz + 1 + CL - 1) / CL, j0 = rank * R;
+  const int j1 = min(nz + 1, j0 + R), n_own = j1 > j0 ? (j1 - j0) * W1 : 0;
+  float *gr = sm, *gzu = sm + cap, *gzd = sm + 2 * cap, *dv = sm + 3 * cap, *x = sm + 4 * cap, *pv = sm + 5 * cap;
+  // r, w, s of parity q at sm + (6 + q) cap, (8 + q) cap, (10 + q) cap
+  auto R_ = [&](int q) { return sm + (6 + q) * cap; };
+  auto W_ = [&](int q) { return sm + (8 + q) * cap; };
+  auto S_ = [&](int q) { return sm + (10 + q) * cap; };
   const int8_t *kind = P.node_kind;
   int par = 0;
-  for (int a = a0; a < hi; a += nt) {
-    const int j = a / W, i = a - j * W;
-    if (i < nr) gr[j * nr + i] = (float)(P.Gr[j * nr + i] * P.gscale);
-    if (j < nz) gz[j * W + i] = (float)(P.Gz[j * W + i] * P.gscale);
-    dv[a] = (float)(P.dinv[a] / P.gscale);
+  // value of the vector at float offset `off` at node (i, j) owned by another CTA
+  auto remote = [&](int off, int i, int j) -> float {
+    const int c = j / R;
+    const int l = (j - c * R) * W1 + i;
+    if (CL == 1) return sm[off + l];
+    return cg::this_cluster().map_shared_rank(sm, c)[off + l];
+  };
+  for (int l = tid; l < n_own; l += nt) {
+    const int j = j0 + l / W1, i = l - (l / W1) * W1, a = j * W1 + i;
+    gr[l] = i < nr ? (float)(P.Gr[j * nr + i] * P.gscale) : 0.0f;
+    gzu[l] = j < nz ? (float)(P.Gz[j * W1 + i] * P.gscale) : 0.0f;
+    gzd[l] = j > 0 ? (float)(P.Gz[(j - 1) * W1 + i] * P.gscale) : 0.0f;
+    dv[l] = kind[a] == 0 ? (float)(P.dinv[a] / P.gscale) : 0.0f;
   }
   cluster_barrier<CL>();
+  // dinv (r - alpha (w + beta s)) at node (i, j) from the parity-q buffers
+  auto u_next = [&](int i, int j, int q, float alpha, float beta) -> float {
+    if (j >= j0 && j < j1) {
+      const int l = (j - j0) * W1 + i;
+      return dv[l] * (R_(q)[l] - alpha * (W_(q)[l] + beta * S_(q)[l]));
+    }
+    const float d = remote(3 * cap, i, j), r = remote((6 + q) * cap, i, j), w = remote((8 + q) * cap, i, j),
+                sv = remote((10 + q) * cap, i, j);
+    return d * (r - alpha * (w + beta * sv));
+  };
   int it = 0, status = -4, outer = 0;
   double b2 = 0.0, r2 = 0.0;
   for (outer = 0; outer < 64; ++outer) {
     double acc[2] = {0.0, 0.0};
-    for (int a = a0; a < hi; a += nt) {
+    for (int l = tid; l < n_own; l += nt) {
+      const int j = j0 + l / W1, i = l - (l / W1) * W1, a = j * W1 + i;
       if (kind[a] != 0) continue;
-      const int j = a / W, i = a - j * W;
       const double pa = P.phi[a];
       double ax = 0.0, lift = 0.0;
       if (i > 0) { const double g = P.Gr[j * nr + i - 1], pb = P.phi[a - 1]; ax += g * (pa - pb); if (kind[a - 1]) lift += g * pb; }
       if (i < nr) { const double g = P.Gr[j * nr + i], pb = P.phi[a + 1]; ax += g * (pa - pb); if (kind[a + 1]) lift += g * pb; }
-      if (j > 0) { const double g = P.Gz[(j - 1) * W + i], pb = P.phi[a - W]; ax += g * (pa - pb); if (kind[a - W]) lift += g * pb; }
-      if (j < nz) { const double g = P.Gz[j * W + i], pb = P.phi[a + W]; ax += g * (pa - pb); if (kind[a + W]) lift += g * pb; }
+      if (j > 0) { const double g = P.Gz[(j - 1) * W1 + i], pb = P.phi[a - W1]; ax += g * (pa - pb); if (kind[a - W1]) lift += g * pb; }
+      if (j < nz) { const double g = P.Gz[j * W1 + i], pb = P.phi[a + W1]; ax += g * (pa - pb); if (kind[a + W1]) lift += g * pb; }
       const double qa = P.qrhs[a], ra = qa - ax, ba = qa + lift;
-      r64[a] = ra;
+      P.work[a] = ra;
       acc[0] += ba * ba;
       acc[1] += ra * ra;
     }
@@ -511,67 +538,90 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_pcg_cluster(const PcgParam
     if (r2 <= target2) { status = 0; break; }
     if (it >= P.maxit) { status = -4; break; }
     const double inv = rsqrt(r2);
-    float rz[1] = {0.0f};
-    for (int a = a0; a < hi; a += nt) {
-      const float ra = kind[a] == 0 ? (float)(r64[a] * inv) : 0.0f;
-      const float za = dv[a] * ra;
-      r[a] = ra;
-      z[a] = za;
-      p[a] = kind[a] == 0 ? za : 0.0f;
-      x[a] = 0.0f;
-      rz[0] += ra * za;
+    // inner start: r0 = residual / ||residual||, x = p = 0, w = s = 0
+    for (int l = tid; l < n_own; l += nt) {
+      const int a = (j0 + l / W1) * W1 + (l - (l / W1) * W1);
+      R_(0)[l] = dv[l] != 0.0f ? (float)(P.work[a] * inv) : 0.0f;
+      W_(0)[l] = 0.0f; S_(0)[l] = 0.0f; R_(1)[l] = 0.0f; W_(1)[l] = 0.0f; S_(1)[l] = 0.0f;
+      x[l] = 0.0f;
+      pv[l] = 0.0f;
     }
-    cluster_sum<CL, float, 1>(rz, slots, bcast, par);  // its barrier also publishes p
-    float rho = rz[0];
+    cluster_barrier<CL>();
+    // w0 = A u0 and the first products
+    float tot[3] = {0.0f, 0.0f, 0.0f};
+    for (int l = tid; l < n_own; l += nt) {
+      if (dv[l] == 0.0f) continue;
+      const int j = j0 + l / W1, i = l - (l / W1) * W1;
+      const float ua = dv[l] * R_(0)[l];
+      float w = 0.0f;
+      if (i > 0) w += gr[l - 1] * (ua - u_next(i - 1, j, 0, 0.0f, 0.0f));
+      if (i < nr) w += gr[l] * (ua - u_next(i + 1, j, 0, 0.0f, 0.0f));
+      if (j > 0) w += gzd[l] * (ua - u_next(i, j - 1, 0, 0.0f, 0.0f));
+      if (j < nz) w += gzu[l] * (ua - u_next(i, j + 1, 0, 0.0f, 0.0f));
+      W_(0)[l] = w;
+      tot[0] += R_(0)[l] * ua;
+      tot[1] += w * ua;
+      tot[2] += R_(0)[l] * R_(0)[l];
+    }
+    cluster_sum<CL, float, 3>(tot, slots, bcast, par);
     float stop = P.inner_tol;
     const float need = (float)sqrt(target2 / r2);
     if (need > stop) stop = need;
     const float stop2 = stop * stop;
+    float gamma = tot[0], delta = tot[1], rho = tot[2], gamma_prev = 1.0f, alpha_prev = 1.0f;
+    int q = 0, k = 0;
     bool bad = false;
-    while (it < P.maxit) {
-      float pq[1] = {0.0f};
-      for (int a = a0; a < hi; a += nt) {
-        if (kind[a] != 0) continue;
-        const int j = a / W, i = a - j * W;
-        const float pa = p[a];
-        float qa = 0.0f;
-        if (i > 0) qa += gr[j * nr + i - 1] * (pa - p[a - 1]);
-        if (i < nr) qa += gr[j * nr + i] * (pa - p[a + 1]);
-        if (j > 0) qa += gz[(j - 1) * W + i] * (pa - p[a - W]);
-        if (j < nz) qa += gz[j * W + i] * (pa - p[a + W]);
-        q[a] = qa;
-        pq[0] += pa * qa;
+    while (true) {
+      if (!isfinite(rho) || !isfinite(gamma) || !isfinite(delta)) { bad = true; break; }
+      if (rho <= stop2 || it >= P.maxit) break;
+      const float beta = k == 0 ? 0.0f : gamma / gamma_prev;
+      const float den = k == 0 ? delta : delta - beta * gamma / alpha_prev;
+      const float alpha = gamma / den;
+      float acc3[3] = {0.0f, 0.0f, 0.0f};
+      float *rq = R_(q), *wq = W_(q), *sq = S_(q), *rn = R_(q ^ 1), *wn = W_(q ^ 1), *sn = S_(q ^ 1);
+      for (int l = tid; l < n_own; l += nt) {
+        const float da = dv[l];
+        if (da == 0.0f) continue;
+        const int j = j0 + l / W1, i = l - (l / W1) * W1;
+        const float ra = rq[l], wa = wq[l], sa = sq[l];
+        const float pa = da * ra + beta * pv[l];
+        const float snew = wa + beta * sa;
+        const float rnew = ra - alpha * snew;
+        const float unew = da * rnew;
+        float wnew = 0.0f;
+        if (i > 0) wnew += gr[l - 1] * (unew - u_next(i - 1, j, q, alpha, beta));
+        if (i < nr) wnew += gr[l] * (unew - u_next(i + 1, j, q, alpha, beta));
+        if (j > 0) wnew += gzd[l] * (unew - u_next(i, j - 1, q, alpha, beta));
+        if (j < nz) wnew += gzu[l] * (unew - u_next(i, j + 1, q, alpha, beta));
+        x[l] += alpha * pa;
+        pv[l] = pa;
+        rn[l] = rnew;
+        wn[l] = wnew;
+        sn[l] = snew;
+        acc3[0] += rnew * unew;
+        acc3[1] += wnew * unew;
+        acc3[2] += rnew * rnew;
       }
-      cluster_sum<CL, float, 1>(pq, slots, bcast, par);
-      const float alpha = rho / pq[0];
-      float red[2] = {0.0f, 0.0f};
-      for (int a = a0; a < hi; a += nt) {
-        if (kind[a] != 0) continue;
-        x[a] += alpha * p[a];
-        const float ra = r[a] - alpha * q[a];
-        const float za = dv[a] * ra;
-        r[a] = ra;
-        z[a] = za;
-        red[0] += ra * za;
-        red[1] += ra * ra;
-      }
-      cluster_sum<CL, float, 2>(red, slots, bcast, par);
+      cluster_sum<CL, float, 3>(acc3, slots, bcast, par);  // its barrier publishes parity q^1
+      q ^= 1;
+      ++k;
       ++it;
-      if (!isfinite(red[0]) || !isfinite(red[1])) { bad = true; break; }
-      if (red[1] <= stop2) break;
-      const float beta = red[0] / rho;
-      rho = red[0];
-      for (int a = a0; a < hi; a += nt)
-        if (kind[a] == 0) p[a] = z[a] + beta * p[a];
-      cluster_barrier<CL>();
+      gamma_prev = gamma;
+      alpha_prev = alpha;
+      gamma = acc3[0];
+      delta = acc3[1];
+      rho = acc3[2];
     }
     if (bad) { status = -7; break; }
     const double back = sqrt(r2) * P.gscale;
-    for (int a = a0; a < hi; a += nt)
-      if (kind[a] == 0) P.phi[a] += (double)x[a] * back;
+    for (int l = tid; l < n_own; l += nt) {
+      if (dv[l] == 0.0f) continue;
+      const int a = (j0 + l / W1) * W1 + (l - (l / W1) * W1);
+      P.phi[a] += (double)x[l] * back;
+    }
     cluster_barrier<CL>();
   }
-  if (rank == 0 && threadIdx.x == 0) {
+  if (rank == 0 && tid == 0) {
     P.out[0] = (double)it;
     P.out[1] = b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
     P.out[2] = (double)status;
@@ -579,38 +629,56 @@ __global__ void __launch_bounds__(kBatchThreads, 1) k_pcg_cluster(const PcgParam
     if (status == -4) atomicOr(P.flags, 0x4u);
     if (status == -7) atomicOr(P.flags, 0x8u);
   }
-  // no CTA may leave while others still read its shared-memory partials
+  // no CTA may leave while others can still read its shared memory
   cluster_barrier<CL>();
 }
 
-int batch_cluster_size(int nn) {
-  int cl = 1;
-  while (cl < 8 && nn > 4096 * cl) cl *= 2;
-  return cl;
+// Nodes per CTA (rows of the grid split over cl CTAs) and its shared memory.
+static int cluster_cap(int nr, int nz, int cl) { return ((nz + 1 + cl - 1) / cl) * (nr + 1); }
+static size_t cluster_smem_bytes(int nr, int nz, int cl) {
+  return sizeof(float) * kSmemFloats * (size_t)cluster_cap(nr, nz, cl);
+}
+static const size_t kClusterSmemLimit = 225 * 1024;
+
+int batch_cluster_size(int nr, int nz) {
+  for (int cl = 1; cl <= 8; cl *= 2) {
+    const bool fits = cluster_smem_bytes(nr, nz, cl) <= kClusterSmemLimit;
+    if (fits && (cluster_cap(nr, nz, cl) <= 4096 || cl == 8)) return cl;
+  }
+  return 0;
 }
 
 template <int CL>
-static cudaError_t launch_cluster(const PcgParams *d_params, int n, cudaStream_t st) {
+static cudaError_t launch_cluster(const PcgParams *d_params, int n, int nr, int nz, cudaStream_t st) {
+  const size_t smem = cluster_smem_bytes(nr, nz, CL);
+  if (smem > kClusterSmemLimit) return cudaErrorInvalidValue;
+  static size_t attr = 0;  // largest dynamic shared memory granted so far (per instance)
+  if (smem > attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_pcg_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(n * CL);
   cfg.blockDim = dim3(kBatchThreads);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = CL;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
+  cudaLaunchAttribute attrs[1];
+  attrs[0].id = cudaLaunchAttributeClusterDimension;
+  attrs[0].val.clusterDim.x = CL;
+  attrs[0].val.clusterDim.y = 1;
+  attrs[0].val.clusterDim.z = 1;
+  cfg.attrs = attrs;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_pcg_cluster<CL>, d_params);
+  return cudaLaunchKernelEx(&cfg, k_pcg_cluster<CL>, d_params, cluster_cap(nr, nz, CL));
 }
 
-cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, cudaStream_t st) {
+cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, int nr, int nz, cudaStream_t st) {
   switch (cluster) {
-    case 1: return launch_cluster<1>(d_params, n, st);
-    case 2: return launch_cluster<2>(d_params, n, st);
-    case 4: return launch_cluster<4>(d_params, n, st);
-    case 8: return launch_cluster<8>(d_params, n, st);
+    case 1: return launch_cluster<1>(d_params, n, nr, nz, st);
+    case 2: return launch_cluster<2>(d_params, n, nr, nz, st);
+    case 4: return launch_cluster<4>(d_params, n, nr, nz, st);
+    case 8: return launch_cluster<8>(d_params, n, nr, nz, st);
     default: return cudaErrorInvalidValue;
   }
 }
