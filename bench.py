@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
-    ap.add_argument("--solver", default="mixed", choices=["plain", "mixed"])
+    ap.add_argument("--solver", default="mixed", choices=["plain", "mixed", "mg"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
@@ -323,7 +323,7 @@ def main():
     from paper_2310_04957_gb300 import pic
 
     prec = pic.PIC_FP32 if args.precision == "fp32" else pic.PIC_FP64
-    solver = pic.PIC_SOLVER_PLAIN if args.solver == "plain" else pic.PIC_SOLVER_MIXED
+    solver = {"plain": pic.PIC_SOLVER_PLAIN, "mixed": pic.PIC_SOLVER_MIXED, "mg": pic.PIC_SOLVER_MG}[args.solver]
     wl = make_workload(args.workload, rank)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):

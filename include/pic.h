@@ -67,6 +67,9 @@ extern "C" {
 #define PIC_SOLVER_PLAIN 0 /* FP64 Jacobi-preconditioned CG                        */
 #define PIC_SOLVER_MIXED 1 /* FP32 inner CG in one thread-block cluster, FP64
                               residual and iterative refinement                    */
+#define PIC_SOLVER_MG 3      /* FP32 CG preconditioned by a multigrid V-cycle
+                              (2x2 aggregation, damped Jacobi smoothing), FP64
+                              residual and iterative refinement                */
 #define PIC_SOLVER_LEARNED 2 /* flexible CG preconditioned by the attached U-Net
                               (pic_attach_unet), FP64 recurrences; the plain or
                               mixed PCG then confirms the residual and finishes
@@ -319,7 +322,7 @@ int pic_conv3x3_op_ex(int op, int H, int W, const void *in, int Cin, const void 
  * the rms of D^-1 r over the covered free nodes, followed by `smooth` (0..8)
  * damped Jacobi steps z += (2/3) D^-1 (r - A z); flexible CG with one stored
  * direction, at most `maxit` network applications per solve, then the solver
- * `finish` (PIC_SOLVER_PLAIN or PIC_SOLVER_MIXED) confirms the FP64 residual
+ * `finish` (PIC_SOLVER_PLAIN, _MIXED or _MG) confirms the FP64 residual
  * and finishes the solve from the learned iterate when needed.  The first
  * application on the warm start's residual is the learned initial-guess
  * correction.  u = NULL detaches.  The handle does not own u; keep it alive

@@ -93,6 +93,7 @@ struct pic_handle {
   double *d_phi_warm = nullptr, *d_lstats = nullptr, *d_pair_s2 = nullptr;
   bool keep_warm = false;
   int learned_finish = PIC_SOLVER_PLAIN;  // solver that confirms / finishes a learned solve
+  MgLevels mg{};                          // multigrid hierarchy of PIC_SOLVER_MG (workspace in mg.ws)
   std::vector<void *> lallocs;  // learned-solver buffers (freed on re-attach)
 };
 
@@ -404,6 +405,7 @@ int enqueue_solve(pic_handle *h, int mode) {
   PcgParams P = pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, h->d_phi, h->cfg.pcg_tol, h->d_pcg_out);
   const int finisher = mode == PIC_SOLVER_LEARNED ? h->learned_finish : mode;
   if (finisher == PIC_SOLVER_MIXED) CK(launch_pcg_mixed(P, h->pcg_grid, h->stream));
+  else if (finisher == PIC_SOLVER_MG) CK(launch_pcg_mg(P, h->mg, h->pcg_grid, h->stream));
   else CK(launch_pcg(P, h->pcg_grid, h->stream));
   return PIC_OK;
 }
@@ -542,7 +544,9 @@ bool check_config(const pic_config *c) {
   if (!c->node_kind || !c->cell_kind || !c->cell_eps || !c->xs_energy || !c->xs_sigma || c->n_xs < 2) return false;
   if (c->circuit < 0 || c->circuit > 2 || c->n_sub < 1 || c->steps_per_rf < 1 || c->pcg_maxit < 1) return false;
   if (c->precision != PIC_FP32 && c->precision != PIC_FP64) return false;
-  if (c->solver != PIC_SOLVER_PLAIN && c->solver != PIC_SOLVER_MIXED && c->solver != PIC_SOLVER_LEARNED) return false;
+  if (c->solver != PIC_SOLVER_PLAIN && c->solver != PIC_SOLVER_MIXED && c->solver != PIC_SOLVER_LEARNED &&
+      c->solver != PIC_SOLVER_MG)
+    return false;
   if (c->capacity[0] < 1 || c->capacity[1] < 1 || c->capacity[0] > 2000000000ll || c->capacity[1] > 2000000000ll)
     return false;
   if (!(c->m[0] > 0) || !(c->m[1] > 0) || !(c->m_gas > 0)) return false;
@@ -822,6 +826,14 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
     DA(h->d_E, 2 * h->esz * nn);
     DA(h->d_work, sizeof(double) * 8 * nn);
     DA(h->d_work32, sizeof(float) * 12 * nn);
+    {
+      const long long mgf = mg_plan(h->nr, h->nz, &h->mg);
+      DA(h->mg.ws, sizeof(float) * (size_t)mgf);
+      const long long lv = mgf - 3LL * (long long)nn;
+      h->mg.p = h->mg.ws + lv;
+      h->mg.q = h->mg.p + nn;
+      h->mg.x = h->mg.q + nn;
+    }
     h->pcg_grid = pcg_grid_size(h->device);
     DA(h->d_partial, sizeof(double) * 16 * (h->pcg_grid + 32));
     DA(h->d_bar, 4 * sizeof(unsigned));
@@ -1041,7 +1053,8 @@ int pic_step_timing(pic_handle *h, double *out7) {
 }
 
 int pic_field_solve(pic_handle *h, int mode, int *iters, double *rel_resid) {
-  if (!h || (mode != PIC_SOLVER_PLAIN && mode != PIC_SOLVER_MIXED && mode != PIC_SOLVER_LEARNED)) return PIC_EINVAL;
+  if (!h || (mode != PIC_SOLVER_PLAIN && mode != PIC_SOLVER_MIXED && mode != PIC_SOLVER_LEARNED && mode != PIC_SOLVER_MG))
+    return PIC_EINVAL;
   if (mode == PIC_SOLVER_LEARNED && !h->fcg_exec) return PIC_EINVAL;
   CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
   int st = enqueue_solve(h, mode);
@@ -1143,7 +1156,7 @@ void pic_batch_destroy(pic_batch *b) {
 
 int pic_attach_unet(pic_handle *h, pic_unet *u, int maxit, int smooth, int finish) {
   if (!h || maxit < 1 || smooth < 0 || smooth > 8) return PIC_EINVAL;
-  if (finish != PIC_SOLVER_PLAIN && finish != PIC_SOLVER_MIXED) return PIC_EINVAL;
+  if (finish != PIC_SOLVER_PLAIN && finish != PIC_SOLVER_MIXED && finish != PIC_SOLVER_MG) return PIC_EINVAL;
   if (sync(h)) return PIC_ECUDA;
   free_learned(h);
   if (!u) return PIC_OK;
@@ -1193,7 +1206,9 @@ int pic_attach_unet(pic_handle *h, pic_unet *u, int maxit, int smooth, int finis
 }
 
 int pic_set_solver(pic_handle *h, int solver) {
-  if (!h || (solver != PIC_SOLVER_PLAIN && solver != PIC_SOLVER_MIXED && solver != PIC_SOLVER_LEARNED)) return PIC_EINVAL;
+  if (!h || (solver != PIC_SOLVER_PLAIN && solver != PIC_SOLVER_MIXED && solver != PIC_SOLVER_LEARNED &&
+             solver != PIC_SOLVER_MG))
+    return PIC_EINVAL;
   if (sync(h)) return PIC_ECUDA;
   if (h->cfg.solver != solver) {
     for (int k = 0; k < 2; ++k)

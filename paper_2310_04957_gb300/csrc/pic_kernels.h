@@ -145,6 +145,27 @@ int batch_cluster_size(int nr, int nz);  // 0: the grid does not fit an 8-CTA cl
 cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, int nr, int nz, cudaStream_t st);
 int pcg_grid_size(int device);
 constexpr int kPcgThreads = 256;
+
+// Multigrid-preconditioned mixed solve: 2x2 aggregation hierarchy of the
+// operator (levels 0..L-1), FP32 workspace ws holding per level the arrays
+// gr, gz, gd (conductance to Dirichlet nodes), diag, dinv, X, Y, B (each
+// ni*nj floats), then the level-0 CG vectors p, q, x.
+constexpr int kMgMaxLevels = 12;
+constexpr int kMgArrays = 8;
+struct MgLevels {
+  int L;
+  int ni[kMgMaxLevels], nj[kMgMaxLevels];
+  long long off[kMgMaxLevels];  // first float of level l's arrays in ws
+  int local_from;               // levels >= local_from run in block 0 alone
+  float omega;                  // Jacobi damping
+  float alpha;                  // coarse-correction scale
+  int coarse_sweeps;            // Jacobi sweeps on the coarsest level
+  float *ws;
+  float *p, *q, *x;
+};
+// Levels and workspace size (floats) for an (nr+1) x (nz+1) node grid.
+long long mg_plan(int nr, int nz, MgLevels *M);
+cudaError_t launch_pcg_mg(const PcgParams &P, const MgLevels &M, int grid, cudaStream_t st);
 cudaError_t launch_efield(const EfieldParams &E, cudaStream_t st);
 cudaError_t launch_energy(int nr, int nz, const int8_t *node_kind, const double *Gr, const double *Gz,
                           const double *phi, double *out2, cudaStream_t st);

@@ -24,6 +24,7 @@
 // norms.  One persistent cooperative launch; bounded barrier waits.
 #include <cooperative_groups.h>
 #include <cstdint>
+#include <cstring>
 
 #include "pic_device.cuh"
 #include "pic_kernels.h"
@@ -681,6 +682,330 @@ cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, int 
     case 8: return launch_cluster<8>(d_params, n, nr, nz, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ---- multigrid-preconditioned mixed solve ----------------------------------------------
+// Same FP64 residual and refinement as k_pcg_mixed; the FP32 inner solve is CG
+// preconditioned by one symmetric V(2,2)-cycle.  The hierarchy aggregates 2x2
+// nodes: with piecewise-constant prolongation P the Galerkin operator
+// P^T A P of a "conductance" operator sum_b G_ab (x_a - x_b) + g_a x_a (g = the
+// conductance to Dirichlet nodes) is again of that form, with coarse edge
+// conductances = sums of the fine edges crossing between two aggregates and
+// coarse g = sum of the aggregate's g.  Smoother: damped Jacobi (omega); the
+// coarse correction is scaled by alpha (piecewise-constant aggregation
+// over-estimates the coarse energy); coarsest level: Jacobi sweeps from zero.
+// Every piece is a fixed linear symmetric map, so the preconditioner is SPD.
+struct MgLv {
+  int ni, nj, n;
+  float *gr, *gz, *gd, *diag, *dinv, *X, *Y, *B;
+};
+
+__device__ __forceinline__ MgLv mg_level(const MgLevels &M, int l) {
+  MgLv v;
+  v.ni = M.ni[l];
+  v.nj = M.nj[l];
+  v.n = v.ni * v.nj;
+  float *b = M.ws + M.off[l];
+  v.gr = b; v.gz = b + v.n; v.gd = b + 2 * (size_t)v.n; v.diag = b + 3 * (size_t)v.n; v.dinv = b + 4 * (size_t)v.n;
+  v.X = b + 5 * (size_t)v.n; v.Y = b + 6 * (size_t)v.n; v.B = b + 7 * (size_t)v.n;
+  return v;
+}
+
+// (A v)_a = diag_a v_a - sum_b G_ab v_b (edges to non-free nodes are 0)
+__device__ __forceinline__ float mg_apply(const MgLv &L, const float *v, int a, int i, int j) {
+  float s = L.diag[a] * v[a];
+  if (i > 0) s -= L.gr[a - 1] * v[a - 1];
+  if (i < L.ni - 1) s -= L.gr[a] * v[a + 1];
+  if (j > 0) s -= L.gz[a - L.ni] * v[a - L.ni];
+  if (j < L.nj - 1) s -= L.gz[a] * v[a + L.ni];
+  return s;
+}
+
+// One pass over level l: grid-wide with a grid barrier after it, or (local)
+// block 0 alone with a block barrier.  Returns false on a barrier timeout.
+template <class F>
+__device__ __forceinline__ bool mg_pass(const PcgParams &P, bool local, int n, F f) {
+  if (local) {
+    if (blockIdx.x == 0) {
+      for (int a = threadIdx.x; a < n; a += blockDim.x) f(a);
+      __syncthreads();
+    }
+    return true;
+  }
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) f(a);
+  return grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags);
+}
+
+// Operator hierarchy from the FP64 conductances (scaled by gscale).
+__device__ bool mg_setup(const PcgParams &P, const MgLevels &M) {
+  const int nr = P.nr, nz = P.nz, W1 = nr + 1;
+  const int8_t *kind = P.node_kind;
+  {
+    const MgLv L0 = mg_level(M, 0);
+    const float gs = (float)P.gscale;
+    if (!mg_pass(P, false, L0.n, [&](int a) {
+          const int j = a / W1, i = a - j * W1;
+          const bool fa = kind[a] == 0;
+          float gr = 0.0f, gz = 0.0f, gd = 0.0f, dg = 0.0f;
+          if (i < nr) {
+            const float g = (float)(P.Gr[j * nr + i] * P.gscale);
+            if (fa && kind[a + 1] == 0) gr = g;
+          }
+          if (j < nz) {
+            const float g = (float)(P.Gz[j * W1 + i] * P.gscale);
+            if (fa && kind[a + W1] == 0) gz = g;
+          }
+          if (fa) {
+            // all four neighbours count in the diagonal; Dirichlet ones also in gd
+            if (i > 0) { const float g = (float)(P.Gr[j * nr + i - 1] * P.gscale); dg += g; if (kind[a - 1]) gd += g; }
+            if (i < nr) { const float g = (float)(P.Gr[j * nr + i] * P.gscale); dg += g; if (kind[a + 1]) gd += g; }
+            if (j > 0) { const float g = (float)(P.Gz[(j - 1) * W1 + i] * P.gscale); dg += g; if (kind[a - W1]) gd += g; }
+            if (j < nz) { const float g = (float)(P.Gz[j * W1 + i] * P.gscale); dg += g; if (kind[a + W1]) gd += g; }
+          }
+          (void)gs;
+          L0.gr[a] = gr; L0.gz[a] = gz; L0.gd[a] = gd; L0.diag[a] = dg; L0.dinv[a] = dg > 0.0f ? 1.0f / dg : 0.0f;
+        }))
+      return false;
+  }
+  for (int l = 0; l + 1 < M.L; ++l) {
+    const MgLv F = mg_level(M, l), C = mg_level(M, l + 1);
+    const bool local = l + 1 >= M.local_from;
+    if (!mg_pass(P, local, C.n, [&](int c) {
+          const int J = c / C.ni, I = c - J * C.ni;
+          const int i0 = 2 * I, j0 = 2 * J;
+          float gr = 0.0f, gz = 0.0f, gd = 0.0f, ext = 0.0f;
+          for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+              const int i = i0 + di, j = j0 + dj;
+              if (i >= F.ni || j >= F.nj) continue;
+              gd += F.gd[j * F.ni + i];
+            }
+          for (int dj = 0; dj < 2; ++dj) {
+            const int j = j0 + dj;
+            if (j >= F.nj) continue;
+            if (i0 + 2 < F.ni) gr += F.gr[j * F.ni + i0 + 1];          // to aggregate I+1
+            if (i0 > 0) ext += F.gr[j * F.ni + i0 - 1];                // from aggregate I-1
+          }
+          for (int di = 0; di < 2; ++di) {
+            const int i = i0 + di;
+            if (i >= F.ni) continue;
+            if (j0 + 2 < F.nj) gz += F.gz[(j0 + 1) * F.ni + i];         // to aggregate J+1
+            if (j0 > 0) ext += F.gz[(j0 - 1) * F.ni + i];               // from aggregate J-1
+          }
+          const float dg = gr + gz + ext + gd;
+          C.gr[c] = gr; C.gz[c] = gz; C.gd[c] = gd; C.diag[c] = dg; C.dinv[c] = dg > 0.0f ? 1.0f / dg : 0.0f;
+        }))
+      return false;
+  }
+  // the local levels were built by block 0: everyone waits for them
+  return M.local_from >= M.L ? true : grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags);
+}
+
+// z = V(r): rhs in level 0's B, result in level 0's Y.
+__device__ bool mg_vcycle(const PcgParams &P, const MgLevels &M) {
+  const float w = M.omega, al = M.alpha;
+  // down
+  for (int l = 0; l + 1 < M.L; ++l) {
+    const MgLv F = mg_level(M, l), C = mg_level(M, l + 1);
+    const bool local = l >= M.local_from;
+    if (local && blockIdx.x != 0) break;
+    if (!mg_pass(P, local, F.n, [&](int a) { F.Y[a] = w * F.dinv[a] * F.B[a]; })) return false;
+    if (!mg_pass(P, local, F.n, [&](int a) {
+          const int j = a / F.ni, i = a - j * F.ni;
+          F.X[a] = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.Y, a, i, j));
+        }))
+      return false;
+    const bool clocal = l + 1 >= M.local_from;
+    if (!mg_pass(P, local, C.n, [&](int c) {
+          const int J = c / C.ni, I = c - J * C.ni;
+          float s = 0.0f;
+          for (int dj = 0; dj < 2; ++dj)
+            for (int di = 0; di < 2; ++di) {
+              const int i = 2 * I + di, j = 2 * J + dj;
+              if (i >= F.ni || j >= F.nj) continue;
+              const int a = j * F.ni + i;
+              if (F.dinv[a] == 0.0f) continue;
+              s += F.B[a] - mg_apply(F, F.X, a, i, j);
+            }
+          C.B[c] = s;
+        }))
+      return false;
+    (void)clocal;
+  }
+  // coarsest (Jacobi from zero, an even number of sweeps ending in Y) and up, in
+  // block 0 for the local levels
+  if (blockIdx.x == 0 || M.local_from >= M.L) {
+    const int lc = M.L - 1;
+    const MgLv C = mg_level(M, lc);
+    const bool local = lc >= M.local_from;
+    if (!local || blockIdx.x == 0) {
+      mg_pass(P, local, C.n, [&](int a) { C.Y[a] = w * C.dinv[a] * C.B[a]; });
+      for (int k = 0; k < M.coarse_sweeps; ++k) {
+        const float *src = (k & 1) ? C.X : C.Y;
+        float *dst = (k & 1) ? C.Y : C.X;
+        mg_pass(P, local, C.n, [&](int a) {
+          const int j = a / C.ni, i = a - j * C.ni;
+          dst[a] = src[a] + w * C.dinv[a] * (C.B[a] - mg_apply(C, src, a, i, j));
+        });
+      }
+    }
+  }
+  for (int l = M.L - 2; l >= 0; --l) {
+    const MgLv F = mg_level(M, l), C = mg_level(M, l + 1);
+    const bool local = l >= M.local_from;
+    if (!local && l + 1 >= M.local_from && M.local_from < M.L) {
+      // leaving the block-local levels: everyone waits for block 0
+      if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) return false;
+    }
+    if (local && blockIdx.x != 0) continue;
+    if (!mg_pass(P, local, F.n, [&](int a) {
+          const int j = a / F.ni, i = a - j * F.ni;
+          const int c = (j >> 1) * C.ni + (i >> 1);
+          F.Y[a] = F.dinv[a] != 0.0f ? F.X[a] + al * C.Y[c] : 0.0f;
+        }))
+      return false;
+    if (!mg_pass(P, local, F.n, [&](int a) {
+          const int j = a / F.ni, i = a - j * F.ni;
+          F.X[a] = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.Y, a, i, j));
+        }))
+      return false;
+    if (!mg_pass(P, local, F.n, [&](int a) {
+          const int j = a / F.ni, i = a - j * F.ni;
+          F.Y[a] = F.X[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.X, a, i, j));
+        }))
+      return false;
+  }
+  // a hierarchy entirely in block 0: the others wait for the result
+  if (M.local_from == 0) return grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags);
+  return true;
+}
+
+__global__ void __launch_bounds__(kPcgThreads) k_pcg_mg(const PcgParams P, const MgLevels M) {
+  const int nn = P.nn;
+  float *part32 = reinterpret_cast<float *>(P.partial + 8 * gridDim.x);
+  double *r64 = P.work;
+  const MgLv L0 = mg_level(M, 0);
+  int it = 0, parity = 0, status = -4, outer = 0;
+  double b2 = 0.0, r2 = 0.0;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
+  if (!mg_setup(P, M)) status = -5;
+  for (outer = 0; outer < 64 && status != -5; ++outer) {
+    double acc2[2] = {0.0, 0.0};
+    residual64(P, r64, acc2);
+    if (!grid_sum<double, 2>(acc2, P.partial, parity, P)) { status = -5; break; }
+    parity ^= 1;
+    b2 = acc2[0];
+    r2 = acc2[1];
+    const double target2 = b2 > 0.0 ? P.tol * P.tol * b2 : 1e-60;
+    if (!isfinite(r2)) { status = -7; break; }
+    if (r2 <= target2) { status = 0; break; }
+    if (it >= P.maxit) { status = -4; break; }
+    const double inv = rsqrt(r2);
+    for (int a = gtid; a < nn; a += gstride) {
+      L0.B[a] = P.node_kind[a] == 0 ? (float)(r64[a] * inv) : 0.0f;
+      M.x[a] = 0.0f;
+    }
+    if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { status = -5; break; }
+    if (!mg_vcycle(P, M)) { status = -5; break; }
+    float t2[2] = {0.0f, 0.0f};
+    for (int a = gtid; a < nn; a += gstride) {
+      const float z = L0.Y[a];
+      M.p[a] = z;
+      t2[0] += L0.B[a] * z;
+      t2[1] += L0.B[a] * L0.B[a];
+    }
+    if (!grid_sum<float, 2>(t2, part32, parity, P)) { status = -5; break; }
+    parity ^= 1;
+    float rz = t2[0];
+    float stop = P.inner_tol;
+    const float need = (float)sqrt(target2 / r2);
+    if (need > stop) stop = need;
+    const float stop2 = stop * stop;
+    bool bad = false, fail = false;
+    while (it < P.maxit) {
+      // q = A p, p.q
+      float pq[1] = {0.0f};
+      for (int a = gtid; a < nn; a += gstride) {
+        const int j = a / L0.ni, i = a - j * L0.ni;
+        const float qa = L0.dinv[a] != 0.0f ? mg_apply(L0, M.p, a, i, j) : 0.0f;
+        M.q[a] = qa;
+        pq[0] += M.p[a] * qa;
+      }
+      if (!grid_sum<float, 1>(pq, part32, parity, P)) { fail = true; break; }
+      parity ^= 1;
+      const float alpha = rz / pq[0];
+      for (int a = gtid; a < nn; a += gstride) {
+        M.x[a] += alpha * M.p[a];
+        L0.B[a] -= alpha * M.q[a];
+      }
+      ++it;
+      // z = V(r) (its first barrier also publishes the new r)
+      if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { fail = true; break; }
+      if (!mg_vcycle(P, M)) { fail = true; break; }
+      float t[2] = {0.0f, 0.0f};
+      for (int a = gtid; a < nn; a += gstride) {
+        t[0] += L0.B[a] * L0.Y[a];
+        t[1] += L0.B[a] * L0.B[a];
+      }
+      if (!grid_sum<float, 2>(t, part32, parity, P)) { fail = true; break; }
+      parity ^= 1;
+      if (!isfinite(t[0]) || !isfinite(t[1])) { bad = true; break; }
+      if (t[1] <= stop2) break;
+      const float beta = t[0] / rz;
+      rz = t[0];
+      for (int a = gtid; a < nn; a += gstride) M.p[a] = L0.Y[a] + beta * M.p[a];
+      if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { fail = true; break; }
+    }
+    if (fail) { status = -5; break; }
+    if (bad) { status = -7; break; }
+    const double back = sqrt(r2) * P.gscale;
+    for (int a = gtid; a < nn; a += gstride)
+      if (P.node_kind[a] == 0) P.phi[a] += (double)M.x[a] * back;
+    if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { status = -5; break; }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    P.out[0] = (double)it;
+    P.out[1] = b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
+    P.out[2] = (double)status;
+    P.out[3] = (double)outer;
+    if (status == -4) atomicOr(P.flags, 0x4u);
+    if (status == -7) atomicOr(P.flags, 0x8u);
+  }
+}
+
+long long mg_plan(int nr, int nz, MgLevels *M) {
+  memset(M, 0, sizeof(*M));
+  int ni = nr + 1, nj = nz + 1;
+  long long off = 0;
+  M->local_from = kMgMaxLevels;
+  for (int l = 0; l < kMgMaxLevels; ++l) {
+    M->ni[l] = ni;
+    M->nj[l] = nj;
+    M->off[l] = off;
+    off += (long long)kMgArrays * ni * nj;
+    M->L = l + 1;
+    if (M->local_from == kMgMaxLevels && (long long)ni * nj <= 4096) M->local_from = l;
+    if ((long long)ni * nj <= 64 || ni < 3 || nj < 3) break;
+    ni = (ni + 1) / 2;
+    nj = (nj + 1) / 2;
+  }
+  M->omega = 0.8f;
+  M->alpha = 1.8f;
+  M->coarse_sweeps = 10;
+  return off + 3LL * (nr + 1) * (nz + 1);
+}
+
+cudaError_t launch_pcg_mg(const PcgParams &P, const MgLevels &M, int grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kPcgThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg_mg, P, M);
 }
 
 int pcg_grid_size(int device) {

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libpic_gb300.so")
 PIC_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT", -6: "EOVERFLOW", -7: "ENAN"}
 PIC_FP32, PIC_FP64 = 0, 1
-PIC_SOLVER_PLAIN, PIC_SOLVER_MIXED, PIC_SOLVER_LEARNED = 0, 1, 2
+PIC_SOLVER_PLAIN, PIC_SOLVER_MIXED, PIC_SOLVER_LEARNED, PIC_SOLVER_MG = 0, 1, 2, 3
 DIAG = {"phi": 0, "Er": 1, "Ez": 2, "chi": 3, "dep_e": 4, "dep_i": 5, "sigma": 6, "vnode": 7, "rho": 8,
         "ne_avg": 9, "ni_avg": 10, "phi_warm": 11}
 DIAG_SCALARS = 100

@@ -108,9 +108,10 @@ def test_rebin_keeps_every_particle_in_its_cell():
         assert len(np.unique(g["id"])) == len(g["id"])
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 3])
 def test_field_solve_parity(mode):
-    """Assembly + field solve (0: plain FP64 PCG, 1: FP32 inner CG with FP64 refinement) from
+    """Assembly + field solve (0: plain FP64 PCG, 1: FP32 inner CG with FP64 refinement,
+    3: FP32 inner CG preconditioned by a multigrid V-cycle, FP64 refinement) from
     identical deposits: phi within 1e-8 relative L2 of the oracle, rho~ and chi identical to
     rounding."""
     wl = small(30_000)
