@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
-    ap.add_argument("--solver", default="mixed", choices=["plain", "mixed", "mg"])
+    ap.add_argument("--solver", default="mg", choices=["plain", "mixed", "mg"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
@@ -203,10 +203,11 @@ def run_reference(args):
 
 def field_solve_comparison(wl, steps=5):
     """Field solve to 1e-10 relative residual from the same warm starts: plain FP64
-    PCG, mixed PCG, and the learned solve (network trained here, on this workload's
-    own run, by the library's kernels: up to 3 network applications, then the mixed
-    PCG finishes).  Medians over `steps` consecutive steps of ms per
-    pic_field_solve call (assembly + solve + E field + one scalar read)."""
+    PCG, mixed PCG, multigrid-preconditioned mixed PCG, and the learned solves
+    (network trained here, on this workload's own run, by the library's kernels:
+    up to 3 network applications, then the mixed or the multigrid PCG finishes).
+    Medians over `steps` consecutive steps of ms per pic_field_solve call
+    (assembly + solve + E field + one scalar read)."""
     import statistics
 
     from paper_2310_04957_gb300 import learned as Lr
@@ -214,23 +215,29 @@ def field_solve_comparison(wl, steps=5):
 
     net, d, info = Lr.train_on_discharge(wl)
     d.keep_warm(True)
-    d.attach_unet(net, maxit=3, finish=pic.PIC_SOLVER_MIXED)
-    rows = {0: [], 1: [], 2: []}
+    modes = (pic.PIC_SOLVER_PLAIN, pic.PIC_SOLVER_MIXED, pic.PIC_SOLVER_MG)
+    rows = {m: [] for m in modes}
+    rows["learned_mixed"], rows["learned_mg"] = [], []
     for _ in range(steps):
         d.step(1)
-        r = Lr.compare_solvers(d, repeats=2)
-        for m in rows:
+        r = Lr.compare_solvers(d, modes=modes, repeats=2)
+        for m in modes:
             rows[m].append(r[m])
+        for key, fin in (("learned_mixed", pic.PIC_SOLVER_MIXED), ("learned_mg", pic.PIC_SOLVER_MG)):
+            d.attach_unet(net, maxit=3, finish=fin)
+            rows[key].append(Lr.compare_solvers(d, modes=(pic.PIC_SOLVER_LEARNED,), repeats=2)[pic.PIC_SOLVER_LEARNED])
     med = lambda m, k: statistics.median(x[k] for x in rows[m])
     out = {"tol": wl.pcg_tol, "steps": steps,
            "plain": {"ms": med(0, 3), "iters": med(0, 1)},
            "mixed": {"ms": med(1, 3), "inner_iters": med(1, 1)},
-           "learned_mixed": {"ms": med(2, 3), "network_applications": statistics.median(x[4][0] for x in rows[2]),
-                             "finisher_inner_iters": med(2, 1),
-                             "max_rel_residual": max(x[2] for x in rows[2])},
+           "mg": {"ms": med(3, 3), "inner_iters": med(3, 1)},
            "training": info}
+    for key in ("learned_mixed", "learned_mg"):
+        out[key] = {"ms": med(key, 3), "network_applications": statistics.median(x[4][0] for x in rows[key]),
+                    "finisher_inner_iters": med(key, 1), "max_rel_residual": max(x[2] for x in rows[key])}
     out["learned_vs_plain"] = out["plain"]["ms"] / out["learned_mixed"]["ms"]
     out["learned_vs_mixed"] = out["mixed"]["ms"] / out["learned_mixed"]["ms"]
+    out["mg_vs_plain"] = out["plain"]["ms"] / out["mg"]["ms"]
     d.close()
     net.close()
     return out

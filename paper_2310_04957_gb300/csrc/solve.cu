@@ -917,7 +917,8 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_mg(const PcgParams P, const
     if (!grid_sum<float, 2>(t2, part32, parity, P)) { status = -5; break; }
     parity ^= 1;
     float rz = t2[0];
-    float stop = P.inner_tol;
+    // the V-cycle makes a deeper FP32 inner solve cheap: one outer step fewer
+    float stop = fminf(P.inner_tol, 1e-5f);
     const float need = (float)sqrt(target2 / r2);
     if (need > stop) stop = need;
     const float stop2 = stop * stop;

@@ -125,7 +125,8 @@ def evaluate(net, store, idx):
     return float(loss.item()) / max(1, len(idx))
 
 
-def compare_solvers(d, modes=(pic.PIC_SOLVER_PLAIN, pic.PIC_SOLVER_MIXED, pic.PIC_SOLVER_LEARNED), repeats=1):
+def compare_solvers(d, modes=(pic.PIC_SOLVER_PLAIN, pic.PIC_SOLVER_MIXED, pic.PIC_SOLVER_MG, pic.PIC_SOLVER_LEARNED),
+                    repeats=1):
     """Solve the last step's system again from its warm start (kept by
     pic_keep_warm or the learned solver) with each mode.  Returns {mode: (status,
     iterations, relative residual, ms, learned stats)}; the handle ends with the
