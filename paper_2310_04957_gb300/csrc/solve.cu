@@ -695,6 +695,10 @@ cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, int 
 // coarse correction is scaled by alpha (piecewise-constant aggregation
 // over-estimates the coarse energy); coarsest level: Jacobi sweeps from zero.
 // Every piece is a fixed linear symmetric map, so the preconditioner is SPD.
+// Threads per block of the multigrid solve (one block per SM; the coarse
+// levels run in block 0, so its width sets their speed).
+constexpr int kMgThreads = 512;
+
 struct MgLv {
   int ni, nj, n;
   float *gr, *gz, *gd, *diag, *dinv, *X, *Y, *B;
@@ -718,6 +722,17 @@ __device__ __forceinline__ float mg_apply(const MgLv &L, const float *v, int a, 
   if (i < L.ni - 1) s -= L.gr[a] * v[a + 1];
   if (j > 0) s -= L.gz[a - L.ni] * v[a - L.ni];
   if (j < L.nj - 1) s -= L.gz[a] * v[a + L.ni];
+  return s;
+}
+
+// (A v)_a with v given by a functor of the node index.
+template <class V>
+__device__ __forceinline__ float mg_apply_f(const MgLv &L, int a, int i, int j, V v) {
+  float s = L.diag[a] * v(a);
+  if (i > 0) s -= L.gr[a - 1] * v(a - 1);
+  if (i < L.ni - 1) s -= L.gr[a] * v(a + 1);
+  if (j > 0) s -= L.gz[a - L.ni] * v(a - L.ni);
+  if (j < L.nj - 1) s -= L.gz[a] * v(a + L.ni);
   return s;
 }
 
@@ -801,7 +816,8 @@ __device__ bool mg_setup(const PcgParams &P, const MgLevels &M) {
   return M.local_from >= M.L ? true : grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags);
 }
 
-// z = V(r): rhs in level 0's B, result in level 0's Y.
+// z = V(r): rhs in level 0's B, result in level 0's X (each level's result is
+// left in its X).
 __device__ bool mg_vcycle(const PcgParams &P, const MgLevels &M) {
   const float w = M.omega, al = M.alpha;
   // down
@@ -809,10 +825,12 @@ __device__ bool mg_vcycle(const PcgParams &P, const MgLevels &M) {
     const MgLv F = mg_level(M, l), C = mg_level(M, l + 1);
     const bool local = l >= M.local_from;
     if (local && blockIdx.x != 0) break;
-    if (!mg_pass(P, local, F.n, [&](int a) { F.Y[a] = w * F.dinv[a] * F.B[a]; })) return false;
+    // two Jacobi sweeps from zero; the first sweep's values (w D^-1 B) are
+    // formed on the fly, so one pass and one barrier suffice
     if (!mg_pass(P, local, F.n, [&](int a) {
           const int j = a / F.ni, i = a - j * F.ni;
-          F.X[a] = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.Y, a, i, j));
+          auto y = [&](int b) { return w * F.dinv[b] * F.B[b]; };
+          F.X[a] = y(a) + w * F.dinv[a] * (F.B[a] - mg_apply_f(F, a, i, j, y));
         }))
       return false;
     const bool clocal = l + 1 >= M.local_from;
@@ -832,17 +850,17 @@ __device__ bool mg_vcycle(const PcgParams &P, const MgLevels &M) {
       return false;
     (void)clocal;
   }
-  // coarsest (Jacobi from zero, an even number of sweeps ending in Y) and up, in
+  // coarsest (Jacobi from zero, an even number of sweeps ending in X) and up, in
   // block 0 for the local levels
   if (blockIdx.x == 0 || M.local_from >= M.L) {
     const int lc = M.L - 1;
     const MgLv C = mg_level(M, lc);
     const bool local = lc >= M.local_from;
     if (!local || blockIdx.x == 0) {
-      mg_pass(P, local, C.n, [&](int a) { C.Y[a] = w * C.dinv[a] * C.B[a]; });
-      for (int k = 0; k < M.coarse_sweeps; ++k) {
-        const float *src = (k & 1) ? C.X : C.Y;
-        float *dst = (k & 1) ? C.Y : C.X;
+      mg_pass(P, local, C.n, [&](int a) { C.X[a] = w * C.dinv[a] * C.B[a]; });
+      for (int k = 0; k < M.coarse_sweeps; ++k) {  // an even count ends in X
+        const float *src = (k & 1) ? C.Y : C.X;
+        float *dst = (k & 1) ? C.X : C.Y;
         mg_pass(P, local, C.n, [&](int a) {
           const int j = a / C.ni, i = a - j * C.ni;
           dst[a] = src[a] + w * C.dinv[a] * (C.B[a] - mg_apply(C, src, a, i, j));
@@ -858,12 +876,18 @@ __device__ bool mg_vcycle(const PcgParams &P, const MgLevels &M) {
       if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) return false;
     }
     if (local && blockIdx.x != 0) continue;
+    // coarse correction folded into the first post-smoothing sweep: the
+    // corrected values are formed on the fly at the node and its neighbours
     if (!mg_pass(P, local, F.n, [&](int a) {
           const int j = a / F.ni, i = a - j * F.ni;
-          const int c = (j >> 1) * C.ni + (i >> 1);
-          F.Y[a] = F.dinv[a] != 0.0f ? F.X[a] + al * C.Y[c] : 0.0f;
+          auto y = [&](int b) {
+            const int jb = b / F.ni, ib = b - jb * F.ni;
+            return F.dinv[b] != 0.0f ? F.X[b] + al * C.X[(jb >> 1) * C.ni + (ib >> 1)] : 0.0f;
+          };
+          F.Y[a] = y(a) + w * F.dinv[a] * (F.B[a] - mg_apply_f(F, a, i, j, y));
         }))
       return false;
+    // second post-smoothing sweep: the level's result, in X
     if (!mg_pass(P, local, F.n, [&](int a) {
           const int j = a / F.ni, i = a - j * F.ni;
           F.X[a] = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.Y, a, i, j));
@@ -880,7 +904,7 @@ __device__ bool mg_vcycle(const PcgParams &P, const MgLevels &M) {
   return true;
 }
 
-__global__ void __launch_bounds__(kPcgThreads) k_pcg_mg(const PcgParams P, const MgLevels M) {
+__global__ void __launch_bounds__(kMgThreads, 1) k_pcg_mg(const PcgParams P, const MgLevels M) {
   const int nn = P.nn;
   float *part32 = reinterpret_cast<float *>(P.partial + 8 * gridDim.x);
   double *r64 = P.work;
@@ -909,7 +933,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_mg(const PcgParams P, const
     if (!mg_vcycle(P, M)) { status = -5; break; }
     float t2[2] = {0.0f, 0.0f};
     for (int a = gtid; a < nn; a += gstride) {
-      const float z = L0.Y[a];
+      const float z = L0.X[a];
       M.p[a] = z;
       t2[0] += L0.B[a] * z;
       t2[1] += L0.B[a] * L0.B[a];
@@ -945,7 +969,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_mg(const PcgParams P, const
       if (!mg_vcycle(P, M)) { fail = true; break; }
       float t[2] = {0.0f, 0.0f};
       for (int a = gtid; a < nn; a += gstride) {
-        t[0] += L0.B[a] * L0.Y[a];
+        t[0] += L0.B[a] * L0.X[a];
         t[1] += L0.B[a] * L0.B[a];
       }
       if (!grid_sum<float, 2>(t, part32, parity, P)) { fail = true; break; }
@@ -954,7 +978,7 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_mg(const PcgParams P, const
       if (t[1] <= stop2) break;
       const float beta = t[0] / rz;
       rz = t[0];
-      for (int a = gtid; a < nn; a += gstride) M.p[a] = L0.Y[a] + beta * M.p[a];
+      for (int a = gtid; a < nn; a += gstride) M.p[a] = L0.X[a] + beta * M.p[a];
       if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { fail = true; break; }
     }
     if (fail) { status = -5; break; }
@@ -999,7 +1023,7 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
 cudaError_t launch_pcg_mg(const PcgParams &P, const MgLevels &M, int grid, cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kPcgThreads);
+  cfg.blockDim = dim3(kMgThreads);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
