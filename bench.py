@@ -140,6 +140,21 @@ class ClockSampler:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def across_ranks(ms, work, dist=None, device="cuda"):
+    """Weak-scaling aggregate over the ranks of a replica run: the slowest rank's
+    time and the sum of all ranks' work (one MAX and one SUM all-reduce; no
+    data-path collective)."""
+    if dist is None:
+        return ms, work
+    import torch
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    w = torch.tensor([work], device=device, dtype=torch.float64)
+    dist.all_reduce(w)
+    return float(t.item()), float(w.item())
+
+
 def make_workload(name, rank=0):
     from paper_2310_04957_gb300 import workloads as W
 
@@ -247,20 +262,35 @@ def run_sweep(args):
     """64 discharges of the seeded Latin-hypercube sweep (uneven grids and
     particle counts): autotuned particle tiles, then each discharge stepped alone
     (the sum of their times) against all of them stepped by one batch graph per
-    step.  Host-timed with the device synchronised on both sides."""
+    step.  Host-timed with the device synchronised on both sides.  Under
+    torchrun the discharges are dealt to the ranks (balanced by particle count);
+    each rank batches its share; value = all ranks' particle-steps over the
+    slowest rank's time (no data-path collective)."""
     import torch
 
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2310_04957_gb300 import build
 
-    build.build()
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
     from paper_2310_04957_gb300 import pic, sweep
 
-    torch.cuda.set_device(0)
     t_setup = time.perf_counter()
-    pts = sweep.design(64, seed=4)
-    wls = sweep.workloads(pts)
+    pts_all = sweep.design(64, seed=4)
+    mine = sweep.shard([p["n_per_species"] for p in pts_all], rank, world)
+    pts = [pts_all[k] for k in mine]
+    wls = [sweep.workloads([pts_all[k]], seed_base=100 + k)[0] for k in mine]
     choice, timings = sweep.autotune_tiles(wls)
-    ds = [pic.Discharge(wl, solver=pic.PIC_SOLVER_MIXED, tile=choice[sweep.tile_class(wl)]) for wl in wls]
+    # solved alone, each discharge uses the fastest single-discharge solver (multigrid)
+    ds = [pic.Discharge(wl, solver=pic.PIC_SOLVER_MG, tile=choice[sweep.tile_class(wl)]) for wl in wls]
     for d in ds:
         d.start()
     torch.cuda.synchronize()
@@ -280,7 +310,9 @@ def run_sweep(args):
     b.step(Wm)
     b.sync()
     n = sum(d.count(0) + d.count(1) for d in ds)
-    with ClockSampler(0) as clk:
+    if dist is not None:
+        dist.barrier()
+    with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         b.step(K)
         b.sync()
@@ -288,14 +320,23 @@ def run_sweep(args):
     flags = 0
     for d in ds:
         flags |= d.status()
-    value = n * K / t_b
+    t_b, n_all = across_ranks(t_b, float(n), dist)
+    seq_s, ps = across_ranks(seq_s, ps, dist)
+    value = n_all * K / t_b
+    if rank != 0:
+        dist.barrier()
+        dist.destroy_process_group()
+        return 0
+    n = int(n_all)
     line = {"metric": "aggregate particle-steps/s, 64-discharge batch vs sequential", "value": value,
-            "unit": "particle-steps/s", "n_gpus": 1, "steps": K, "warmup": Wm, "ms_per_step": 1e3 * t_b / K,
+            "unit": "particle-steps/s", "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": 1e3 * t_b / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "sweep-64-gec-lhs", "discharges": len(ds), "particles": int(n),
+            "config": {"workload": "sweep-64-gec-lhs", "discharges": len(pts_all), "particles": int(n),
                        "grids": sorted({f"{w.nr}x{w.nz}" for w in wls}), "solver": "batched mixed (one thread-block cluster per discharge, CG state in shared memory)",
-                       "parallelism": "single", "l2": "inputs larger than L2"},
-            "sequential": {"value": ps / seq_s, "ms_per_step": 1e3 * seq_s / K, "solver": "mixed, one discharge at a time"},
+                       "parallelism": f"discharges dealt to {world} ranks" if world > 1 else "single",
+                       "l2": "inputs larger than L2"},
+            "sequential": {"value": ps / seq_s, "ms_per_step": 1e3 * seq_s / K,
+                           "solver": "multigrid-preconditioned mixed, one discharge at a time"},
             "speedup_vs_sequential": (n * K / t_b) / (ps / seq_s),
             "autotuned_tiles": {f"{c[0]}x{c[1]}": list(t) for c, t in choice.items()},
             "autotune_ms": {f"{c[0]}x{c[1]}": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in tv.items()}
@@ -303,6 +344,9 @@ def run_sweep(args):
             "setup_s": t_setup, "status_flags": flags, "clocks": clk.summary(),
             "gpu_launches": None, "e2e": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
@@ -361,15 +405,7 @@ def main():
     n_avg = 0.5 * (n0 + n1)
     particle_steps = n_avg * args.steps
     # slowest rank's time; all ranks' work
-    t_max = ms_total
-    tot_ps = particle_steps
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-        w = torch.tensor([particle_steps], device="cuda", dtype=torch.float64)
-        dist.all_reduce(w)
-        tot_ps = float(w.item())
+    t_max, tot_ps = across_ranks(ms_total, particle_steps, dist)
     value = tot_ps / (t_max * 1e-3)
     k_ms = phases[1] / args.steps
     bpp = BYTES_PER_PARTICLE_STEP[args.precision]

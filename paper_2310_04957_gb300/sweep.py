@@ -56,6 +56,21 @@ def workloads(points, scale=1.0, seed_base=100):
             for k, p in enumerate(points)]
 
 
+def shard(weights, rank, world):
+    """Indices of the items rank `rank` of `world` takes: items dealt largest
+    first, each to the rank with the least weight so far (ties to the lowest
+    rank).  The shares are disjoint, cover every item and are balanced."""
+    order = sorted(range(len(weights)), key=lambda k: (-weights[k], k))
+    load = [0] * world
+    mine = []
+    for k in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += weights[k]
+        if r == rank:
+            mine.append(k)
+    return sorted(mine)
+
+
 def tile_class(wl):
     """Discharges of one grid size share a tile choice."""
     return (wl.nr, wl.nz)
