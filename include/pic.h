@@ -357,13 +357,12 @@ int pic_learned_stats(pic_handle *h, double *out4);
  * pic_batch_create -- step n independent discharges (a parameter sweep with
  * uneven grids and particle counts) together.  Each step is one CUDA graph
  * launch holding one independent chain per discharge: particle phase, circuit
- * and assembly, then its field solve in one thread-block cluster of 1-8 CTAs
- * by grid size with the CG state in the cluster's shared memory (FP32 Jacobi
- * CG inside FP64 residual refinement to the discharge's pcg_tol, whatever its
- * cfg.solver; no grid-wide barrier, so the chains never wait on one another),
- * then its E field and diagnostics.  Each grid must fit an 8-CTA cluster
- * (48 B per node, at most ~4800 nodes per CTA: up to about 256 x 128 cells),
- * else PIC_EINVAL.  The handles must share a device and be at the same buffer
+ * and assembly, then its field solve on one thread-block cluster of 1-8 CTAs
+ * by grid size (the PIC_SOLVER_MG method -- multigrid-preconditioned FP32 CG
+ * inside FP64 residual refinement to the discharge's pcg_tol -- whatever its
+ * cfg.solver, with hardware cluster barriers instead of a grid barrier, so the
+ * chains never wait on one another), then its E field and diagnostics.  The
+ * handles must share a device and be at the same buffer
  * parity (stepped the same number of times); they stay owned by the caller and
  * must outlive the batch.  Unstarted handles are started.
  * pic_batch_step advances all of them by nsteps (asynchronous, except at RF

@@ -102,7 +102,6 @@ struct pic_batch {
   std::vector<pic_handle *> hs;
   cudaStream_t stream = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  PcgParams *d_params = nullptr;
 };
 
 namespace {
@@ -683,7 +682,6 @@ int download_species(pic_handle *h, int s, pic_particles *out, int64_t capn, int
 void batch_free(pic_batch *b) {
   for (int k = 0; k < 2; ++k)
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
-  if (b->d_params) cudaFree(b->d_params);
   if (b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -706,9 +704,9 @@ cudaError_t add_child(cudaGraph_t G, pic_handle *h, cudaStream_t cap, const cuda
 }
 
 // One step of every discharge: per discharge the chain [layout, particles,
-// circuit, assembly] -> [field solve: one thread-block cluster] -> [E field,
-// diagnostics]; the chains are independent branches of one graph, so one
-// discharge's solve overlaps another's particle phase.
+// circuit, assembly] -> [multigrid field solve on one thread-block cluster] ->
+// [E field, diagnostics]; the chains are independent branches of one graph, so
+// one discharge's solve overlaps another's particle phase.
 cudaError_t batch_build(pic_batch *b, int parity) {
   cudaGraph_t G = nullptr;
   cudaError_t e = cudaGraphCreate(&G, 0);
@@ -719,11 +717,9 @@ cudaError_t batch_build(pic_batch *b, int parity) {
     e = add_child(G, b->hs[i], b->stream, nullptr, 0, &pre[i],
                   [&](pic_handle *h) { return enqueue_step_pre(h, parity, nullptr); });
     if (e != cudaSuccess) break;
-    const PcgParams *params = b->d_params + i;
     e = add_child(G, b->hs[i], b->stream, &pre[i], 1, &solve[i], [&](pic_handle *h) {
-      return launch_pcg_batch(params, 1, batch_cluster_size(h->nr, h->nz), h->nr, h->nz, h->stream) == cudaSuccess
-                 ? PIC_OK
-                 : PIC_ECUDA;
+      const PcgParams P = pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, h->d_phi, h->cfg.pcg_tol, h->d_pcg_out);
+      return launch_pcg_mg_cluster(P, h->mg, mg_cluster_size(h->nn), h->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
     });
     if (e != cudaSuccess) break;
     e = add_child(G, b->hs[i], b->stream, &solve[i], 1, &post[i],
@@ -1076,7 +1072,6 @@ int pic_batch_create(pic_handle *const *hs, int n, pic_batch **out) {
   if (!b) return PIC_ENOMEM;
   for (int i = 0; i < n; ++i) {
     if (!hs[i] || hs[i]->device != hs[0]->device || hs[i]->cur != hs[0]->cur) { delete b; return PIC_EINVAL; }
-    if (batch_cluster_size(hs[i]->nr, hs[i]->nz) == 0) { delete b; return PIC_EINVAL; }
     for (int k = 0; k < i; ++k)
       if (hs[k] == hs[i]) { delete b; return PIC_EINVAL; }
     b->hs.push_back(hs[i]);
@@ -1088,14 +1083,7 @@ int pic_batch_create(pic_handle *const *hs, int n, pic_batch **out) {
     }
     if (sync(h)) { delete b; return PIC_ECUDA; }
   }
-  std::vector<PcgParams> P(n);
-  for (int i = 0; i < n; ++i) {
-    pic_handle *h = b->hs[i];
-    P[i] = pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, h->d_phi, h->cfg.pcg_tol, h->d_pcg_out);
-  }
-  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaMalloc(&b->d_params, sizeof(PcgParams) * n) != cudaSuccess ||
-      cudaMemcpy(b->d_params, P.data(), sizeof(PcgParams) * n, cudaMemcpyHostToDevice) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     batch_free(b);
     delete b;

@@ -137,12 +137,6 @@ cudaError_t launch_assemble_edges_only(const FieldParams &F, cudaStream_t st);
 cudaError_t launch_set_dirichlet(int nn, const int8_t *kind, double *phi, double U, cudaStream_t st);
 cudaError_t launch_pcg(const PcgParams &P, int grid, cudaStream_t st);
 cudaError_t launch_pcg_mixed(const PcgParams &P, int grid, cudaStream_t st);
-// n independent systems of one grid size (device array of parameters), one
-// cluster of `cluster` CTAs (1, 2, 4, 8) each, mixed precision with the CG
-// state resident in the cluster's shared memory.
-constexpr int kBatchThreads = 1024;
-int batch_cluster_size(int nr, int nz);  // 0: the grid does not fit an 8-CTA cluster
-cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, int nr, int nz, cudaStream_t st);
 int pcg_grid_size(int device);
 constexpr int kPcgThreads = 256;
 
@@ -166,6 +160,10 @@ struct MgLevels {
 // Levels and workspace size (floats) for an (nr+1) x (nz+1) node grid.
 long long mg_plan(int nr, int nz, MgLevels *M);
 cudaError_t launch_pcg_mg(const PcgParams &P, const MgLevels &M, int grid, cudaStream_t st);
+// The same solve on one thread-block cluster (1, 2, 4, 8 CTAs; mg_cluster_size
+// picks it from the node count): for many discharges solved at once.
+int mg_cluster_size(int nn);
+cudaError_t launch_pcg_mg_cluster(const PcgParams &P, const MgLevels &M, int cluster, cudaStream_t st);
 cudaError_t launch_efield(const EfieldParams &E, cudaStream_t st);
 cudaError_t launch_energy(int nr, int nz, const int8_t *node_kind, const double *Gr, const double *Gz,
                           const double *phi, double *out2, cudaStream_t st);

@@ -407,283 +407,6 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_mixed(const PcgParams P) {
   }
 }
 
-// ---- batched: one thread-block cluster per discharge, mixed precision ------------------
-// Many independent small systems (the discharges of a sweep), each solved by
-// its own cluster of CL CTAs (1..8, by grid size): no grid-wide barrier, so
-// the solves of different discharges never wait on one another.  Block sums
-// are combined across the cluster through distributed shared memory; the
-// hardware cluster barrier orders the neighbour reads.
-template <typename T, int K>
-__device__ __forceinline__ void cta_sum(T v[K]) {
-  __shared__ T s[K][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    T x = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane == 0) s[k][wid] = x;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    T x = (T)0;
-    for (int w = 0; w < nw; ++w) x += s[k][w];
-    v[k] = x;
-  }
-  __syncthreads();
-}
-
-// Cluster-wide sum (every thread of every CTA gets the same total: the CTA
-// partials are added in rank order).  slots: this CTA's [2][4] doubles, used
-// by alternating parity so one cluster barrier per sum suffices.
-template <int CL, typename T, int K>
-__device__ __forceinline__ void cluster_sum(T v[K], double (*slots)[4], double *bcast, int &par) {
-  cta_sum<T, K>(v);
-  if (CL == 1) return;
-  cg::cluster_group cl = cg::this_cluster();
-  if (threadIdx.x < K) slots[par][threadIdx.x] = (double)v[threadIdx.x];
-  cl.sync();
-  // K threads gather the CL partials (rank order) and broadcast through shared memory
-  if (threadIdx.x < K) {
-    double t = 0.0;
-    for (int r = 0; r < CL; ++r) t += cl.map_shared_rank(&slots[par][0], r)[threadIdx.x];
-    bcast[threadIdx.x] = t;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = (T)bcast[k];
-  par ^= 1;
-}
-
-template <int CL>
-__device__ __forceinline__ void cluster_barrier() {
-  if (CL == 1) __syncthreads();
-  else cg::this_cluster().sync();
-}
-
-// Shared-memory-resident version: the nodes are split by rows over the CL
-// CTAs of the cluster; each CTA keeps the FP32 operator (scaled) and the CG
-// vectors of its rows in shared memory and reads its neighbours' rows through
-// distributed shared memory.  Inner CG in the Chronopoulos-Gear arrangement
-// of cg_iteration (one cluster-wide reduction per iteration; r, w, s
-// double-buffered so the neighbours' next preconditioned residual is rebuilt
-// on the fly); FP64 residual and refinement in global memory around it.
-constexpr int kSmemFloats = 12;  // per node: gr gzu gzd dinv x p r[2] w[2] s[2]
-
-template <int CL>
-__global__ void __launch_bounds__(kBatchThreads, 1) k_pcg_cluster(const PcgParams *__restrict__ Ps, int cap) {
-  extern __shared__ __align__(16) float sm[];
-  __shared__ double slots[2][4];
-  __shared__ double bcast[4];
-  const PcgParams &P = Ps[blockIdx.x / CL];
-  const int rank = CL == 1 ? 0 : (int)cg::this_cluster().block_rank();
-  const int nr = P.nr, nz = P.nz, W1 = nr + 1, tid = threadIdx.x, nt = blockDim.x;
-  const int R = (nz + 1 + CL - 1) / CL, j0 = rank * R;
-  const int j1 = min(nz + 1, j0 + R), n_own = j1 > j0 ? (j1 - j0) * W1 : 0;
-  float *gr = sm, *gzu = sm + cap, *gzd = sm + 2 * cap, *dv = sm + 3 * cap, *x = sm + 4 * cap, *pv = sm + 5 * cap;
-  // r, w, s of parity q at sm + (6 + q) cap, (8 + q) cap, (10 + q) cap
-  auto R_ = [&](int q) { return sm + (6 + q) * cap; };
-  auto W_ = [&](int q) { return sm + (8 + q) * cap; };
-  auto S_ = [&](int q) { return sm + (10 + q) * cap; };
-  const int8_t *kind = P.node_kind;
-  int par = 0;
-  // value of the vector at float offset `off` at node (i, j) owned by another CTA
-  auto remote = [&](int off, int i, int j) -> float {
-    const int c = j / R;
-    const int l = (j - c * R) * W1 + i;
-    if (CL == 1) return sm[off + l];
-    return cg::this_cluster().map_shared_rank(sm, c)[off + l];
-  };
-  for (int l = tid; l < n_own; l += nt) {
-    const int j = j0 + l / W1, i = l - (l / W1) * W1, a = j * W1 + i;
-    gr[l] = i < nr ? (float)(P.Gr[j * nr + i] * P.gscale) : 0.0f;
-    gzu[l] = j < nz ? (float)(P.Gz[j * W1 + i] * P.gscale) : 0.0f;
-    gzd[l] = j > 0 ? (float)(P.Gz[(j - 1) * W1 + i] * P.gscale) : 0.0f;
-    dv[l] = kind[a] == 0 ? (float)(P.dinv[a] / P.gscale) : 0.0f;
-  }
-  cluster_barrier<CL>();
-  // dinv (r - alpha (w + beta s)) at node (i, j) from the parity-q buffers
-  auto u_next = [&](int i, int j, int q, float alpha, float beta) -> float {
-    if (j >= j0 && j < j1) {
-      const int l = (j - j0) * W1 + i;
-      return dv[l] * (R_(q)[l] - alpha * (W_(q)[l] + beta * S_(q)[l]));
-    }
-    const float d = remote(3 * cap, i, j), r = remote((6 + q) * cap, i, j), w = remote((8 + q) * cap, i, j),
-                sv = remote((10 + q) * cap, i, j);
-    return d * (r - alpha * (w + beta * sv));
-  };
-  int it = 0, status = -4, outer = 0;
-  double b2 = 0.0, r2 = 0.0;
-  for (outer = 0; outer < 64; ++outer) {
-    double acc[2] = {0.0, 0.0};
-    for (int l = tid; l < n_own; l += nt) {
-      const int j = j0 + l / W1, i = l - (l / W1) * W1, a = j * W1 + i;
-      if (kind[a] != 0) continue;
-      const double pa = P.phi[a];
-      double ax = 0.0, lift = 0.0;
-      if (i > 0) { const double g = P.Gr[j * nr + i - 1], pb = P.phi[a - 1]; ax += g * (pa - pb); if (kind[a - 1]) lift += g * pb; }
-      if (i < nr) { const double g = P.Gr[j * nr + i], pb = P.phi[a + 1]; ax += g * (pa - pb); if (kind[a + 1]) lift += g * pb; }
-      if (j > 0) { const double g = P.Gz[(j - 1) * W1 + i], pb = P.phi[a - W1]; ax += g * (pa - pb); if (kind[a - W1]) lift += g * pb; }
-      if (j < nz) { const double g = P.Gz[j * W1 + i], pb = P.phi[a + W1]; ax += g * (pa - pb); if (kind[a + W1]) lift += g * pb; }
-      const double qa = P.qrhs[a], ra = qa - ax, ba = qa + lift;
-      P.work[a] = ra;
-      acc[0] += ba * ba;
-      acc[1] += ra * ra;
-    }
-    cluster_sum<CL, double, 2>(acc, slots, bcast, par);
-    b2 = acc[0];
-    r2 = acc[1];
-    const double target2 = b2 > 0.0 ? P.tol * P.tol * b2 : 1e-60;
-    if (!isfinite(r2)) { status = -7; break; }
-    if (r2 <= target2) { status = 0; break; }
-    if (it >= P.maxit) { status = -4; break; }
-    const double inv = rsqrt(r2);
-    // inner start: r0 = residual / ||residual||, x = p = 0, w = s = 0
-    for (int l = tid; l < n_own; l += nt) {
-      const int a = (j0 + l / W1) * W1 + (l - (l / W1) * W1);
-      R_(0)[l] = dv[l] != 0.0f ? (float)(P.work[a] * inv) : 0.0f;
-      W_(0)[l] = 0.0f; S_(0)[l] = 0.0f; R_(1)[l] = 0.0f; W_(1)[l] = 0.0f; S_(1)[l] = 0.0f;
-      x[l] = 0.0f;
-      pv[l] = 0.0f;
-    }
-    cluster_barrier<CL>();
-    // w0 = A u0 and the first products
-    float tot[3] = {0.0f, 0.0f, 0.0f};
-    for (int l = tid; l < n_own; l += nt) {
-      if (dv[l] == 0.0f) continue;
-      const int j = j0 + l / W1, i = l - (l / W1) * W1;
-      const float ua = dv[l] * R_(0)[l];
-      float w = 0.0f;
-      if (i > 0) w += gr[l - 1] * (ua - u_next(i - 1, j, 0, 0.0f, 0.0f));
-      if (i < nr) w += gr[l] * (ua - u_next(i + 1, j, 0, 0.0f, 0.0f));
-      if (j > 0) w += gzd[l] * (ua - u_next(i, j - 1, 0, 0.0f, 0.0f));
-      if (j < nz) w += gzu[l] * (ua - u_next(i, j + 1, 0, 0.0f, 0.0f));
-      W_(0)[l] = w;
-      tot[0] += R_(0)[l] * ua;
-      tot[1] += w * ua;
-      tot[2] += R_(0)[l] * R_(0)[l];
-    }
-    cluster_sum<CL, float, 3>(tot, slots, bcast, par);
-    float stop = P.inner_tol;
-    const float need = (float)sqrt(target2 / r2);
-    if (need > stop) stop = need;
-    const float stop2 = stop * stop;
-    float gamma = tot[0], delta = tot[1], rho = tot[2], gamma_prev = 1.0f, alpha_prev = 1.0f;
-    int q = 0, k = 0;
-    bool bad = false;
-    while (true) {
-      if (!isfinite(rho) || !isfinite(gamma) || !isfinite(delta)) { bad = true; break; }
-      if (rho <= stop2 || it >= P.maxit) break;
-      const float beta = k == 0 ? 0.0f : gamma / gamma_prev;
-      const float den = k == 0 ? delta : delta - beta * gamma / alpha_prev;
-      const float alpha = gamma / den;
-      float acc3[3] = {0.0f, 0.0f, 0.0f};
-      float *rq = R_(q), *wq = W_(q), *sq = S_(q), *rn = R_(q ^ 1), *wn = W_(q ^ 1), *sn = S_(q ^ 1);
-      for (int l = tid; l < n_own; l += nt) {
-        const float da = dv[l];
-        if (da == 0.0f) continue;
-        const int j = j0 + l / W1, i = l - (l / W1) * W1;
-        const float ra = rq[l], wa = wq[l], sa = sq[l];
-        const float pa = da * ra + beta * pv[l];
-        const float snew = wa + beta * sa;
-        const float rnew = ra - alpha * snew;
-        const float unew = da * rnew;
-        float wnew = 0.0f;
-        if (i > 0) wnew += gr[l - 1] * (unew - u_next(i - 1, j, q, alpha, beta));
-        if (i < nr) wnew += gr[l] * (unew - u_next(i + 1, j, q, alpha, beta));
-        if (j > 0) wnew += gzd[l] * (unew - u_next(i, j - 1, q, alpha, beta));
-        if (j < nz) wnew += gzu[l] * (unew - u_next(i, j + 1, q, alpha, beta));
-        x[l] += alpha * pa;
-        pv[l] = pa;
-        rn[l] = rnew;
-        wn[l] = wnew;
-        sn[l] = snew;
-        acc3[0] += rnew * unew;
-        acc3[1] += wnew * unew;
-        acc3[2] += rnew * rnew;
-      }
-      cluster_sum<CL, float, 3>(acc3, slots, bcast, par);  // its barrier publishes parity q^1
-      q ^= 1;
-      ++k;
-      ++it;
-      gamma_prev = gamma;
-      alpha_prev = alpha;
-      gamma = acc3[0];
-      delta = acc3[1];
-      rho = acc3[2];
-    }
-    if (bad) { status = -7; break; }
-    const double back = sqrt(r2) * P.gscale;
-    for (int l = tid; l < n_own; l += nt) {
-      if (dv[l] == 0.0f) continue;
-      const int a = (j0 + l / W1) * W1 + (l - (l / W1) * W1);
-      P.phi[a] += (double)x[l] * back;
-    }
-    cluster_barrier<CL>();
-  }
-  if (rank == 0 && tid == 0) {
-    P.out[0] = (double)it;
-    P.out[1] = b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
-    P.out[2] = (double)status;
-    P.out[3] = (double)outer;
-    if (status == -4) atomicOr(P.flags, 0x4u);
-    if (status == -7) atomicOr(P.flags, 0x8u);
-  }
-  // no CTA may leave while others can still read its shared memory
-  cluster_barrier<CL>();
-}
-
-// Nodes per CTA (rows of the grid split over cl CTAs) and its shared memory.
-static int cluster_cap(int nr, int nz, int cl) { return ((nz + 1 + cl - 1) / cl) * (nr + 1); }
-static size_t cluster_smem_bytes(int nr, int nz, int cl) {
-  return sizeof(float) * kSmemFloats * (size_t)cluster_cap(nr, nz, cl);
-}
-static const size_t kClusterSmemLimit = 225 * 1024;
-
-int batch_cluster_size(int nr, int nz) {
-  for (int cl = 1; cl <= 8; cl *= 2) {
-    const bool fits = cluster_smem_bytes(nr, nz, cl) <= kClusterSmemLimit;
-    if (fits && (cluster_cap(nr, nz, cl) <= 4096 || cl == 8)) return cl;
-  }
-  return 0;
-}
-
-template <int CL>
-static cudaError_t launch_cluster(const PcgParams *d_params, int n, int nr, int nz, cudaStream_t st) {
-  const size_t smem = cluster_smem_bytes(nr, nz, CL);
-  if (smem > kClusterSmemLimit) return cudaErrorInvalidValue;
-  static size_t attr = 0;  // largest dynamic shared memory granted so far (per instance)
-  if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_pcg_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = smem;
-  }
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(n * CL);
-  cfg.blockDim = dim3(kBatchThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attrs[1];
-  attrs[0].id = cudaLaunchAttributeClusterDimension;
-  attrs[0].val.clusterDim.x = CL;
-  attrs[0].val.clusterDim.y = 1;
-  attrs[0].val.clusterDim.z = 1;
-  cfg.attrs = attrs;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_pcg_cluster<CL>, d_params, cluster_cap(nr, nz, CL));
-}
-
-cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, int nr, int nz, cudaStream_t st) {
-  switch (cluster) {
-    case 1: return launch_cluster<1>(d_params, n, nr, nz, st);
-    case 2: return launch_cluster<2>(d_params, n, nr, nz, st);
-    case 4: return launch_cluster<4>(d_params, n, nr, nz, st);
-    case 8: return launch_cluster<8>(d_params, n, nr, nz, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
 // ---- multigrid-preconditioned mixed solve ----------------------------------------------
 // Same FP64 residual and refinement as k_pcg_mixed; the FP32 inner solve is CG
 // preconditioned by one symmetric V(2,2)-cycle.  The hierarchy aggregates 2x2
@@ -698,6 +421,66 @@ cudaError_t launch_pcg_batch(const PcgParams *d_params, int n, int cluster, int 
 // Threads per block of the multigrid solve (one block per SM; the coarse
 // levels run in block 0, so its width sets their speed).
 constexpr int kMgThreads = 512;
+
+// Synchronisation scope of the multigrid solve: the whole grid (one
+// cooperative launch, bounded grid barrier) or one thread-block cluster
+// (hardware cluster barrier).
+struct GridScope {
+  __device__ int nblk() const { return (int)gridDim.x; }
+  __device__ int bid() const { return (int)blockIdx.x; }
+  __device__ bool sync(const PcgParams &P) const { return grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags); }
+};
+template <int CL>
+struct ClusterScope {
+  __device__ int nblk() const { return CL; }
+  __device__ int bid() const { return (int)cg::this_cluster().block_rank(); }
+  __device__ bool sync(const PcgParams &) const {
+    cg::this_cluster().sync();
+    return true;
+  }
+};
+
+// grid_sum and residual64 over a scope's blocks.
+template <typename A, int K, class S>
+__device__ __forceinline__ bool grid_sum_s(const S &sc, A v[K], A *partial, int parity, const PcgParams &P) {
+  block_sum<A, K>(v);
+  A *part = partial + parity * 4 * sc.nblk();
+  if (threadIdx.x < K) part[sc.bid() * 4 + threadIdx.x] = v[threadIdx.x];
+  if (!sc.sync(P)) return false;
+  A w[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) w[k] = (A)0;
+  for (int b = threadIdx.x; b < sc.nblk(); b += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) w[k] += __ldcg(part + b * 4 + k);
+  }
+  block_sum<A, K>(w);
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = w[k];
+  return true;
+}
+
+template <class S>
+__device__ __forceinline__ void residual64_s(const S &sc, const PcgParams &P, double *r64, double acc[2]) {
+  const int nr = P.nr, W = nr + 1;
+  const int chunk = (P.nn + sc.nblk() - 1) / sc.nblk();
+  const int lo = sc.bid() * chunk, hi = min(P.nn, lo + chunk);
+  for (int a = lo + threadIdx.x; a < hi; a += blockDim.x) {
+    if (P.node_kind[a] != 0) continue;
+    const int j = a / W, i = a - j * W;
+    const double pa = __ldcg(P.phi + a);
+    double ax = 0.0, lift = 0.0;
+    if (i > 0) { const double g = __ldg(P.Gr + j * nr + i - 1), pb = __ldcg(P.phi + a - 1); ax += g * (pa - pb); if (P.node_kind[a - 1] != 0) lift += g * pb; }
+    if (i < nr) { const double g = __ldg(P.Gr + j * nr + i), pb = __ldcg(P.phi + a + 1); ax += g * (pa - pb); if (P.node_kind[a + 1] != 0) lift += g * pb; }
+    if (j > 0) { const double g = __ldg(P.Gz + (j - 1) * W + i), pb = __ldcg(P.phi + a - W); ax += g * (pa - pb); if (P.node_kind[a - W] != 0) lift += g * pb; }
+    if (j < P.nz) { const double g = __ldg(P.Gz + j * W + i), pb = __ldcg(P.phi + a + W); ax += g * (pa - pb); if (P.node_kind[a + W] != 0) lift += g * pb; }
+    const double q = __ldg(P.qrhs + a);
+    const double r = q - ax, b = q + lift;
+    r64[a] = r;
+    acc[0] += b * b;
+    acc[1] += r * r;
+  }
+}
 
 struct MgLv {
   int ni, nj, n;
@@ -738,27 +521,28 @@ __device__ __forceinline__ float mg_apply_f(const MgLv &L, int a, int i, int j, 
 
 // One pass over level l: grid-wide with a grid barrier after it, or (local)
 // block 0 alone with a block barrier.  Returns false on a barrier timeout.
-template <class F>
-__device__ __forceinline__ bool mg_pass(const PcgParams &P, bool local, int n, F f) {
+template <class S, class F>
+__device__ __forceinline__ bool mg_pass(const S &sc, const PcgParams &P, bool local, int n, F f) {
   if (local) {
-    if (blockIdx.x == 0) {
+    if (sc.bid() == 0) {
       for (int a = threadIdx.x; a < n; a += blockDim.x) f(a);
       __syncthreads();
     }
     return true;
   }
-  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < n; a += gridDim.x * blockDim.x) f(a);
-  return grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags);
+  for (int a = sc.bid() * blockDim.x + threadIdx.x; a < n; a += sc.nblk() * blockDim.x) f(a);
+  return sc.sync(P);
 }
 
 // Operator hierarchy from the FP64 conductances (scaled by gscale).
-__device__ bool mg_setup(const PcgParams &P, const MgLevels &M) {
+template <class S>
+__device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M) {
   const int nr = P.nr, nz = P.nz, W1 = nr + 1;
   const int8_t *kind = P.node_kind;
   {
     const MgLv L0 = mg_level(M, 0);
     const float gs = (float)P.gscale;
-    if (!mg_pass(P, false, L0.n, [&](int a) {
+    if (!mg_pass(sc, P, false, L0.n, [&](int a) {
           const int j = a / W1, i = a - j * W1;
           const bool fa = kind[a] == 0;
           float gr = 0.0f, gz = 0.0f, gd = 0.0f, dg = 0.0f;
@@ -785,7 +569,7 @@ __device__ bool mg_setup(const PcgParams &P, const MgLevels &M) {
   for (int l = 0; l + 1 < M.L; ++l) {
     const MgLv F = mg_level(M, l), C = mg_level(M, l + 1);
     const bool local = l + 1 >= M.local_from;
-    if (!mg_pass(P, local, C.n, [&](int c) {
+    if (!mg_pass(sc, P, local, C.n, [&](int c) {
           const int J = c / C.ni, I = c - J * C.ni;
           const int i0 = 2 * I, j0 = 2 * J;
           float gr = 0.0f, gz = 0.0f, gd = 0.0f, ext = 0.0f;
@@ -813,28 +597,29 @@ __device__ bool mg_setup(const PcgParams &P, const MgLevels &M) {
       return false;
   }
   // the local levels were built by block 0: everyone waits for them
-  return M.local_from >= M.L ? true : grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags);
+  return M.local_from >= M.L ? true : sc.sync(P);
 }
 
 // z = V(r): rhs in level 0's B, result in level 0's X (each level's result is
 // left in its X).
-__device__ bool mg_vcycle(const PcgParams &P, const MgLevels &M) {
+template <class S>
+__device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M) {
   const float w = M.omega, al = M.alpha;
   // down
   for (int l = 0; l + 1 < M.L; ++l) {
     const MgLv F = mg_level(M, l), C = mg_level(M, l + 1);
     const bool local = l >= M.local_from;
-    if (local && blockIdx.x != 0) break;
+    if (local && sc.bid() != 0) break;
     // two Jacobi sweeps from zero; the first sweep's values (w D^-1 B) are
     // formed on the fly, so one pass and one barrier suffice
-    if (!mg_pass(P, local, F.n, [&](int a) {
+    if (!mg_pass(sc, P, local, F.n, [&](int a) {
           const int j = a / F.ni, i = a - j * F.ni;
           auto y = [&](int b) { return w * F.dinv[b] * F.B[b]; };
           F.X[a] = y(a) + w * F.dinv[a] * (F.B[a] - mg_apply_f(F, a, i, j, y));
         }))
       return false;
     const bool clocal = l + 1 >= M.local_from;
-    if (!mg_pass(P, local, C.n, [&](int c) {
+    if (!mg_pass(sc, P, local, C.n, [&](int c) {
           const int J = c / C.ni, I = c - J * C.ni;
           float s = 0.0f;
           for (int dj = 0; dj < 2; ++dj)
@@ -852,16 +637,16 @@ __device__ bool mg_vcycle(const PcgParams &P, const MgLevels &M) {
   }
   // coarsest (Jacobi from zero, an even number of sweeps ending in X) and up, in
   // block 0 for the local levels
-  if (blockIdx.x == 0 || M.local_from >= M.L) {
+  if (sc.bid() == 0 || M.local_from >= M.L) {
     const int lc = M.L - 1;
     const MgLv C = mg_level(M, lc);
     const bool local = lc >= M.local_from;
-    if (!local || blockIdx.x == 0) {
-      mg_pass(P, local, C.n, [&](int a) { C.X[a] = w * C.dinv[a] * C.B[a]; });
+    if (!local || sc.bid() == 0) {
+      mg_pass(sc, P, local, C.n, [&](int a) { C.X[a] = w * C.dinv[a] * C.B[a]; });
       for (int k = 0; k < M.coarse_sweeps; ++k) {  // an even count ends in X
         const float *src = (k & 1) ? C.Y : C.X;
         float *dst = (k & 1) ? C.X : C.Y;
-        mg_pass(P, local, C.n, [&](int a) {
+        mg_pass(sc, P, local, C.n, [&](int a) {
           const int j = a / C.ni, i = a - j * C.ni;
           dst[a] = src[a] + w * C.dinv[a] * (C.B[a] - mg_apply(C, src, a, i, j));
         });
@@ -873,12 +658,12 @@ __device__ bool mg_vcycle(const PcgParams &P, const MgLevels &M) {
     const bool local = l >= M.local_from;
     if (!local && l + 1 >= M.local_from && M.local_from < M.L) {
       // leaving the block-local levels: everyone waits for block 0
-      if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) return false;
+      if (!sc.sync(P)) return false;
     }
-    if (local && blockIdx.x != 0) continue;
+    if (local && sc.bid() != 0) continue;
     // coarse correction folded into the first post-smoothing sweep: the
     // corrected values are formed on the fly at the node and its neighbours
-    if (!mg_pass(P, local, F.n, [&](int a) {
+    if (!mg_pass(sc, P, local, F.n, [&](int a) {
           const int j = a / F.ni, i = a - j * F.ni;
           auto y = [&](int b) {
             const int jb = b / F.ni, ib = b - jb * F.ni;
@@ -888,35 +673,36 @@ __device__ bool mg_vcycle(const PcgParams &P, const MgLevels &M) {
         }))
       return false;
     // second post-smoothing sweep: the level's result, in X
-    if (!mg_pass(P, local, F.n, [&](int a) {
+    if (!mg_pass(sc, P, local, F.n, [&](int a) {
           const int j = a / F.ni, i = a - j * F.ni;
           F.X[a] = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.Y, a, i, j));
         }))
       return false;
-    if (!mg_pass(P, local, F.n, [&](int a) {
+    if (!mg_pass(sc, P, local, F.n, [&](int a) {
           const int j = a / F.ni, i = a - j * F.ni;
           F.Y[a] = F.X[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.X, a, i, j));
         }))
       return false;
   }
   // a hierarchy entirely in block 0: the others wait for the result
-  if (M.local_from == 0) return grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags);
+  if (M.local_from == 0) return sc.sync(P);
   return true;
 }
 
-__global__ void __launch_bounds__(kMgThreads, 1) k_pcg_mg(const PcgParams P, const MgLevels M) {
+template <class S>
+__device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) {
   const int nn = P.nn;
-  float *part32 = reinterpret_cast<float *>(P.partial + 8 * gridDim.x);
+  float *part32 = reinterpret_cast<float *>(P.partial + 8 * sc.nblk());
   double *r64 = P.work;
   const MgLv L0 = mg_level(M, 0);
   int it = 0, parity = 0, status = -4, outer = 0;
   double b2 = 0.0, r2 = 0.0;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gstride = gridDim.x * blockDim.x;
-  if (!mg_setup(P, M)) status = -5;
+  const int gtid = sc.bid() * blockDim.x + threadIdx.x, gstride = sc.nblk() * blockDim.x;
+  if (!mg_setup(sc, P, M)) status = -5;
   for (outer = 0; outer < 64 && status != -5; ++outer) {
     double acc2[2] = {0.0, 0.0};
-    residual64(P, r64, acc2);
-    if (!grid_sum<double, 2>(acc2, P.partial, parity, P)) { status = -5; break; }
+    residual64_s(sc, P, r64, acc2);
+    if (!grid_sum_s<double, 2>(sc, acc2, P.partial, parity, P)) { status = -5; break; }
     parity ^= 1;
     b2 = acc2[0];
     r2 = acc2[1];
@@ -929,8 +715,8 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_pcg_mg(const PcgParams P, con
       L0.B[a] = P.node_kind[a] == 0 ? (float)(r64[a] * inv) : 0.0f;
       M.x[a] = 0.0f;
     }
-    if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { status = -5; break; }
-    if (!mg_vcycle(P, M)) { status = -5; break; }
+    if (!sc.sync(P)) { status = -5; break; }
+    if (!mg_vcycle(sc, P, M)) { status = -5; break; }
     float t2[2] = {0.0f, 0.0f};
     for (int a = gtid; a < nn; a += gstride) {
       const float z = L0.X[a];
@@ -938,7 +724,7 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_pcg_mg(const PcgParams P, con
       t2[0] += L0.B[a] * z;
       t2[1] += L0.B[a] * L0.B[a];
     }
-    if (!grid_sum<float, 2>(t2, part32, parity, P)) { status = -5; break; }
+    if (!grid_sum_s<float, 2>(sc, t2, part32, parity, P)) { status = -5; break; }
     parity ^= 1;
     float rz = t2[0];
     // the V-cycle makes a deeper FP32 inner solve cheap: one outer step fewer
@@ -956,7 +742,7 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_pcg_mg(const PcgParams P, con
         M.q[a] = qa;
         pq[0] += M.p[a] * qa;
       }
-      if (!grid_sum<float, 1>(pq, part32, parity, P)) { fail = true; break; }
+      if (!grid_sum_s<float, 1>(sc, pq, part32, parity, P)) { fail = true; break; }
       parity ^= 1;
       const float alpha = rz / pq[0];
       for (int a = gtid; a < nn; a += gstride) {
@@ -965,30 +751,30 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_pcg_mg(const PcgParams P, con
       }
       ++it;
       // z = V(r) (its first barrier also publishes the new r)
-      if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { fail = true; break; }
-      if (!mg_vcycle(P, M)) { fail = true; break; }
+      if (!sc.sync(P)) { fail = true; break; }
+      if (!mg_vcycle(sc, P, M)) { fail = true; break; }
       float t[2] = {0.0f, 0.0f};
       for (int a = gtid; a < nn; a += gstride) {
         t[0] += L0.B[a] * L0.X[a];
         t[1] += L0.B[a] * L0.B[a];
       }
-      if (!grid_sum<float, 2>(t, part32, parity, P)) { fail = true; break; }
+      if (!grid_sum_s<float, 2>(sc, t, part32, parity, P)) { fail = true; break; }
       parity ^= 1;
       if (!isfinite(t[0]) || !isfinite(t[1])) { bad = true; break; }
       if (t[1] <= stop2) break;
       const float beta = t[0] / rz;
       rz = t[0];
       for (int a = gtid; a < nn; a += gstride) M.p[a] = L0.X[a] + beta * M.p[a];
-      if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { fail = true; break; }
+      if (!sc.sync(P)) { fail = true; break; }
     }
     if (fail) { status = -5; break; }
     if (bad) { status = -7; break; }
     const double back = sqrt(r2) * P.gscale;
     for (int a = gtid; a < nn; a += gstride)
       if (P.node_kind[a] == 0) P.phi[a] += (double)M.x[a] * back;
-    if (!grid_barrier(P.bar, gridDim.x, P.spin_limit, P.flags)) { status = -5; break; }
+    if (!sc.sync(P)) { status = -5; break; }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (sc.bid() == 0 && threadIdx.x == 0) {
     P.out[0] = (double)it;
     P.out[1] = b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
     P.out[2] = (double)status;
@@ -996,6 +782,20 @@ __global__ void __launch_bounds__(kMgThreads, 1) k_pcg_mg(const PcgParams P, con
     if (status == -4) atomicOr(P.flags, 0x4u);
     if (status == -7) atomicOr(P.flags, 0x8u);
   }
+}
+
+__global__ void __launch_bounds__(kMgThreads, 1) k_pcg_mg(const PcgParams P, const MgLevels M) {
+  GridScope sc;
+  pcg_mg_body(sc, P, M);
+}
+
+// One discharge per cluster of CL CTAs (the batched sweep): the same solve with
+// hardware cluster barriers in place of the grid barrier, so many solves run
+// at once without waiting on one another.
+template <int CL>
+__global__ void __launch_bounds__(kMgThreads, 1) k_pcg_mg_cluster(const PcgParams P, const MgLevels M) {
+  ClusterScope<CL> sc;
+  pcg_mg_body(sc, P, M);
 }
 
 long long mg_plan(int nr, int nz, MgLevels *M) {
@@ -1018,6 +818,34 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
   M->alpha = 1.8f;
   M->coarse_sweeps = 10;
   return off + 3LL * (nr + 1) * (nz + 1);
+}
+
+template <int CL>
+static cudaError_t launch_mg_cluster(const PcgParams &P, const MgLevels &M, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(kMgThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg_mg_cluster<CL>, P, M);
+}
+
+int mg_cluster_size(int nn) { return nn <= 4096 ? 1 : nn <= 9000 ? 2 : nn <= 20000 ? 4 : 8; }
+
+cudaError_t launch_pcg_mg_cluster(const PcgParams &P, const MgLevels &M, int cluster, cudaStream_t st) {
+  switch (cluster) {
+    case 1: return launch_mg_cluster<1>(P, M, st);
+    case 2: return launch_mg_cluster<2>(P, M, st);
+    case 4: return launch_mg_cluster<4>(P, M, st);
+    case 8: return launch_mg_cluster<8>(P, M, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_pcg_mg(const PcgParams &P, const MgLevels &M, int grid, cudaStream_t st) {
