@@ -332,7 +332,7 @@ def run_sweep(args):
             "unit": "particle-steps/s", "n_gpus": world, "steps": K, "warmup": Wm, "ms_per_step": 1e3 * t_b / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "sweep-64-gec-lhs", "discharges": len(pts_all), "particles": int(n),
-                       "grids": sorted({f"{w.nr}x{w.nz}" for w in wls}), "solver": "batched mixed (one thread-block cluster per discharge, CG state in shared memory)",
+                       "grids": sorted({f"{w.nr}x{w.nz}" for w in wls}), "solver": "multigrid-preconditioned mixed CG, one thread-block cluster per discharge",
                        "parallelism": f"discharges dealt to {world} ranks" if world > 1 else "single",
                        "l2": "inputs larger than L2"},
             "sequential": {"value": ps / seq_s, "ms_per_step": 1e3 * seq_s / K,

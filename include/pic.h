@@ -65,7 +65,7 @@ extern "C" {
 #define PIC_FP64 1 /* everything in FP64 (the plain method)                          */
 
 #define PIC_SOLVER_PLAIN 0 /* FP64 Jacobi-preconditioned CG                        */
-#define PIC_SOLVER_MIXED 1 /* FP32 inner CG in one thread-block cluster, FP64
+#define PIC_SOLVER_MIXED 1 /* FP32 Jacobi-preconditioned inner CG, FP64
                               residual and iterative refinement                    */
 #define PIC_SOLVER_MG 3      /* FP32 CG preconditioned by a multigrid V-cycle
                               (2x2 aggregation, damped Jacobi smoothing), FP64

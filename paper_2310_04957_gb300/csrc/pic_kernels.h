@@ -146,11 +146,15 @@ constexpr int kPcgThreads = 256;
 // ni*nj floats), then the level-0 CG vectors p, q, x.
 constexpr int kMgMaxLevels = 12;
 constexpr int kMgArrays = 8;
+constexpr int kMgSmemFloats = 40 * 1024;  // at most 160 KB of shared memory for the local levels
 struct MgLevels {
   int L;
   int ni[kMgMaxLevels], nj[kMgMaxLevels];
   long long off[kMgMaxLevels];  // first float of level l's arrays in ws
   int local_from;               // levels >= local_from run in block 0 alone
+  int smem_from;                // levels >= smem_from live in block 0's shared memory (L: none)
+  long long soff[kMgMaxLevels]; // their offsets (floats) in it
+  int smem_floats;              // its size
   float omega;                  // Jacobi damping
   float alpha;                  // coarse-correction scale
   int coarse_sweeps;            // Jacobi sweeps on the coarsest level

@@ -487,6 +487,19 @@ struct MgLv {
   float *gr, *gz, *gd, *diag, *dinv, *X, *Y, *B;
 };
 
+// Level l's arrays: the levels from M.smem_from on live in block 0's shared
+// memory (sm != nullptr only there); everything else in the global workspace.
+__device__ __forceinline__ MgLv mg_level(const MgLevels &M, int l, float *sm) {
+  MgLv v;
+  v.ni = M.ni[l];
+  v.nj = M.nj[l];
+  v.n = v.ni * v.nj;
+  float *b = (sm != nullptr && l >= M.smem_from) ? sm + M.soff[l] : M.ws + M.off[l];
+  v.gr = b; v.gz = b + v.n; v.gd = b + 2 * (size_t)v.n; v.diag = b + 3 * (size_t)v.n; v.dinv = b + 4 * (size_t)v.n;
+  v.X = b + 5 * (size_t)v.n; v.Y = b + 6 * (size_t)v.n; v.B = b + 7 * (size_t)v.n;
+  return v;
+}
+
 __device__ __forceinline__ MgLv mg_level(const MgLevels &M, int l) {
   MgLv v;
   v.ni = M.ni[l];
@@ -536,7 +549,7 @@ __device__ __forceinline__ bool mg_pass(const S &sc, const PcgParams &P, bool lo
 
 // Operator hierarchy from the FP64 conductances (scaled by gscale).
 template <class S>
-__device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M) {
+__device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, float *sm) {
   const int nr = P.nr, nz = P.nz, W1 = nr + 1;
   const int8_t *kind = P.node_kind;
   {
@@ -567,7 +580,7 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M) {
       return false;
   }
   for (int l = 0; l + 1 < M.L; ++l) {
-    const MgLv F = mg_level(M, l), C = mg_level(M, l + 1);
+    const MgLv F = mg_level(M, l, sm), C = mg_level(M, l + 1, sm);
     const bool local = l + 1 >= M.local_from;
     if (!mg_pass(sc, P, local, C.n, [&](int c) {
           const int J = c / C.ni, I = c - J * C.ni;
@@ -603,13 +616,24 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M) {
 // z = V(r): rhs in level 0's B, result in level 0's X (each level's result is
 // left in its X).
 template <class S>
-__device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M) {
+__device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, float *sm) {
   const float w = M.omega, al = M.alpha;
+  const int lf = M.local_from;
+  // block 0 takes the first local level's right-hand side (restricted
+  // grid-wide into the global copy) into shared memory
+  auto take_in = [&]() {
+    if (sm == nullptr || lf < M.smem_from || lf >= M.L) return;
+    const MgLv G = mg_level(M, lf, nullptr), Sh = mg_level(M, lf, sm);
+    for (int a = threadIdx.x; a < G.n; a += blockDim.x) Sh.B[a] = __ldcg(G.B + a);
+    __syncthreads();
+  };
   // down
   for (int l = 0; l + 1 < M.L; ++l) {
-    const MgLv F = mg_level(M, l), C = mg_level(M, l + 1);
-    const bool local = l >= M.local_from;
+    const bool local = l >= lf;
     if (local && sc.bid() != 0) break;
+    if (l == lf) take_in();
+    // the grid-wide restriction into the first local level writes its global copy
+    const MgLv F = mg_level(M, l, sm), C = mg_level(M, l + 1, l + 1 == lf ? nullptr : sm);
     // two Jacobi sweeps from zero; the first sweep's values (w D^-1 B) are
     // formed on the fly, so one pass and one barrier suffice
     if (!mg_pass(sc, P, local, F.n, [&](int a) {
@@ -618,7 +642,6 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M) {
           F.X[a] = y(a) + w * F.dinv[a] * (F.B[a] - mg_apply_f(F, a, i, j, y));
         }))
       return false;
-    const bool clocal = l + 1 >= M.local_from;
     if (!mg_pass(sc, P, local, C.n, [&](int c) {
           const int J = c / C.ni, I = c - J * C.ni;
           float s = 0.0f;
@@ -633,13 +656,13 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M) {
           C.B[c] = s;
         }))
       return false;
-    (void)clocal;
   }
+  if (lf == M.L - 1) take_in();  // the coarsest level is the only local one
   // coarsest (Jacobi from zero, an even number of sweeps ending in X) and up, in
   // block 0 for the local levels
   if (sc.bid() == 0 || M.local_from >= M.L) {
     const int lc = M.L - 1;
-    const MgLv C = mg_level(M, lc);
+    const MgLv C = mg_level(M, lc, sm);
     const bool local = lc >= M.local_from;
     if (!local || sc.bid() == 0) {
       mg_pass(sc, P, local, C.n, [&](int a) { C.X[a] = w * C.dinv[a] * C.B[a]; });
@@ -654,12 +677,17 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M) {
     }
   }
   for (int l = M.L - 2; l >= 0; --l) {
-    const MgLv F = mg_level(M, l), C = mg_level(M, l + 1);
-    const bool local = l >= M.local_from;
-    if (!local && l + 1 >= M.local_from && M.local_from < M.L) {
-      // leaving the block-local levels: everyone waits for block 0
+    const bool local = l >= lf;
+    if (!local && l + 1 >= lf && lf < M.L) {
+      // leaving the block-local levels: block 0 publishes the first local
+      // level's result, and everyone waits for it
+      if (sm != nullptr && lf >= M.smem_from) {
+        const MgLv G = mg_level(M, lf, nullptr), Sh = mg_level(M, lf, sm);
+        for (int a = threadIdx.x; a < G.n; a += blockDim.x) G.X[a] = Sh.X[a];
+      }
       if (!sc.sync(P)) return false;
     }
+    const MgLv F = mg_level(M, l, sm), C = mg_level(M, l + 1, l + 1 == lf ? nullptr : sm);
     if (local && sc.bid() != 0) continue;
     // coarse correction folded into the first post-smoothing sweep: the
     // corrected values are formed on the fly at the node and its neighbours
@@ -678,11 +706,6 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M) {
           F.X[a] = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.Y, a, i, j));
         }))
       return false;
-    if (!mg_pass(sc, P, local, F.n, [&](int a) {
-          const int j = a / F.ni, i = a - j * F.ni;
-          F.Y[a] = F.X[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.X, a, i, j));
-        }))
-      return false;
   }
   // a hierarchy entirely in block 0: the others wait for the result
   if (M.local_from == 0) return sc.sync(P);
@@ -691,6 +714,8 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M) {
 
 template <class S>
 __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) {
+  extern __shared__ __align__(16) float mg_sm[];
+  float *sm = (sc.bid() == 0 && M.smem_from < M.L) ? mg_sm : nullptr;
   const int nn = P.nn;
   float *part32 = reinterpret_cast<float *>(P.partial + 8 * sc.nblk());
   double *r64 = P.work;
@@ -698,7 +723,7 @@ __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) 
   int it = 0, parity = 0, status = -4, outer = 0;
   double b2 = 0.0, r2 = 0.0;
   const int gtid = sc.bid() * blockDim.x + threadIdx.x, gstride = sc.nblk() * blockDim.x;
-  if (!mg_setup(sc, P, M)) status = -5;
+  if (!mg_setup(sc, P, M, sm)) status = -5;
   for (outer = 0; outer < 64 && status != -5; ++outer) {
     double acc2[2] = {0.0, 0.0};
     residual64_s(sc, P, r64, acc2);
@@ -716,7 +741,7 @@ __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) 
       M.x[a] = 0.0f;
     }
     if (!sc.sync(P)) { status = -5; break; }
-    if (!mg_vcycle(sc, P, M)) { status = -5; break; }
+    if (!mg_vcycle(sc, P, M, sm)) { status = -5; break; }
     float t2[2] = {0.0f, 0.0f};
     for (int a = gtid; a < nn; a += gstride) {
       const float z = L0.X[a];
@@ -752,7 +777,7 @@ __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) 
       ++it;
       // z = V(r) (its first barrier also publishes the new r)
       if (!sc.sync(P)) { fail = true; break; }
-      if (!mg_vcycle(sc, P, M)) { fail = true; break; }
+      if (!mg_vcycle(sc, P, M, sm)) { fail = true; break; }
       float t[2] = {0.0f, 0.0f};
       for (int a = gtid; a < nn; a += gstride) {
         t[0] += L0.B[a] * L0.X[a];
@@ -814,6 +839,21 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
     ni = (ni + 1) / 2;
     nj = (nj + 1) / 2;
   }
+  // the block-local levels (below level 0) live in block 0's shared memory
+  // for the whole solve when they fit
+  M->smem_from = M->L;
+  M->smem_floats = 0;
+  if (M->local_from >= 1 && M->local_from < M->L) {
+    long long sf = 0;
+    for (int l = M->local_from; l < M->L; ++l) {
+      M->soff[l] = sf;
+      sf += (long long)kMgArrays * M->ni[l] * M->nj[l];
+    }
+    if (sf <= kMgSmemFloats) {
+      M->smem_from = M->local_from;
+      M->smem_floats = (int)sf;
+    }
+  }
   M->omega = 0.8f;
   M->alpha = 1.8f;
   M->coarse_sweeps = 10;
@@ -825,7 +865,15 @@ static cudaError_t launch_mg_cluster(const PcgParams &P, const MgLevels &M, cuda
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(kMgThreads);
+  cfg.dynamicSmemBytes = sizeof(float) * (size_t)M.smem_floats;
   cfg.stream = st;
+  static bool smem_set = false;
+  if (!smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_pcg_mg_cluster<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float) * kMgSmemFloats));
+    if (e != cudaSuccess) return e;
+    smem_set = true;
+  }
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CL;
@@ -849,9 +897,17 @@ cudaError_t launch_pcg_mg_cluster(const PcgParams &P, const MgLevels &M, int clu
 }
 
 cudaError_t launch_pcg_mg(const PcgParams &P, const MgLevels &M, int grid, cudaStream_t st) {
+  static bool smem_set = false;
+  if (!smem_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_pcg_mg, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float) * kMgSmemFloats));
+    if (e != cudaSuccess) return e;
+    smem_set = true;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kMgThreads);
+  cfg.dynamicSmemBytes = sizeof(float) * (size_t)M.smem_floats;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -1,7 +1,7 @@
 """Parity of the CUDA path with the FP64 oracle, through the C ABI.
 
 Every comparison starts both sides from the same state and the same seeded
-inputs.  Tolerances (the benchmark spec): positions/velocities <= 1e-5 relative per
+inputs.  Tolerances: positions/velocities <= 1e-5 relative per
 particle; rho~ <= 1e-6 relative L2; phi <= 1e-8 relative L2; collision-branch
 divergences <= 1e-4 of particles per step; FP64 path: near machine precision.
 """
@@ -106,6 +106,38 @@ def test_rebin_keeps_every_particle_in_its_cell():
         co = np.bincount(go["cell"], minlength=wl.nr * wl.nz)
         assert np.array_equal(cd, co)
         assert len(np.unique(g["id"])) == len(g["id"])
+
+
+@pytest.mark.parametrize("nr,nz", [(96, 48), (128, 64), (256, 128)])
+def test_multigrid_solve_parity_on_deeper_hierarchies(nr, nz):
+    """The multigrid-preconditioned solve on grids whose coarse levels run in
+    one block (in its shared memory) below one or two grid-wide levels: phi
+    and Ez within 1e-8 relative L2 of the oracle's FP64 PCG solve of the same
+    system."""
+    wl = W.gec_case(nr, nz, 30.0, 150.0, n_per_species=20_000)
+    wl = dataclasses.replace(wl, phase_src=1.0)
+    d, o = make_pair(wl, FP32)
+    o.init_fields()
+    d.start()
+    er, ez = random_field(wl, 9, precision=FP32)
+    for x in (d, o):
+        x.set_field("Er", er)
+        x.set_field("Ez", ez)
+    d.particle_phase()
+    # the deposits and the surface charge the particle phase left on the dielectric
+    for name in ("dep_e", "dep_i", "sigma"):
+        o.set_field(name, d.field(name))
+    o.assemble()
+    st_o, _, rel_o = o.field_solve()
+    st_d, it_d, rel_d = d.field_solve(3)
+    assert st_o == 0 and st_d == 0
+    assert rel_d <= wl.pcg_tol and rel_o <= wl.pcg_tol
+    assert rel_l2(d.field("rho"), o.field("rho")) <= 1e-13
+    assert rel_l2(d.field("chi"), o.field("chi")) <= 1e-13
+    assert it_d <= 100
+    assert rel_l2(d.field("phi"), o.field("phi")) <= 1e-8
+    assert rel_l2(d.field("Ez"), o.field("Ez")) <= 1e-8
+    assert d.status() == 0
 
 
 @pytest.mark.parametrize("mode", [0, 1, 3])

@@ -37,7 +37,8 @@ def test_learned_solve_matches_oracle(finish):
         x.set_field("Er", er)
         x.set_field("Ez", ez)
     d.particle_phase()
-    for name in ("dep_e", "dep_i"):
+    # the deposits and the surface charge the particle phase left on the dielectric
+    for name in ("dep_e", "dep_i", "sigma"):
         o.set_field(name, d.field(name))
     o.assemble()
     st_o, _, rel_o = o.field_solve()
