@@ -34,29 +34,27 @@ namespace cg = cooperative_groups;
 namespace pic {
 
 __device__ bool grid_barrier(unsigned *bar, unsigned nblocks, long long limit, uint32_t *flags) {
+  // One release-add per block and nothing after the last arrival: block 0 adds
+  // 2^31 - (nblocks - 1), the others 1, so the arrivals of all blocks together
+  // flip bit 31 and leave the low bits as they were (the host zeroes the word
+  // before each launch).  Each block waits, with an acquire load, for the flip.
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned *gen = bar + 1;
-    unsigned g = *gen;
-    __threadfence();
-    unsigned prev = atomicAdd(bar, 1u);
+    const unsigned add = blockIdx.x == 0 ? 0x80000000u - (nblocks - 1u) : 1u;
+    unsigned old, cur;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(bar), "r"(add) : "memory");
     int ok = 1;
-    if (prev == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long t0 = clock64();
-      while (*gen == g) {
-        if (clock64() - t0 > limit) {
-          ok = 0;
-          atomicOr(flags, 0x2u);
-          break;
-        }
+    const long long t0 = clock64();
+    while (true) {
+      asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(cur) : "l"(bar) : "memory");
+      if ((old ^ cur) & 0x80000000u) break;
+      if (clock64() - t0 > limit) {
+        ok = 0;
+        atomicOr(flags, 0x2u);
+        break;
       }
     }
-    __threadfence();
     s_ok = ok;
   }
   __syncthreads();
