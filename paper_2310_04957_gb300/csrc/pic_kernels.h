@@ -147,6 +147,7 @@ constexpr int kPcgThreads = 256;
 constexpr int kMgMaxLevels = 12;
 constexpr int kMgArrays = 8;
 constexpr int kMgSmemFloats = 40 * 1024;  // at most 160 KB of shared memory for the local levels
+constexpr int kMgDenseMax = 64;           // coarsest levels up to this many nodes are inverted
 struct MgLevels {
   int L;
   int ni[kMgMaxLevels], nj[kMgMaxLevels];
@@ -157,7 +158,9 @@ struct MgLevels {
   int smem_floats;              // its size
   float omega;                  // Jacobi damping
   float alpha;                  // coarse-correction scale
-  int coarse_sweeps;            // Jacobi sweeps on the coarsest level
+  int coarse_sweeps;            // Jacobi sweeps on the coarsest level (when not dense)
+  int cinv_off;                 // dense inverse of the coarsest operator in block 0's
+                                // shared memory at this offset (floats); -1: Jacobi
   float *ws;
   float *p, *q, *x;
 };

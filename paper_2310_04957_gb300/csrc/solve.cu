@@ -414,8 +414,11 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_mixed(const PcgParams P) {
 // conductances = sums of the fine edges crossing between two aggregates and
 // coarse g = sum of the aggregate's g.  Smoother: damped Jacobi (omega); the
 // coarse correction is scaled by alpha (piecewise-constant aggregation
-// over-estimates the coarse energy); coarsest level: Jacobi sweeps from zero.
-// Every piece is a fixed linear symmetric map, so the preconditioner is SPD.
+// over-estimates the coarse energy); coarsest level (at most kMgDenseMax
+// nodes): its inverse, formed at setup by Gauss-Jordan elimination in block 0's
+// shared memory, applied as one matrix-vector product (Jacobi sweeps from zero
+// on larger coarsest levels).  Every piece is a fixed linear symmetric map, so
+// the preconditioner is SPD.
 // Threads per block of the multigrid solve (one block per SM; the coarse
 // levels run in block 0, so its width sets their speed).
 constexpr int kMgThreads = 512;
@@ -607,6 +610,48 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
         }))
       return false;
   }
+  // dense inverse of the coarsest operator (SPD: no pivoting), in place, with
+  // column k and row k staged so that each elimination step is one pass
+  if (M.cinv_off >= 0 && sc.bid() == 0) {
+    __shared__ float colk[kMgDenseMax], rowk[kMgDenseMax];
+    const MgLv C = mg_level(M, M.L - 1, sm);
+    const int n = C.n;
+    float *Ai = sm + M.cinv_off;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int r = e / n, c = e - r * n;
+      const int jr = r / C.ni, ir = r - jr * C.ni;
+      float v = 0.0f;
+      if (C.diag[r] == 0.0f || C.diag[c] == 0.0f) {
+        v = r == c ? 1.0f : 0.0f;  // an aggregate without unknowns: identity row
+      } else if (r == c) {
+        v = C.diag[r];
+      } else if (c == r + 1 && ir + 1 < C.ni) {
+        v = -C.gr[r];
+      } else if (c == r - 1 && ir > 0) {
+        v = -C.gr[c];
+      } else if (c == r + C.ni) {
+        v = -C.gz[r];
+      } else if (c == r - C.ni) {
+        v = -C.gz[c];
+      }
+      Ai[e] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k < n; ++k) {
+      for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        colk[t] = Ai[t * n + k];
+        rowk[t] = Ai[k * n + t];
+      }
+      __syncthreads();
+      const float ip = 1.0f / colk[k];
+      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        const int r = e / n, c = e - r * n;
+        const float rk = (c == k ? 1.0f : rowk[c]) * ip;  // row k after scaling
+        Ai[e] = r == k ? rk : (c == k ? 0.0f : Ai[e]) - colk[r] * rk;
+      }
+      __syncthreads();
+    }
+  }
   // the local levels were built by block 0: everyone waits for them
   return M.local_from >= M.L ? true : sc.sync(P);
 }
@@ -656,9 +701,23 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
       return false;
   }
   if (lf == M.L - 1) take_in();  // the coarsest level is the only local one
-  // coarsest (Jacobi from zero, an even number of sweeps ending in X) and up, in
-  // block 0 for the local levels
-  if (sc.bid() == 0 || M.local_from >= M.L) {
+  // coarsest (dense inverse, or Jacobi from zero with an even number of sweeps
+  // ending in X) and up, in block 0 for the local levels
+  if (M.cinv_off >= 0) {
+    if (sc.bid() == 0) {
+      const MgLv C = mg_level(M, M.L - 1, sm);
+      const float *Ai = sm + M.cinv_off;
+      const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int r = threadIdx.x >> 5; r < C.n; r += nw) {
+        float v = 0.0f;
+        for (int c = lane; c < C.n; c += 32) v += Ai[r * C.n + c] * C.B[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) C.X[r] = v;
+      }
+      __syncthreads();
+    }
+  } else if (sc.bid() == 0 || M.local_from >= M.L) {
     const int lc = M.L - 1;
     const MgLv C = mg_level(M, lc, sm);
     const bool local = lc >= M.local_from;
@@ -713,7 +772,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
 template <class S>
 __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) {
   extern __shared__ __align__(16) float mg_sm[];
-  float *sm = (sc.bid() == 0 && M.smem_from < M.L) ? mg_sm : nullptr;
+  float *sm = (sc.bid() == 0 && M.smem_floats > 0) ? mg_sm : nullptr;
   const int nn = P.nn;
   float *part32 = reinterpret_cast<float *>(P.partial + 8 * sc.nblk());
   double *r64 = P.work;
@@ -847,10 +906,18 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
       M->soff[l] = sf;
       sf += (long long)kMgArrays * M->ni[l] * M->nj[l];
     }
-    if (sf <= kMgSmemFloats) {
+    if (sf <= kMgSmemFloats - kMgDenseMax * kMgDenseMax) {
       M->smem_from = M->local_from;
       M->smem_floats = (int)sf;
     }
+  }
+  // the coarsest level is block 0's (at most kMgDenseMax nodes is at most
+  // 4096): its dense inverse follows the levels in shared memory
+  const int nc = M->ni[M->L - 1] * M->nj[M->L - 1];
+  M->cinv_off = -1;
+  if (nc <= kMgDenseMax && M->local_from < M->L) {
+    M->cinv_off = M->smem_floats;
+    M->smem_floats += nc * nc;
   }
   M->omega = 0.8f;
   M->alpha = 1.8f;
