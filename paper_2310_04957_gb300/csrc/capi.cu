@@ -825,10 +825,12 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
     {
       const long long mgf = mg_plan(h->nr, h->nz, &h->mg);
       DA(h->mg.ws, sizeof(float) * (size_t)mgf);
-      const long long lv = mgf - 3LL * (long long)nn;
+      const long long lv = mgf - 5LL * (long long)nn;
       h->mg.p = h->mg.ws + lv;
-      h->mg.q = h->mg.p + nn;
+      h->mg.p2 = h->mg.p + nn;
+      h->mg.q = h->mg.p2 + nn;
       h->mg.x = h->mg.q + nn;
+      h->mg.r2 = h->mg.x + nn;
     }
     h->pcg_grid = pcg_grid_size(h->device);
     DA(h->d_partial, sizeof(double) * 16 * (h->pcg_grid + 32));

@@ -162,7 +162,7 @@ struct MgLevels {
   int cinv_off;                 // dense inverse of the coarsest operator in block 0's
                                 // shared memory at this offset (floats); -1: Jacobi
   float *ws;
-  float *p, *q, *x;
+  float *p, *p2, *q, *x, *r2;  // CG vectors (p and r alternate between two buffers)
 };
 // Levels and workspace size (floats) for an (nr+1) x (nz+1) node grid.
 long long mg_plan(int nr, int nz, MgLevels *M);

@@ -522,29 +522,47 @@ __device__ __forceinline__ float mg_apply(const MgLv &L, const float *v, int a, 
   return s;
 }
 
-// (A v)_a with v given by a functor of the node index.
+// (A v)_a with v_a = va and the neighbours' values given by a functor of
+// (node, i, j).
 template <class V>
-__device__ __forceinline__ float mg_apply_f(const MgLv &L, int a, int i, int j, V v) {
-  float s = L.diag[a] * v(a);
-  if (i > 0) s -= L.gr[a - 1] * v(a - 1);
-  if (i < L.ni - 1) s -= L.gr[a] * v(a + 1);
-  if (j > 0) s -= L.gz[a - L.ni] * v(a - L.ni);
-  if (j < L.nj - 1) s -= L.gz[a] * v(a + L.ni);
+__device__ __forceinline__ float mg_apply_f(const MgLv &L, int a, int i, int j, float va, V v) {
+  float s = L.diag[a] * va;
+  if (i > 0) s -= L.gr[a - 1] * v(a - 1, i - 1, j);
+  if (i < L.ni - 1) s -= L.gr[a] * v(a + 1, i + 1, j);
+  if (j > 0) s -= L.gz[a - L.ni] * v(a - L.ni, i, j - 1);
+  if (j < L.nj - 1) s -= L.gz[a] * v(a + L.ni, i, j + 1);
   return s;
 }
 
-// One pass over level l: grid-wide with a grid barrier after it, or (local)
-// block 0 alone with a block barrier.  Returns false on a barrier timeout.
+// f(a, i, j) for the nodes a = first, first + stride, ... of an ni-wide grid of
+// n nodes, with (i, j) stepped along instead of divided out at every node (the
+// block-local passes run on one SM, where the divisions would dominate).
+template <class F>
+__device__ __forceinline__ void mg_nodes(int first, int stride, int n, int ni, F f) {
+  if (first >= n) return;
+  int j = first / ni, i = first - j * ni;
+  const int sj = stride / ni, si = stride - sj * ni;
+  for (int a = first; a < n; a += stride) {
+    f(a, i, j);
+    i += si;
+    j += sj;
+    if (i >= ni) { i -= ni; ++j; }
+  }
+}
+
+// One pass over an ni-wide level of n nodes: grid-wide with a grid barrier
+// after it, or (local) block 0 alone with a block barrier.  Returns false on a
+// barrier timeout.
 template <class S, class F>
-__device__ __forceinline__ bool mg_pass(const S &sc, const PcgParams &P, bool local, int n, F f) {
+__device__ __forceinline__ bool mg_pass(const S &sc, const PcgParams &P, bool local, int n, int ni, F f) {
   if (local) {
     if (sc.bid() == 0) {
-      for (int a = threadIdx.x; a < n; a += blockDim.x) f(a);
+      mg_nodes(threadIdx.x, blockDim.x, n, ni, f);
       __syncthreads();
     }
     return true;
   }
-  for (int a = sc.bid() * blockDim.x + threadIdx.x; a < n; a += sc.nblk() * blockDim.x) f(a);
+  mg_nodes(sc.bid() * blockDim.x + threadIdx.x, sc.nblk() * blockDim.x, n, ni, f);
   return sc.sync(P);
 }
 
@@ -556,8 +574,7 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
   {
     const MgLv L0 = mg_level(M, 0);
     const float gs = (float)P.gscale;
-    if (!mg_pass(sc, P, false, L0.n, [&](int a) {
-          const int j = a / W1, i = a - j * W1;
+    if (!mg_pass(sc, P, false, L0.n, W1, [&](int a, int i, int j) {
           const bool fa = kind[a] == 0;
           float gr = 0.0f, gz = 0.0f, gd = 0.0f, dg = 0.0f;
           if (i < nr) {
@@ -583,8 +600,7 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
   for (int l = 0; l + 1 < M.L; ++l) {
     const MgLv F = mg_level(M, l, sm), C = mg_level(M, l + 1, sm);
     const bool local = l + 1 >= M.local_from;
-    if (!mg_pass(sc, P, local, C.n, [&](int c) {
-          const int J = c / C.ni, I = c - J * C.ni;
+    if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
           const int i0 = 2 * I, j0 = 2 * J;
           float gr = 0.0f, gz = 0.0f, gd = 0.0f, ext = 0.0f;
           for (int dj = 0; dj < 2; ++dj)
@@ -656,10 +672,35 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
   return M.local_from >= M.L ? true : sc.sync(P);
 }
 
-// z = V(r): rhs in level 0's B, result in level 0's X (each level's result is
-// left in its X).
-template <class S>
-__device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, float *sm) {
+// Level 0's right-hand side as the V-cycle's first pass reads it: r itself
+// (RhsPlain), or the CG update r - alpha q (RhsUpdate), formed on the fly at
+// the neighbours while the owner of each node writes it to the next r buffer
+// and advances x there.
+struct RhsPlain {
+  const float *b;
+  __device__ __forceinline__ float own(int a) const { return b[a]; }
+  __device__ __forceinline__ float nb(int a) const { return b[a]; }
+};
+struct RhsUpdate {
+  const float *r, *q, *p;
+  float *rn, *x;
+  float alpha;
+  __device__ __forceinline__ float own(int a) const {
+    const float v = r[a] - alpha * q[a];
+    rn[a] = v;
+    x[a] += alpha * p[a];
+    return v;
+  }
+  __device__ __forceinline__ float nb(int a) const { return r[a] - alpha * q[a]; }
+};
+
+// z = V(b0): b0 is level 0's right-hand side (the first pass reads it through
+// rhs), the result is left in level 0's X (each level's result in its X).  The
+// last level-0 pass also forms (b0.z, b0.b0) and sums them over the scope into
+// dots: the sum's barrier ends that pass.
+template <class S, class R>
+__device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, float *sm, float *b0, const R &rhs,
+                          float dots[2], float *part32, int parity) {
   const float w = M.omega, al = M.alpha;
   const int lf = M.local_from;
   // block 0 takes the first local level's right-hand side (restricted
@@ -676,17 +717,26 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
     if (local && sc.bid() != 0) break;
     if (l == lf) take_in();
     // the grid-wide restriction into the first local level writes its global copy
-    const MgLv F = mg_level(M, l, sm), C = mg_level(M, l + 1, l + 1 == lf ? nullptr : sm);
+    MgLv F = mg_level(M, l, sm);
+    const MgLv C = mg_level(M, l + 1, l + 1 == lf ? nullptr : sm);
+    if (l == 0) F.B = b0;
     // two Jacobi sweeps from zero; the first sweep's values (w D^-1 B) are
     // formed on the fly, so one pass and one barrier suffice
-    if (!mg_pass(sc, P, local, F.n, [&](int a) {
-          const int j = a / F.ni, i = a - j * F.ni;
-          auto y = [&](int b) { return w * F.dinv[b] * F.B[b]; };
-          F.X[a] = y(a) + w * F.dinv[a] * (F.B[a] - mg_apply_f(F, a, i, j, y));
-        }))
+    if (l == 0) {
+      if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
+            auto y = [&](int b, int, int) { return w * F.dinv[b] * rhs.nb(b); };
+            const float ba = rhs.own(a), da = w * F.dinv[a], ya = da * ba;
+            F.X[a] = ya + da * (ba - mg_apply_f(F, a, i, j, ya, y));
+          }))
+        return false;
+    } else if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
+                 auto y = [&](int b, int, int) { return w * F.dinv[b] * F.B[b]; };
+                 const float ba = F.B[a], da = w * F.dinv[a], ya = da * ba;
+                 F.X[a] = ya + da * (ba - mg_apply_f(F, a, i, j, ya, y));
+               })) {
       return false;
-    if (!mg_pass(sc, P, local, C.n, [&](int c) {
-          const int J = c / C.ni, I = c - J * C.ni;
+    }
+    if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
           float s = 0.0f;
           for (int dj = 0; dj < 2; ++dj)
             for (int di = 0; di < 2; ++di) {
@@ -722,17 +772,17 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
     const MgLv C = mg_level(M, lc, sm);
     const bool local = lc >= M.local_from;
     if (!local || sc.bid() == 0) {
-      mg_pass(sc, P, local, C.n, [&](int a) { C.X[a] = w * C.dinv[a] * C.B[a]; });
+      mg_pass(sc, P, local, C.n, C.ni, [&](int a, int, int) { C.X[a] = w * C.dinv[a] * C.B[a]; });
       for (int k = 0; k < M.coarse_sweeps; ++k) {  // an even count ends in X
         const float *src = (k & 1) ? C.Y : C.X;
         float *dst = (k & 1) ? C.X : C.Y;
-        mg_pass(sc, P, local, C.n, [&](int a) {
-          const int j = a / C.ni, i = a - j * C.ni;
+        mg_pass(sc, P, local, C.n, C.ni, [&](int a, int i, int j) {
           dst[a] = src[a] + w * C.dinv[a] * (C.B[a] - mg_apply(C, src, a, i, j));
         });
       }
     }
   }
+  float t[2] = {0.0f, 0.0f};
   for (int l = M.L - 2; l >= 0; --l) {
     const bool local = l >= lf;
     if (!local && l + 1 >= lf && lf < M.L) {
@@ -744,28 +794,42 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
       }
       if (!sc.sync(P)) return false;
     }
-    const MgLv F = mg_level(M, l, sm), C = mg_level(M, l + 1, l + 1 == lf ? nullptr : sm);
+    MgLv F = mg_level(M, l, sm);
+    const MgLv C = mg_level(M, l + 1, l + 1 == lf ? nullptr : sm);
+    if (l == 0) F.B = b0;
     if (local && sc.bid() != 0) continue;
     // coarse correction folded into the first post-smoothing sweep: the
     // corrected values are formed on the fly at the node and its neighbours
-    if (!mg_pass(sc, P, local, F.n, [&](int a) {
-          const int j = a / F.ni, i = a - j * F.ni;
-          auto y = [&](int b) {
-            const int jb = b / F.ni, ib = b - jb * F.ni;
+    if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
+          auto y = [&](int b, int ib, int jb) {
             return F.dinv[b] != 0.0f ? F.X[b] + al * C.X[(jb >> 1) * C.ni + (ib >> 1)] : 0.0f;
           };
-          F.Y[a] = y(a) + w * F.dinv[a] * (F.B[a] - mg_apply_f(F, a, i, j, y));
+          const float ya = y(a, i, j);
+          F.Y[a] = ya + w * F.dinv[a] * (F.B[a] - mg_apply_f(F, a, i, j, ya, y));
         }))
       return false;
-    // second post-smoothing sweep: the level's result, in X
-    if (!mg_pass(sc, P, local, F.n, [&](int a) {
-          const int j = a / F.ni, i = a - j * F.ni;
-          F.X[a] = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.Y, a, i, j));
-        }))
+    // second post-smoothing sweep: the level's result, in X (at level 0 with
+    // the dot products, whose sum below ends the pass)
+    auto sweep = [&](int a, int i, int j) {
+      const float x = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.Y, a, i, j));
+      F.X[a] = x;
+      return x;
+    };
+    if (l == 0) {
+      mg_nodes(local ? (int)threadIdx.x : sc.bid() * (int)blockDim.x + (int)threadIdx.x,
+               local ? (int)blockDim.x : sc.nblk() * (int)blockDim.x, F.n, F.ni, [&](int a, int i, int j) {
+                 const float x = sweep(a, i, j), b = F.B[a];
+                 t[0] += b * x;
+                 t[1] += b * b;
+               });
+    } else if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) { sweep(a, i, j); })) {
       return false;
+    }
   }
-  // a hierarchy entirely in block 0: the others wait for the result
-  if (M.local_from == 0) return sc.sync(P);
+  // every block joins the sum (a hierarchy entirely in block 0: the others add 0)
+  if (!grid_sum_s<float, 2>(sc, t, part32, parity, P)) return false;
+  dots[0] = t[0];
+  dots[1] = t[1];
   return true;
 }
 
@@ -777,6 +841,9 @@ __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) 
   float *part32 = reinterpret_cast<float *>(P.partial + 8 * sc.nblk());
   double *r64 = P.work;
   const MgLv L0 = mg_level(M, 0);
+  // r and p buffers k = 0, 1
+  auto rb = [&](int k) { return k ? M.r2 : L0.B; };
+  auto pb = [&](int k) { return k ? M.p2 : M.p; };
   int it = 0, parity = 0, status = -4, outer = 0;
   double b2 = 0.0, r2 = 0.0;
   const int gtid = sc.bid() * blockDim.x + threadIdx.x, gstride = sc.nblk() * blockDim.x;
@@ -794,19 +861,12 @@ __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) 
     if (it >= P.maxit) { status = -4; break; }
     const double inv = rsqrt(r2);
     for (int a = gtid; a < nn; a += gstride) {
-      L0.B[a] = P.node_kind[a] == 0 ? (float)(r64[a] * inv) : 0.0f;
+      rb(0)[a] = P.node_kind[a] == 0 ? (float)(r64[a] * inv) : 0.0f;
       M.x[a] = 0.0f;
     }
     if (!sc.sync(P)) { status = -5; break; }
-    if (!mg_vcycle(sc, P, M, sm)) { status = -5; break; }
-    float t2[2] = {0.0f, 0.0f};
-    for (int a = gtid; a < nn; a += gstride) {
-      const float z = L0.X[a];
-      M.p[a] = z;
-      t2[0] += L0.B[a] * z;
-      t2[1] += L0.B[a] * L0.B[a];
-    }
-    if (!grid_sum_s<float, 2>(sc, t2, part32, parity, P)) { status = -5; break; }
+    float t2[2];
+    if (!mg_vcycle(sc, P, M, sm, rb(0), RhsPlain{rb(0)}, t2, part32, parity)) { status = -5; break; }
     parity ^= 1;
     float rz = t2[0];
     // the V-cycle makes a deeper FP32 inner solve cheap: one outer step fewer
@@ -815,39 +875,40 @@ __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) 
     if (need > stop) stop = need;
     const float stop2 = stop * stop;
     bool bad = false, fail = false;
+    // r and p alternate between two buffers: a pass forms the new values of
+    // the neighbours on the fly from the old ones, so no barrier is needed
+    // between an update and its first use
+    int rc = 0, pc = 0;
+    float beta = 0.0f;
     while (it < P.maxit) {
-      // q = A p, p.q
+      // p <- z + beta p (into the other buffer), q = A p, p.q
+      const float *pold = pb(pc);
+      float *pnew = pb(pc ^ 1);
       float pq[1] = {0.0f};
-      for (int a = gtid; a < nn; a += gstride) {
-        const int j = a / L0.ni, i = a - j * L0.ni;
-        const float qa = L0.dinv[a] != 0.0f ? mg_apply(L0, M.p, a, i, j) : 0.0f;
+      mg_nodes(gtid, gstride, nn, L0.ni, [&](int a, int i, int j) {
+        auto pv = [&](int b, int, int) { return beta != 0.0f ? L0.X[b] + beta * pold[b] : L0.X[b]; };
+        const float pa = pv(a, i, j);
+        pnew[a] = pa;
+        const float qa = L0.dinv[a] != 0.0f ? mg_apply_f(L0, a, i, j, pa, pv) : 0.0f;
         M.q[a] = qa;
-        pq[0] += M.p[a] * qa;
-      }
+        pq[0] += pa * qa;
+      });
       if (!grid_sum_s<float, 1>(sc, pq, part32, parity, P)) { fail = true; break; }
       parity ^= 1;
       const float alpha = rz / pq[0];
-      for (int a = gtid; a < nn; a += gstride) {
-        M.x[a] += alpha * M.p[a];
-        L0.B[a] -= alpha * M.q[a];
-      }
       ++it;
-      // z = V(r) (its first barrier also publishes the new r)
-      if (!sc.sync(P)) { fail = true; break; }
-      if (!mg_vcycle(sc, P, M, sm)) { fail = true; break; }
-      float t[2] = {0.0f, 0.0f};
-      for (int a = gtid; a < nn; a += gstride) {
-        t[0] += L0.B[a] * L0.X[a];
-        t[1] += L0.B[a] * L0.B[a];
-      }
-      if (!grid_sum_s<float, 2>(sc, t, part32, parity, P)) { fail = true; break; }
+      // z = V(r - alpha q): the V-cycle's first pass also writes the new r and
+      // advances x, its last one forms r.z and r.r
+      float t[2];
+      const RhsUpdate upd{rb(rc), M.q, pnew, rb(rc ^ 1), M.x, alpha};
+      if (!mg_vcycle(sc, P, M, sm, rb(rc ^ 1), upd, t, part32, parity)) { fail = true; break; }
       parity ^= 1;
+      rc ^= 1;
+      pc ^= 1;
       if (!isfinite(t[0]) || !isfinite(t[1])) { bad = true; break; }
       if (t[1] <= stop2) break;
-      const float beta = t[0] / rz;
+      beta = t[0] / rz;
       rz = t[0];
-      for (int a = gtid; a < nn; a += gstride) M.p[a] = L0.X[a] + beta * M.p[a];
-      if (!sc.sync(P)) { fail = true; break; }
     }
     if (fail) { status = -5; break; }
     if (bad) { status = -7; break; }
@@ -922,7 +983,7 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
   M->omega = 0.8f;
   M->alpha = 1.8f;
   M->coarse_sweeps = 10;
-  return off + 3LL * (nr + 1) * (nz + 1);
+  return off + 5LL * (nr + 1) * (nz + 1);
 }
 
 template <int CL>
