@@ -145,8 +145,8 @@ constexpr int kPcgThreads = 256;
 // gr, gz, gd (conductance to Dirichlet nodes), diag, dinv, X, Y, B (each
 // ni*nj floats), then the level-0 CG vectors p, q, x.
 constexpr int kMgMaxLevels = 12;
-constexpr int kMgArrays = 8;
-constexpr int kMgSmemFloats = 40 * 1024;  // at most 160 KB of shared memory for the local levels
+constexpr int kMgArrays = 10;  // per level: 5 stencil / prolongation arrays, diag, dinv, X, Y, B
+constexpr int kMgSmemFloats = 52 * 1024;  // at most 208 KB of shared memory for the local levels
 constexpr int kMgDenseMax = 64;           // coarsest levels up to this many nodes are inverted
 struct MgLevels {
   int L;
@@ -157,7 +157,9 @@ struct MgLevels {
   long long soff[kMgMaxLevels]; // their offsets (floats) in it
   int smem_floats;              // its size
   float omega;                  // Jacobi damping
-  float alpha;                  // coarse-correction scale
+  float alpha;                  // coarse-correction scale below level 1
+  float alpha0;                 // coarse-correction scale of level 1 into level 0
+  float omega_s;                // prolongation smoothing of level 0
   int coarse_sweeps;            // Jacobi sweeps on the coarsest level (when not dense)
   int cinv_off;                 // dense inverse of the coarsest operator in block 0's
                                 // shared memory at this offset (floats); -1: Jacobi

@@ -483,55 +483,99 @@ __device__ __forceinline__ void residual64_s(const S &sc, const PcgParams &P, do
   }
 }
 
+// One multigrid level.  Level 0 is the fine operator in conductance form:
+// (A v)_a = diag_a v_a - sum_b G_ab v_b with c0 = G to i+1, c1 = G to j+1 (0
+// across non-free nodes), and c2..c4 = the smoothed-prolongation weights of
+// the node (phs: its own aggregate; phx, phy: the aggregate across the
+// aggregate boundary in i, in j).  Coarser levels hold 9-point matrix entries:
+// c0 to (i+1, j), c1 to (i, j+1), c2 to (i+1, j+1), c3 to (i-1, j+1); the
+// entries towards lower indices are the neighbour's.
 struct MgLv {
   int ni, nj, n;
-  float *gr, *gz, *gd, *diag, *dinv, *X, *Y, *B;
+  float *c0, *c1, *c2, *c3, *c4, *diag, *dinv, *X, *Y, *B;
 };
+
+__device__ __forceinline__ MgLv mg_view(float *b, int ni, int nj) {
+  MgLv v;
+  v.ni = ni;
+  v.nj = nj;
+  v.n = ni * nj;
+  const size_t n = (size_t)v.n;
+  v.c0 = b; v.c1 = b + n; v.c2 = b + 2 * n; v.c3 = b + 3 * n; v.c4 = b + 4 * n;
+  v.diag = b + 5 * n; v.dinv = b + 6 * n; v.X = b + 7 * n; v.Y = b + 8 * n; v.B = b + 9 * n;
+  return v;
+}
 
 // Level l's arrays: the levels from M.smem_from on live in block 0's shared
 // memory (sm != nullptr only there); everything else in the global workspace.
 __device__ __forceinline__ MgLv mg_level(const MgLevels &M, int l, float *sm) {
-  MgLv v;
-  v.ni = M.ni[l];
-  v.nj = M.nj[l];
-  v.n = v.ni * v.nj;
   float *b = (sm != nullptr && l >= M.smem_from) ? sm + M.soff[l] : M.ws + M.off[l];
-  v.gr = b; v.gz = b + v.n; v.gd = b + 2 * (size_t)v.n; v.diag = b + 3 * (size_t)v.n; v.dinv = b + 4 * (size_t)v.n;
-  v.X = b + 5 * (size_t)v.n; v.Y = b + 6 * (size_t)v.n; v.B = b + 7 * (size_t)v.n;
-  return v;
+  return mg_view(b, M.ni[l], M.nj[l]);
 }
 
-__device__ __forceinline__ MgLv mg_level(const MgLevels &M, int l) {
-  MgLv v;
-  v.ni = M.ni[l];
-  v.nj = M.nj[l];
-  v.n = v.ni * v.nj;
-  float *b = M.ws + M.off[l];
-  v.gr = b; v.gz = b + v.n; v.gd = b + 2 * (size_t)v.n; v.diag = b + 3 * (size_t)v.n; v.dinv = b + 4 * (size_t)v.n;
-  v.X = b + 5 * (size_t)v.n; v.Y = b + 6 * (size_t)v.n; v.B = b + 7 * (size_t)v.n;
-  return v;
-}
+__device__ __forceinline__ MgLv mg_level(const MgLevels &M, int l) { return mg_view(M.ws + M.off[l], M.ni[l], M.nj[l]); }
 
-// (A v)_a = diag_a v_a - sum_b G_ab v_b (edges to non-free nodes are 0)
+// Level 0: (A v)_a with conductances.
 __device__ __forceinline__ float mg_apply(const MgLv &L, const float *v, int a, int i, int j) {
   float s = L.diag[a] * v[a];
-  if (i > 0) s -= L.gr[a - 1] * v[a - 1];
-  if (i < L.ni - 1) s -= L.gr[a] * v[a + 1];
-  if (j > 0) s -= L.gz[a - L.ni] * v[a - L.ni];
-  if (j < L.nj - 1) s -= L.gz[a] * v[a + L.ni];
+  if (i > 0) s -= L.c0[a - 1] * v[a - 1];
+  if (i < L.ni - 1) s -= L.c0[a] * v[a + 1];
+  if (j > 0) s -= L.c1[a - L.ni] * v[a - L.ni];
+  if (j < L.nj - 1) s -= L.c1[a] * v[a + L.ni];
   return s;
 }
 
-// (A v)_a with v_a = va and the neighbours' values given by a functor of
+// Level 0: (A v)_a with v_a = va and the neighbours' values from a functor of
 // (node, i, j).
 template <class V>
 __device__ __forceinline__ float mg_apply_f(const MgLv &L, int a, int i, int j, float va, V v) {
   float s = L.diag[a] * va;
-  if (i > 0) s -= L.gr[a - 1] * v(a - 1, i - 1, j);
-  if (i < L.ni - 1) s -= L.gr[a] * v(a + 1, i + 1, j);
-  if (j > 0) s -= L.gz[a - L.ni] * v(a - L.ni, i, j - 1);
-  if (j < L.nj - 1) s -= L.gz[a] * v(a + L.ni, i, j + 1);
+  if (i > 0) s -= L.c0[a - 1] * v(a - 1, i - 1, j);
+  if (i < L.ni - 1) s -= L.c0[a] * v(a + 1, i + 1, j);
+  if (j > 0) s -= L.c1[a - L.ni] * v(a - L.ni, i, j - 1);
+  if (j < L.nj - 1) s -= L.c1[a] * v(a + L.ni, i, j + 1);
   return s;
+}
+
+// Coarser levels: (A v)_a over the 9-point stencil, neighbours from a functor.
+template <class V>
+__device__ __forceinline__ float mg_apply9_f(const MgLv &L, int a, int i, int j, float va, V v) {
+  const int ni = L.ni;
+  const bool w = i > 0, e = i < ni - 1, s = j > 0, nn = j < L.nj - 1;
+  float r = L.diag[a] * va;
+  if (e) r += L.c0[a] * v(a + 1, i + 1, j);
+  if (w) r += L.c0[a - 1] * v(a - 1, i - 1, j);
+  if (nn) r += L.c1[a] * v(a + ni, i, j + 1);
+  if (s) r += L.c1[a - ni] * v(a - ni, i, j - 1);
+  if (nn && e) r += L.c2[a] * v(a + ni + 1, i + 1, j + 1);
+  if (s && w) r += L.c2[a - ni - 1] * v(a - ni - 1, i - 1, j - 1);
+  if (nn && w) r += L.c3[a] * v(a + ni - 1, i - 1, j + 1);
+  if (s && e) r += L.c3[a - ni + 1] * v(a - ni + 1, i + 1, j - 1);
+  return r;
+}
+
+// (A v)_a on level l (l == 0: conductance form; else 9-point).
+__device__ __forceinline__ float mg_apply_l(const MgLv &L, bool l0, const float *v, int a, int i, int j) {
+  if (l0) return mg_apply(L, v, a, i, j);
+  return mg_apply9_f(L, a, i, j, v[a], [&](int b, int, int) { return v[b]; });
+}
+
+// Matrix entry A(r, c) of level L for two nodes at most one step apart in i and
+// j (0 otherwise).
+__device__ __forceinline__ float mg_entry(const MgLv &L, bool l0, int r, int c) {
+  const int jr = r / L.ni, ir = r - jr * L.ni, jc = c / L.ni, ic = c - jc * L.ni;
+  const int di = ic - ir, dj = jc - jr;
+  if (di < -1 || di > 1 || dj < -1 || dj > 1) return 0.0f;
+  if (di == 0 && dj == 0) return L.diag[r];
+  if (l0) {
+    if (dj == 0) return -L.c0[min(r, c)];
+    if (di == 0) return -L.c1[min(r, c)];
+    return 0.0f;
+  }
+  if (dj == 0) return L.c0[min(r, c)];
+  if (di == 0) return L.c1[min(r, c)];
+  if (di == dj) return L.c2[min(r, c)];  // (1,1) or (-1,-1)
+  return L.c3[di < 0 ? r : c];            // (-1,1) stored at r, (1,-1) stored at c
 }
 
 // f(a, i, j) for the nodes a = first, first + stride, ... of an ni-wide grid of
@@ -566,90 +610,133 @@ __device__ __forceinline__ bool mg_pass(const S &sc, const PcgParams &P, bool lo
   return sc.sync(P);
 }
 
-// Operator hierarchy from the FP64 conductances (scaled by gscale).
+// Operator hierarchy from the FP64 conductances (scaled by gscale): level 0
+// with its smoothed-prolongation weights, level 1 = P^T A P with the smoothed
+// prolongation (its entries two aggregates apart moved onto the diagonal, row
+// sums kept), coarser levels by plain 2x2 aggregation of the 9-point operator.
 template <class S>
 __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, float *sm) {
   const int nr = P.nr, nz = P.nz, W1 = nr + 1;
   const int8_t *kind = P.node_kind;
+  const float oms = M.omega_s;
   {
     const MgLv L0 = mg_level(M, 0);
-    const float gs = (float)P.gscale;
     if (!mg_pass(sc, P, false, L0.n, W1, [&](int a, int i, int j) {
           const bool fa = kind[a] == 0;
-          float gr = 0.0f, gz = 0.0f, gd = 0.0f, dg = 0.0f;
-          if (i < nr) {
-            const float g = (float)(P.Gr[j * nr + i] * P.gscale);
-            if (fa && kind[a + 1] == 0) gr = g;
-          }
-          if (j < nz) {
-            const float g = (float)(P.Gz[j * W1 + i] * P.gscale);
-            if (fa && kind[a + W1] == 0) gz = g;
-          }
+          // conductance to a neighbour, 0 unless both nodes are free
+          auto gf = [&](int i2, int j2) {
+            if (i2 < 0 || j2 < 0 || i2 > nr || j2 > nz) return 0.0f;
+            const int b = j2 * W1 + i2;
+            if (!fa || kind[b] != 0) return 0.0f;
+            return j2 == j ? (float)(P.Gr[j * nr + min(i, i2)] * P.gscale) : (float)(P.Gz[min(j, j2) * W1 + i] * P.gscale);
+          };
+          float dg = 0.0f;
           if (fa) {
-            // all four neighbours count in the diagonal; Dirichlet ones also in gd
-            if (i > 0) { const float g = (float)(P.Gr[j * nr + i - 1] * P.gscale); dg += g; if (kind[a - 1]) gd += g; }
-            if (i < nr) { const float g = (float)(P.Gr[j * nr + i] * P.gscale); dg += g; if (kind[a + 1]) gd += g; }
-            if (j > 0) { const float g = (float)(P.Gz[(j - 1) * W1 + i] * P.gscale); dg += g; if (kind[a - W1]) gd += g; }
-            if (j < nz) { const float g = (float)(P.Gz[j * W1 + i] * P.gscale); dg += g; if (kind[a + W1]) gd += g; }
+            // all four neighbours count in the diagonal, Dirichlet ones included
+            if (i > 0) dg += (float)(P.Gr[j * nr + i - 1] * P.gscale);
+            if (i < nr) dg += (float)(P.Gr[j * nr + i] * P.gscale);
+            if (j > 0) dg += (float)(P.Gz[(j - 1) * W1 + i] * P.gscale);
+            if (j < nz) dg += (float)(P.Gz[j * W1 + i] * P.gscale);
           }
-          (void)gs;
-          L0.gr[a] = gr; L0.gz[a] = gz; L0.gd[a] = gd; L0.diag[a] = dg; L0.dinv[a] = dg > 0.0f ? 1.0f / dg : 0.0f;
+          const float di = dg > 0.0f ? 1.0f / dg : 0.0f;
+          L0.c0[a] = gf(i + 1, j);
+          L0.c1[a] = gf(i, j + 1);
+          // smoothed-prolongation weights: partner inside the 2x2 aggregate
+          // and neighbour across its boundary, in i and in j
+          const int ip = (i & 1) ? i - 1 : i + 1, jp = (j & 1) ? j - 1 : j + 1;
+          const int ix = (i & 1) ? i + 1 : i - 1, jx = (j & 1) ? j + 1 : j - 1;
+          L0.c2[a] = fa ? 1.0f - oms * di * (dg - gf(ip, j) - gf(i, jp)) : 0.0f;
+          L0.c3[a] = oms * di * gf(ix, j);
+          L0.c4[a] = oms * di * gf(i, jx);
+          L0.diag[a] = dg;
+          L0.dinv[a] = di;
         }))
       return false;
   }
   for (int l = 0; l + 1 < M.L; ++l) {
     const MgLv F = mg_level(M, l, sm), C = mg_level(M, l + 1, sm);
     const bool local = l + 1 >= M.local_from;
-    if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
-          const int i0 = 2 * I, j0 = 2 * J;
-          float gr = 0.0f, gz = 0.0f, gd = 0.0f, ext = 0.0f;
-          for (int dj = 0; dj < 2; ++dj)
-            for (int di = 0; di < 2; ++di) {
-              const int i = i0 + di, j = j0 + dj;
-              if (i >= F.ni || j >= F.nj) continue;
-              gd += F.gd[j * F.ni + i];
-            }
-          for (int dj = 0; dj < 2; ++dj) {
-            const int j = j0 + dj;
-            if (j >= F.nj) continue;
-            if (i0 + 2 < F.ni) gr += F.gr[j * F.ni + i0 + 1];          // to aggregate I+1
-            if (i0 > 0) ext += F.gr[j * F.ni + i0 - 1];                // from aggregate I-1
-          }
-          for (int di = 0; di < 2; ++di) {
-            const int i = i0 + di;
-            if (i >= F.ni) continue;
-            if (j0 + 2 < F.nj) gz += F.gz[(j0 + 1) * F.ni + i];         // to aggregate J+1
-            if (j0 > 0) ext += F.gz[(j0 - 1) * F.ni + i];               // from aggregate J-1
-          }
-          const float dg = gr + gz + ext + gd;
-          C.gr[c] = gr; C.gz[c] = gz; C.gd[c] = gd; C.diag[c] = dg; C.dinv[c] = dg > 0.0f ? 1.0f / dg : 0.0f;
-        }))
-      return false;
+    if (l == 0) {
+      // Galerkin product with the smoothed prolongation: A1(I, K) = sum over
+      // level-0 pairs (a, b) of phi_I(a) A0(a, b) phi_K(b)
+      if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
+            // acc: to (I, J), (I+1, J), (I, J+1), (I+1, J+1), (I-1, J+1); far:
+            // to the aggregates two steps away along i or j
+            float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, far = 0.0f;
+            auto add = [&](int K, int L, float v) {
+              const int dk = K - I, dl = L - J;
+              acc[0] += (dk == 0 && dl == 0) ? v : 0.0f;
+              acc[1] += (dk == 1 && dl == 0) ? v : 0.0f;
+              acc[2] += (dk == 0 && dl == 1) ? v : 0.0f;
+              acc[3] += (dk == 1 && dl == 1) ? v : 0.0f;
+              acc[4] += (dk == -1 && dl == 1) ? v : 0.0f;
+              far += ((dl == 0 && (dk == 2 || dk == -2)) || (dk == 0 && (dl == 2 || dl == -2))) ? v : 0.0f;
+            };
+#pragma unroll
+            for (int dj = -1; dj <= 2; ++dj)
+#pragma unroll
+              for (int di = -1; di <= 2; ++di) {
+                const bool ri = di == -1 || di == 2, rj = dj == -1 || dj == 2;
+                if (ri && rj) continue;
+                const int i = 2 * I + di, j = 2 * J + dj;
+                if (i < 0 || j < 0 || i >= F.ni || j >= F.nj) continue;
+                const int a = j * F.ni + i;
+                const float pa = ri ? F.c3[a] : (rj ? F.c4[a] : F.c2[a]);  // phi_IJ(a)
+#pragma unroll
+                for (int t = 0; t < 5; ++t) {
+                  const int bi = t == 1 ? i - 1 : (t == 2 ? i + 1 : i), bj = t == 3 ? j - 1 : (t == 4 ? j + 1 : j);
+                  if (bi < 0 || bj < 0 || bi >= F.ni || bj >= F.nj) continue;
+                  const int b = bj * F.ni + bi;
+                  const float av = pa * (t == 0 ? F.diag[a]
+                                                : (t <= 2 ? -F.c0[j * F.ni + min(i, bi)] : -F.c1[min(j, bj) * F.ni + i]));
+                  // node b belongs to its own aggregate (weight phs) and to the
+                  // aggregates across its boundaries in i (phx) and in j (phy)
+                  const int bx = (bi & 1) ? bi + 1 : bi - 1, by = (bj & 1) ? bj + 1 : bj - 1;
+                  add(bi >> 1, bj >> 1, av * F.c2[b]);
+                  if (bx >= 0) add(bx >> 1, bj >> 1, av * F.c3[b]);
+                  if (by >= 0) add(bi >> 1, by >> 1, av * F.c4[b]);
+                }
+              }
+            const float dg = acc[0] + far;
+            C.c0[c] = acc[1]; C.c1[c] = acc[2]; C.c2[c] = acc[3]; C.c3[c] = acc[4]; C.c4[c] = 0.0f;
+            C.diag[c] = dg;
+            C.dinv[c] = dg > 0.0f ? 1.0f / dg : 0.0f;
+          }))
+        return false;
+    } else {
+      // plain aggregation of the 9-point operator
+      if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
+            const int i0 = 2 * I, j0 = 2 * J;
+            auto g = [&](const float *x, int i, int j) {
+              return (i >= 0 && j >= 0 && i < F.ni && j < F.nj) ? x[j * F.ni + i] : 0.0f;
+            };
+            float dg = g(F.diag, i0, j0) + g(F.diag, i0 + 1, j0) + g(F.diag, i0, j0 + 1) + g(F.diag, i0 + 1, j0 + 1);
+            dg += 2.0f * (g(F.c0, i0, j0) + g(F.c0, i0, j0 + 1) + g(F.c1, i0, j0) + g(F.c1, i0 + 1, j0) +
+                          g(F.c2, i0, j0) + g(F.c3, i0 + 1, j0));
+            C.c0[c] = g(F.c0, i0 + 1, j0) + g(F.c0, i0 + 1, j0 + 1) + g(F.c2, i0 + 1, j0) + g(F.c3, i0 + 2, j0);
+            C.c1[c] = g(F.c1, i0, j0 + 1) + g(F.c1, i0 + 1, j0 + 1) + g(F.c2, i0, j0 + 1) + g(F.c3, i0 + 1, j0 + 1);
+            C.c2[c] = g(F.c2, i0 + 1, j0 + 1);
+            C.c3[c] = g(F.c3, i0, j0 + 1);
+            C.c4[c] = 0.0f;
+            C.diag[c] = dg;
+            C.dinv[c] = dg > 0.0f ? 1.0f / dg : 0.0f;
+          }))
+        return false;
+    }
   }
   // dense inverse of the coarsest operator (SPD: no pivoting), in place, with
   // column k and row k staged so that each elimination step is one pass
   if (M.cinv_off >= 0 && sc.bid() == 0) {
     __shared__ float colk[kMgDenseMax], rowk[kMgDenseMax];
     const MgLv C = mg_level(M, M.L - 1, sm);
+    const bool l0 = M.L == 1;
     const int n = C.n;
     float *Ai = sm + M.cinv_off;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
       const int r = e / n, c = e - r * n;
-      const int jr = r / C.ni, ir = r - jr * C.ni;
-      float v = 0.0f;
-      if (C.diag[r] == 0.0f || C.diag[c] == 0.0f) {
-        v = r == c ? 1.0f : 0.0f;  // an aggregate without unknowns: identity row
-      } else if (r == c) {
-        v = C.diag[r];
-      } else if (c == r + 1 && ir + 1 < C.ni) {
-        v = -C.gr[r];
-      } else if (c == r - 1 && ir > 0) {
-        v = -C.gr[c];
-      } else if (c == r + C.ni) {
-        v = -C.gz[r];
-      } else if (c == r - C.ni) {
-        v = -C.gz[c];
-      }
+      float v;
+      if (C.diag[r] == 0.0f || C.diag[c] == 0.0f) v = r == c ? 1.0f : 0.0f;  // no unknowns: identity row
+      else v = mg_entry(C, l0, r, c);
       Ai[e] = v;
     }
     __syncthreads();
@@ -701,7 +788,7 @@ struct RhsUpdate {
 template <class S, class R>
 __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, float *sm, float *b0, const R &rhs,
                           float dots[2], float *part32, int parity) {
-  const float w = M.omega, al = M.alpha;
+  const float w = M.omega, al = M.alpha, al0 = M.alpha0;
   const int lf = M.local_from;
   // block 0 takes the first local level's right-hand side (restricted
   // grid-wide into the global copy) into shared memory
@@ -719,36 +806,57 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
     // the grid-wide restriction into the first local level writes its global copy
     MgLv F = mg_level(M, l, sm);
     const MgLv C = mg_level(M, l + 1, l + 1 == lf ? nullptr : sm);
-    if (l == 0) F.B = b0;
     // two Jacobi sweeps from zero; the first sweep's values (w D^-1 B) are
     // formed on the fly, so one pass and one barrier suffice
     if (l == 0) {
+      F.B = b0;
       if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
             auto y = [&](int b, int, int) { return w * F.dinv[b] * rhs.nb(b); };
             const float ba = rhs.own(a), da = w * F.dinv[a], ya = da * ba;
             F.X[a] = ya + da * (ba - mg_apply_f(F, a, i, j, ya, y));
           }))
         return false;
-    } else if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
-                 auto y = [&](int b, int, int) { return w * F.dinv[b] * F.B[b]; };
-                 const float ba = F.B[a], da = w * F.dinv[a], ya = da * ba;
-                 F.X[a] = ya + da * (ba - mg_apply_f(F, a, i, j, ya, y));
-               })) {
-      return false;
+      // restriction with the smoothed prolongation: sum over the aggregate
+      // and its ring of phi_IJ times the residual
+      if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
+            float s = 0.0f;
+#pragma unroll
+            for (int dj = -1; dj <= 2; ++dj)
+#pragma unroll
+              for (int di = -1; di <= 2; ++di) {
+                const bool ri = di == -1 || di == 2, rj = dj == -1 || dj == 2;
+                if (ri && rj) continue;  // corners: outside the column's support
+                const int i = 2 * I + di, j = 2 * J + dj;
+                if (i < 0 || j < 0 || i >= F.ni || j >= F.nj) continue;
+                const int a = j * F.ni + i;
+                // the aggregate's own nodes weigh phs, the ring across i phx, across j phy
+                const float ph = ri ? F.c3[a] : (rj ? F.c4[a] : F.c2[a]);
+                s += ph * (F.B[a] - mg_apply(F, F.X, a, i, j));
+              }
+            C.B[c] = s;
+          }))
+        return false;
+    } else {
+      if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
+            auto y = [&](int b, int, int) { return w * F.dinv[b] * F.B[b]; };
+            const float ba = F.B[a], da = w * F.dinv[a], ya = da * ba;
+            F.X[a] = ya + da * (ba - mg_apply9_f(F, a, i, j, ya, y));
+          }))
+        return false;
+      if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
+            float s = 0.0f;
+            for (int dj = 0; dj < 2; ++dj)
+              for (int di = 0; di < 2; ++di) {
+                const int i = 2 * I + di, j = 2 * J + dj;
+                if (i >= F.ni || j >= F.nj) continue;
+                const int a = j * F.ni + i;
+                if (F.dinv[a] == 0.0f) continue;
+                s += F.B[a] - mg_apply_l(F, false, F.X, a, i, j);
+              }
+            C.B[c] = s;
+          }))
+        return false;
     }
-    if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
-          float s = 0.0f;
-          for (int dj = 0; dj < 2; ++dj)
-            for (int di = 0; di < 2; ++di) {
-              const int i = 2 * I + di, j = 2 * J + dj;
-              if (i >= F.ni || j >= F.nj) continue;
-              const int a = j * F.ni + i;
-              if (F.dinv[a] == 0.0f) continue;
-              s += F.B[a] - mg_apply(F, F.X, a, i, j);
-            }
-          C.B[c] = s;
-        }))
-      return false;
   }
   if (lf == M.L - 1) take_in();  // the coarsest level is the only local one
   // coarsest (dense inverse, or Jacobi from zero with an even number of sweeps
@@ -770,14 +878,14 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
   } else if (sc.bid() == 0 || M.local_from >= M.L) {
     const int lc = M.L - 1;
     const MgLv C = mg_level(M, lc, sm);
-    const bool local = lc >= M.local_from;
+    const bool local = lc >= M.local_from, l0 = lc == 0;
     if (!local || sc.bid() == 0) {
       mg_pass(sc, P, local, C.n, C.ni, [&](int a, int, int) { C.X[a] = w * C.dinv[a] * C.B[a]; });
       for (int k = 0; k < M.coarse_sweeps; ++k) {  // an even count ends in X
         const float *src = (k & 1) ? C.Y : C.X;
         float *dst = (k & 1) ? C.X : C.Y;
         mg_pass(sc, P, local, C.n, C.ni, [&](int a, int i, int j) {
-          dst[a] = src[a] + w * C.dinv[a] * (C.B[a] - mg_apply(C, src, a, i, j));
+          dst[a] = src[a] + w * C.dinv[a] * (C.B[a] - mg_apply_l(C, l0, src, a, i, j));
         });
       }
     }
@@ -800,18 +908,37 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
     if (local && sc.bid() != 0) continue;
     // coarse correction folded into the first post-smoothing sweep: the
     // corrected values are formed on the fly at the node and its neighbours
-    if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
-          auto y = [&](int b, int ib, int jb) {
-            return F.dinv[b] != 0.0f ? F.X[b] + al * C.X[(jb >> 1) * C.ni + (ib >> 1)] : 0.0f;
-          };
-          const float ya = y(a, i, j);
-          F.Y[a] = ya + w * F.dinv[a] * (F.B[a] - mg_apply_f(F, a, i, j, ya, y));
-        }))
-      return false;
+    if (l == 0) {
+      // smoothed prolongation: the node's own aggregate and the two across
+      // its boundary, with the node's weights
+      if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
+            auto y = [&](int b, int ib, int jb) {
+              const int I = ib >> 1, J = jb >> 1;
+              const int ix = (ib & 1) ? ib + 1 : ib - 1, jx = (jb & 1) ? jb + 1 : jb - 1;
+              const int cx = (ix >= 0 && ix < F.ni) ? (ix >> 1) : I, cy = (jx >= 0 && jx < F.nj) ? (jx >> 1) : J;
+              // (the weights are 0 where the neighbour across is missing or not free)
+              const float c = F.c2[b] * C.X[J * C.ni + I] + F.c3[b] * C.X[J * C.ni + cx] + F.c4[b] * C.X[cy * C.ni + I];
+              return F.dinv[b] != 0.0f ? F.X[b] + al0 * c : 0.0f;
+            };
+            const float ya = y(a, i, j);
+            F.Y[a] = ya + w * F.dinv[a] * (F.B[a] - mg_apply_f(F, a, i, j, ya, y));
+          }))
+        return false;
+    } else {
+      if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
+            auto y = [&](int b, int ib, int jb) {
+              return F.dinv[b] != 0.0f ? F.X[b] + al * C.X[(jb >> 1) * C.ni + (ib >> 1)] : 0.0f;
+            };
+            const float ya = y(a, i, j);
+            F.Y[a] = ya + w * F.dinv[a] * (F.B[a] - mg_apply9_f(F, a, i, j, ya, y));
+          }))
+        return false;
+    }
     // second post-smoothing sweep: the level's result, in X (at level 0 with
     // the dot products, whose sum below ends the pass)
+    const bool l0 = l == 0;
     auto sweep = [&](int a, int i, int j) {
-      const float x = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply(F, F.Y, a, i, j));
+      const float x = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply_l(F, l0, F.Y, a, i, j));
       F.X[a] = x;
       return x;
     };
@@ -982,6 +1109,8 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
   }
   M->omega = 0.8f;
   M->alpha = 1.8f;
+  M->alpha0 = 1.0f;
+  M->omega_s = 2.0f / 3.0f;  // 4 / (3 lambda_max) with lambda_max(D^-1 A) <= 2
   M->coarse_sweeps = 10;
   return off + 5LL * (nr + 1) * (nz + 1);
 }
