@@ -658,51 +658,73 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
     const bool local = l + 1 >= M.local_from;
     if (l == 0) {
       // Galerkin product with the smoothed prolongation: A1(I, K) = sum over
-      // level-0 pairs (a, b) of phi_I(a) A0(a, b) phi_K(b)
-      if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
-            // acc: to (I, J), (I+1, J), (I, J+1), (I+1, J+1), (I-1, J+1); far:
-            // to the aggregates two steps away along i or j
-            float acc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, far = 0.0f;
-            auto add = [&](int K, int L, float v) {
-              const int dk = K - I, dl = L - J;
-              acc[0] += (dk == 0 && dl == 0) ? v : 0.0f;
-              acc[1] += (dk == 1 && dl == 0) ? v : 0.0f;
-              acc[2] += (dk == 0 && dl == 1) ? v : 0.0f;
-              acc[3] += (dk == 1 && dl == 1) ? v : 0.0f;
-              acc[4] += (dk == -1 && dl == 1) ? v : 0.0f;
-              far += ((dl == 0 && (dk == 2 || dk == -2)) || (dk == 0 && (dl == 2 || dl == -2))) ? v : 0.0f;
-            };
+      // level-0 pairs (a, b) of phi_I(a) A0(a, b) phi_K(b).  Sixteen lanes per
+      // coarse node, one per position of the 4x4 box of level-0 nodes around
+      // its aggregate (the corners, outside phi_I's support, idle); the lanes'
+      // sums are reduced with shuffles within the half-warp.
+      auto body = [&](int first, int stride) {
+        const int total = C.n * 16;
+        // first is congruent to the lane mod 16 and stride a multiple of 16:
+        // the 16 lanes of a half-warp always work on the same coarse node
+        for (int task = first; task < total; task += stride) {
+          const int c = task >> 4, pos = task & 15;
+          const int J = c / C.ni, I = c - J * C.ni;
+          const int di = (pos & 3) - 1, dj = (pos >> 2) - 1;
+          // acc: to (I, J), (I+1, J), (I, J+1), (I+1, J+1), (I-1, J+1); acc[5]:
+          // to the aggregates two steps away along i or j
+          float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          auto add = [&](int K, int L, float v) {
+            const int dk = K - I, dl = L - J;
+            acc[0] += (dk == 0 && dl == 0) ? v : 0.0f;
+            acc[1] += (dk == 1 && dl == 0) ? v : 0.0f;
+            acc[2] += (dk == 0 && dl == 1) ? v : 0.0f;
+            acc[3] += (dk == 1 && dl == 1) ? v : 0.0f;
+            acc[4] += (dk == -1 && dl == 1) ? v : 0.0f;
+            acc[5] += ((dl == 0 && (dk == 2 || dk == -2)) || (dk == 0 && (dl == 2 || dl == -2))) ? v : 0.0f;
+          };
+          const bool ri = di == -1 || di == 2, rj = dj == -1 || dj == 2;
+          const int i = 2 * I + di, j = 2 * J + dj;
+          if (!(ri && rj) && i >= 0 && j >= 0 && i < F.ni && j < F.nj) {
+            const int a = j * F.ni + i;
+            // the aggregate's own nodes weigh phs, the ring across i phx, across j phy
+            const float pa = ri ? F.c3[a] : (rj ? F.c4[a] : F.c2[a]);
 #pragma unroll
-            for (int dj = -1; dj <= 2; ++dj)
+            for (int t = 0; t < 5; ++t) {
+              const int bi = t == 1 ? i - 1 : (t == 2 ? i + 1 : i), bj = t == 3 ? j - 1 : (t == 4 ? j + 1 : j);
+              if (bi < 0 || bj < 0 || bi >= F.ni || bj >= F.nj) continue;
+              const int b = bj * F.ni + bi;
+              const float av = pa * (t == 0 ? F.diag[a]
+                                            : (t <= 2 ? -F.c0[j * F.ni + min(i, bi)] : -F.c1[min(j, bj) * F.ni + i]));
+              // node b belongs to its own aggregate (weight phs) and to the
+              // aggregates across its boundaries in i (phx) and in j (phy)
+              const int bx = (bi & 1) ? bi + 1 : bi - 1, by = (bj & 1) ? bj + 1 : bj - 1;
+              add(bi >> 1, bj >> 1, av * F.c2[b]);
+              if (bx >= 0) add(bx >> 1, bj >> 1, av * F.c3[b]);
+              if (by >= 0) add(bi >> 1, by >> 1, av * F.c4[b]);
+            }
+          }
+          const unsigned half = 0xffffu << (threadIdx.x & 16);
 #pragma unroll
-              for (int di = -1; di <= 2; ++di) {
-                const bool ri = di == -1 || di == 2, rj = dj == -1 || dj == 2;
-                if (ri && rj) continue;
-                const int i = 2 * I + di, j = 2 * J + dj;
-                if (i < 0 || j < 0 || i >= F.ni || j >= F.nj) continue;
-                const int a = j * F.ni + i;
-                const float pa = ri ? F.c3[a] : (rj ? F.c4[a] : F.c2[a]);  // phi_IJ(a)
+          for (int k = 0; k < 6; ++k)
 #pragma unroll
-                for (int t = 0; t < 5; ++t) {
-                  const int bi = t == 1 ? i - 1 : (t == 2 ? i + 1 : i), bj = t == 3 ? j - 1 : (t == 4 ? j + 1 : j);
-                  if (bi < 0 || bj < 0 || bi >= F.ni || bj >= F.nj) continue;
-                  const int b = bj * F.ni + bi;
-                  const float av = pa * (t == 0 ? F.diag[a]
-                                                : (t <= 2 ? -F.c0[j * F.ni + min(i, bi)] : -F.c1[min(j, bj) * F.ni + i]));
-                  // node b belongs to its own aggregate (weight phs) and to the
-                  // aggregates across its boundaries in i (phx) and in j (phy)
-                  const int bx = (bi & 1) ? bi + 1 : bi - 1, by = (bj & 1) ? bj + 1 : bj - 1;
-                  add(bi >> 1, bj >> 1, av * F.c2[b]);
-                  if (bx >= 0) add(bx >> 1, bj >> 1, av * F.c3[b]);
-                  if (by >= 0) add(bi >> 1, by >> 1, av * F.c4[b]);
-                }
-              }
-            const float dg = acc[0] + far;
+            for (int o = 8; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(half, acc[k], o);
+          if (pos == 0) {
+            const float dg = acc[0] + acc[5];
             C.c0[c] = acc[1]; C.c1[c] = acc[2]; C.c2[c] = acc[3]; C.c3[c] = acc[4]; C.c4[c] = 0.0f;
             C.diag[c] = dg;
             C.dinv[c] = dg > 0.0f ? 1.0f / dg : 0.0f;
-          }))
-        return false;
+          }
+        }
+      };
+      if (local) {
+        if (sc.bid() == 0) {
+          body(threadIdx.x, blockDim.x);
+          __syncthreads();
+        }
+      } else {
+        body(sc.bid() * blockDim.x + threadIdx.x, sc.nblk() * blockDim.x);
+        if (!sc.sync(P)) return false;
+      }
     } else {
       // plain aggregation of the 9-point operator
       if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
@@ -727,31 +749,35 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
   // dense inverse of the coarsest operator (SPD: no pivoting), in place, with
   // column k and row k staged so that each elimination step is one pass
   if (M.cinv_off >= 0 && sc.bid() == 0) {
-    __shared__ float colk[kMgDenseMax], rowk[kMgDenseMax];
+    // warps take rows, lanes columns; column k and row k of the next step are
+    // staged by the owners of those elements into the other buffer, so each
+    // elimination step is one pass and one block barrier
+    __shared__ float colk[2][kMgDenseMax], rowk[2][kMgDenseMax];
     const MgLv C = mg_level(M, M.L - 1, sm);
     const bool l0 = M.L == 1;
-    const int n = C.n;
+    const int n = C.n, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float *Ai = sm + M.cinv_off;
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int r = e / n, c = e - r * n;
-      float v;
-      if (C.diag[r] == 0.0f || C.diag[c] == 0.0f) v = r == c ? 1.0f : 0.0f;  // no unknowns: identity row
-      else v = mg_entry(C, l0, r, c);
-      Ai[e] = v;
-    }
+    for (int r = wid; r < n; r += nw)
+      for (int c = lane; c < n; c += 32) {
+        float v;
+        if (C.diag[r] == 0.0f || C.diag[c] == 0.0f) v = r == c ? 1.0f : 0.0f;  // no unknowns: identity row
+        else v = mg_entry(C, l0, r, c);
+        Ai[r * n + c] = v;
+        if (c == 0) colk[0][r] = v;
+        if (r == 0) rowk[0][c] = v;
+      }
     __syncthreads();
     for (int k = 0; k < n; ++k) {
-      for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        colk[t] = Ai[t * n + k];
-        rowk[t] = Ai[k * n + t];
-      }
-      __syncthreads();
-      const float ip = 1.0f / colk[k];
-      for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-        const int r = e / n, c = e - r * n;
-        const float rk = (c == k ? 1.0f : rowk[c]) * ip;  // row k after scaling
-        Ai[e] = r == k ? rk : (c == k ? 0.0f : Ai[e]) - colk[r] * rk;
-      }
+      const int cur = k & 1, nxt = cur ^ 1;
+      const float ip = 1.0f / colk[cur][k];
+      for (int r = wid; r < n; r += nw)
+        for (int c = lane; c < n; c += 32) {
+          const float rk = (c == k ? 1.0f : rowk[cur][c]) * ip;  // row k after scaling
+          const float v = r == k ? rk : (c == k ? 0.0f : Ai[r * n + c]) - colk[cur][r] * rk;
+          Ai[r * n + c] = v;
+          if (c == k + 1) colk[nxt][r] = v;
+          if (r == k + 1) rowk[nxt][c] = v;
+        }
       __syncthreads();
     }
   }
@@ -837,12 +863,20 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
           }))
         return false;
     } else {
-      if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
-            auto y = [&](int b, int, int) { return w * F.dinv[b] * F.B[b]; };
-            const float ba = F.B[a], da = w * F.dinv[a], ya = da * ba;
-            F.X[a] = ya + da * (ba - mg_apply9_f(F, a, i, j, ya, y));
-          }))
+      if (local) {
+        // block 0 alone is bound by instructions, not barriers: the first
+        // sweep is stored instead of being re-formed at every neighbour
+        mg_pass(sc, P, true, F.n, F.ni, [&](int a, int, int) { F.Y[a] = w * F.dinv[a] * F.B[a]; });
+        mg_pass(sc, P, true, F.n, F.ni, [&](int a, int i, int j) {
+          F.X[a] = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply_l(F, false, F.Y, a, i, j));
+        });
+      } else if (!mg_pass(sc, P, false, F.n, F.ni, [&](int a, int i, int j) {
+                   auto y = [&](int b, int, int) { return w * F.dinv[b] * F.B[b]; };
+                   const float ba = F.B[a], da = w * F.dinv[a], ya = da * ba;
+                   F.X[a] = ya + da * (ba - mg_apply9_f(F, a, i, j, ya, y));
+                 })) {
         return false;
+      }
       if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
             float s = 0.0f;
             for (int dj = 0; dj < 2; ++dj)
@@ -924,8 +958,17 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
             F.Y[a] = ya + w * F.dinv[a] * (F.B[a] - mg_apply_f(F, a, i, j, ya, y));
           }))
         return false;
+    } else if (local) {
+      // block 0: the corrected values are stored once (in place in X), then
+      // the first sweep reads them
+      mg_pass(sc, P, true, F.n, F.ni, [&](int a, int i, int j) {
+        F.X[a] = F.dinv[a] != 0.0f ? F.X[a] + al * C.X[(j >> 1) * C.ni + (i >> 1)] : 0.0f;
+      });
+      mg_pass(sc, P, true, F.n, F.ni, [&](int a, int i, int j) {
+        F.Y[a] = F.X[a] + w * F.dinv[a] * (F.B[a] - mg_apply_l(F, false, F.X, a, i, j));
+      });
     } else {
-      if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
+      if (!mg_pass(sc, P, false, F.n, F.ni, [&](int a, int i, int j) {
             auto y = [&](int b, int ib, int jb) {
               return F.dinv[b] != 0.0f ? F.X[b] + al * C.X[(jb >> 1) * C.ni + (ib >> 1)] : 0.0f;
             };
