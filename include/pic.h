@@ -68,7 +68,8 @@ extern "C" {
 #define PIC_SOLVER_MIXED 1 /* FP32 Jacobi-preconditioned inner CG, FP64
                               residual and iterative refinement                    */
 #define PIC_SOLVER_MG 3      /* FP32 CG preconditioned by a multigrid V-cycle
-                              (2x2 aggregation, damped Jacobi smoothing), FP64
+                              (2x2 aggregation, smoothed prolongation at the
+                              finest level, damped Jacobi smoothing), FP64
                               residual and iterative refinement                */
 #define PIC_SOLVER_LEARNED 2 /* flexible CG preconditioned by the attached U-Net
                               (pic_attach_unet), FP64 recurrences; the plain or

@@ -407,18 +407,20 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_mixed(const PcgParams P) {
 
 // ---- multigrid-preconditioned mixed solve ----------------------------------------------
 // Same FP64 residual and refinement as k_pcg_mixed; the FP32 inner solve is CG
-// preconditioned by one symmetric V(2,2)-cycle.  The hierarchy aggregates 2x2
-// nodes: with piecewise-constant prolongation P the Galerkin operator
-// P^T A P of a "conductance" operator sum_b G_ab (x_a - x_b) + g_a x_a (g = the
-// conductance to Dirichlet nodes) is again of that form, with coarse edge
-// conductances = sums of the fine edges crossing between two aggregates and
-// coarse g = sum of the aggregate's g.  Smoother: damped Jacobi (omega); the
-// coarse correction is scaled by alpha (piecewise-constant aggregation
-// over-estimates the coarse energy); coarsest level (at most kMgDenseMax
-// nodes): its inverse, formed at setup by Gauss-Jordan elimination in block 0's
-// shared memory, applied as one matrix-vector product (Jacobi sweeps from zero
-// on larger coarsest levels).  Every piece is a fixed linear symmetric map, so
-// the preconditioner is SPD.
+// preconditioned by one symmetric V(2,2)-cycle over a hierarchy of 2x2 node
+// aggregates.  Level 0 -> 1 uses the smoothed-aggregation prolongation
+// P = (I - omega_s D^-1 A) P0 (P0: aggregation of the free nodes, omega_s =
+// 4 / (3 lambda_max) with lambda_max(D^-1 A) <= 2): level 1 is the Galerkin
+// product P^T A P, whose entries two aggregates apart (a few % of the
+// diagonal) are moved onto the diagonal with row sums kept, leaving 9 points;
+// coarser levels aggregate the 9-point operator plainly (it stays 9-point).
+// Smoother: damped Jacobi (omega); coarse corrections scaled by alpha0 into
+// level 0 and alpha below (piecewise-constant aggregation over-estimates the
+// coarse energy); coarsest level (at most kMgDenseMax nodes): its inverse,
+// formed at setup by Gauss-Jordan elimination in block 0's shared memory,
+// applied as one matrix-vector product (Jacobi sweeps from zero on larger
+// coarsest levels).  Every piece is a fixed linear symmetric map, so the
+// preconditioner is SPD.
 // Threads per block of the multigrid solve (one block per SM; the coarse
 // levels run in block 0, so its width sets their speed).
 constexpr int kMgThreads = 512;
