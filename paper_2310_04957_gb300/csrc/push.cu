@@ -632,15 +632,31 @@ __device__ __forceinline__ void process(const PushParams<T> &P, int s, bool acti
   }
 }
 
+// One species' CTA (species known at compile time: its store views, charge
+// to mass ratio and deposit array are fixed kernel-parameter operands, and only
+// its own collision code is compiled in).
+// Shared memory of a particle CTA (declared once in the kernel, shared by both
+// species' code): the node tile of the deposit, the tile's bin prefix and
+// offsets, and (FP32) the double-buffered next-round particle state.
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_particles(const PushParams<T> P) {
+struct ParticleSmem {
+  static constexpr int kPf = sizeof(T) == 4 ? kThreads : 1;
+  unsigned long long tile[(TX + 1 + 2 * kHalo) * (TY + 1 + 2 * kHalo)];
+  int pre[TX * TY + 1];
+  int off[TX * TY];
+  float pf[2][8][kPf];
+  unsigned long long pid[2][kPf];
+  int plo[2][kPf];
+};
+
+template <typename T, int TX, int TY, int s>
+__device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSmem<T, TX, TY> &sh) {
   constexpr int per = TX * TY;
   constexpr int TW = TX + 1 + 2 * kHalo, TH = TY + 1 + 2 * kHalo;
-  const int s = blockIdx.y;
   const StoreView<T> &A = P.in[s];
-  __shared__ unsigned long long smem[TW * TH];
-  __shared__ int s_pre[per + 1];
-  __shared__ int s_off[per];
+  unsigned long long *smem = sh.tile;
+  int *s_pre = sh.pre;
+  int *s_off = sh.off;
   const int ntiles = P.map.ntiles();
   if ((int)blockIdx.x < ntiles) {
     const int tile = blockIdx.x;
@@ -683,9 +699,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_particles(
       // fetched itself, so no block barrier is needed.  (The E field at the
       // cell's nodes is read directly: it is small and L1-resident, and staging
       // it as well measured slower.)
-      __shared__ float pf[2][8][kThreads];
-      __shared__ unsigned long long pid[2][kThreads];
-      __shared__ int plo[2][kThreads];
+      auto &pf = sh.pf;
+      auto &pid = sh.pid;
+      auto &plo = sh.plo;
       const int tid = threadIdx.x;
       auto issue = [&](int base, int b) {
         const int k = base + tid;
@@ -787,6 +803,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_particles(
       process<T, TX, TY>(P, s, active, p, tc, en);
     }
   }
+}
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_particles(const PushParams<T> P) {
+  __shared__ ParticleSmem<T, TX, TY> sh;
+  if (blockIdx.y == 0) particles_cta<T, TX, TY, 0>(P, sh);
+  else particles_cta<T, TX, TY, 1>(P, sh);
 }
 
 // ---------------------------------------------------------------------------
