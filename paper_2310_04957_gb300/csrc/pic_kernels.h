@@ -160,6 +160,7 @@ struct MgLevels {
   float alpha;                  // coarse-correction scale below level 1
   float alpha0;                 // coarse-correction scale of level 1 into level 0
   float omega_s;                // prolongation smoothing of level 0
+  int single_sweep;             // grid-wide levels below 0 smooth once before and after
   int coarse_sweeps;            // Jacobi sweeps on the coarsest level (when not dense)
   int cinv_off;                 // dense inverse of the coarsest operator in block 0's
                                 // shared memory at this offset (floats); -1: Jacobi

@@ -818,6 +818,9 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
                           float dots[2], float *part32, int parity) {
   const float w = M.omega, al = M.alpha, al0 = M.alpha0;
   const int lf = M.local_from;
+  // grid-wide coarse levels smooth once before and once after their coarse
+  // correction (each sweep there is a grid barrier); their result is left in Y
+  auto single = [&](int l) { return M.single_sweep && l >= 1 && l < lf; };
   // block 0 takes the first local level's right-hand side (restricted
   // grid-wide into the global copy) into shared memory
   auto take_in = [&]() {
@@ -860,6 +863,24 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
                 // the aggregate's own nodes weigh phs, the ring across i phx, across j phy
                 const float ph = ri ? F.c3[a] : (rj ? F.c4[a] : F.c2[a]);
                 s += ph * (F.B[a] - mg_apply(F, F.X, a, i, j));
+              }
+            C.B[c] = s;
+          }))
+        return false;
+    } else if (single(l)) {
+      // one sweep from zero, x = w D^-1 B, formed on the fly by the restriction,
+      // which also stores it for the correction on the way up
+      if (!mg_pass(sc, P, false, C.n, C.ni, [&](int c, int I, int J) {
+            auto y = [&](int b, int, int) { return w * F.dinv[b] * F.B[b]; };
+            float s = 0.0f;
+            for (int dj = 0; dj < 2; ++dj)
+              for (int di = 0; di < 2; ++di) {
+                const int i = 2 * I + di, j = 2 * J + dj;
+                if (i >= F.ni || j >= F.nj) continue;
+                const int a = j * F.ni + i;
+                const float xa = w * F.dinv[a] * F.B[a];
+                F.X[a] = xa;
+                if (F.dinv[a] != 0.0f) s += F.B[a] - mg_apply9_f(F, a, i, j, xa, y);
               }
             C.B[c] = s;
           }))
@@ -939,8 +960,13 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
       if (!sc.sync(P)) return false;
     }
     MgLv F = mg_level(M, l, sm);
-    const MgLv C = mg_level(M, l + 1, l + 1 == lf ? nullptr : sm);
+    MgLv C = mg_level(M, l + 1, l + 1 == lf ? nullptr : sm);
     if (l == 0) F.B = b0;
+    if (single(l + 1)) {  // that level's result is in its Y
+      float *const t = C.X;
+      C.X = C.Y;
+      C.Y = t;
+    }
     if (local && sc.bid() != 0) continue;
     // coarse correction folded into the first post-smoothing sweep: the
     // corrected values are formed on the fly at the node and its neighbours
@@ -994,7 +1020,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
                  t[0] += b * x;
                  t[1] += b * b;
                });
-    } else if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) { sweep(a, i, j); })) {
+    } else if (!single(l) && !mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) { sweep(a, i, j); })) {
       return false;
     }
   }
@@ -1155,6 +1181,7 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
   M->omega = 0.8f;
   M->alpha = 1.8f;
   M->alpha0 = 1.0f;
+  M->single_sweep = 1;
   M->omega_s = 2.0f / 3.0f;  // 4 / (3 lambda_max) with lambda_max(D^-1 A) <= 2
   M->coarse_sweeps = 10;
   return off + 5LL * (nr + 1) * (nz + 1);
