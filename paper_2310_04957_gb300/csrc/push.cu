@@ -606,7 +606,9 @@ __device__ __forceinline__ void load_particle(const StoreView<T> &S, int slot, P
 template <typename T, int TX, int TY>
 __device__ __forceinline__ void process(const PushParams<T> &P, int s, bool active, Part<T> &p, const TileCtx &tc,
                                         const typename V2<T>::type en[4]) {
-  Part<T> be = p, bi = p;
+  // the newborn electron and ion are written in full by an ionizing collision
+  // (and read only after one), so nothing of them is live during the push
+  Part<T> be, bi;
   Outcome o{0, -1, 0, -1, 0};
   if (active) o = advance(P, s, p, be, bi, en);
   tally(P, s, o, active);
@@ -616,6 +618,10 @@ __device__ __forceinline__ void process(const PushParams<T> &P, int s, bool acti
     count_warp(P.counters + CNT_BORN + 0, birth);
     count_warp(P.counters + CNT_BORN + 1, birth);
     bool e_alive = false;
+    if (!birth) {  // lanes without a birth take part in the warp-wide emit as dead lanes
+      be.ci = 0;
+      be.cj = 0;
+    }
     if (birth) {
       predict(P, be);
       e_alive = in_plasma(P, be.ci, be.cj);
@@ -806,7 +812,7 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
 }
 
 template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_particles(const PushParams<T> P) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 5 : 2) k_particles(const PushParams<T> P) {
   __shared__ ParticleSmem<T, TX, TY> sh;
   if (blockIdx.y == 0) particles_cta<T, TX, TY, 0>(P, sh);
   else particles_cta<T, TX, TY, 1>(P, sh);
