@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile", default="auto",
+                    help="particle tile RxZ in cells, or auto: chosen by the tile autotuner before timing")
     return ap.parse_args()
 
 
@@ -376,9 +378,20 @@ def main():
     prec = pic.PIC_FP32 if args.precision == "fp32" else pic.PIC_FP64
     solver = {"plain": pic.PIC_SOLVER_PLAIN, "mixed": pic.PIC_SOLVER_MIXED, "mg": pic.PIC_SOLVER_MG}[args.solver]
     wl = make_workload(args.workload, rank)
+    # particle tile: the library's autotuner times the particle phase of this
+    # workload with each candidate tile (untimed, before the warm-up)
+    tune_ms = None
+    if args.tile == "auto":
+        from paper_2310_04957_gb300 import sweep
+
+        choice, timings = sweep.autotune_tiles([wl], candidates=((2, 2), (4, 2), (4, 4), (8, 4)), precision=prec)
+        tile = choice[sweep.tile_class(wl)]
+        tune_ms = {"%dx%d" % t: round(v, 4) for t, v in timings[sweep.tile_class(wl)].items()}
+    else:
+        tile = tuple(int(x) for x in args.tile.split("x"))
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        d = pic.Discharge(wl, precision=prec, solver=solver, stream=stream.cuda_stream)
+        d = pic.Discharge(wl, precision=prec, solver=solver, stream=stream.cuda_stream, tile=tile)
         d.start()
         d.step(args.warmup)
         torch.cuda.synchronize()
@@ -423,7 +436,7 @@ def main():
         with torch.cuda.stream(stream):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            d2 = pic.Discharge(wl, precision=prec, solver=solver, stream=stream.cuda_stream)
+            d2 = pic.Discharge(wl, precision=prec, solver=solver, stream=stream.cuda_stream, tile=tile)
             d2.start()
             for _ in range(args.steps):
                 d2.step(1)
@@ -449,6 +462,7 @@ def main():
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": wl.name, "grid": [wl.nr, wl.nz], "particles": int(n_avg),
                        "precision": args.precision, "solver": args.solver,
+                       "tile": list(tile), "tile_autotune_ms": tune_ms,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (particle store %.0f MB per buffer)" % (n_avg * bpp / 2 / 1e6)},
             "roofline": {"bound": "hbm", "kernel": "k_particles", "achieved": achieved, "peak": peak, "unit": "GB/s",
