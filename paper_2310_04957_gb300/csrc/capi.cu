@@ -560,61 +560,66 @@ bool check_config(const pic_config *c) {
   return true;
 }
 
+// Upload of one species: the raw FP64 columns go to the device as they are,
+// and the device bins them (cell, rank within the bin, scatter into the
+// store); the host only scans the bins' counts.
 template <typename T>
 int upload_species(pic_handle *h, int s, int64_t n, const pic_particles *p) {
   const pic_config &c = h->cfg;
-  std::vector<int> bin_of(n);
-  std::vector<int> counts(h->nbins, 0);
-  std::vector<T> fr(n), fz(n);
-  for (int64_t k = 0; k < n; ++k) {
-    double r = p->r[k], z = p->z[k];
-    if (!(r >= 0.0) || !(z >= 0.0)) return PIC_EINVAL;
-    double x = r / c.dr, y = z / c.dz;
-    int i = (int)std::floor(x), j = (int)std::floor(y);
-    if (i < 0 || j < 0 || i >= h->nr || j >= h->nz) return PIC_EINVAL;
-    if (h->cell_kind[(size_t)j * h->nr + i] != PIC_CELL_PLASMA) return PIC_EINVAL;
-    T a = (T)(x - i), b = (T)(y - j);
-    const T below1 = (T)1 - (T)(sizeof(T) == 4 ? 5.9604645e-8 : 1.1102230246251565e-16);
-    if (a >= (T)1) a = below1;
-    if (b >= (T)1) b = below1;
-    if (a < (T)0) a = (T)0;
-    if (b < (T)0) b = (T)0;
-    fr[k] = a; fz[k] = b;
-    int bin = h->map.bin(i, j);
-    bin_of[k] = bin;
-    counts[bin]++;
-  }
-  std::vector<int> start(h->nbins), fill(h->nbins);
-  int run = 0;
-  for (int b = 0; b < h->nbins; ++b) { start[b] = run; fill[b] = counts[b]; run += counts[b]; }
-  std::vector<int> pos(start);
-  std::vector<T> a_fr(n), a_fz(n), a_vr(n), a_vt(n), a_vz(n), a_ar(n), a_at(n), a_az(n);
-  std::vector<unsigned long long> a_id(n);
-  for (int64_t k = 0; k < n; ++k) {
-    int d = pos[bin_of[k]]++;
-    a_fr[d] = fr[k]; a_fz[d] = fz[k];
-    a_vr[d] = (T)p->vr[k]; a_vt[d] = (T)p->vt[k]; a_vz[d] = (T)p->vz[k];
-    a_ar[d] = (T)p->ar[k]; a_at[d] = (T)p->at[k]; a_az[d] = (T)p->az[k];
-    a_id[d] = p->id[k];
-  }
   Store &S = h->st[h->cur][s];
-  size_t bytes = sizeof(T) * (size_t)n;
-  if (n) {
-    CK(cudaMemcpy(S.fr, a_fr.data(), bytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(S.fz, a_fz.data(), bytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(S.vr, a_vr.data(), bytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(S.vt, a_vt.data(), bytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(S.vz, a_vz.data(), bytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(S.ar, a_ar.data(), bytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(S.at, a_at.data(), bytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(S.az, a_az.data(), bytes, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(S.id, a_id.data(), sizeof(unsigned long long) * n, cudaMemcpyHostToDevice));
+  const int nb = h->nbins;
+  std::vector<int> start(nb, 0), fill(nb, 0);
+  if (n > 0) {
+    struct DevTmp {  // freed on every return
+      void *p = nullptr;
+      ~DevTmp() { if (p) cudaFree(p); }
+    } raw, work, bins;
+    const size_t m = (size_t)n;
+    CK(cudaMalloc(&raw.p, 9 * sizeof(double) * m));
+    CK(cudaMalloc(&work.p, (sizeof(int2) + 2 * sizeof(T)) * m));
+    CK(cudaMalloc(&bins.p, sizeof(int) * (2 * (size_t)nb + 1)));
+    double *d_raw = static_cast<double *>(raw.p);
+    const double *cols[8] = {p->r, p->z, p->vr, p->vt, p->vz, p->ar, p->at, p->az};
+    for (int k = 0; k < 8; ++k)
+      CK(cudaMemcpyAsync(d_raw + k * m, cols[k], sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
+    auto *d_id = reinterpret_cast<unsigned long long *>(d_raw + 8 * m);
+    CK(cudaMemcpyAsync(d_id, p->id, sizeof(unsigned long long) * m, cudaMemcpyHostToDevice, h->stream));
+    int *d_count = static_cast<int *>(bins.p), *d_start = d_count + nb;
+    unsigned *d_err = reinterpret_cast<unsigned *>(d_start + nb);
+    CK(cudaMemsetAsync(d_count, 0, sizeof(int) * ((size_t)nb + 0), h->stream));
+    CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned), h->stream));
+    UploadParams<T> U;
+    U.n = n;
+    U.r = d_raw; U.z = d_raw + m; U.vr = d_raw + 2 * m; U.vt = d_raw + 3 * m; U.vz = d_raw + 4 * m;
+    U.ar = d_raw + 5 * m; U.at = d_raw + 6 * m; U.az = d_raw + 7 * m;
+    U.id = d_id;
+    U.dr = c.dr; U.dz = c.dz;
+    U.map = h->map;
+    U.cell_kind = h->d_cell_kind;
+    U.count = d_count;
+    U.start = d_start;
+    U.bin_rank = static_cast<int2 *>(work.p);
+    U.fr_tmp = reinterpret_cast<T *>(U.bin_rank + m);
+    U.fz_tmp = U.fr_tmp + m;
+    U.err = d_err;
+    U.out = view<T>(h, h->cur, s);
+    CK(launch_upload_bin<T>(U, h->stream));
+    unsigned err = 0;
+    CK(cudaMemcpyAsync(fill.data(), d_count, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+    if (sync(h)) return PIC_ECUDA;
+    if (err) return PIC_EINVAL;  // a particle outside the plasma: the store is untouched
+    int run = 0;
+    for (int b = 0; b < nb; ++b) { start[b] = run; run += fill[b]; }
+    CK(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, h->stream));
+    CK(launch_upload_scatter<T>(U, h->stream));
+    if (sync(h)) return PIC_ECUDA;
   }
-  CK(cudaMemcpy(S.start, start.data(), sizeof(int) * h->nbins, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(S.cap, fill.data(), sizeof(int) * h->nbins, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(S.fill, fill.data(), sizeof(int) * h->nbins, cudaMemcpyHostToDevice));
-  BinMeta m{(int)n, 0, (long long)n};
-  CK(cudaMemcpy(S.meta, &m, sizeof(BinMeta), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(S.start, start.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(S.cap, fill.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(S.fill, fill.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+  BinMeta meta{(int)n, 0, (long long)n};
+  CK(cudaMemcpy(S.meta, &meta, sizeof(BinMeta), cudaMemcpyHostToDevice));
   return PIC_OK;
 }
 

@@ -130,6 +130,25 @@ struct LayoutParams {
   int *use_slack;           // [2]
 };
 cudaError_t launch_layout(const LayoutParams &L, cudaStream_t st);
+
+// Upload of one species from raw FP64 device columns into the binned store.
+template <typename T>
+struct UploadParams {
+  int64_t n;
+  const double *r, *z, *vr, *vt, *vz, *ar, *at, *az;
+  const unsigned long long *id;
+  double dr, dz;
+  BinMap map;
+  const int8_t *cell_kind;
+  int *count;        // [nbins] particles per bin (pass 1 adds)
+  const int *start;  // [nbins] first slot of each bin (pass 2)
+  int2 *bin_rank;    // [n] bin and rank within it
+  T *fr_tmp, *fz_tmp;
+  unsigned *err;     // set to 1 if any particle is outside the plasma
+  StoreView<T> out;
+};
+template <typename T> cudaError_t launch_upload_bin(const UploadParams<T> &U, cudaStream_t st);
+template <typename T> cudaError_t launch_upload_scatter(const UploadParams<T> &U, cudaStream_t st);
 cudaError_t launch_philox(int64_t n, const uint32_t *ctr, const uint32_t *key, uint32_t *out, cudaStream_t st);
 
 cudaError_t launch_assemble(const FieldParams &F, cudaStream_t st);
