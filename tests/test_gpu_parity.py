@@ -287,3 +287,35 @@ def test_rf_period_statistics_match_oracle():
     i1d, i1o = math.hypot(sd["i1_re"], sd["i1_im"]), math.hypot(so["i1_re"], so["i1_im"])
     assert i1d == pytest.approx(i1o, rel=0.02)
     assert d.status() == 0
+
+
+def test_upload_round_trip_and_rejection():
+    """The device-side upload bins every particle: downloaded by id, each keeps
+    its velocity (FP32-rounded), its position within the FP32 cell offset's
+    rounding and its cell; every id comes back once, and the store's per-cell
+    counts match the cells of the input.  A particle in a metal cell (the
+    powered electrode of the GEC-like cell) makes the upload fail."""
+    wl = W.gec_case(96, 48, 30.0, 150.0, n_per_species=50_000)
+    P = pic()
+    d = P.Discharge(wl, precision=FP32)
+    for s in (0, 1):
+        src = wl.particles[s]
+        g = by_id(d.get_particles(s))
+        order = np.argsort(src.id, kind="stable")
+        assert np.array_equal(g["id"], src.id[order])
+        for k in ("vr", "vt", "vz", "ar", "at", "az"):
+            np.testing.assert_array_equal(g[k], getattr(src, k)[order].astype(np.float32).astype(np.float64))
+        # position: cell-relative FP32 offsets, so within ~1e-7 of a cell
+        np.testing.assert_allclose(g["r"], src.r[order], rtol=0, atol=2e-7 * wl.dr)
+        np.testing.assert_allclose(g["z"], src.z[order], rtol=0, atol=2e-7 * wl.dz)
+        ci = np.floor(src.r[order] / wl.dr).astype(int)
+        cj = np.floor(src.z[order] / wl.dz).astype(int)
+        assert np.array_equal(g["cell"], cj * wl.nr + ci)
+    assert d.status() == 0
+    d.close()
+    # a particle inside the powered electrode (r = 1 cm, z = 0.5 cm: metal)
+    cell = np.asarray(wl.cell_kind).reshape(wl.nz, wl.nr)
+    i, j = int(0.01 / wl.dr), int(0.005 / wl.dz)
+    assert cell[j, i] != 0
+    with pytest.raises(P.PicError):
+        P.Discharge(with_particles(wl, electrons=beam(3, 0.01, 0.005, (0.0, 0.0, 0.0))), precision=FP32)
