@@ -175,6 +175,7 @@ struct MgLevels {
   int smem_from;                // levels >= smem_from live in block 0's shared memory (L: none)
   long long soff[kMgMaxLevels]; // their offsets (floats) in it
   int smem_floats;              // its size
+  int redundant;                // 1: every block runs the local levels in its own shared memory
   float omega;                  // Jacobi damping
   float alpha;                  // coarse-correction scale below level 1
   float alpha0;                 // coarse-correction scale of level 1 into level 0

@@ -596,13 +596,22 @@ __device__ __forceinline__ void mg_nodes(int first, int stride, int n, int ni, F
   }
 }
 
+// Does this block run the block-local levels?  Block 0 alone, or, when those
+// levels live in shared memory, every block on its own copy (the same
+// arithmetic in each, so no block has to publish them to the others).
+template <class S>
+__device__ __forceinline__ bool mg_runs_local(const S &sc, const MgLevels &M) {
+  return M.redundant || sc.bid() == 0;
+}
+
 // One pass over an ni-wide level of n nodes: grid-wide with a grid barrier
-// after it, or (local) block 0 alone with a block barrier.  Returns false on a
-// barrier timeout.
+// after it, or (local) by the blocks that run the local levels, with a block
+// barrier.  Returns false on a barrier timeout.
 template <class S, class F>
-__device__ __forceinline__ bool mg_pass(const S &sc, const PcgParams &P, bool local, int n, int ni, F f) {
+__device__ __forceinline__ bool mg_pass(const S &sc, const PcgParams &P, const MgLevels &M, bool local, int n, int ni,
+                                        F f) {
   if (local) {
-    if (sc.bid() == 0) {
+    if (mg_runs_local(sc, M)) {
       mg_nodes(threadIdx.x, blockDim.x, n, ni, f);
       __syncthreads();
     }
@@ -623,7 +632,7 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
   const float oms = M.omega_s;
   {
     const MgLv L0 = mg_level(M, 0);
-    if (!mg_pass(sc, P, false, L0.n, W1, [&](int a, int i, int j) {
+    if (!mg_pass(sc, P, M, false, L0.n, W1, [&](int a, int i, int j) {
           const bool fa = kind[a] == 0;
           // conductance to a neighbour, 0 unless both nodes are free
           auto gf = [&](int i2, int j2) {
@@ -719,7 +728,7 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
         }
       };
       if (local) {
-        if (sc.bid() == 0) {
+        if (mg_runs_local(sc, M)) {
           body(threadIdx.x, blockDim.x);
           __syncthreads();
         }
@@ -729,7 +738,7 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
       }
     } else {
       // plain aggregation of the 9-point operator
-      if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
+      if (!mg_pass(sc, P, M, local, C.n, C.ni, [&](int c, int I, int J) {
             const int i0 = 2 * I, j0 = 2 * J;
             auto g = [&](const float *x, int i, int j) {
               return (i >= 0 && j >= 0 && i < F.ni && j < F.nj) ? x[j * F.ni + i] : 0.0f;
@@ -750,7 +759,7 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
   }
   // dense inverse of the coarsest operator (SPD: no pivoting), in place, with
   // column k and row k staged so that each elimination step is one pass
-  if (M.cinv_off >= 0 && sc.bid() == 0) {
+  if (M.cinv_off >= 0 && mg_runs_local(sc, M)) {
     // warps take rows, lanes columns; column k and row k of the next step are
     // staged by the owners of those elements into the other buffer, so each
     // elimination step is one pass and one block barrier
@@ -832,7 +841,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
   // down
   for (int l = 0; l + 1 < M.L; ++l) {
     const bool local = l >= lf;
-    if (local && sc.bid() != 0) break;
+    if (local && !mg_runs_local(sc, M)) break;
     if (l == lf) take_in();
     // the grid-wide restriction into the first local level writes its global copy
     MgLv F = mg_level(M, l, sm);
@@ -841,7 +850,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
     // formed on the fly, so one pass and one barrier suffice
     if (l == 0) {
       F.B = b0;
-      if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
+      if (!mg_pass(sc, P, M, local, F.n, F.ni, [&](int a, int i, int j) {
             auto y = [&](int b, int, int) { return w * F.dinv[b] * rhs.nb(b); };
             const float ba = rhs.own(a), da = w * F.dinv[a], ya = da * ba;
             F.X[a] = ya + da * (ba - mg_apply_f(F, a, i, j, ya, y));
@@ -849,7 +858,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
         return false;
       // restriction with the smoothed prolongation: sum over the aggregate
       // and its ring of phi_IJ times the residual
-      if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
+      if (!mg_pass(sc, P, M, local, C.n, C.ni, [&](int c, int I, int J) {
             float s = 0.0f;
 #pragma unroll
             for (int dj = -1; dj <= 2; ++dj)
@@ -870,7 +879,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
     } else if (single(l)) {
       // one sweep from zero, x = w D^-1 B, formed on the fly by the restriction,
       // which also stores it for the correction on the way up
-      if (!mg_pass(sc, P, false, C.n, C.ni, [&](int c, int I, int J) {
+      if (!mg_pass(sc, P, M, false, C.n, C.ni, [&](int c, int I, int J) {
             auto y = [&](int b, int, int) { return w * F.dinv[b] * F.B[b]; };
             float s = 0.0f;
             for (int dj = 0; dj < 2; ++dj)
@@ -889,18 +898,18 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
       if (local) {
         // block 0 alone is bound by instructions, not barriers: the first
         // sweep is stored instead of being re-formed at every neighbour
-        mg_pass(sc, P, true, F.n, F.ni, [&](int a, int, int) { F.Y[a] = w * F.dinv[a] * F.B[a]; });
-        mg_pass(sc, P, true, F.n, F.ni, [&](int a, int i, int j) {
+        mg_pass(sc, P, M, true, F.n, F.ni, [&](int a, int, int) { F.Y[a] = w * F.dinv[a] * F.B[a]; });
+        mg_pass(sc, P, M, true, F.n, F.ni, [&](int a, int i, int j) {
           F.X[a] = F.Y[a] + w * F.dinv[a] * (F.B[a] - mg_apply_l(F, false, F.Y, a, i, j));
         });
-      } else if (!mg_pass(sc, P, false, F.n, F.ni, [&](int a, int i, int j) {
+      } else if (!mg_pass(sc, P, M, false, F.n, F.ni, [&](int a, int i, int j) {
                    auto y = [&](int b, int, int) { return w * F.dinv[b] * F.B[b]; };
                    const float ba = F.B[a], da = w * F.dinv[a], ya = da * ba;
                    F.X[a] = ya + da * (ba - mg_apply9_f(F, a, i, j, ya, y));
                  })) {
         return false;
       }
-      if (!mg_pass(sc, P, local, C.n, C.ni, [&](int c, int I, int J) {
+      if (!mg_pass(sc, P, M, local, C.n, C.ni, [&](int c, int I, int J) {
             float s = 0.0f;
             for (int dj = 0; dj < 2; ++dj)
               for (int di = 0; di < 2; ++di) {
@@ -919,7 +928,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
   // coarsest (dense inverse, or Jacobi from zero with an even number of sweeps
   // ending in X) and up, in block 0 for the local levels
   if (M.cinv_off >= 0) {
-    if (sc.bid() == 0) {
+    if (mg_runs_local(sc, M)) {
       const MgLv C = mg_level(M, M.L - 1, sm);
       const float *Ai = sm + M.cinv_off;
       const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -932,16 +941,16 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
       }
       __syncthreads();
     }
-  } else if (sc.bid() == 0 || M.local_from >= M.L) {
+  } else if (mg_runs_local(sc, M) || M.local_from >= M.L) {
     const int lc = M.L - 1;
     const MgLv C = mg_level(M, lc, sm);
     const bool local = lc >= M.local_from, l0 = lc == 0;
-    if (!local || sc.bid() == 0) {
-      mg_pass(sc, P, local, C.n, C.ni, [&](int a, int, int) { C.X[a] = w * C.dinv[a] * C.B[a]; });
+    if (!local || mg_runs_local(sc, M)) {
+      mg_pass(sc, P, M, local, C.n, C.ni, [&](int a, int, int) { C.X[a] = w * C.dinv[a] * C.B[a]; });
       for (int k = 0; k < M.coarse_sweeps; ++k) {  // an even count ends in X
         const float *src = (k & 1) ? C.Y : C.X;
         float *dst = (k & 1) ? C.X : C.Y;
-        mg_pass(sc, P, local, C.n, C.ni, [&](int a, int i, int j) {
+        mg_pass(sc, P, M, local, C.n, C.ni, [&](int a, int i, int j) {
           dst[a] = src[a] + w * C.dinv[a] * (C.B[a] - mg_apply_l(C, l0, src, a, i, j));
         });
       }
@@ -950,7 +959,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
   float t[2] = {0.0f, 0.0f};
   for (int l = M.L - 2; l >= 0; --l) {
     const bool local = l >= lf;
-    if (!local && l + 1 >= lf && lf < M.L) {
+    if (!local && l + 1 >= lf && lf < M.L && !M.redundant) {
       // leaving the block-local levels: block 0 publishes the first local
       // level's result, and everyone waits for it
       if (sm != nullptr && lf >= M.smem_from) {
@@ -960,20 +969,22 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
       if (!sc.sync(P)) return false;
     }
     MgLv F = mg_level(M, l, sm);
-    MgLv C = mg_level(M, l + 1, l + 1 == lf ? nullptr : sm);
+    // the first local level's result: the global copy block 0 published, or
+    // this block's own
+    MgLv C = mg_level(M, l + 1, (l + 1 == lf && !M.redundant) ? nullptr : sm);
     if (l == 0) F.B = b0;
     if (single(l + 1)) {  // that level's result is in its Y
       float *const t = C.X;
       C.X = C.Y;
       C.Y = t;
     }
-    if (local && sc.bid() != 0) continue;
+    if (local && !mg_runs_local(sc, M)) continue;
     // coarse correction folded into the first post-smoothing sweep: the
     // corrected values are formed on the fly at the node and its neighbours
     if (l == 0) {
       // smoothed prolongation: the node's own aggregate and the two across
       // its boundary, with the node's weights
-      if (!mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) {
+      if (!mg_pass(sc, P, M, local, F.n, F.ni, [&](int a, int i, int j) {
             auto y = [&](int b, int ib, int jb) {
               const int I = ib >> 1, J = jb >> 1;
               const int ix = (ib & 1) ? ib + 1 : ib - 1, jx = (jb & 1) ? jb + 1 : jb - 1;
@@ -989,14 +1000,14 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
     } else if (local) {
       // block 0: the corrected values are stored once (in place in X), then
       // the first sweep reads them
-      mg_pass(sc, P, true, F.n, F.ni, [&](int a, int i, int j) {
+      mg_pass(sc, P, M, true, F.n, F.ni, [&](int a, int i, int j) {
         F.X[a] = F.dinv[a] != 0.0f ? F.X[a] + al * C.X[(j >> 1) * C.ni + (i >> 1)] : 0.0f;
       });
-      mg_pass(sc, P, true, F.n, F.ni, [&](int a, int i, int j) {
+      mg_pass(sc, P, M, true, F.n, F.ni, [&](int a, int i, int j) {
         F.Y[a] = F.X[a] + w * F.dinv[a] * (F.B[a] - mg_apply_l(F, false, F.X, a, i, j));
       });
     } else {
-      if (!mg_pass(sc, P, false, F.n, F.ni, [&](int a, int i, int j) {
+      if (!mg_pass(sc, P, M, false, F.n, F.ni, [&](int a, int i, int j) {
             auto y = [&](int b, int ib, int jb) {
               return F.dinv[b] != 0.0f ? F.X[b] + al * C.X[(jb >> 1) * C.ni + (ib >> 1)] : 0.0f;
             };
@@ -1020,7 +1031,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
                  t[0] += b * x;
                  t[1] += b * b;
                });
-    } else if (!single(l) && !mg_pass(sc, P, local, F.n, F.ni, [&](int a, int i, int j) { sweep(a, i, j); })) {
+    } else if (!single(l) && !mg_pass(sc, P, M, local, F.n, F.ni, [&](int a, int i, int j) { sweep(a, i, j); })) {
       return false;
     }
   }
@@ -1034,7 +1045,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
 template <class S>
 __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) {
   extern __shared__ __align__(16) float mg_sm[];
-  float *sm = (sc.bid() == 0 && M.smem_floats > 0) ? mg_sm : nullptr;
+  float *sm = (mg_runs_local(sc, M) && M.smem_floats > 0) ? mg_sm : nullptr;
   const int nn = P.nn;
   float *part32 = reinterpret_cast<float *>(P.partial + 8 * sc.nblk());
   double *r64 = P.work;
@@ -1168,6 +1179,7 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
     if (sf <= kMgSmemFloats - kMgDenseMax * kMgDenseMax) {
       M->smem_from = M->local_from;
       M->smem_floats = (int)sf;
+      M->redundant = 1;  // every block runs the local levels on its own copy
     }
   }
   // the coarsest level is block 0's (at most kMgDenseMax nodes is at most
