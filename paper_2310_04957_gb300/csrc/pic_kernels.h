@@ -171,8 +171,8 @@ struct MgLevels {
   int L;
   int ni[kMgMaxLevels], nj[kMgMaxLevels];
   long long off[kMgMaxLevels];  // first float of level l's arrays in ws
-  int local_from;               // levels >= local_from run in block 0 alone
-  int smem_from;                // levels >= smem_from live in block 0's shared memory (L: none)
+  int local_from;               // levels >= local_from run within a block (block 0, or each block)
+  int smem_from;                // levels >= smem_from live in shared memory (L: none)
   long long soff[kMgMaxLevels]; // their offsets (floats) in it
   int smem_floats;              // its size
   int redundant;                // 1: every block runs the local levels in its own shared memory
@@ -182,7 +182,7 @@ struct MgLevels {
   float omega_s;                // prolongation smoothing of level 0
   int single_sweep;             // grid-wide levels below 0 smooth once before and after
   int coarse_sweeps;            // Jacobi sweeps on the coarsest level (when not dense)
-  int cinv_off;                 // dense inverse of the coarsest operator in block 0's
+  int cinv_off;                 // dense inverse of the coarsest operator in the block's
                                 // shared memory at this offset (floats); -1: Jacobi
   float *ws;
   float *p, *p2, *q, *x, *r2;  // CG vectors (p and r alternate between two buffers)

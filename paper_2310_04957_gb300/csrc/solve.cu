@@ -417,12 +417,12 @@ __global__ void __launch_bounds__(kPcgThreads) k_pcg_mixed(const PcgParams P) {
 // Smoother: damped Jacobi (omega); coarse corrections scaled by alpha0 into
 // level 0 and alpha below (piecewise-constant aggregation over-estimates the
 // coarse energy); coarsest level (at most kMgDenseMax nodes): its inverse,
-// formed at setup by Gauss-Jordan elimination in block 0's shared memory,
+// formed at setup by Gauss-Jordan elimination in shared memory,
 // applied as one matrix-vector product (Jacobi sweeps from zero on larger
 // coarsest levels).  Every piece is a fixed linear symmetric map, so the
 // preconditioner is SPD.
 // Threads per block of the multigrid solve (one block per SM; the coarse
-// levels run in block 0, so its width sets their speed).
+// levels run within one block, so its width sets their speed).
 constexpr int kMgThreads = 512;
 
 // Synchronisation scope of the multigrid solve: the whole grid (one
@@ -508,8 +508,9 @@ __device__ __forceinline__ MgLv mg_view(float *b, int ni, int nj) {
   return v;
 }
 
-// Level l's arrays: the levels from M.smem_from on live in block 0's shared
-// memory (sm != nullptr only there); everything else in the global workspace.
+// Level l's arrays: the levels from M.smem_from on live in the shared memory
+// of the blocks that run them (sm != nullptr only there); everything else in
+// the global workspace.
 __device__ __forceinline__ MgLv mg_level(const MgLevels &M, int l, float *sm) {
   float *b = (sm != nullptr && l >= M.smem_from) ? sm + M.soff[l] : M.ws + M.off[l];
   return mg_view(b, M.ni[l], M.nj[l]);
@@ -792,7 +793,7 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
       __syncthreads();
     }
   }
-  // the local levels were built by block 0: everyone waits for them
+  // the local levels were built block-locally: everyone waits for them
   return M.local_from >= M.L ? true : sc.sync(P);
 }
 
@@ -830,8 +831,9 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
   // grid-wide coarse levels smooth once before and once after their coarse
   // correction (each sweep there is a grid barrier); their result is left in Y
   auto single = [&](int l) { return M.single_sweep && l >= 1 && l < lf; };
-  // block 0 takes the first local level's right-hand side (restricted
-  // grid-wide into the global copy) into shared memory
+  // each block that runs the local levels takes the first local level's
+  // right-hand side (restricted grid-wide into the global copy) into its
+  // shared memory
   auto take_in = [&]() {
     if (sm == nullptr || lf < M.smem_from || lf >= M.L) return;
     const MgLv G = mg_level(M, lf, nullptr), Sh = mg_level(M, lf, sm);
@@ -896,7 +898,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
         return false;
     } else {
       if (local) {
-        // block 0 alone is bound by instructions, not barriers: the first
+        // one block's pass is bound by instructions, not barriers: the first
         // sweep is stored instead of being re-formed at every neighbour
         mg_pass(sc, P, M, true, F.n, F.ni, [&](int a, int, int) { F.Y[a] = w * F.dinv[a] * F.B[a]; });
         mg_pass(sc, P, M, true, F.n, F.ni, [&](int a, int i, int j) {
@@ -926,7 +928,7 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
   }
   if (lf == M.L - 1) take_in();  // the coarsest level is the only local one
   // coarsest (dense inverse, or Jacobi from zero with an even number of sweeps
-  // ending in X) and up, in block 0 for the local levels
+  // ending in X) and up, block-locally for the local levels
   if (M.cinv_off >= 0) {
     if (mg_runs_local(sc, M)) {
       const MgLv C = mg_level(M, M.L - 1, sm);
@@ -998,8 +1000,8 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
           }))
         return false;
     } else if (local) {
-      // block 0: the corrected values are stored once (in place in X), then
-      // the first sweep reads them
+      // block-local: the corrected values are stored once (in place in X),
+      // then the first sweep reads them
       mg_pass(sc, P, M, true, F.n, F.ni, [&](int a, int i, int j) {
         F.X[a] = F.dinv[a] != 0.0f ? F.X[a] + al * C.X[(j >> 1) * C.ni + (i >> 1)] : 0.0f;
       });
@@ -1035,7 +1037,8 @@ __device__ bool mg_vcycle(const S &sc, const PcgParams &P, const MgLevels &M, fl
       return false;
     }
   }
-  // every block joins the sum (a hierarchy entirely in block 0: the others add 0)
+  // every block joins the sum (a hierarchy entirely in block 0, the case of
+  // small grids: the others add 0)
   if (!grid_sum_s<float, 2>(sc, t, part32, parity, P)) return false;
   dots[0] = t[0];
   dots[1] = t[1];
@@ -1166,8 +1169,8 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
     ni = (ni + 1) / 2;
     nj = (nj + 1) / 2;
   }
-  // the block-local levels (below level 0) live in block 0's shared memory
-  // for the whole solve when they fit
+  // the block-local levels (below level 0) live in shared memory for the
+  // whole solve when they fit, one copy per block
   M->smem_from = M->L;
   M->smem_floats = 0;
   if (M->local_from >= 1 && M->local_from < M->L) {
@@ -1182,7 +1185,7 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
       M->redundant = 1;  // every block runs the local levels on its own copy
     }
   }
-  // the coarsest level is block 0's (at most kMgDenseMax nodes is at most
+  // the coarsest level is block-local (at most kMgDenseMax nodes is at most
   // 4096): its dense inverse follows the levels in shared memory
   const int nc = M->ni[M->L - 1] * M->nj[M->L - 1];
   M->cinv_off = -1;
