@@ -836,6 +836,8 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
       h->mg.q = h->mg.p2 + nn;
       h->mg.x = h->mg.q + nn;
       h->mg.r2 = h->mg.x + nn;
+      DA(h->mg.persist, sizeof(float) * (size_t)(h->mg.smem_floats > 0 ? h->mg.smem_floats : 1));
+      DA(h->mg.solves, sizeof(int));
     }
     h->pcg_grid = pcg_grid_size(h->device);
     DA(h->d_partial, sizeof(double) * 16 * (h->pcg_grid + 32));

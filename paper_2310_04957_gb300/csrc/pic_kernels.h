@@ -181,6 +181,9 @@ struct MgLevels {
   float alpha0;                 // coarse-correction scale of level 1 into level 0
   float omega_s;                // prolongation smoothing of level 0
   int single_sweep;             // grid-wide levels below 0 smooth once before and after
+  int rebuild_every;            // the coarse hierarchy is rebuilt every n-th solve (1: always)
+  int *solves;                  // solves so far (device counter)
+  float *persist;               // [smem_floats] the shared-memory part of the last build
   int coarse_sweeps;            // Jacobi sweeps on the coarsest level (when not dense)
   int cinv_off;                 // dense inverse of the coarsest operator in the block's
                                 // shared memory at this offset (floats); -1: Jacobi

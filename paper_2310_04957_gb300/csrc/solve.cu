@@ -665,6 +665,19 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
         }))
       return false;
   }
+  // Level 0 (the inner CG's operator and the smoother's) is always current.
+  // The coarse hierarchy below it changes little from one step to the next:
+  // it is rebuilt every rebuild_every-th solve of the discharge and reused in
+  // between, its shared-memory part reloaded from the copy kept in global
+  // memory.  A coarse correction from a slightly older operator leaves the
+  // V-cycle symmetric positive definite, so the CG stays valid.
+  if (M.rebuild_every > 1 && *M.solves % M.rebuild_every != 0) {
+    if (sm != nullptr) {
+      for (int a = threadIdx.x; a < M.smem_floats; a += blockDim.x) sm[a] = __ldcg(M.persist + a);
+      __syncthreads();
+    }
+    return true;
+  }
   for (int l = 0; l + 1 < M.L; ++l) {
     const MgLv F = mg_level(M, l, sm), C = mg_level(M, l + 1, sm);
     const bool local = l + 1 >= M.local_from;
@@ -792,6 +805,10 @@ __device__ bool mg_setup(const S &sc, const PcgParams &P, const MgLevels &M, flo
         }
       __syncthreads();
     }
+  }
+  // keep the shared-memory part for the solves that reuse the hierarchy
+  if (sm != nullptr && sc.bid() == 0) {
+    for (int a = threadIdx.x; a < M.smem_floats; a += blockDim.x) M.persist[a] = sm[a];
   }
   // the local levels were built block-locally: everyone waits for them
   return M.local_from >= M.L ? true : sc.sync(P);
@@ -1136,6 +1153,7 @@ __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) 
     P.out[3] = (double)outer;
     if (status == -4) atomicOr(P.flags, 0x4u);
     if (status == -7) atomicOr(P.flags, 0x8u);
+    *M.solves += 1;  // every block has read it (at setup, before the first barrier)
   }
 }
 
@@ -1197,6 +1215,7 @@ long long mg_plan(int nr, int nz, MgLevels *M) {
   M->alpha = 1.8f;
   M->alpha0 = 1.0f;
   M->single_sweep = 1;
+  M->rebuild_every = 8;
   M->omega_s = 2.0f / 3.0f;  // 4 / (3 lambda_max) with lambda_max(D^-1 A) <= 2
   M->coarse_sweeps = 10;
   return off + 5LL * (nr + 1) * (nz + 1);
