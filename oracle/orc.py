@@ -86,6 +86,8 @@ def lib():
         L.orc_scatter_cos.argtypes = [ctypes.c_double, ctypes.c_double]
         L.orc_scatter_cos.restype = ctypes.c_double
         L.orc_turn.argtypes = [P, ctypes.c_double, ctypes.c_double]
+        L.orc_trace.argtypes = [P, ctypes.c_int, P]
+        L.orc_child_ids.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, P, P]
         _lib = L
     return _lib
 
@@ -108,6 +110,14 @@ def philox(ctr, key):
     o = np.zeros(4, np.uint32)
     lib().orc_philox(_p(c), _p(k), _p(o))
     return o
+
+
+def child_ids(step, seed, parents):
+    """[n, 2] ids of the electron and ion an ionization of each parent creates in `step`."""
+    p = np.ascontiguousarray(parents, np.uint64)
+    out = np.zeros((len(p), 2), np.uint64)
+    lib().orc_child_ids(step, seed, len(p), _p(p), _p(out))
+    return out
 
 
 class Oracle:
@@ -273,6 +283,15 @@ class Oracle:
 
     def xs(self, proc, E):
         return lib().orc_xs(self.h, proc, float(E))
+
+    def trace(self, enable):
+        """Decision-margin tracing: enable=True resets and starts recording,
+        False stops, None only reads.  Returns the margins recorded so far:
+        (random-number / energy thresholds, relative; position tests, cell
+        units; predictor rotation conditioning)."""
+        out = np.zeros(3)
+        lib().orc_trace(self.h, -1 if enable is None else int(bool(enable)), _p(out))
+        return tuple(out.tolist())
 
 
 def scatter_cos(E, R):

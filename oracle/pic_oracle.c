@@ -132,9 +132,62 @@ struct orc_sim {
   double ion_q_sum[3], ion_cur_avg[3];
   double dft_re, dft_im, i1_re, i1_im;
   int win_count, windows_done;
+  /* decision margins (test instrumentation, see orc_trace): [0] random-number
+   * and energy thresholds, relative; [1] position tests, cell units; [2]
+   * conditioning of the predictor's rotation angle */
+  int trace;
+  double margin[3];
 };
 
 static int nidx(const orc_sim *s, int i, int j) { return j * (s->cfg.nr + 1) + i; }
+
+/* ------------------------------------------------------------------------ */
+/* Decision margins.  Every branch of a particle's step is decided by        */
+/* comparing a computed quantity with a threshold: a uniform with P_null, a  */
+/* scaled uniform with the cumulative collision frequencies, an energy with  */
+/* an inelastic threshold, a position with a cell face across which the      */
+/* particle leaves the plasma, a radius with the axis.  A second             */
+/* implementation that rounds differently (FP32) can take the other branch   */
+/* only where the quantity lies within its own rounding of the threshold.    */
+/* When tracing is on the step records the smallest such distance; it never  */
+/* changes what the step computes.                                           */
+/* ------------------------------------------------------------------------ */
+static void note_margin(orc_sim *s, int kind, double v) {
+  if (s->trace && v < s->margin[kind]) s->margin[kind] = v;
+}
+
+/* Plasma membership of cell (i,j); outside the domain nothing is plasma,
+ * except across the axis, which is a symmetry line, not a boundary. */
+static int member(const orc_sim *s, int i, int j) {
+  if (i < 0) i = 0;
+  if (i >= s->cfg.nr || j < 0 || j >= s->cfg.nz) return 0;
+  return s->cell_kind[j * s->cfg.nr + i] == ORC_CELL_PLASMA;
+}
+
+/* Distance, in cell units, from (r,z) to the nearest cell face (or corner)
+ * across which plasma membership changes. */
+static double face_margin(const orc_sim *s, double r, double z) {
+  double x = r / s->cfg.dr, y = z / s->cfg.dz;
+  int i = (int)floor(x), j = (int)floor(y);
+  int in = member(s, i, j);
+  double lo_x = x - i, hi_x = i + 1 - x, lo_y = y - j, hi_y = j + 1 - y;
+  double m = 1e300;
+  if (member(s, i - 1, j) != in && lo_x < m) m = lo_x;
+  if (member(s, i + 1, j) != in && hi_x < m) m = hi_x;
+  if (member(s, i, j - 1) != in && lo_y < m) m = lo_y;
+  if (member(s, i, j + 1) != in && hi_y < m) m = hi_y;
+  for (int di = -1; di <= 1; di += 2)
+    for (int dj = -1; dj <= 1; dj += 2)
+      if (member(s, i + di, j + dj) != in) {
+        double dx = di < 0 ? lo_x : hi_x, dy = dj < 0 ? lo_y : hi_y;
+        double d = dx > dy ? dx : dy;
+        if (d < m) m = d;
+      }
+  return m;
+}
+
+/* Relative distance of x from threshold t (t > 0). */
+static double rel_gap(double x, double t) { return fabs(x - t) / t; }
 
 /* ------------------------------------------------------------------------ */
 /* Cross sections: linear interpolation in E between bracketing table nodes  */
@@ -305,6 +358,7 @@ static void mcc_electron(orc_sim *s, orc_particle *p, double r, double z) {
   const orc_setup *c = &s->cfg;
   double u[4];
   draw(p->id, s->step, 0, 0, c->seed, u);
+  note_margin(s, 0, rel_gap(u[0], s->pcoll[0]));
   if (!(u[0] < s->pcoll[0])) return;
   double v2 = p->vr * p->vr + p->vt * p->vt + p->vz * p->vz;
   double speed = sqrt(v2);
@@ -313,6 +367,13 @@ static void mcc_electron(orc_sim *s, orc_particle *p, double r, double z) {
   double nu_ex = c->n_gas * xs_lookup(s, 1, E) * speed;
   double nu_iz = c->n_gas * xs_lookup(s, 2, E) * speed;
   double x = u[1] * s->numax[0];
+  if (s->trace) {
+    note_margin(s, 0, rel_gap(E, c->thr_ex));
+    note_margin(s, 0, rel_gap(E, c->thr_iz));
+    double cum[3] = {nu_el, nu_el + nu_ex, nu_el + nu_ex + nu_iz};
+    for (int k = 0; k < 3; ++k)
+      if (cum[k] > 0.0) note_margin(s, 0, rel_gap(x, cum[k]));
+  }
   if (speed <= 0.0) return;
   double dir[3] = {p->vr / speed, p->vt / speed, p->vz / speed};
   if (x < nu_el) {
@@ -367,6 +428,7 @@ static void mcc_ion(orc_sim *s, orc_particle *p) {
   const orc_setup *c = &s->cfg;
   double u[4], u1[4];
   draw(p->id, s->step, 0, 1, c->seed, u);
+  note_margin(s, 0, rel_gap(u[0], s->pcoll[1]));
   if (!(u[0] < s->pcoll[1])) return;
   draw(p->id, s->step, 1, 1, c->seed, u1);
   double n0, n1, n2, n3;
@@ -381,6 +443,10 @@ static void mcc_ion(orc_sim *s, orc_particle *p) {
   double nu_iso = c->n_gas * xs_lookup(s, 3, eps) * gm;
   double nu_cx = c->n_gas * xs_lookup(s, 4, eps) * gm;
   double x = u[1] * s->numax[1];
+  if (s->trace) {
+    if (nu_iso > 0.0) note_margin(s, 0, rel_gap(x, nu_iso));
+    if (nu_iso + nu_cx > 0.0) note_margin(s, 0, rel_gap(x, nu_iso + nu_cx));
+  }
   if (x < nu_iso) {
     double mi = c->m[1], M = c->m_gas;
     double ct = 1.0 - 2.0 * u[2];
@@ -403,13 +469,15 @@ static void mcc_ion(orc_sim *s, orc_particle *p) {
  * the particle moves by dt*u in its local Cartesian frame (x along r, y along
  * theta); the new radius is |(r + dt u_r, dt u_theta)| and (v_r, v_theta),
  * (a_r, a_theta) are turned by the swept angle alpha. */
-static void predict(const orc_sim *s, orc_particle *p, double r, double z) {
+static void predict(orc_sim *s, orc_particle *p, double r, double z) {
   double dt = s->cfg.dt;
   double ur = p->vr + 0.5 * dt * p->ar;
   double ut = p->vt + 0.5 * dt * p->at;
   double uz = p->vz + 0.5 * dt * p->az;
   double X = r + dt * ur, Y = dt * ut;
   double rn = sqrt(X * X + Y * Y);
+  /* the swept angle's sensitivity to a position error grows as 1/rn */
+  note_margin(s, 2, rn / (s->cfg.dr + dt * sqrt(ur * ur + ut * ut)));
   double ca = 1.0, sa = 0.0;
   if (rn > 0.0) { ca = X / rn; sa = Y / rn; }
   double vr = ca * p->vr + sa * p->vt, vt = -sa * p->vr + ca * p->vt;
@@ -423,6 +491,7 @@ static void predict(const orc_sim *s, orc_particle *p, double r, double z) {
  * test at x~_{n+1}, deposit.  Returns 1 if it stays. */
 static int finish_particle(orc_sim *s, int spc, orc_particle *p, double r, double z, int32_t *cell) {
   predict(s, p, r, z);
+  note_margin(s, 1, face_margin(s, p->r, p->z));
   int i, j;
   if (!inside_plasma(s, p->r, p->z, &i, &j)) {
     credit(s, spc, p->r, p->z);
@@ -496,7 +565,9 @@ static int particle_phase(orc_sim *s) {
       p.at = 0.5 * (0.0 + p.at);
       p.az = 0.5 * (an_z + p.az);
       p.vr += dt * p.ar; p.vt += dt * p.at; p.vz += dt * p.az;
+      note_margin(s, 1, fabs(r) / s->cfg.dr);
       if (r < 0.0) { r = -r; p.vr = -p.vr; p.vt = -p.vt; p.ar = -p.ar; p.at = -p.at; }
+      note_margin(s, 1, face_margin(s, r, z));
       if (!inside_plasma(s, r, z, &i, &j)) { credit(s, spc, r, z); continue; }
       if (spc == 0) mcc_electron(s, &p, r, z); else mcc_ion(s, &p);
       int32_t cell;
@@ -1193,6 +1264,34 @@ int orc_scalars(const orc_sim *s, double *o, int n) {
   v[42] = s->i1_re; v[43] = s->i1_im; v[44] = s->windows_done; v[45] = s->ceq_gauss; v[46] = s->pcg_status;
   for (int k = 0; k < n && k < 47; ++k) o[k] = v[k];
   return ORC_OK;
+}
+
+/* Decision-margin tracing (test instrumentation): enable = 1 resets the
+ * three margins to +inf and starts recording them in later particle phases,
+ * 0 stops; out3 (may be NULL) receives the margins recorded so far:
+ * [0] smallest relative gap between a uniform or an energy and its threshold,
+ * [1] smallest distance (cell units) from a tested position to a face across
+ * which the particle would change plasma membership, or to the axis,
+ * [2] smallest |(X, Y)| / (dr + dt |u_perp|) of a predictor rotation. */
+int orc_trace(orc_sim *s, int enable, double *out3) {
+  if (out3)
+    for (int k = 0; k < 3; ++k) out3[k] = s->margin[k];
+  if (enable == 1) {
+    s->trace = 1;
+    for (int k = 0; k < 3; ++k) s->margin[k] = 1e300;
+  } else if (enable == 0) {
+    s->trace = 0;
+  }
+  return ORC_OK;
+}
+
+/* Ids of the electron (out[2k]) and ion (out[2k+1]) that an ionization of
+ * parents[k] would create in `step` (test hook). */
+void orc_child_ids(uint32_t step, uint32_t seed, int64_t n, const uint64_t *parents, uint64_t *out) {
+  for (int64_t k = 0; k < n; ++k) {
+    out[2 * k] = child_id(parents[k], step, 0, seed);
+    out[2 * k + 1] = child_id(parents[k], step, 1, seed);
+  }
 }
 
 /* Test hooks. */
