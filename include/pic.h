@@ -37,6 +37,7 @@ extern "C" {
 #define PIC_ETIMEOUT -5  /* a bounded device-side wait ran out */
 #define PIC_EOVERFLOW -6 /* particle store or overflow region full */
 #define PIC_ENAN -7      /* non-finite value in the field solve */
+#define PIC_EIO -8       /* restart file could not be written or read, or is not one */
 
 /* status-word bits (pic_status) */
 #define PIC_FLAG_OVERFLOW 0x1u
@@ -112,6 +113,9 @@ typedef struct pic_config {
   int32_t solver;              /* PIC_SOLVER_*                                     */
   int32_t tile_r, tile_z;      /* cells per CTA tile (0 = library default)         */
   double bin_slack;            /* extra bin room as a fraction of last count (0 = default) */
+  int64_t spin_limit;          /* clock cycles a field-solve grid barrier may wait
+                                  for the other blocks before the solve gives up
+                                  with PIC_ETIMEOUT (0 = default, 4e9: ~2 s)     */
 } pic_config;
 
 /* Particle arrays of one species in FP64 host memory (caller-owned).  Position
@@ -189,6 +193,17 @@ int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss);
 #define PIC_DIAG_PHI_WARM 11 /* warm start of the last solve, V (kept by
                                 pic_keep_warm or the learned solver) [nodes] */
 #define PIC_DIAG_SCALARS 100 /* PIC_NSCALARS doubles, see below  */
+#define PIC_DIAG_STORE 101   /* 8 doubles: per species (electrons, then ions)
+                                particles in their cell bins, particles in the
+                                overflow region (those that did not fit their
+                                bin at the last re-bin), capacity, first slot
+                                of the overflow region */
+#define PIC_DIAG_SOLVER 102  /* 5 doubles: multigrid solves counter (the next
+                                PIC_SOLVER_MG solve rebuilds the coarse
+                                hierarchy when it is a multiple of [1], else
+                                reuses it; a failed solve resets it to 0),
+                                rebuild period, last solve's iterations,
+                                outer refinement steps, status */
 #define PIC_NSCALARS 47
 /* Scalars: [0] step, [1] t, [2] U_E, [3] Q_E, [4] C_eq, [5] I_conv, [6] I_ccp,
  * [7..12] circuit state (RLC: Qb, Ib, QE; IMN: Q1, Q2, I2, Qccp, Istray, QE),
@@ -223,6 +238,18 @@ int pic_circuit_run(pic_handle *h, int n, double *U_out);
  * (PIC_FLAG_*), then clear them. */
 int pic_status(pic_handle *h, uint32_t *flags);
 
+/* pic_check -- synchronise and turn the accumulated status bits into a code:
+ * PIC_OK when none is set, else the most severe one's -- PIC_EOVERFLOW (a
+ * particle was dropped: store or overflow region full), PIC_ETIMEOUT (a
+ * bounded device-side wait ran out), PIC_ENAN (non-finite residual),
+ * PIC_ENOCONV (iteration cap).  The bits stay set until pic_status reads them.
+ * Errors: PIC_ECUDA if the stream reports a CUDA error. */
+int pic_check(pic_handle *h);
+
+/* pic_set_spin_limit -- change cfg.spin_limit (clock cycles per grid-barrier
+ * wait, 0 = default) for later solves and steps. */
+int pic_set_spin_limit(pic_handle *h, int64_t cycles);
+
 /* pic_philox -- fill host `out[4*n]` with Philox4x32-10 outputs computed on
  * the device for counters ctr[4*n] and keys key[2*n] (host arrays); used to
  * check that device and host generators agree bit for bit. */
@@ -237,17 +264,40 @@ int pic_philox(pic_handle *h, int64_t n, const uint32_t *ctr, const uint32_t *ke
 int pic_enable_timing(pic_handle *h, int on);
 int pic_step_timing(pic_handle *h, double *out7);
 
+/* pic_save -- write the discharge's complete state to the restart file
+ * `path`.  The paper's runs (Sec. 2) write their state out and continue over
+ * thousands of RF cycles; here that state is one binary file holding the
+ * configuration and its arrays, the step counter, the circuit and electrode
+ * state with C_eq (Eqs. 5, 8-10), the particle stores exactly as stored
+ * (cell-relative positions in the handle's precision, bins and overflow
+ * region), phi, the gather field, the deposits, the surface charge, the
+ * RF-window sums and the multigrid hierarchy.  A handle restored by pic_load
+ * continues bit for bit as this one would: the random numbers are keyed on
+ * particle id and step, so no generator state exists.  Not saved: an
+ * attached U-Net (attach it again before a PIC_SOLVER_LEARNED step), the
+ * timing and keep-warm switches.  The file is in the host's byte order, for
+ * the same library build on the same kind of host.  Synchronises.
+ * Errors: PIC_EINVAL (NULL argument), PIC_EIO, PIC_ENOMEM, PIC_ECUDA. */
+int pic_save(pic_handle *h, const char *path);
+
+/* pic_load -- create a handle on the current device, enqueueing on
+ * `cuda_stream`, from a file written by pic_save; *out receives it (the
+ * caller destroys it with pic_destroy).  Errors: PIC_EIO (missing, truncated
+ * or foreign file, or sizes that do not match its configuration),
+ * PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA. */
+int pic_load(const char *path, void *cuda_stream, pic_handle **out);
+
 /* pic_pcg_solve_static -- the paper has no counterpart to this entry point;
  * it exists for callers that cannot allocate GPU memory when they need a
  * field solve (an application that owns all device memory through its own
- * pool, code running while a stream is captured into a CUDA graph, a plugin
- * called from a loop that must not wait on the allocator).  It solves the
- * same system as the plain solver of pic_field_solve -- Jacobi-preconditioned
- * CG in FP64 on the free nodes of sum_b G_ab (phi_a - phi_b) = qrhs_a, warm
- * start from phi, stop at ||r|| <= tol ||b|| -- on arrays the caller owns, and
- * allocates nothing: its work vectors live in one fixed array inside the
- * library, sized for PIC_STATIC_MAX_NODES nodes, which every GPU that loads
- * the library keeps until the process exits.
+ * pool, a plugin called from a loop that must not wait on the allocator).
+ * It solves the same system as the plain solver of pic_field_solve --
+ * Jacobi-preconditioned CG in FP64 on the free nodes of
+ * sum_b G_ab (phi_a - phi_b) = qrhs_a, warm start from phi, stop at
+ * ||r|| <= tol ||b|| -- on arrays the caller owns, and allocates nothing: its
+ * work vectors live in one fixed array inside the library, sized for
+ * PIC_STATIC_MAX_NODES nodes (about 10 MB), which every GPU that loads the
+ * library keeps until the process exits.
  *   nr, nz     grid cells (nodes (nr+1)*(nz+1) <= PIC_STATIC_MAX_NODES, else
  *              PIC_EINVAL)
  *   node_kind  device [(nz+1)*(nr+1)] PIC_NODE_* (Dirichlet where non-zero)
@@ -256,16 +306,24 @@ int pic_step_timing(pic_handle *h, double *out7);
  *   phi        device [(nz+1)*(nr+1)], in: Dirichlet values + initial guess,
  *              out: solution
  *   iters, rel_resid  host, may both be NULL: then the call returns once the
- *              work is enqueued on cuda_stream; otherwise it synchronises the
- *              stream and returns PIC_ENOCONV / PIC_ETIMEOUT / PIC_ENAN on failure.
+ *              work is enqueued on cuda_stream and reports no failure itself
+ *              (pic_pcg_static_result reads the outcome later); otherwise it
+ *              synchronises the stream and returns PIC_ENOCONV / PIC_ETIMEOUT /
+ *              PIC_ENAN on failure.
  * The first call on each device looks up the work array's device address;
  * make that first call before any stream capture.  All calls share the work
- * array: calls that can overlap on the GPU (other streams, other host threads
- * on the same device) race on it and must be serialised by the caller. */
+ * array and it keeps the last call's contents: calls that can overlap on the
+ * GPU (other streams, other host threads on the same device) race on it and
+ * must be serialised by the caller. */
 #define PIC_STATIC_MAX_NODES 139264
 int pic_pcg_solve_static(int32_t nr, int32_t nz, const int8_t *node_kind, const double *Gr, const double *Gz,
                          const double *qrhs, double *phi, double tol, int32_t maxit, void *cuda_stream,
                          int32_t *iters, double *rel_resid);
+/* pic_pcg_static_result -- outcome of the last pic_pcg_solve_static call on
+ * the current device (a later call overwrites it): synchronises cuda_stream,
+ * fills iters and rel_resid (each may be NULL) and returns PIC_OK,
+ * PIC_ENOCONV, PIC_ETIMEOUT or PIC_ENAN as that call would have. */
+int pic_pcg_static_result(void *cuda_stream, int32_t *iters, double *rel_resid);
 
 /* ---- learned field-solve preconditioner (U-Net) -------------------------
  * A 4-level U-Net (32 base channels, BF16 weights and activations, FP32

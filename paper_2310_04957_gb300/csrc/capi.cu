@@ -12,11 +12,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/pic.h"
-#include "learned.h"
-#include "pic_device.cuh"
-#include "pic_kernels.h"
-#include "unet.h"
+#include "handle.h"
 
 using namespace pic;
 
@@ -26,85 +22,6 @@ const double kEps0 = 8.8541878128e-12;   // F/m
 const double kQe = 1.602176634e-19;      // C
 const double kKB = 1.380649e-23;         // J/K
 const double kPi = 3.141592653589793238462643383279;
-
-struct Store {
-  void *fr = nullptr, *fz = nullptr, *vr = nullptr, *vt = nullptr, *vz = nullptr, *ar = nullptr, *at = nullptr,
-       *az = nullptr;
-  unsigned long long *id = nullptr;
-  int *cell = nullptr, *start = nullptr, *cap = nullptr, *fill = nullptr;
-  BinMeta *meta = nullptr;
-};
-
-}  // namespace
-
-struct pic_handle {
-  pic_config cfg{};
-  std::vector<int8_t> node_kind, cell_kind;
-  std::vector<double> cell_eps, xs_E, xs_S;
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int nr = 0, nz = 0, nn = 0, nc = 0;
-  int prec = PIC_FP32;
-  size_t esz = 4;
-  BinMap map{};
-  int nbins = 0, ntiles = 0;
-  float slack = 0.25f;
-  int64_t capacity[2] = {0, 0};
-  // device: geometry, operator, fields
-  int8_t *d_node_kind = nullptr, *d_cell_kind = nullptr, *d_bin_plasma = nullptr;
-  double *d_Gvac_r = nullptr, *d_Gpl_r = nullptr, *d_Gvac_z = nullptr, *d_Gpl_z = nullptr, *d_vnode = nullptr;
-  double *d_chi = nullptr, *d_zero = nullptr, *d_qrhs = nullptr, *d_phi = nullptr, *d_Gr = nullptr, *d_Gz = nullptr,
-         *d_dinv = nullptr, *d_Er = nullptr, *d_Ez = nullptr;
-  void *d_E = nullptr;
-  // PCG scratch
-  double *d_work = nullptr, *d_partial = nullptr, *d_pcg_out = nullptr;
-  float *d_work32 = nullptr;
-  unsigned *d_bar = nullptr;
-  // C_eq solve
-  double *d_phiL = nullptr, *d_Grc = nullptr, *d_Gzc = nullptr, *d_dinvc = nullptr, *d_energy = nullptr,
-         *d_ceq_out = nullptr;
-  // particles, deposits, counters
-  unsigned long long *d_dep[2] = {nullptr, nullptr}, *d_surf[2] = {nullptr, nullptr}, *d_counters = nullptr;
-  Store st[2][2];  // [buffer][species]
-  int cur = 0;
-  void *d_xsE = nullptr, *d_xsS = nullptr;
-  double *d_scalars = nullptr, *d_prop = nullptr;
-  long long *d_lay_part = nullptr, *d_lay_boff = nullptr;
-  int *d_lay_use = nullptr;
-  uint32_t *d_step = nullptr, *d_flags = nullptr;
-  double *d_dens_sum[2] = {nullptr, nullptr}, *d_dens_avg[2] = {nullptr, nullptr};
-  // host mirrors
-  uint32_t step = 0;
-  double numax[2] = {0, 0}, pcoll[2] = {0, 0};
-  int pcg_grid = 0;
-  bool started = false;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  bool graph_failed = false;
-  bool timing = false;
-  double timing_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  std::vector<cudaEvent_t> tev;  // 8 events per timed step
-  std::vector<void *> allocs;
-  // learned preconditioner (PIC_SOLVER_LEARNED)
-  pic_unet *net = nullptr;
-  cudaGraphExec_t fcg_exec = nullptr;
-  cudaStream_t side = nullptr;
-  learned::FcgParams fcg{};
-  int fcg_nblk = 0;
-  double *d_phi_warm = nullptr, *d_lstats = nullptr, *d_pair_s2 = nullptr;
-  bool keep_warm = false;
-  int learned_finish = PIC_SOLVER_PLAIN;  // solver that confirms / finishes a learned solve
-  MgLevels mg{};                          // multigrid hierarchy of PIC_SOLVER_MG (workspace in mg.ws)
-  std::vector<void *> lallocs;  // learned-solver buffers (freed on re-attach)
-};
-
-// A sweep of independent discharges stepped together (see pic_batch_create).
-struct pic_batch {
-  std::vector<pic_handle *> hs;
-  cudaStream_t stream = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-};
-
-namespace {
 
 #define CK(call)                                   \
   do {                                             \
@@ -298,7 +215,7 @@ PcgParams pcg_params(pic_handle *h, const double *Gr, const double *Gz, const do
   P.maxit = h->cfg.pcg_maxit;
   P.out = out;
   P.flags = h->d_flags;
-  P.spin_limit = 4000000000ll;  // ~2 s at 2 GHz per barrier wait
+  P.spin_limit = h->cfg.spin_limit > 0 ? h->cfg.spin_limit : 4000000000ll;  // ~2 s at 2 GHz per barrier wait
   return P;
 }
 
@@ -374,7 +291,6 @@ int launch_push(pic_handle *h, int in_buf) {
 // Layout of the write buffer from the read buffer's fill counts, then zeroed
 // deposits and counters, then the particle kernel.
 int enqueue_particle_phase(pic_handle *h, int in_buf) {
-  int out = in_buf ^ 1;
   CK(launch_layout(layout_params(h, in_buf), h->stream));
   CK(cudaMemsetAsync(h->d_dep[0], 0, sizeof(unsigned long long) * h->nn, h->stream));
   CK(cudaMemsetAsync(h->d_dep[1], 0, sizeof(unsigned long long) * h->nn, h->stream));
@@ -548,6 +464,7 @@ bool check_config(const pic_config *c) {
     return false;
   if (c->capacity[0] < 1 || c->capacity[1] < 1 || c->capacity[0] > 2000000000ll || c->capacity[1] > 2000000000ll)
     return false;
+  if (c->spin_limit < 0) return false;
   if (!(c->m[0] > 0) || !(c->m[1] > 0) || !(c->m_gas > 0)) return false;
   for (int k = 0; k + 1 < c->n_xs; ++k)
     if (!(c->xs_energy[k + 1] > c->xs_energy[k]) || !(c->xs_energy[k] > 0)) return false;
@@ -754,6 +671,7 @@ const char *pic_strerror(int code) {
     case PIC_ETIMEOUT: return "a bounded device-side wait timed out";
     case PIC_EOVERFLOW: return "particle store overflow";
     case PIC_ENAN: return "non-finite value in the field solve";
+    case PIC_EIO: return "restart file could not be written or read, or is not a restart file";
     default: return "unknown error";
   }
 }
@@ -1310,6 +1228,40 @@ int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
     o[46] = pcg[2];
     return PIC_OK;
   }
+  if (what == PIC_DIAG_SOLVER) {
+    if (bytes < sizeof(double) * 5) return PIC_EINVAL;
+    int solves = 0;
+    double pcg[4];
+    CK(cudaMemcpy(&solves, h->mg.solves, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(pcg, h->d_pcg_out, sizeof(pcg), cudaMemcpyDeviceToHost));
+    o[0] = solves;
+    o[1] = h->mg.rebuild_every;
+    o[2] = pcg[0];
+    o[3] = pcg[3];
+    o[4] = pcg[2];
+    return PIC_OK;
+  }
+  if (what == PIC_DIAG_STORE) {
+    if (bytes < sizeof(double) * 8) return PIC_EINVAL;
+    std::vector<int> cap(h->nbins), fill(h->nbins);
+    for (int s = 0; s < 2; ++s) {
+      const Store &S = h->st[h->cur][s];
+      BinMeta m;
+      CK(cudaMemcpy(cap.data(), S.cap, sizeof(int) * h->nbins, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(fill.data(), S.fill, sizeof(int) * h->nbins, cudaMemcpyDeviceToHost));
+      CK(cudaMemcpy(&m, S.meta, sizeof(BinMeta), cudaMemcpyDeviceToHost));
+      int64_t in_bins = 0;
+      for (int b = 0; b < h->nbins; ++b) in_bins += fill[b] < cap[b] ? fill[b] : cap[b];
+      int64_t novf = m.ovf_n;
+      if (novf > h->capacity[s] - m.ovf_base) novf = h->capacity[s] - m.ovf_base;
+      if (novf < 0) novf = 0;
+      o[4 * s + 0] = (double)in_bins;
+      o[4 * s + 1] = (double)novf;
+      o[4 * s + 2] = (double)h->capacity[s];
+      o[4 * s + 3] = (double)m.ovf_base;
+    }
+    return PIC_OK;
+  }
   if (bytes < nb) return PIC_EINVAL;
   switch (what) {
     case PIC_DIAG_PHI: CK(cudaMemcpy(o, h->d_phi, nb, cudaMemcpyDeviceToHost)); return PIC_OK;
@@ -1449,6 +1401,32 @@ int pic_status(pic_handle *h, uint32_t *flags) {
   uint32_t z = 0;
   CK(cudaMemcpy(h->d_flags, &z, sizeof(z), cudaMemcpyHostToDevice));
   *flags = f;
+  return PIC_OK;
+}
+
+int pic_check(pic_handle *h) {
+  if (!h) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  uint32_t f = 0;
+  CK(cudaMemcpy(&f, h->d_flags, sizeof(f), cudaMemcpyDeviceToHost));
+  if (f & PIC_FLAG_OVERFLOW) return PIC_EOVERFLOW;
+  if (f & PIC_FLAG_TIMEOUT) return PIC_ETIMEOUT;
+  if (f & PIC_FLAG_NAN) return PIC_ENAN;
+  if (f & PIC_FLAG_NOCONV) return PIC_ENOCONV;
+  return PIC_OK;
+}
+
+int pic_set_spin_limit(pic_handle *h, int64_t cycles) {
+  if (!h || cycles < 0) return PIC_EINVAL;
+  if (sync(h)) return PIC_ECUDA;
+  if (h->cfg.spin_limit != cycles) {
+    // the step graphs hold the solve's parameters: capture them again
+    for (int k = 0; k < 2; ++k)
+      if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    h->graph[0] = h->graph[1] = nullptr;
+    h->graph_failed = false;
+  }
+  h->cfg.spin_limit = cycles;
   return PIC_OK;
 }
 

@@ -315,6 +315,8 @@ __global__ void k_circuit_prepare(const CircuitParams C) {
     o[48 + r] = r < n ? g[r] : 0.0;
   }
   o[54] = n;
+  // U_E = Q_E / C_eq (Eq. 5) with the C_eq this propagator was built for
+  S[SC_UE] = S[SC_QE] / ceq;
 }
 
 __global__ void k_circuit(const CircuitParams C) {

@@ -1153,7 +1153,11 @@ __device__ void pcg_mg_body(const S &sc, const PcgParams &P, const MgLevels &M) 
     P.out[3] = (double)outer;
     if (status == -4) atomicOr(P.flags, 0x4u);
     if (status == -7) atomicOr(P.flags, 0x8u);
-    *M.solves += 1;  // every block has read it (at setup, before the first barrier)
+    // Every block read the counter at setup, before its first barrier.  A
+    // failed solve may have left the global coarse levels half rebuilt: the
+    // next solve then rebuilds the hierarchy (counter 0).
+    if (status == 0) *M.solves += 1;
+    else *M.solves = 0;
   }
 }
 

@@ -3,13 +3,12 @@
 //
 // Some callers cannot allocate GPU memory at the point where they need a
 // field solve: an application whose device memory is owned by its own pool
-// allocator and that forbids allocations outside it, code that runs while a
-// stream is being captured into a CUDA graph (where allocation calls are not
-// allowed), or a plugin invoked from a real-time loop that must not block on
-// the allocator.  For them, pic_pcg_solve_static runs the same Jacobi PCG as
-// pic_field_solve on arrays they already own, and keeps its work vectors in
-// one fixed-size device array that lives in this library for the life of the
-// process (on every GPU that loads it).
+// allocator and that forbids allocations outside it, or a plugin invoked from
+// a real-time loop that must not block on the allocator.  For them,
+// pic_pcg_solve_static runs the same Jacobi PCG as pic_field_solve on arrays
+// they already own, and keeps its work vectors in one fixed-size device array
+// that lives in this library for the life of the process (on every GPU that
+// loads it).  pic_pcg_static_result reads back the last call's outcome.
 #include <cstdint>
 #include <mutex>
 
@@ -102,6 +101,23 @@ extern "C" int pic_pcg_solve_static(int32_t nr, int32_t nz, const int8_t *node_k
   P.spin_limit = 4000000000ll;
   if (pic::launch_pcg(P, grid, s) != cudaSuccess) return PIC_ECUDA;
   if (!iters && !rel_resid) return PIC_OK;
+  double res[3];
+  if (cudaMemcpyAsync(res, out, sizeof(res), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PIC_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+  if (iters) *iters = (int32_t)res[0];
+  if (rel_resid) *rel_resid = res[1];
+  int code = (int)res[2];
+  return code == 0 ? PIC_OK : (code == -5 ? PIC_ETIMEOUT : (code == -7 ? PIC_ENAN : PIC_ENOCONV));
+}
+
+// Outcome of the last pic_pcg_solve_static call on the current device, read
+// from the result slots of the shared work area after `cuda_stream` drains.
+extern "C" int pic_pcg_static_result(void *cuda_stream, int32_t *iters, double *rel_resid) {
+  double *base = nullptr;
+  int st = scratch_address(&base);
+  if (st) return st;
+  const double *out = base + kVecs * (size_t)PIC_STATIC_MAX_NODES + kPartial;
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   double res[3];
   if (cudaMemcpyAsync(res, out, sizeof(res), cudaMemcpyDeviceToHost, s) != cudaSuccess) return PIC_ECUDA;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;

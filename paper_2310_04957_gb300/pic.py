@@ -15,12 +15,17 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpic_gb300.so")
 
 PIC_OK = 0
-ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT", -6: "EOVERFLOW", -7: "ENAN"}
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT", -6: "EOVERFLOW", -7: "ENAN",
+          -8: "EIO"}
+PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ENOCONV, PIC_ETIMEOUT, PIC_EOVERFLOW, PIC_ENAN, PIC_EIO = range(-1, -9, -1)
+PIC_FLAG_OVERFLOW, PIC_FLAG_TIMEOUT, PIC_FLAG_NOCONV, PIC_FLAG_NAN = 0x1, 0x2, 0x4, 0x8
 PIC_FP32, PIC_FP64 = 0, 1
 PIC_SOLVER_PLAIN, PIC_SOLVER_MIXED, PIC_SOLVER_LEARNED, PIC_SOLVER_MG = 0, 1, 2, 3
 DIAG = {"phi": 0, "Er": 1, "Ez": 2, "chi": 3, "dep_e": 4, "dep_i": 5, "sigma": 6, "vnode": 7, "rho": 8,
         "ne_avg": 9, "ni_avg": 10, "phi_warm": 11}
 DIAG_SCALARS = 100
+DIAG_STORE = 101
+DIAG_SOLVER = 102
 NSCALARS = 47
 SCALARS = ["step", "t", "U_E", "Q_E", "C_eq", "I_conv", "I_ccp", "y0", "y1", "y2", "y3", "y4", "y5", "pcg_iters",
            "pcg_relres", "numax_e", "numax_i", "pcoll_e", "pcoll_i", "absq_e_pow", "absq_e_gnd", "absq_e_surf",
@@ -37,7 +42,8 @@ EXPORTS = ["pic_init", "pic_set_particles", "pic_count", "pic_get_particles", "p
            "pic_unet_forward", "pic_unet_backward", "pic_unet_adam", "pic_unet_status", "pic_conv3x3_op",
            "pic_conv3x3_op_ex", "pic_attach_unet", "pic_keep_warm", "pic_learned_pair", "pic_learned_stats",
            "pic_unet_loss_backward", "pic_learned_snapshot", "pic_batch_create", "pic_batch_step", "pic_batch_sync",
-           "pic_batch_destroy", "pic_set_solver"]
+           "pic_batch_destroy", "pic_set_solver", "pic_check", "pic_set_spin_limit", "pic_save", "pic_load",
+           "pic_pcg_static_result"]
 STATIC_MAX_NODES = 139264
 
 
@@ -61,6 +67,7 @@ class Config(ctypes.Structure):
         ("pcg_maxit", ctypes.c_int32), ("ceq_refresh", ctypes.c_int32), ("seed", ctypes.c_uint32),
         ("capacity", ctypes.c_int64 * 2), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
         ("tile_r", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("bin_slack", ctypes.c_double),
+        ("spin_limit", ctypes.c_int64),
     ]
 
 
@@ -102,6 +109,11 @@ def lib():
         L.pic_strerror.argtypes = [I]
         L.pic_strerror.restype = ctypes.c_char_p
         L.pic_destroy.argtypes = [P]
+        L.pic_pcg_static_result.argtypes = [P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(D)]
+        L.pic_check.argtypes = [P]
+        L.pic_set_spin_limit.argtypes = [P, ctypes.c_int64]
+        L.pic_save.argtypes = [P, ctypes.c_char_p]
+        L.pic_load.argtypes = [ctypes.c_char_p, P, ctypes.POINTER(P)]
         L.pic_pcg_solve_static.argtypes = [ctypes.c_int32, ctypes.c_int32, P, P, P, P, P, D, ctypes.c_int32, P,
                                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(D)]
         _lib = L
@@ -129,7 +141,7 @@ class Discharge:
     """One discharge on the current CUDA device (wraps a pic_handle)."""
 
     def __init__(self, wl, precision=PIC_FP32, solver=PIC_SOLVER_PLAIN, stream=None, tile=(0, 0), bin_slack=0.0,
-                 capacity=None, load=True):
+                 capacity=None, load=True, spin_limit=0):
         L = lib()
         self.wl = wl
         self.nr, self.nz = wl.nr, wl.nz
@@ -161,6 +173,7 @@ class Discharge:
         c.precision, c.solver = precision, solver
         c.tile_r, c.tile_z = tile
         c.bin_slack = bin_slack
+        c.spin_limit = spin_limit
         h = ctypes.c_void_p()
         _check(L.pic_init(ctypes.byref(c), _stream(stream), ctypes.byref(h)), "pic_init")
         self.h = h
@@ -235,6 +248,19 @@ class Discharge:
         v = np.ascontiguousarray(values, np.float64).ravel()
         _check(lib().pic_set_field(self.h, DIAG[name], _p(v), v.size), f"pic_set_field({name})")
 
+    def store_stats(self):
+        """Per species: particles in bins, in the overflow region, capacity, overflow start."""
+        o = np.zeros(8)
+        _check(lib().pic_diag(self.h, DIAG_STORE, _p(o), o.nbytes), "pic_diag(store)")
+        keys = ("in_bins", "overflow", "capacity", "overflow_start")
+        return [dict(zip(keys, o[4 * s:4 * s + 4].astype(np.int64).tolist())) for s in (0, 1)]
+
+    def solver_state(self):
+        """Multigrid solves counter, rebuild period, last iterations, outer steps, status."""
+        o = np.zeros(5)
+        _check(lib().pic_diag(self.h, DIAG_SOLVER, _p(o), o.nbytes), "pic_diag(solver)")
+        return dict(zip(("mg_solves", "rebuild_every", "iters", "outer", "status"), o.astype(np.int64).tolist()))
+
     def scalars(self):
         o = np.zeros(NSCALARS)
         _check(lib().pic_diag(self.h, DIAG_SCALARS, _p(o), o.nbytes), "pic_diag(scalars)")
@@ -262,6 +288,27 @@ class Discharge:
         f = ctypes.c_uint32()
         _check(lib().pic_status(self.h, ctypes.byref(f)), "pic_status")
         return f.value
+
+    def check(self):
+        """PIC_OK or the code of the most severe accumulated status bit (not cleared)."""
+        return lib().pic_check(self.h)
+
+    def set_spin_limit(self, cycles):
+        _check(lib().pic_set_spin_limit(self.h, int(cycles)), "pic_set_spin_limit")
+
+    def save(self, path):
+        _check(lib().pic_save(self.h, os.fsencode(path)), "pic_save")
+
+    @classmethod
+    def load(cls, path, wl, stream=None):
+        """Restore a discharge written by save(); `wl` (the workload it was made
+        from) only supplies the grid shape and inputs for reference."""
+        h = ctypes.c_void_p()
+        _check(lib().pic_load(os.fsencode(path), _stream(stream), ctypes.byref(h)), "pic_load")
+        d = cls.__new__(cls)
+        d.wl, d.nr, d.nz, d.h = wl, wl.nr, wl.nz, h
+        d.capacity = tuple(wl.capacity)
+        return d
 
     def philox(self, ctr, key):
         ctr = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
@@ -313,16 +360,26 @@ class Discharge:
         return o
 
 
-def pcg_solve_static(nr, nz, node_kind, Gr, Gz, qrhs, phi, tol, maxit, stream=None):
+def pcg_solve_static(nr, nz, node_kind, Gr, Gz, qrhs, phi, tol, maxit, stream=None, wait=True):
     """Call pic_pcg_solve_static on caller-owned device arrays (raw device pointers as ints).
 
-    The library allocates nothing for this solve; it returns (status, iterations,
-    relative residual) after synchronising the stream."""
+    The library allocates nothing for this solve.  wait=True: returns (status,
+    iterations, relative residual) after synchronising the stream; wait=False:
+    only enqueues it (NULL outputs) and returns (status of the enqueue, None, None);
+    pcg_static_result() reads the outcome later."""
     it = ctypes.c_int32()
     rr = ctypes.c_double()
+    outs = (ctypes.byref(it), ctypes.byref(rr)) if wait else (None, None)
     st = lib().pic_pcg_solve_static(nr, nz, ctypes.c_void_p(node_kind), ctypes.c_void_p(Gr), ctypes.c_void_p(Gz),
-                                    ctypes.c_void_p(qrhs), ctypes.c_void_p(phi), tol, maxit, _stream(stream),
-                                    ctypes.byref(it), ctypes.byref(rr))
+                                    ctypes.c_void_p(qrhs), ctypes.c_void_p(phi), tol, maxit, _stream(stream), *outs)
+    return (st, it.value, rr.value) if wait else (st, None, None)
+
+
+def pcg_static_result(stream=None):
+    """(status, iterations, relative residual) of the last pic_pcg_solve_static call."""
+    it = ctypes.c_int32()
+    rr = ctypes.c_double()
+    st = lib().pic_pcg_static_result(_stream(stream), ctypes.byref(it), ctypes.byref(rr))
     return st, it.value, rr.value
 
 

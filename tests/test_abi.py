@@ -39,3 +39,17 @@ def test_strerror_without_gpu():
     build.build()
     assert pic.lib().pic_strerror(-4) == b"field solve did not converge within its iteration cap"
     assert pic.lib().pic_strerror(0) == b"ok"
+
+
+def test_load_rejects_missing_and_foreign_files(tmp_path):
+    """pic_load checks the file before it touches a GPU: a missing file and a
+    file that is not a restart file both give PIC_EIO."""
+    from paper_2310_04957_gb300 import build, pic
+
+    build.build()
+    h = ctypes.c_void_p()
+    L = pic.lib()
+    assert L.pic_load(str(tmp_path / "none").encode(), None, ctypes.byref(h)) == pic.PIC_EIO
+    (tmp_path / "junk").write_bytes(b"not a restart file" * 10)
+    assert L.pic_load(str(tmp_path / "junk").encode(), None, ctypes.byref(h)) == pic.PIC_EIO
+    assert L.pic_strerror(pic.PIC_EIO).startswith(b"restart file")

@@ -71,7 +71,7 @@ def test_learned_pair_definition():
     kind = wl.node_kind[:H, :Wd]
     free = kind == 0
     assert s > 0
-    assert np.sqrt(np.mean(x[0][free] ** 2)) == pytest.approx(1.0, rel=1e-5)
+    assert np.sqrt(np.mean(x[0][free] ** 2)) == pytest.approx(1.0, rel=1e-5, abs=0)
     np.testing.assert_array_equal(x[2], (kind != 0).astype(np.float64))
     assert np.all(x[0][~free] == 0) and np.all(t[~free] == 0)
     np.testing.assert_allclose(x[1], d.field("chi")[:H, :Wd].astype(np.float32), rtol=0, atol=0)

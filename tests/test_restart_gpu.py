@@ -1,0 +1,74 @@
+"""Checkpoint and resume (pic_save / pic_load) through the C ABI: k steps,
+save, k more steps equals load + k steps, bit for bit, in FP64 and FP32, on
+the GEC-like cell with the matching network.  The span crosses RF-window ends
+(C_eq refresh) and a rebuild of the multigrid hierarchy, so the state that
+carries over between steps (circuit, C_eq, surface charge, window sums,
+multigrid hierarchy, particle store with its overflow region) is all covered.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+from gpu_common import pic
+from parity_tools import by_id
+from paper_2310_04957_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("phi", "Er", "Ez", "chi", "dep_e", "dep_i", "sigma", "rho", "ne_avg", "ni_avg")
+
+
+def snapshot(d):
+    out = {f"p{s}": by_id(d.get_particles(s)) for s in (0, 1)}
+    for f in FIELDS:
+        out[f] = d.field(f)
+    out["scalars"] = d.scalars()
+    out["store"] = d.store_stats()
+    return out
+
+
+@pytest.mark.parametrize("precision", [1, 0], ids=["fp64", "fp32"])
+def test_save_load_continues_bit_for_bit(precision, tmp_path):
+    P = pic()
+    wl = dataclasses.replace(W.gec_case(128, 64, 30.0, 150.0, n_per_species=100_000, seed_index=22),
+                             steps_per_rf=5, phase_src=0.4)
+    d = P.Discharge(wl, precision=precision, solver=P.PIC_SOLVER_MG, bin_slack=0.05)
+    d.start()
+    d.step(8)
+    path = str(tmp_path / "state.picrst")
+    d.save(path)
+    d.step(8)
+    a = snapshot(d)
+    d.close()
+    e = P.Discharge.load(path, wl)
+    e.step(8)
+    b = snapshot(e)
+    assert a["scalars"]["windows"] == 3
+    for s in (0, 1):
+        for k, v in a[f"p{s}"].items():
+            assert np.array_equal(v, b[f"p{s}"][k]), (s, k)
+    for f in FIELDS:
+        assert np.array_equal(a[f], b[f], equal_nan=True), f
+    for k, v in a["scalars"].items():
+        assert v == b["scalars"][k] or (np.isnan(v) and np.isnan(b["scalars"][k])), (k, v, b["scalars"][k])
+    assert e.status() == 0
+    e.close()
+
+
+def test_load_rejects_truncated_file(tmp_path):
+    P = pic()
+    wl = W.gec_case(64, 32, 30.0, 150.0, n_per_species=10_000)
+    d = P.Discharge(wl)
+    d.start()
+    path = tmp_path / "state.picrst"
+    d.save(str(path))
+    raw = path.read_bytes()
+    (tmp_path / "cut").write_bytes(raw[: len(raw) // 2])
+    with pytest.raises(P.PicError) as ei:
+        P.Discharge.load(str(tmp_path / "cut"), wl)
+    assert ei.value.code == P.PIC_EIO
+    (tmp_path / "long").write_bytes(raw + b"x")
+    with pytest.raises(P.PicError) as ei:
+        P.Discharge.load(str(tmp_path / "long"), wl)
+    assert ei.value.code == P.PIC_EIO

@@ -1,14 +1,14 @@
 """The allocation-free field solve, pic_pcg_solve_static.
 
 Callers that cannot allocate GPU memory at solve time (a host application that
-owns all device memory through its own pool, code running during CUDA-graph
-stream capture, a real-time loop that must not wait on the allocator) use this
-entry point on arrays they own.  This file checks, through the C ABI, that it
-returns the same potential as the handle-based pic_field_solve, within the
-tolerance the other field-solve tests use, on two calls in a row (the second
-call runs on the work array the first one left behind).  It sits last in the
-collection order so that a failure here stops a -x run only after every other
-test has run.
+owns all device memory through its own pool, a real-time loop that must not
+wait on the allocator) use this entry point on arrays they own.  This file
+checks, through the C ABI, that it returns the same potential as the
+handle-based pic_field_solve, within the tolerance the other field-solve tests
+use, on two calls in a row (the second call runs on the work array the first
+one left behind), and that a call that only enqueues the solve reports its
+outcome through pic_pcg_static_result.  It sits last in the collection order
+so that a failure here stops a -x run only after every other test has run.
 """
 import dataclasses
 
@@ -63,6 +63,16 @@ def test_static_solve_matches_field_solve_twice():
         assert rel <= wl.pcg_tol
         assert abs(it - it_ref) <= max(3, 0.05 * it_ref)
         assert rel_l2(phi.cpu().numpy().reshape(phi_ref.shape), phi_ref) <= 1e-8
+        # the same solve enqueued without waiting: the result slots report it
+        phi2 = _device(o.field("phi"), torch, torch.float64)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream().cuda_stream
+        st, _, _ = P.pcg_solve_static(wl.nr, wl.nz, kind.data_ptr(), g_r.data_ptr(), g_z.data_ptr(), q.data_ptr(),
+                                      phi2.data_ptr(), wl.pcg_tol, wl.pcg_maxit, stream=stream, wait=False)
+        assert st == 0
+        st, it2, rel2 = P.pcg_static_result(stream=stream)
+        assert st == 0 and it2 == it and rel2 == rel
+        assert torch.equal(phi2, phi)
 
 
 def test_static_solve_rejects_oversized_grids():
