@@ -87,6 +87,7 @@ def lib():
         L.orc_scatter_cos.restype = ctypes.c_double
         L.orc_turn.argtypes = [P, ctypes.c_double, ctypes.c_double]
         L.orc_trace.argtypes = [P, ctypes.c_int, P]
+        L.orc_circuit_diag.argtypes = [P, P]
         L.orc_child_ids.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, P, P]
         _lib = L
     return _lib
@@ -110,6 +111,16 @@ def philox(ctr, key):
     o = np.zeros(4, np.uint32)
     lib().orc_philox(_p(c), _p(k), _p(o))
     return o
+
+
+CIRCUIT_KEYS = ("z_ccp", "z_load", "gamma", "gamma_abs", "p_source", "p_rs", "p_series", "p_stray", "p_ccp",
+                "p_forward", "p_ref", "u1")
+
+
+def circuit_dict(o):
+    return {"z_ccp": complex(o[0], o[1]), "z_load": complex(o[2], o[3]), "gamma": complex(o[4], o[5]),
+            "gamma_abs": o[6], "p_source": o[7], "p_rs": o[8], "p_series": o[9], "p_stray": o[10], "p_ccp": o[11],
+            "p_forward": o[12], "p_ref": o[13], "u1": complex(o[14], o[15])}
 
 
 def child_ids(step, seed, parents):
@@ -283,6 +294,12 @@ class Oracle:
 
     def xs(self, proc, E):
         return lib().orc_xs(self.h, proc, float(E))
+
+    def circuit_diag(self):
+        """Circuit post-processing of the last closed window (Eqs. 11-14), as a dict."""
+        o = np.zeros(16)
+        lib().orc_circuit_diag(self.h, _p(o))
+        return circuit_dict(o)
 
     def trace(self, enable):
         """Decision-margin tracing: enable=True resets and starts recording,

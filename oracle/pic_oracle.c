@@ -132,6 +132,12 @@ struct orc_sim {
   double ion_q_sum[3], ion_cur_avg[3];
   double dft_re, dft_im, i1_re, i1_im;
   int win_count, windows_done;
+  /* circuit post-processing over the window (Sec. 3, Eqs. 11-14): first-harmonic
+   * DFT sums of five waveforms (U_s, source-loop current I_1, matching-network
+   * input voltage U_in, U_E = U_ccp, I_ccp) and sums of the five powers U_s I_1,
+   * R_s I_1^2, series-element loss, stray-branch loss, U_ccp I_ccp, U_in I_1 */
+  double cw_re[5], cw_im[5], cp_sum[6];
+  double circ_out[16];
   /* decision margins (test instrumentation, see orc_trace): [0] random-number
    * and energy thresholds, relative; [1] position tests, cell units; [2]
    * conditioning of the predictor's rotation angle */
@@ -978,6 +984,73 @@ static int field_solve(orc_sim *s) {
   return st;
 }
 
+/* The waveforms and element powers of the circuit at t_{n+1} (Sec. 3): the
+ * source voltage U_s, the current I_1 leaving the source, the voltage U_in at
+ * the matching network's input (after R_s), U_E = U_ccp and I_ccp; powers
+ * U_s I_1, R_s I_1^2, the series element's loss (R_m I_2^2 in circuit II,
+ * R_b I_b^2 in circuit I), the stray branch's loss R_stray I_stray^2,
+ * U_ccp I_ccp and U_in I_1. */
+static void circuit_waveforms(const orc_sim *s, double t1, double w[5], double p[6]) {
+  const orc_setup *c = &s->cfg;
+  double Us = source_voltage(c, t1);
+  for (int k = 0; k < 6; ++k) p[k] = 0.0;
+  if (c->circuit == ORC_CIRCUIT_IMN) {
+    double Rs = c->circ[0], Cm1 = c->circ[1], Rm = c->circ[4], Rst = c->circ[6];
+    double Uin = (s->y[0] - s->y[1]) / Cm1;
+    double I1 = (Us - Uin) / Rs;
+    double I2 = s->y[2], Ist = s->y[4];
+    w[0] = Us; w[1] = I1; w[2] = Uin;
+    p[1] = Rs * I1 * I1;
+    p[2] = Rm * I2 * I2;
+    p[3] = Rst * Ist * Ist;
+    p[5] = Uin * I1;
+    p[0] = Us * I1;
+  } else if (c->circuit == ORC_CIRCUIT_RLC) {
+    double Ib = s->y[1];
+    w[0] = Us; w[1] = Ib; w[2] = Us;
+    p[0] = Us * Ib;
+    p[2] = c->circ[0] * Ib * Ib;
+    p[5] = Us * Ib;
+  } else {
+    w[0] = s->U_E; w[1] = s->I_ccp; w[2] = s->U_E;
+    p[0] = p[5] = s->U_E * s->I_ccp;
+  }
+  w[3] = s->U_E;
+  w[4] = s->I_ccp;
+  p[4] = s->U_E * s->I_ccp;
+}
+
+/* Close the circuit window (Sec. 3): Z = U_1 / I_1 of the fundamental
+ * (Eq. 11: modulus ratio and phase difference of the two first harmonics),
+ * Gamma = (Z_load - R_s) / (Z_load + R_s) (Eq. 12), period-averaged powers
+ * (Eq. 13) and P_ref = P_forward |Gamma|^2 (Eq. 14) with P_forward the power
+ * into the matching network's input. */
+static void circuit_window(orc_sim *s, int N) {
+  double Ur = s->cw_re[3], Ui = s->cw_im[3], Ir = s->cw_re[4], Ii = s->cw_im[4];
+  double den = Ir * Ir + Ii * Ii;
+  double zc_re = den > 0 ? (Ur * Ir + Ui * Ii) / den : 0.0, zc_im = den > 0 ? (Ui * Ir - Ur * Ii) / den : 0.0;
+  Ur = s->cw_re[2]; Ui = s->cw_im[2]; Ir = s->cw_re[1]; Ii = s->cw_im[1];
+  den = Ir * Ir + Ii * Ii;
+  double zl_re = den > 0 ? (Ur * Ir + Ui * Ii) / den : 0.0, zl_im = den > 0 ? (Ui * Ir - Ur * Ii) / den : 0.0;
+  double g_re = 0.0, g_im = 0.0;
+  if (s->cfg.circuit == ORC_CIRCUIT_IMN) {
+    double Rs = s->cfg.circ[0];
+    double nr = zl_re - Rs, ni = zl_im, dr = zl_re + Rs, di = zl_im;
+    double dd = dr * dr + di * di;
+    g_re = (nr * dr + ni * di) / dd;
+    g_im = (ni * dr - nr * di) / dd;
+  }
+  double g2 = g_re * g_re + g_im * g_im;
+  double *o = s->circ_out;
+  o[0] = zc_re; o[1] = zc_im; o[2] = zl_re; o[3] = zl_im; o[4] = g_re; o[5] = g_im; o[6] = sqrt(g2);
+  for (int k = 0; k < 6; ++k) o[7 + k] = s->cp_sum[k] / N;
+  o[13] = o[12] * g2;
+  o[14] = 2.0 * s->cw_re[3] / N; /* first harmonic of U_E */
+  o[15] = 2.0 * s->cw_im[3] / N;
+  for (int k = 0; k < 5; ++k) s->cw_re[k] = s->cw_im[k] = 0.0;
+  for (int k = 0; k < 6; ++k) s->cp_sum[k] = 0.0;
+}
+
 static void diag_accumulate(orc_sim *s) {
   const orc_setup *c = &s->cfg;
   for (int spc = 0; spc < 2; ++spc)
@@ -988,6 +1061,13 @@ static void diag_accumulate(orc_sim *s) {
   double ph = TWO_PI * c->f_src * t1;
   s->dft_re += s->I_ccp * cos(ph);
   s->dft_im -= s->I_ccp * sin(ph);
+  double w[5], p[6];
+  circuit_waveforms(s, t1, w, p);
+  for (int k = 0; k < 5; ++k) {
+    s->cw_re[k] += w[k] * cos(ph);
+    s->cw_im[k] -= w[k] * sin(ph);
+  }
+  for (int k = 0; k < 6; ++k) s->cp_sum[k] += p[k];
   s->win_count++;
   if (s->win_count == c->steps_per_rf) {
     int N = s->win_count;
@@ -997,6 +1077,7 @@ static void diag_accumulate(orc_sim *s) {
     s->i1_re = 2.0 * s->dft_re / N;
     s->i1_im = 2.0 * s->dft_im / N;
     s->dft_re = s->dft_im = 0.0;
+    circuit_window(s, N);
     s->win_count = 0;
     s->windows_done++;
   }
@@ -1294,6 +1375,16 @@ void orc_child_ids(uint32_t step, uint32_t seed, int64_t n, const uint64_t *pare
   }
 }
 
+/* Circuit post-processing of the last closed window (Sec. 3, Eqs. 11-14):
+ * [0..1] Z_ccp, [2..3] Z_load (ohm, Re/Im), [4..5] Gamma, [6] |Gamma|,
+ * [7] P_source, [8] P_Rs, [9] series-element loss (P_IMN; R_b in circuit I),
+ * [10] P_stray, [11] P_ccp, [12] P_forward, [13] P_ref (W), [14..15] first
+ * harmonic of U_E (V, Re/Im). */
+int orc_circuit_diag(const orc_sim *s, double *out16) {
+  for (int k = 0; k < 16; ++k) out16[k] = s->circ_out[k];
+  return ORC_OK;
+}
+
 /* Test hooks. */
 void orc_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out) { philox4x32_10(ctr, key, out); }
 double orc_xs(const orc_sim *s, int proc, double E) { return xs_lookup(s, proc, E); }
@@ -1305,6 +1396,7 @@ void orc_turn(double *c, double cc, double phi) { turn(c, cc, phi); }
 int orc_circuit_run(orc_sim *s, int n, double *U_out) {
   for (int k = 0; k < n; ++k) {
     circuit_advance(s);
+    diag_accumulate(s);
     s->step++;
     if (U_out) U_out[k] = s->U_E;
   }

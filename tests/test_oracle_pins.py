@@ -816,3 +816,94 @@ def test_chi_filled_coaxial_capacitor():
     c_chi, g_chi = o.ceq(with_chi=True)
     assert c_chi == pytest.approx(want, rel=1e-10, abs=0)
     assert g_chi == pytest.approx(c_chi, rel=1e-8, abs=0)
+
+
+# ---------------------------------------------------------------- circuit post-processing
+def _paper_vacuum_circuit():
+    g = {}
+    for line in open(os.path.join(GOLDEN, "paper_circuit2_vacuum.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            g[k] = float(v)
+    return g
+
+
+def _phasor_circuit_ii(g, C_load):
+    """Steady state of circuit II (Eq. 10's network) with a capacitive load C_load by complex
+    impedances: source V (amplitude) and R_s, shunt C_m1, series R_m + L_m + C_m2, then the
+    stray branch (R, L, C) in parallel with the load.  Returns the currents, voltages, the
+    impedances Z_ccp and Z_load, Gamma and the period-averaged powers 1/2 Re(U I*)."""
+    w = 2 * math.pi * g["f"]
+    zc = lambda C: 1 / (1j * w * C)
+    z_ccp = zc(C_load)
+    z_st = g["R_stray"] + 1j * w * g["L_stray"] + zc(g["C_stray"])
+    z_b = 1 / (1 / z_ccp + 1 / z_st)
+    z_a = g["R_m"] + 1j * w * g["L_m"] + zc(g["C_m2"]) + z_b
+    z_load = 1 / (1 / zc(g["C_m1"]) + 1 / z_a)
+    V = g["V_source"]
+    I1 = V / (g["R_s"] + z_load)
+    Uin = I1 * z_load
+    I2 = Uin / z_a
+    Ub = I2 * z_b
+    Iccp, Ist = Ub / z_ccp, Ub / z_st
+    gamma = (z_load - g["R_s"]) / (z_load + g["R_s"])
+    P = lambda U, I: 0.5 * (U * I.conjugate()).real
+    pf = P(Uin, I1)
+    # the time-domain state at t = 0 of Eq. 10 (Q_1, Q_2, I_2, Q_ccp, I_stray, Q_E) for a
+    # source V sin(w t) = Re(-j V e^{jwt}): x(0) = Re(X) with X the phasor, charge = current / (j w)
+    s = -1j  # phasors above are for a source V e^{jwt}; a sine source multiplies them by -j
+    q = lambda I: (s * I / (1j * w)).real
+    y0 = np.array([q(I1), q(I2), (s * I2).real, q(Iccp), (s * Ist).real, q(Iccp)])
+    return dict(z_ccp=z_ccp, z_load=z_load, gamma=gamma, Ub=Ub, p_source=P(V, I1), p_rs=0.5 * g["R_s"] * abs(I1) ** 2,
+                p_series=0.5 * g["R_m"] * abs(I2) ** 2, p_stray=0.5 * g["R_stray"] * abs(Ist) ** 2, p_ccp=P(Ub, Iccp),
+                p_forward=pf, p_ref=pf * abs(gamma) ** 2, y0=y0)
+
+
+def _vacuum_match_run(g, ref, n_sub, periods=5):
+    base = W.small_cylinder(n_per_species=16)
+    circ = (g["R_s"], g["C_m1"], g["L_m"], g["C_m2"], g["R_m"], g["C_stray"], g["R_stray"], g["L_stray"])
+    wl = dataclasses.replace(with_particles(base), circuit=W.CIRCUIT_IMN, circ=circ, V_src=g["V_source"],
+                             f_src=g["f"], phase_src=0.0, steps_per_rf=200, dt=1 / g["f"] / 200, ceq_refresh=0,
+                             n_sub=n_sub)
+    o = orc.Oracle(wl)
+    o.set_ceq(g["C_eq"])
+    o.set_circuit_state(ref["y0"])
+    o.set_conv_current(0.0)
+    o.set_step(0)
+    out = []
+    for _ in range(periods):
+        o.circuit_run(wl.steps_per_rf)
+        out.append(o.circuit_diag())
+    return out
+
+
+def test_circuit_postprocessing_matches_phasor_solution_of_the_vacuum_match():
+    """Circuit II loaded by the paper's vacuum C_eq = 892.07 pF with its matching network
+    (golden fixture, Sec. 3), driven at 77 V from its periodic steady state: the window's
+    post-processing -- Z = U_1/I_1 of the fundamental (Eq. 11), Gamma (Eq. 12), the
+    period-averaged element powers (Eq. 13) and P_ref = P_forward |Gamma|^2 (Eq. 14) -- equals
+    the complex-impedance solution of the same network up to the trapezoidal rule's O(h^2)
+    error, which falls 16x when the substeps go from 16 to 64.  Z_ccp = -j / (w C_eq) =
+    -j 13.157 ohm (Table 1's reactance) and the electrode amplitude is ~100 V as the paper
+    states.  Had the circuit equations or the post-processing a wrong term, the run would
+    neither stay periodic nor converge to the network solution."""
+    g = _paper_vacuum_circuit()
+    ref = _phasor_circuit_ii(g, g["C_eq"])
+    coarse, fine = _vacuum_match_run(g, ref, 16), _vacuum_match_run(g, ref, 64)
+    b = fine[-1]
+    assert abs(b["z_ccp"] - fine[-2]["z_ccp"]) <= 1e-7 * abs(b["z_ccp"])  # periodic
+    e16, e64 = abs(coarse[-1]["z_load"] - ref["z_load"]), abs(b["z_load"] - ref["z_load"])
+    assert 12 < e16 / e64 < 20, (e16, e64)  # second order in the substep
+    assert abs(b["z_ccp"] - ref["z_ccp"]) <= 1e-7 * abs(ref["z_ccp"])
+    assert abs(b["z_ccp"].imag + 13.157) < 5e-4 and abs(b["z_ccp"].real) < 1e-5
+    assert e64 <= 1e-4
+    assert abs(b["gamma"] - ref["gamma"]) <= 1e-6
+    assert abs(ref["gamma"]) < 1e-3  # the paper's matching is nearly perfect in vacuum
+    for k in ("p_source", "p_rs", "p_series", "p_stray", "p_forward"):
+        assert b[k] == pytest.approx(ref[k], rel=1e-6, abs=0), k
+    assert abs(b["p_ccp"]) <= 1e-6 * b["p_source"]  # a capacitor takes no active power
+    assert b["p_ref"] == pytest.approx(b["p_forward"] * b["gamma_abs"] ** 2, rel=1e-12, abs=0)
+    # energy balance over a period: what the source delivers is dissipated in the elements
+    assert b["p_source"] == pytest.approx(b["p_rs"] + b["p_series"] + b["p_stray"] + b["p_ccp"], rel=1e-6, abs=0)
+    assert abs(b["u1"]) == pytest.approx(abs(ref["Ub"]), rel=1e-6, abs=0)
+    assert abs(b["u1"]) == pytest.approx(g["U_electrode_amplitude"], rel=5e-3, abs=0)
