@@ -2,8 +2,9 @@
 
 One step = the whole hot path: bin layout, fused particle kernel (gather, D1
 push, null-collision MCC, re-bin, deposit), circuit, assembly, field solve,
-E field, diagnostics.  Workload (default): the 256x128 GEC-like cell with
-4 M electrons + 4 M Ar+ (10 mTorr, 150 V through the L-network), synthetic
+E field, diagnostics.  Workload (default): the 512x256 GEC-like cell with
+32 M electrons + 32 M Ar+ (30 mTorr, 150 V through the L-network), the largest
+single-GPU configuration; c2 is the 256x128 cell with 4 M + 4 M.  Synthetic
 seeded inputs.  Prints one JSON line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -29,7 +30,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "particle-steps/s (push+MCC+deposit); field-solve ms to 1e-10 residual, vs plain"
-BYTES_PER_PARTICLE_STEP = {"fp32": 80, "fp64": 144}  # state read once + written once
+# Algorithmic bytes per particle-step of the particle kernel: the state read once
+# and written once.  The roofline uses the hot-path scope's figure, 2 x 44 B in FP32
+# (eight FP32 state words, a 64-bit id and a 32-bit cell index); this store keeps the
+# cell implicit in the particle's bin, so the kernel itself moves 2 x 40 B.
+BYTES_PER_PARTICLE_STEP = {"fp32": 88, "fp64": 152}
+STORED_BYTES_PER_PARTICLE_STEP = {"fp32": 80, "fp64": 144}
 KERNELS_PER_STEP = 10  # layout x3, particles, circuit, assemble x2, solve, efield, diag
 KERNELS_PER_WINDOW = 6  # diag window, C_eq refresh (edges, dirichlet, solve, energy), circuit propagator
 
@@ -40,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--workload", default="c3", choices=["c1", "c2", "c3", "c4", "selfbias"])
+    ap.add_argument("--periods", type=int, default=50, help="RF periods per amplitude (--workload selfbias)")
     ap.add_argument("--solver", default="mg", choices=["plain", "mixed", "mg"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-e2e", action="store_true")
@@ -245,14 +252,16 @@ def field_solve_comparison(wl, steps=5):
     d.keep_warm(True)
     modes = (pic.PIC_SOLVER_PLAIN, pic.PIC_SOLVER_MIXED, pic.PIC_SOLVER_MG)
     rows = {m: [] for m in modes}
-    rows["learned_mixed"], rows["learned_mg"] = [], []
+    rows["learned_mixed"], rows["learned_mg"], rows["learned_mg_guess"] = [], [], []
     for _ in range(steps):
         d.step(1)
         r = Lr.compare_solvers(d, modes=modes, repeats=2)
         for m in modes:
             rows[m].append(r[m])
-        for key, fin in (("learned_mixed", pic.PIC_SOLVER_MIXED), ("learned_mg", pic.PIC_SOLVER_MG)):
-            d.attach_unet(net, maxit=3, finish=fin)
+        # up to 3 network applications, or one (the learned initial guess alone)
+        for key, fin, apps in (("learned_mixed", pic.PIC_SOLVER_MIXED, 3), ("learned_mg", pic.PIC_SOLVER_MG, 3),
+                               ("learned_mg_guess", pic.PIC_SOLVER_MG, 1)):
+            d.attach_unet(net, maxit=apps, finish=fin)
             rows[key].append(Lr.compare_solvers(d, modes=(pic.PIC_SOLVER_LEARNED,), repeats=2)[pic.PIC_SOLVER_LEARNED])
     med = lambda m, k: statistics.median(x[k] for x in rows[m])
     out = {"tol": wl.pcg_tol, "steps": steps,
@@ -260,12 +269,14 @@ def field_solve_comparison(wl, steps=5):
            "mixed": {"ms": med(1, 3), "inner_iters": med(1, 1)},
            "mg": {"ms": med(3, 3), "inner_iters": med(3, 1)},
            "training": info}
-    for key in ("learned_mixed", "learned_mg"):
+    for key in ("learned_mixed", "learned_mg", "learned_mg_guess"):
         out[key] = {"ms": med(key, 3), "network_applications": statistics.median(x[4][0] for x in rows[key]),
                     "finisher_inner_iters": med(key, 1), "max_rel_residual": max(x[2] for x in rows[key])}
     out["learned_vs_plain"] = out["plain"]["ms"] / out["learned_mixed"]["ms"]
     out["learned_vs_mixed"] = out["mixed"]["ms"] / out["learned_mixed"]["ms"]
     out["mg_vs_plain"] = out["plain"]["ms"] / out["mg"]["ms"]
+    out["learned_mg_vs_mg"] = out["mg"]["ms"] / out["learned_mg"]["ms"]
+    out["learned_guess_vs_mg"] = out["mg"]["ms"] / out["learned_mg_guess"]["ms"]
     d.close()
     net.close()
     return out
@@ -363,12 +374,58 @@ def run_sweep(args):
     return 0
 
 
+def run_selfbias(args):
+    """Circuit I (Eq. 9) self-bias study, the analogue of Sec. 3's Fig. 2 on synthetic
+    cross sections: the GEC-like cell at 128x64 and 100 mTorr, 200 k + 200 k particles,
+    the source coupled through R_b = 0.5 ohm, L_b = 0.01 uH and the 5 nF blocking capacitor;
+    for each source amplitude the discharge runs `--periods` RF periods and the last window's
+    mean electrode potential (the DC self-bias) and mean electron density are reported."""
+    import dataclasses
+
+    import torch
+
+    from paper_2310_04957_gb300 import build
+
+    build.build()
+    from paper_2310_04957_gb300 import pic
+    from paper_2310_04957_gb300 import workloads as W
+
+    rows, t_all = [], 0.0
+    for V in (50.0, 100.0, 150.0, 200.0, 250.0, 300.0):
+        wl = W.gec_case(128, 64, 100.0, V, n_per_species=200_000, seed_index=31)
+        wl = dataclasses.replace(wl, circuit=W.CIRCUIT_RLC, circ=(0.5, 0.01e-6, 5e-9, 0, 0, 0, 0, 0))
+        d = pic.Discharge(wl, solver=pic.PIC_SOLVER_MG)
+        d.start()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        d.step(args.periods * wl.steps_per_rf)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        t_all += t
+        c = d.circuit_diag()
+        ne = d.field("ne_avg")
+        rows.append({"V": V, "self_bias_V": c["u_dc"], "u1_amplitude_V": abs(c["u1"]),
+                     "ne_mean_m3": float(ne[ne > 0].mean()), "electrons": d.count(0), "seconds": t,
+                     "status": d.status()})
+        d.close()
+    steps = args.periods * 200 * len(rows)
+    line = {"metric": "DC self-bias vs source amplitude, circuit I", "value": rows[-1]["self_bias_V"], "unit": "V",
+            "n_gpus": 1, "steps": steps, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "gec-128x64-100mT-circuitI", "periods": args.periods, "rows": rows},
+            "ms_per_step": 1e3 * t_all / steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "c4":
         return run_sweep(args)
+    if args.workload == "selfbias":
+        return run_selfbias(args)
     rank, world, local = dist_env()
     import torch
 
@@ -482,7 +539,8 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "k_particles", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
                          "traffic": traffic["bytes"] / traffic["particles"] * n_avg if traffic else None,
-                         "bytes_per_particle_step": bpp},
+                         "bytes_per_particle_step": bpp,
+                         "stored_bytes_per_particle_step": STORED_BYTES_PER_PARTICLE_STEP[args.precision]},
             "phases_ms": {"layout": phases[0] / args.steps, "particles": k_ms, "circuit": phases[2] / args.steps,
                           "assembly": phases[3] / args.steps, "field_solve": phases[4] / args.steps,
                           "efield": phases[5] / args.steps, "diag": phases[6] / args.steps},

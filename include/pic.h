@@ -198,6 +198,23 @@ int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss);
                                 overflow region (those that did not fit their
                                 bin at the last re-bin), capacity, first slot
                                 of the overflow region */
+#define PIC_DIAG_CIRCUIT 103 /* 18 doubles, circuit post-processing of the last
+                                RF window (Sec. 3): [0..1] Z_ccp = U_E,1 / I_ccp,1
+                                and [2..3] Z_load = U_in,1 / I_1,1 (ohm, Re, Im;
+                                first harmonics by DFT over the window, Eq. 11;
+                                U_in is the voltage after the source resistance,
+                                I_1 the source current), [4..5] Gamma =
+                                (Z_load - R_s)/(Z_load + R_s) (Eq. 12; circuit II
+                                only), [6] |Gamma|, window-averaged powers
+                                (Eq. 13, W): [7] source U_s I_1, [8] R_s, [9] the
+                                series element (R_m of the matching network; R_b
+                                in circuit I), [10] stray branch, [11] plasma load
+                                U_E I_ccp, [12] forward (U_in I_1), [13] reflected
+                                P_forward |Gamma|^2 (Eq. 14); [14..15] first
+                                harmonic of U_E (V); [16] mean U_E over the
+                                window, the DC self-bias of Sec. 3's circuit I
+                                (V); [17] mean I_ccp (A).  Direct drive: U_s =
+                                U_in = U_E and I_1 = I_ccp. */
 #define PIC_DIAG_SOLVER 102  /* 5 doubles: multigrid solves counter (the next
                                 PIC_SOLVER_MG solve rebuilds the coarse
                                 hierarchy when it is a multiple of [1], else

@@ -120,7 +120,7 @@ CIRCUIT_KEYS = ("z_ccp", "z_load", "gamma", "gamma_abs", "p_source", "p_rs", "p_
 def circuit_dict(o):
     return {"z_ccp": complex(o[0], o[1]), "z_load": complex(o[2], o[3]), "gamma": complex(o[4], o[5]),
             "gamma_abs": o[6], "p_source": o[7], "p_rs": o[8], "p_series": o[9], "p_stray": o[10], "p_ccp": o[11],
-            "p_forward": o[12], "p_ref": o[13], "u1": complex(o[14], o[15])}
+            "p_forward": o[12], "p_ref": o[13], "u1": complex(o[14], o[15]), "u_dc": o[16], "i_dc": o[17]}
 
 
 def child_ids(step, seed, parents):
@@ -297,7 +297,7 @@ class Oracle:
 
     def circuit_diag(self):
         """Circuit post-processing of the last closed window (Eqs. 11-14), as a dict."""
-        o = np.zeros(16)
+        o = np.zeros(18)
         lib().orc_circuit_diag(self.h, _p(o))
         return circuit_dict(o)
 

@@ -136,8 +136,8 @@ struct orc_sim {
    * DFT sums of five waveforms (U_s, source-loop current I_1, matching-network
    * input voltage U_in, U_E = U_ccp, I_ccp) and sums of the five powers U_s I_1,
    * R_s I_1^2, series-element loss, stray-branch loss, U_ccp I_ccp, U_in I_1 */
-  double cw_re[5], cw_im[5], cp_sum[6];
-  double circ_out[16];
+  double cw_re[5], cw_im[5], cp_sum[6], cdc[2];
+  double circ_out[18];
   /* decision margins (test instrumentation, see orc_trace): [0] random-number
    * and energy thresholds, relative; [1] position tests, cell units; [2]
    * conditioning of the predictor's rotation angle */
@@ -1047,8 +1047,11 @@ static void circuit_window(orc_sim *s, int N) {
   o[13] = o[12] * g2;
   o[14] = 2.0 * s->cw_re[3] / N; /* first harmonic of U_E */
   o[15] = 2.0 * s->cw_im[3] / N;
+  o[16] = s->cdc[0] / N;          /* mean U_E: the DC self-bias (Sec. 3, circuit I) */
+  o[17] = s->cdc[1] / N;          /* mean I_ccp */
   for (int k = 0; k < 5; ++k) s->cw_re[k] = s->cw_im[k] = 0.0;
   for (int k = 0; k < 6; ++k) s->cp_sum[k] = 0.0;
+  s->cdc[0] = s->cdc[1] = 0.0;
 }
 
 static void diag_accumulate(orc_sim *s) {
@@ -1068,6 +1071,8 @@ static void diag_accumulate(orc_sim *s) {
     s->cw_im[k] -= w[k] * sin(ph);
   }
   for (int k = 0; k < 6; ++k) s->cp_sum[k] += p[k];
+  s->cdc[0] += w[3];
+  s->cdc[1] += w[4];
   s->win_count++;
   if (s->win_count == c->steps_per_rf) {
     int N = s->win_count;
@@ -1379,9 +1384,10 @@ void orc_child_ids(uint32_t step, uint32_t seed, int64_t n, const uint64_t *pare
  * [0..1] Z_ccp, [2..3] Z_load (ohm, Re/Im), [4..5] Gamma, [6] |Gamma|,
  * [7] P_source, [8] P_Rs, [9] series-element loss (P_IMN; R_b in circuit I),
  * [10] P_stray, [11] P_ccp, [12] P_forward, [13] P_ref (W), [14..15] first
- * harmonic of U_E (V, Re/Im). */
-int orc_circuit_diag(const orc_sim *s, double *out16) {
-  for (int k = 0; k < 16; ++k) out16[k] = s->circ_out[k];
+ * harmonic of U_E (V, Re/Im), [16] mean U_E (the DC self-bias), [17] mean
+ * I_ccp. */
+int orc_circuit_diag(const orc_sim *s, double *out18) {
+  for (int k = 0; k < 18; ++k) out18[k] = s->circ_out[k];
   return ORC_OK;
 }
 

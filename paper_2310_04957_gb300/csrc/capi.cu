@@ -127,8 +127,7 @@ template <typename T>
 StoreView<T> view(pic_handle *h, int buf, int s) {
   Store &S = h->st[buf][s];
   StoreView<T> v;
-  v.fr = (T *)S.fr; v.fz = (T *)S.fz; v.vr = (T *)S.vr; v.vt = (T *)S.vt; v.vz = (T *)S.vz;
-  v.ar = (T *)S.ar; v.at = (T *)S.at; v.az = (T *)S.az;
+  v.pa = (Vec4<T> *)S.pa; v.pb = (Vec4<T> *)S.pb;
   v.id = S.id; v.cell = S.cell; v.start = S.start; v.cap = S.cap; v.fill = S.fill; v.meta = S.meta;
   v.capacity = (int)h->capacity[s];
   return v;
@@ -156,6 +155,7 @@ PushParams<T> push_params(pic_handle *h, int in_buf) {
   }
   P.n_gas = (T)c.n_gas;
   P.xs_E = (const T *)h->d_xsE; P.xs_S = (const T *)h->d_xsS; P.n_xs = c.n_xs;
+  P.xs_g = h->d_xsG;
   double l0 = std::log2(h->xs_E[0]), l1 = std::log2(h->xs_E[c.n_xs - 1]);
   P.log2E0 = (T)l0; P.inv_dlog2 = (T)((c.n_xs - 1) / (l1 - l0));
   P.thr_ex = (T)c.thr_ex; P.thr_iz = (T)c.thr_iz; P.B_ej = (T)c.B_ej;
@@ -249,6 +249,9 @@ DiagParams diag_params(pic_handle *h) {
   DiagParams D;
   memset(&D, 0, sizeof(D));
   D.nn = h->nn; D.vnode = h->d_vnode;
+  D.kind = c.circuit;
+  for (int k = 0; k < 8; ++k) D.c[k] = c.circ[k];
+  D.V = c.V_src; D.phase = c.phase_src;
   D.dep[0] = h->d_dep[0]; D.dep[1] = h->d_dep[1];
   D.dep_inv_scale = dep_inv_scale(h);
   D.w[0] = c.w[0]; D.w[1] = c.w[1];
@@ -560,27 +563,21 @@ int download_species(pic_handle *h, int s, pic_particles *out, int64_t capn, int
   if (total > capn) return PIC_EINVAL;
   size_t used = (size_t)m.ovf_base + novf;
   if (used == 0) return PIC_OK;
-  std::vector<T> fr(used), fz(used), vr(used), vt(used), vz(used), ar(used), at(used), az(used);
+  std::vector<Vec4<T>> va(used), vb(used);
   std::vector<unsigned long long> id(used);
   std::vector<int> cell(used);
-  size_t bytes = sizeof(T) * used;
-  CK(cudaMemcpy(fr.data(), S.fr, bytes, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(fz.data(), S.fz, bytes, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(vr.data(), S.vr, bytes, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(vt.data(), S.vt, bytes, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(vz.data(), S.vz, bytes, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(ar.data(), S.ar, bytes, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(at.data(), S.at, bytes, cudaMemcpyDeviceToHost));
-  CK(cudaMemcpy(az.data(), S.az, bytes, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(va.data(), S.pa, sizeof(Vec4<T>) * used, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(vb.data(), S.pb, sizeof(Vec4<T>) * used, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(id.data(), S.id, sizeof(unsigned long long) * used, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(cell.data(), S.cell, sizeof(int) * used, cudaMemcpyDeviceToHost));
   const double dr = h->cfg.dr, dz = h->cfg.dz;
   int64_t k = 0;
   auto put = [&](size_t slot, int i, int j) {
-    out->r[k] = ((double)i + (double)fr[slot]) * dr;
-    out->z[k] = ((double)j + (double)fz[slot]) * dz;
-    out->vr[k] = vr[slot]; out->vt[k] = vt[slot]; out->vz[k] = vz[slot];
-    out->ar[k] = ar[slot]; out->at[k] = at[slot]; out->az[k] = az[slot];
+    const Vec4<T> &a = va[slot], &b = vb[slot];
+    out->r[k] = ((double)i + (double)a.x) * dr;
+    out->z[k] = ((double)j + (double)a.y) * dz;
+    out->vr[k] = a.z; out->vt[k] = a.w; out->vz[k] = b.x;
+    out->ar[k] = b.y; out->at[k] = b.z; out->az[k] = b.w;
     out->id[k] = id[slot];
     if (out->cell) out->cell[k] = j * h->nr + i;
     ++k;
@@ -780,6 +777,7 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
     DA(h->d_flags, sizeof(uint32_t) * 2);
     DA(h->d_xsE, h->esz * cfg->n_xs);
     DA(h->d_xsS, h->esz * 5 * cfg->n_xs);
+    DA(h->d_xsG, sizeof(float4) * 3 * (cfg->n_xs - 1));
     for (int s = 0; s < 2; ++s) {
       DA(h->d_dep[s], sizeof(unsigned long long) * nn);
       DA(h->d_surf[s], sizeof(unsigned long long) * nn);
@@ -788,9 +786,8 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
       for (int b = 0; b < 2; ++b) {
         Store &S = h->st[b][s];
         size_t cap = (size_t)h->capacity[s];
-        DA(S.fr, h->esz * cap); DA(S.fz, h->esz * cap);
-        DA(S.vr, h->esz * cap); DA(S.vt, h->esz * cap); DA(S.vz, h->esz * cap);
-        DA(S.ar, h->esz * cap); DA(S.at, h->esz * cap); DA(S.az, h->esz * cap);
+        DA(S.pa, 4 * h->esz * cap);
+        DA(S.pb, 4 * h->esz * cap);
         DA(S.id, sizeof(unsigned long long) * cap);
         DA(S.cell, sizeof(int) * cap);
         DA(S.start, sizeof(int) * h->nbins);
@@ -820,6 +817,19 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
       std::vector<float> e(h->xs_E.begin(), h->xs_E.end()), s(h->xs_S.begin(), h->xs_S.end());
       CK(cudaMemcpy(h->d_xsE, e.data(), 4 * e.size(), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(h->d_xsS, s.data(), 4 * s.size(), cudaMemcpyHostToDevice));
+      // lookup groups: on interval k the linear interpolation of Sec. 2's tables is
+      // sigma(E) = sigma_k + (E - E_k) (sigma_{k+1} - sigma_k) / (E_{k+1} - E_k)
+      const int n = cfg->n_xs;
+      std::vector<float4> g(3 * (size_t)(n - 1));
+      auto sg = [&](int p, int k) { return h->xs_S[(size_t)p * n + k]; };
+      for (int k = 0; k + 1 < n; ++k) {
+        const double w = h->xs_E[k + 1] - h->xs_E[k];
+        auto sl = [&](int p) { return (float)((sg(p, k + 1) - sg(p, k)) / w); };
+        g[3 * k + 0] = make_float4((float)sg(0, k), (float)sg(1, k), (float)sg(2, k), 0.0f);
+        g[3 * k + 1] = make_float4(sl(0), sl(1), sl(2), 0.0f);
+        g[3 * k + 2] = make_float4((float)sg(3, k), (float)sg(4, k), sl(3), sl(4));
+      }
+      CK(cudaMemcpy(h->d_xsG, g.data(), sizeof(float4) * g.size(), cudaMemcpyHostToDevice));
     } else {
       CK(cudaMemcpy(h->d_xsE, h->xs_E.data(), 8 * h->xs_E.size(), cudaMemcpyHostToDevice));
       CK(cudaMemcpy(h->d_xsS, h->xs_S.data(), 8 * h->xs_S.size(), cudaMemcpyHostToDevice));
@@ -1226,6 +1236,11 @@ int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
     for (int k = 0; k < 3; ++k) o[39 + k] = sc[SC_IONCUR + k];
     o[42] = sc[SC_I1_RE]; o[43] = sc[SC_I1_IM]; o[44] = sc[SC_WINDOWS]; o[45] = sc[SC_CEQ_GAUSS];
     o[46] = pcg[2];
+    return PIC_OK;
+  }
+  if (what == PIC_DIAG_CIRCUIT) {
+    if (bytes < sizeof(double) * 18) return PIC_EINVAL;
+    CK(cudaMemcpy(o, h->d_scalars + SC_COUT, sizeof(double) * 18, cudaMemcpyDeviceToHost));
     return PIC_OK;
   }
   if (what == PIC_DIAG_SOLVER) {

@@ -377,8 +377,51 @@ cudaError_t launch_circuit(const CircuitParams &C, cudaStream_t st) {
 }
 
 // ---- diagnostics -----------------------------------------------------------------
+// Circuit waveforms at t_{n+1} for the window's post-processing (Sec. 3): source
+// voltage U_s, the current I_1 leaving the source, the matching network's
+// input voltage U_in, U_E (= U_ccp) and I_ccp; and the element powers U_s I_1,
+// R_s I_1^2, the series element's loss (R_m I_2^2; R_b I_b^2 in circuit I),
+// the stray branch's loss R_stray I_stray^2, U_ccp I_ccp and U_in I_1.
+__device__ void circuit_waveforms(const DiagParams &D, const double *S, double t1, double w[5], double p[6]) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const double Us = D.V * sin(two_pi * D.f * t1 + D.phase);
+  for (int k = 0; k < 6; ++k) p[k] = 0.0;
+  const double UE = S[SC_UE], Iccp = S[SC_ICCP];
+  if (D.kind == 2) {
+    const double Uin = (S[SC_Y0 + 0] - S[SC_Y0 + 1]) / D.c[1];
+    const double I1 = (Us - Uin) / D.c[0];
+    const double I2 = S[SC_Y0 + 2], Ist = S[SC_Y0 + 4];
+    w[0] = Us; w[1] = I1; w[2] = Uin;
+    p[0] = Us * I1;
+    p[1] = D.c[0] * I1 * I1;
+    p[2] = D.c[4] * I2 * I2;
+    p[3] = D.c[6] * Ist * Ist;
+    p[5] = Uin * I1;
+  } else if (D.kind == 1) {
+    const double Ib = S[SC_Y0 + 1];
+    w[0] = Us; w[1] = Ib; w[2] = Us;
+    p[0] = Us * Ib;
+    p[2] = D.c[0] * Ib * Ib;
+    p[5] = Us * Ib;
+  } else {
+    w[0] = UE; w[1] = Iccp; w[2] = UE;
+    p[0] = p[5] = UE * Iccp;
+  }
+  w[3] = UE;
+  w[4] = Iccp;
+  p[4] = UE * Iccp;
+}
+
+// Complex ratio (ar + i ai) / (br + i bi); 0 when the divisor vanishes.
+__device__ void cdiv(double ar, double ai, double br, double bi, double &r, double &i) {
+  const double d = br * br + bi * bi;
+  r = d > 0.0 ? (ar * br + ai * bi) / d : 0.0;
+  i = d > 0.0 ? (ai * br - ar * bi) / d : 0.0;
+}
+
 // Per step: running sums of node densities, ion charge to each surface kind,
-// first-harmonic DFT of I_ccp at t_{n+1}; then the step counter advances.
+// first-harmonic DFT of I_ccp and of the circuit waveforms at t_{n+1}, element
+// power sums; then the step counter advances.
 __global__ void k_diag(const DiagParams D) {
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < D.nn; a += gridDim.x * blockDim.x) {
     double v = D.vnode[a];
@@ -393,8 +436,18 @@ __global__ void k_diag(const DiagParams D) {
     const double two_pi = 6.283185307179586476925286766559;
     double t1 = (double)(step + 1) * D.dt;
     double ph = two_pi * D.f * t1;
-    S[SC_DFT_RE] += S[SC_ICCP] * cos(ph);
-    S[SC_DFT_IM] -= S[SC_ICCP] * sin(ph);
+    const double cph = cos(ph), sph = sin(ph);
+    S[SC_DFT_RE] += S[SC_ICCP] * cph;
+    S[SC_DFT_IM] -= S[SC_ICCP] * sph;
+    double w[5], p[6];
+    circuit_waveforms(D, S, t1, w, p);
+    for (int k = 0; k < 5; ++k) {
+      S[SC_CW_RE + k] += w[k] * cph;
+      S[SC_CW_IM + k] -= w[k] * sph;
+    }
+    for (int k = 0; k < 6; ++k) S[SC_CP + k] += p[k];
+    S[SC_CDC + 0] += w[3];
+    S[SC_CDC + 1] += w[4];
     for (int k = 0; k < 3; ++k) S[SC_IONQ + k] += D.qw_ion * (double)D.counters[CNT_ABS + 3 + k];
     S[SC_WINCOUNT] += 1.0;
     *D.step_mut = step + 1;
@@ -418,6 +471,25 @@ __global__ void k_diag_window(const DiagParams D) {
     S[SC_I1_RE] = 2.0 * S[SC_DFT_RE] / N;
     S[SC_I1_IM] = 2.0 * S[SC_DFT_IM] / N;
     S[SC_DFT_RE] = S[SC_DFT_IM] = 0.0;
+    // circuit post-processing (Sec. 3): Z = U_1 / I_1 of the fundamental (Eq. 11),
+    // Gamma = (Z_load - R_s) / (Z_load + R_s) (Eq. 12), period-averaged powers
+    // (Eq. 13), P_ref = P_forward |Gamma|^2 (Eq. 14)
+    double *o = S + SC_COUT;
+    cdiv(S[SC_CW_RE + 3], S[SC_CW_IM + 3], S[SC_CW_RE + 4], S[SC_CW_IM + 4], o[0], o[1]);
+    cdiv(S[SC_CW_RE + 2], S[SC_CW_IM + 2], S[SC_CW_RE + 1], S[SC_CW_IM + 1], o[2], o[3]);
+    o[4] = o[5] = 0.0;
+    if (D.kind == 2) cdiv(o[2] - D.c[0], o[3], o[2] + D.c[0], o[3], o[4], o[5]);
+    const double g2 = o[4] * o[4] + o[5] * o[5];
+    o[6] = sqrt(g2);
+    for (int k = 0; k < 6; ++k) o[7 + k] = S[SC_CP + k] / N;
+    o[13] = o[12] * g2;
+    o[14] = 2.0 * S[SC_CW_RE + 3] / N;
+    o[15] = 2.0 * S[SC_CW_IM + 3] / N;
+    o[16] = S[SC_CDC + 0] / N;  // mean U_E: the DC self-bias (Sec. 3, circuit I)
+    o[17] = S[SC_CDC + 1] / N;
+    for (int k = 0; k < 5; ++k) S[SC_CW_RE + k] = S[SC_CW_IM + k] = 0.0;
+    for (int k = 0; k < 6; ++k) S[SC_CP + k] = 0.0;
+    S[SC_CDC + 0] = S[SC_CDC + 1] = 0.0;
     S[SC_WINCOUNT] = 0.0;
     S[SC_WINDOWS] += 1.0;
   }

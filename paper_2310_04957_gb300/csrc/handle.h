@@ -16,8 +16,7 @@ namespace pic {
 
 // Device buffers of one particle store (one species, one of the two buffers).
 struct Store {
-  void *fr = nullptr, *fz = nullptr, *vr = nullptr, *vt = nullptr, *vz = nullptr, *ar = nullptr, *at = nullptr,
-       *az = nullptr;
+  void *pa = nullptr, *pb = nullptr;  // Vec4 (fr, fz, vr, vt) and (vz, ar, at, az)
   unsigned long long *id = nullptr;
   int *cell = nullptr, *start = nullptr, *cap = nullptr, *fill = nullptr;
   BinMeta *meta = nullptr;
@@ -56,6 +55,7 @@ struct pic_handle {
   pic::Store st[2][2];  // [buffer][species]
   int cur = 0;
   void *d_xsE = nullptr, *d_xsS = nullptr;
+  float4 *d_xsG = nullptr;  // FP32 cross-section lookup groups (PushParams::xs_g)
   double *d_scalars = nullptr, *d_prop = nullptr;
   long long *d_lay_part = nullptr, *d_lay_boff = nullptr;
   int *d_lay_use = nullptr;

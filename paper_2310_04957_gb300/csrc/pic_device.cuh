@@ -1,7 +1,9 @@
 // pic_device.cuh -- device-side types and helpers of the GB300 r-z PIC/MCC library.
 //
-// Particle store: per species, two buffers (read / write) of structure-of-arrays
-// state (fr, fz, vr, vt, vz, ar, at, az, id).  Positions are cell-relative:
+// Particle store: per species, two buffers (read / write).  A particle's state
+// is two 4-vectors and its id: pa = (fr, fz, vr, vt), pb = (vz, ar, at, az) --
+// one 16-byte load or store each in FP32 (32 bytes in FP64) -- and the 64-bit
+// id in an array of its own.  Positions are cell-relative:
 // the cell is implied by the bin the particle sits in, (fr, fz) in [0,1) is
 // the offset inside it in cell units, so FP32 keeps ~1e-7 of a cell at any
 // radius.  Bins are cells in tile-major order: TX x TY cells per tile, the
@@ -38,7 +40,12 @@ enum Scalar : int {
   SC_IONQ = 19,                               // 3 sums over the window
   SC_IONCUR = 22,                             // 3 window averages
   SC_WINDOWS = 25, SC_WINCOUNT, SC_CEQ_GAUSS, SC_BNORM, SC_ENERGY,
-  SC_N = 32
+  SC_CW_RE = 32,                              // 5 first-harmonic DFT sums of the circuit
+  SC_CW_IM = 37,                              //   waveforms (U_s, I_1, U_in, U_E, I_ccp)
+  SC_CP = 42,                                 // 6 sums of the element powers
+  SC_CDC = 48,                                // 2 sums of U_E and I_ccp (DC parts)
+  SC_COUT = 50,                               // 18 results of the last window (PIC_DIAG_CIRCUIT)
+  SC_N = 72
 };
 
 struct BinMeta {
@@ -47,9 +54,15 @@ struct BinMeta {
   long long total;
 };
 
+// Four values of a particle's state, aligned for one vector access.
+template <typename T> struct Vec4;
+template <> struct alignas(16) Vec4<float> { float x, y, z, w; };
+template <> struct alignas(32) Vec4<double> { double x, y, z, w; };
+
 template <typename T>
 struct StoreView {
-  T *fr, *fz, *vr, *vt, *vz, *ar, *at, *az;
+  Vec4<T> *pa;    // (fr, fz, vr, vt)
+  Vec4<T> *pb;    // (vz, ar, at, az)
   unsigned long long *id;
   int *cell;      // only meaningful in the overflow region
   int *start;     // [nbins] first slot of each bin

@@ -20,6 +20,9 @@ struct PushParams {
   T qm[2];
   T pcoll[2], numax[2], n_gas;
   const T *xs_E, *xs_S;     // [n_xs], [5*n_xs]
+  const float4 *xs_g;       // FP32 lookup groups: per interval k, electrons (sigma_el,
+                            // sigma_ex, sigma_iz at E_k, 0) then their slopes per eV,
+                            // then ions (sigma_iso, sigma_cx, slopes): [3*(n_xs-1)]
   int n_xs;
   T log2E0, inv_dlog2;
   T thr_ex, thr_iz, B_ej;
@@ -100,6 +103,9 @@ struct CircuitParams {
 
 struct DiagParams {
   int nn;
+  int kind;                 // circuit (PIC_CIRCUIT_*) and its parameters, for the
+  double c[8];              // circuit post-processing of the window
+  double V, phase;
   const double *vnode;
   const unsigned long long *dep[2];
   double dep_inv_scale;

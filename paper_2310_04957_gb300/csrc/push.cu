@@ -57,8 +57,8 @@ __device__ __forceinline__ float rsq(float q) {
 }
 __device__ __forceinline__ double rsq(double q) { return 1.0 / sqrt(q); }
 
-__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
 }
 __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
@@ -110,37 +110,105 @@ __device__ __forceinline__ int exit_node(const PushParams<T> &P, int ci, T fr, i
   return nj * (P.nr + 1) + ni;
 }
 
-// Cross section of process `proc` at energy E (eV): linear interpolation between
-// the bracketing log-spaced table nodes, clamped outside the table.
+// Cross sections at energy E (eV): linear interpolation between the bracketing
+// log-spaced table nodes, clamped outside the table.  xs_interval returns the
+// interval k with E_k <= E < E_{k+1} (-1 below the table, n-1 above it): a guess
+// from log2 E, corrected by one node either way.
 template <typename T>
-__device__ __forceinline__ T xs(const PushParams<T> &P, int proc, T E) {
+__device__ __forceinline__ int xs_interval(const PushParams<T> &P, T E) {
   const T *Et = P.xs_E;
-  const T *S = P.xs_S + proc * P.n_xs;
-  int n = P.n_xs;
-  if (E <= __ldg(Et)) return __ldg(S);
-  if (E >= __ldg(Et + n - 1)) return __ldg(S + n - 1);
-  int k = (int)((m_log2(E) - P.log2E0) * P.inv_dlog2);
+  const int n = P.n_xs;
+  if (E <= __ldg(Et)) return -1;
+  if (E >= __ldg(Et + n - 1)) return n - 1;
+  int k;
+  if constexpr (sizeof(T) == 4) k = (int)((__log2f(E) - P.log2E0) * P.inv_dlog2);
+  else k = (int)((m_log2(E) - P.log2E0) * P.inv_dlog2);
   k = k < 0 ? 0 : (k > n - 2 ? n - 2 : k);
   if (E < __ldg(Et + k) && k > 0) --k;
-  if (E > __ldg(Et + k + 1) && k < n - 2) ++k;
-  T e0 = __ldg(Et + k), e1 = __ldg(Et + k + 1);
+  else if (E >= __ldg(Et + k + 1) && k < n - 2) ++k;
+  return k;
+}
+
+// sigma of process `proc` on interval k (FP64: the table's own arithmetic).
+template <typename T>
+__device__ __forceinline__ T xs_at(const PushParams<T> &P, int proc, int k, T E) {
+  const T *S = P.xs_S + proc * P.n_xs;
+  if (k < 0) return __ldg(S);
+  if (k >= P.n_xs - 1) return __ldg(S + P.n_xs - 1);
+  T e0 = __ldg(P.xs_E + k), e1 = __ldg(P.xs_E + k + 1);
   T s0 = __ldg(S + k), s1 = __ldg(S + k + 1);
   return s0 + (E - e0) / (e1 - e0) * (s1 - s0);
 }
 
-// Electron scattering-angle cosine (Vahedi & Surendra): written with
-// expm1/log1p as 1 - 2 ((1+E)^R - 1)/E, algebraically the same as
-// (2 + E - 2 (1+E)^R)/E, without its cancellation in FP32.
-template <typename T>
-__device__ __forceinline__ T scatter_cos(T E, T R) {
-  T c = E < (T)1e-6 ? (T)1 - (T)2 * R : (T)1 - (T)2 * m_expm1(R * m_log1p(E)) / E;
-  return c > (T)1 ? (T)1 : (c < (T)-1 ? (T)-1 : c);
+// The three electron cross sections (elastic, excitation, ionization) at E.
+__device__ __forceinline__ void xs_electron(const PushParams<float> &P, float E, float s[3]) {
+  const int k = xs_interval(P, E);
+  if (k < 0 || k >= P.n_xs - 1) {
+#pragma unroll
+    for (int p = 0; p < 3; ++p) s[p] = __ldg(P.xs_S + p * P.n_xs + (k < 0 ? 0 : P.n_xs - 1));
+    return;
+  }
+  const float4 a = __ldg(P.xs_g + 3 * k), b = __ldg(P.xs_g + 3 * k + 1);
+  const float dE = E - __ldg(P.xs_E + k);
+  s[0] = a.x + dE * b.x;
+  s[1] = a.y + dE * b.y;
+  s[2] = a.z + dE * b.z;
+}
+__device__ __forceinline__ void xs_electron(const PushParams<double> &P, double E, double s[3]) {
+  const int k = xs_interval(P, E);
+#pragma unroll
+  for (int p = 0; p < 3; ++p) s[p] = xs_at(P, p, k, E);
 }
 
-// Turn unit vector d by polar angle (cosine cc) and azimuth 2 pi u.
+// The two ion cross sections (isotropic, charge exchange) at table energy E.
+__device__ __forceinline__ void xs_ion(const PushParams<float> &P, float E, float s[2]) {
+  const int k = xs_interval(P, E);
+  if (k < 0 || k >= P.n_xs - 1) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) s[p] = __ldg(P.xs_S + (3 + p) * P.n_xs + (k < 0 ? 0 : P.n_xs - 1));
+    return;
+  }
+  const float4 c = __ldg(P.xs_g + 3 * k + 2);
+  const float dE = E - __ldg(P.xs_E + k);
+  s[0] = c.x + dE * c.z;
+  s[1] = c.y + dE * c.w;
+}
+__device__ __forceinline__ void xs_ion(const PushParams<double> &P, double E, double s[2]) {
+  const int k = xs_interval(P, E);
+  s[0] = xs_at(P, 3, k, E);
+  s[1] = xs_at(P, 4, k, E);
+}
+
+// Electron scattering angle (Vahedi & Surendra): cos chi = (2 + E - 2 (1+E)^R)/E,
+// returned as (cos chi, sin chi).  FP64 keeps the plain form, sin chi =
+// sqrt(1 - cos^2 chi).  In FP32 that square root loses accuracy as chi -> 0
+// or pi, so with x = ((1+E)^R - 1)/E the angle is cos chi = 1 - 2x and
+// sin chi = 2 sqrt(x (1-x)), where x and 1 - x = (1+E)(1 - (1+E)^(R-1))/E are
+// both formed by expm1/log1p without cancellation (R and 1 - R are exact).
+__device__ __forceinline__ void scatter_cs(float E, float R, float &cc, float &sc) {
+  float x, y;
+  if (E < 1e-6f) {
+    x = R;
+    y = 1.0f - R;
+  } else {
+    const float L = log1pf(E), inv = 1.0f / E;
+    x = expm1f(R * L) * inv;
+    y = -(1.0f + E) * expm1f(-(1.0f - R) * L) * inv;
+  }
+  x = fminf(fmaxf(x, 0.0f), 1.0f);
+  y = fminf(fmaxf(y, 0.0f), 1.0f);
+  cc = x < 0.5f ? 1.0f - 2.0f * x : 2.0f * y - 1.0f;
+  sc = 2.0f * sqrtf(x * y);
+}
+__device__ __forceinline__ void scatter_cs(double E, double R, double &cc, double &sc) {
+  double c = E < 1e-6 ? 1.0 - 2.0 * R : 1.0 - 2.0 * expm1(R * log1p(E)) / E;
+  cc = c > 1.0 ? 1.0 : (c < -1.0 ? -1.0 : c);
+  sc = sqrt(1.0 - cc * cc > 0.0 ? 1.0 - cc * cc : 0.0);
+}
+
+// Turn unit vector d by the polar angle (cos cc, sin sc) and azimuth 2 pi u.
 template <typename T>
-__device__ __forceinline__ void turn(T d[3], T cc, T u) {
-  T sc = m_sqrt((T)1 - cc * cc > (T)0 ? (T)1 - cc * cc : (T)0);
+__device__ __forceinline__ void turn(T d[3], T cc, T sc, T u) {
   T sp, cp;
   m_sincospi((T)2 * u, &sp, &cp);
   T st = m_sqrt(d[0] * d[0] + d[1] * d[1]);
@@ -157,6 +225,17 @@ __device__ __forceinline__ void turn(T d[3], T cc, T u) {
     o2 = cc * sg;
   }
   d[0] = o0; d[1] = o1; d[2] = o2;
+}
+
+// Isotropic polar angle from uniform u: cos theta = 1 - 2u, sin theta =
+// 2 sqrt(u (1-u)) (exact in FP32; the FP64 path keeps sqrt(1 - cos^2)).
+__device__ __forceinline__ void iso_cs(float u, float &ct, float &st) {
+  ct = 1.0f - 2.0f * u;
+  st = 2.0f * sqrtf(u * (1.0f - u));
+}
+__device__ __forceinline__ void iso_cs(double u, double &ct, double &st) {
+  ct = 1.0 - 2.0 * u;
+  st = sqrt(1.0 - ct * ct > 0.0 ? 1.0 - ct * ct : 0.0);
 }
 
 template <typename T>
@@ -222,63 +301,93 @@ struct Outcome {
   int birth;      // 1 -> electron + ion born at x_n (electrons only)
 };
 
-// Electron collision (Sec. 2, null-collision MCC; kinematics of Vahedi & Surendra).
+// Electron null-collision test (Sec. 2, Vahedi's method): -1 for a null
+// collision, else the process (0 elastic, 1 excitation, 2 ionization).  Returns
+// the energy E (eV) and the uniforms u2, u3 its kinematics use.
 template <typename T>
-__device__ __forceinline__ int mcc_electron(const PushParams<T> &P, Part<T> &p, Part<T> &be, Part<T> &bi) {
+__device__ __forceinline__ int mcc_electron_choose(const PushParams<T> &P, const Part<T> &p, T &E, T &u2, T &u3) {
   T u[4];
   draw4(P, p.id, 0u, 0u, u);
   if (!(u[0] < P.pcoll[0])) return -1;
   T v2 = p.vr * p.vr + p.vt * p.vt + p.vz * p.vz;
   T speed = m_sqrt(v2);
   if (!(speed > (T)0)) return -1;
-  T E = P.e_per_v2[0] * v2;
+  E = P.e_per_v2[0] * v2;
+  u2 = u[2];
+  u3 = u[3];
   T ng_v = P.n_gas * speed;
-  T nu_el = ng_v * xs(P, 0, E);
-  T nu_ex = E < P.thr_ex ? (T)0 : ng_v * xs(P, 1, E);
-  T nu_iz = E < P.thr_iz ? (T)0 : ng_v * xs(P, 2, E);
+  T sg[3];
+  xs_electron(P, E, sg);
+  T nu_el = ng_v * sg[0];
+  T nu_ex = E < P.thr_ex ? (T)0 : ng_v * sg[1];
+  T nu_iz = E < P.thr_iz ? (T)0 : ng_v * sg[2];
   T x = u[1] * P.numax[0];
+  if (x < nu_el) return 0;
+  if (x < nu_el + nu_ex) return 1;
+  if (x < nu_el + nu_ex + nu_iz) return 2;
+  return -1;
+}
+
+// Kinematics of electron process `coll` at energy E (Vahedi & Surendra): the
+// scattered velocity, and for an ionization the ejected electron `be` and the
+// new ion `bi` (Maxwellian at the gas temperature) at the parent's x_n.
+template <typename T>
+__device__ __forceinline__ void mcc_electron_apply(const PushParams<T> &P, Part<T> &p, int coll, T E, T u2, T u3,
+                                                   Part<T> &be, Part<T> &bi) {
+  T speed = m_sqrt(p.vr * p.vr + p.vt * p.vt + p.vz * p.vz);
   T d[3] = {p.vr / speed, p.vt / speed, p.vz / speed};
-  if (x < nu_el) {
-    T cc = scatter_cos(E, u[2]);
+  if (coll == 0) {
+    T cc, sc;
+    scatter_cs(E, u2, cc, sc);
     T frac = (T)1 - P.two_me_over_M * ((T)1 - cc);
-    turn(d, cc, u[3]);
+    turn(d, cc, sc, u3);
     T sp = speed * m_sqrt(frac);
     p.vr = sp * d[0]; p.vt = sp * d[1]; p.vz = sp * d[2];
-    return 0;
+    return;
   }
-  if (x < nu_el + nu_ex) {
+  if (coll == 1) {
     T En = E - P.thr_ex;
-    turn(d, scatter_cos(En, u[2]), u[3]);
+    T cc, sc;
+    scatter_cs(En, u2, cc, sc);
+    turn(d, cc, sc, u3);
     T sp = m_sqrt(En * P.v2_per_e[0]);
     p.vr = sp * d[0]; p.vt = sp * d[1]; p.vz = sp * d[2];
-    return 1;
+    return;
   }
-  if (x < nu_el + nu_ex + nu_iz) {
-    T Eex = E - P.thr_iz;
-    T Eej = P.B_ej * m_tan(u[2] * m_atan(Eex / ((T)2 * P.B_ej)));
-    T Esc = Eex - Eej;
-    if (Esc < (T)0) Esc = (T)0;
-    T u1[4], u2[4];
-    draw4(P, p.id, 1u, 0u, u1);
-    draw4(P, p.id, 2u, 0u, u2);
-    T ds[3] = {d[0], d[1], d[2]}, de[3] = {d[0], d[1], d[2]};
-    turn(ds, scatter_cos(Esc, u1[0]), u1[1]);
-    turn(de, scatter_cos(Eej, u1[2]), u1[3]);
-    T ssc = m_sqrt(Esc * P.v2_per_e[0]), sej = m_sqrt(Eej * P.v2_per_e[0]);
-    p.vr = ssc * ds[0]; p.vt = ssc * ds[1]; p.vz = ssc * ds[2];
-    be = p;
-    be.vr = sej * de[0]; be.vt = sej * de[1]; be.vz = sej * de[2];
-    be.ar = be.at = be.az = (T)0;
-    be.id = child_id(P, p.id, 0u);
-    T n0, n1, n2, n3;
-    box_muller(u2[0], u2[1], n0, n1);
-    box_muller(u2[2], u2[3], n2, n3);
-    bi = be;
-    bi.vr = P.vth_gas * n0; bi.vt = P.vth_gas * n1; bi.vz = P.vth_gas * n2;
-    bi.id = child_id(P, p.id, 1u);
-    return 2;
-  }
-  return -1;
+  T Eex = E - P.thr_iz;
+  T Eej = P.B_ej * m_tan(u2 * m_atan(Eex / ((T)2 * P.B_ej)));
+  T Esc = Eex - Eej;
+  if (Esc < (T)0) Esc = (T)0;
+  T w1[4], w2[4];
+  draw4(P, p.id, 1u, 0u, w1);
+  draw4(P, p.id, 2u, 0u, w2);
+  T ds[3] = {d[0], d[1], d[2]}, de[3] = {d[0], d[1], d[2]};
+  T cc, sc;
+  scatter_cs(Esc, w1[0], cc, sc);
+  turn(ds, cc, sc, w1[1]);
+  scatter_cs(Eej, w1[2], cc, sc);
+  turn(de, cc, sc, w1[3]);
+  T ssc = m_sqrt(Esc * P.v2_per_e[0]), sej = m_sqrt(Eej * P.v2_per_e[0]);
+  p.vr = ssc * ds[0]; p.vt = ssc * ds[1]; p.vz = ssc * ds[2];
+  be = p;
+  be.vr = sej * de[0]; be.vt = sej * de[1]; be.vz = sej * de[2];
+  be.ar = be.at = be.az = (T)0;
+  be.id = child_id(P, p.id, 0u);
+  T n0, n1, n2, n3;
+  box_muller(w2[0], w2[1], n0, n1);
+  box_muller(w2[2], w2[3], n2, n3);
+  bi = be;
+  bi.vr = P.vth_gas * n0; bi.vt = P.vth_gas * n1; bi.vz = P.vth_gas * n2;
+  bi.id = child_id(P, p.id, 1u);
+}
+
+// Electron collision: test, then kinematics when one occurs.
+template <typename T>
+__device__ __forceinline__ int mcc_electron(const PushParams<T> &P, Part<T> &p, Part<T> &be, Part<T> &bi) {
+  T E = (T)0, u2 = (T)0, u3 = (T)0;
+  const int c = mcc_electron_choose(P, p, E, u2, u3);
+  if (c >= 0) mcc_electron_apply(P, p, c, E, u2, u3, be, bi);
+  return c;
 }
 
 // Ion collision against a neutral drawn from the gas Maxwellian (Sec. 2):
@@ -299,12 +408,14 @@ __device__ __forceinline__ int mcc_ion(const PushParams<T> &P, Part<T> &p) {
   T gm = m_sqrt(gg);
   T eps = P.e_per_v2[1] * gg;
   T ng_g = P.n_gas * gm;
-  T nu_iso = ng_g * xs(P, 3, eps);
-  T nu_cx = ng_g * xs(P, 4, eps);
+  T sg[2];
+  xs_ion(P, eps, sg);
+  T nu_iso = ng_g * sg[0];
+  T nu_cx = ng_g * sg[1];
   T x = u[1] * P.numax[1];
   if (x < nu_iso) {
-    T ct = (T)1 - (T)2 * u[2];
-    T st = m_sqrt((T)1 - ct * ct > (T)0 ? (T)1 - ct * ct : (T)0);
+    T ct, st;
+    iso_cs(u[2], ct, st);
     T sp, cp;
     m_sincospi((T)2 * u[3], &sp, &cp);
     T wi = P.mi_frac, wn = (T)1 - P.mi_frac;  // m_i/(m_i+M), M/(m_i+M)
@@ -395,9 +506,8 @@ __device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T
 template <typename T>
 __device__ __forceinline__ void store_particle(const StoreView<T> &S, int slot, const Part<T> &p, int cell_rowmajor,
                                                bool ovf) {
-  S.fr[slot] = p.fr; S.fz[slot] = p.fz;
-  S.vr[slot] = p.vr; S.vt[slot] = p.vt; S.vz[slot] = p.vz;
-  S.ar[slot] = p.ar; S.at[slot] = p.at; S.az[slot] = p.az;
+  S.pa[slot] = Vec4<T>{p.fr, p.fz, p.vr, p.vt};
+  S.pb[slot] = Vec4<T>{p.vz, p.ar, p.at, p.az};
   S.id[slot] = p.id;
   if (ovf) S.cell[slot] = cell_rowmajor;
 }
@@ -595,10 +705,39 @@ __device__ __forceinline__ void tally(const PushParams<T> &P, int s, const Outco
 
 template <typename T>
 __device__ __forceinline__ void load_particle(const StoreView<T> &S, int slot, Part<T> &p) {
-  p.fr = S.fr[slot]; p.fz = S.fz[slot];
-  p.vr = S.vr[slot]; p.vt = S.vt[slot]; p.vz = S.vz[slot];
-  p.ar = S.ar[slot]; p.at = S.at[slot]; p.az = S.az[slot];
+  const Vec4<T> a = S.pa[slot], b = S.pb[slot];
+  p.fr = a.x; p.fz = a.y; p.vr = a.z; p.vt = a.w;
+  p.vz = b.x; p.ar = b.y; p.at = b.z; p.az = b.w;
   p.id = S.id[slot];
+}
+
+// The pair an ionization created (lanes with `birth`): predictor and absorption
+// test of the newborn electron, warp-wide emit, then the newborn ion.
+// Warp-collective.
+template <typename T, int TX, int TY>
+__device__ __forceinline__ void emit_births(const PushParams<T> &P, bool birth, Part<T> &be, Part<T> &bi,
+                                            const TileCtx &tc) {
+  if (!__any_sync(0xffffffffu, birth)) return;
+  count_warp(P.counters + CNT_BORN + 0, birth);
+  count_warp(P.counters + CNT_BORN + 1, birth);
+  bool e_alive = false;
+  if (!birth) {  // lanes without a birth take part in the warp-wide emit as dead lanes
+    be.ci = 0;
+    be.cj = 0;
+  }
+  if (birth) {
+    predict(P, be);
+    e_alive = in_plasma(P, be.ci, be.cj);
+    if (!e_alive) {
+      int node = exit_node(P, be.ci, be.fr, be.cj, be.fz);
+      int k = (int)__ldg(P.node_kind + node);
+      k = k == 1 ? 0 : (k == 2 ? 1 : 2);
+      atomicAdd(P.counters + CNT_ABS + k, 1ull);
+      if (k == 2) atomicAdd(P.surf[0] + node, 1ull);
+    }
+  }
+  emit<T, TX, TY>(P, 0, e_alive, be, tc);
+  if (birth) emit_ion_birth<T, TX, TY>(P, bi);
 }
 
 // Process one particle (already loaded) of species s: step, tallies, emit,
@@ -613,29 +752,7 @@ __device__ __forceinline__ void process(const PushParams<T> &P, int s, bool acti
   if (active) o = advance(P, s, p, be, bi, en);
   tally(P, s, o, active);
   emit<T, TX, TY>(P, s, active && o.alive, p, tc);
-  bool birth = active && o.birth;
-  if (__any_sync(0xffffffffu, birth)) {
-    count_warp(P.counters + CNT_BORN + 0, birth);
-    count_warp(P.counters + CNT_BORN + 1, birth);
-    bool e_alive = false;
-    if (!birth) {  // lanes without a birth take part in the warp-wide emit as dead lanes
-      be.ci = 0;
-      be.cj = 0;
-    }
-    if (birth) {
-      predict(P, be);
-      e_alive = in_plasma(P, be.ci, be.cj);
-      if (!e_alive) {
-        int node = exit_node(P, be.ci, be.fr, be.cj, be.fz);
-        int k = (int)__ldg(P.node_kind + node);
-        k = k == 1 ? 0 : (k == 2 ? 1 : 2);
-        atomicAdd(P.counters + CNT_ABS + k, 1ull);
-        if (k == 2) atomicAdd(P.surf[0] + node, 1ull);
-      }
-    }
-    emit<T, TX, TY>(P, 0, e_alive, be, tc);
-    if (birth) emit_ion_birth<T, TX, TY>(P, bi);
-  }
+  emit_births<T, TX, TY>(P, active && o.birth, be, bi, tc);
 }
 
 // One species' CTA (species known at compile time: its store views, charge
@@ -650,7 +767,7 @@ struct ParticleSmem {
   unsigned long long tile[(TX + 1 + 2 * kHalo) * (TY + 1 + 2 * kHalo)];
   int pre[TX * TY + 1];
   int off[TX * TY];
-  float pf[2][8][kPf];
+  Vec4<float> pa[2][kPf], pb[2][kPf];
   unsigned long long pid[2][kPf];
   int plo[2][kPf];
 };
@@ -701,11 +818,12 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
     if constexpr (sizeof(T) == 4) {
       // Software pipeline: while a round of blockDim.x particles is processed,
       // the state of each thread's particle of the next round streams from HBM
-      // into shared memory with cp.async.  A thread only reads back what it
+      // into shared memory with cp.async (two 16-byte copies and the id).  A thread only reads back what it
       // fetched itself, so no block barrier is needed.  (The E field at the
       // cell's nodes is read directly: it is small and L1-resident, and staging
       // it as well measured slower.)
-      auto &pf = sh.pf;
+      auto &spa = sh.pa;
+      auto &spb = sh.pb;
       auto &pid = sh.pid;
       auto &plo = sh.plo;
       const int tid = threadIdx.x;
@@ -717,14 +835,8 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
           for (int step = per / 2; step >= 1; step >>= 1)
             if (lo + step < per && s_pre[lo + step] <= k) lo += step;
           const int slot = s_off[lo] + (k - s_pre[lo]);
-          cp_async4(&pf[b][0][tid], A.fr + slot);
-          cp_async4(&pf[b][1][tid], A.fz + slot);
-          cp_async4(&pf[b][2][tid], A.vr + slot);
-          cp_async4(&pf[b][3][tid], A.vt + slot);
-          cp_async4(&pf[b][4][tid], A.vz + slot);
-          cp_async4(&pf[b][5][tid], A.ar + slot);
-          cp_async4(&pf[b][6][tid], A.at + slot);
-          cp_async4(&pf[b][7][tid], A.az + slot);
+          cp_async16(&spa[b][tid], A.pa + slot);
+          cp_async16(&spb[b][tid], A.pb + slot);
           cp_async8(&pid[b][tid], A.id + slot);
           plo[b][tid] = lo;
         }
@@ -745,9 +857,9 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
         p.ci = 0; p.cj = 0;
         float2 en[4];
         if (active) {
-          p.fr = pf[b][0][tid]; p.fz = pf[b][1][tid];
-          p.vr = pf[b][2][tid]; p.vt = pf[b][3][tid]; p.vz = pf[b][4][tid];
-          p.ar = pf[b][5][tid]; p.at = pf[b][6][tid]; p.az = pf[b][7][tid];
+          const Vec4<float> va = spa[b][tid], vb = spb[b][tid];
+          p.fr = va.x; p.fz = va.y; p.vr = va.z; p.vt = va.w;
+          p.vz = vb.x; p.ar = vb.y; p.at = vb.z; p.az = vb.w;
           p.id = pid[b][tid];
           const int lo = plo[b][tid];
           p.ci = tc.ci0 + (lo & (TX - 1));

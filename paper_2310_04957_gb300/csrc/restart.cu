@@ -128,9 +128,8 @@ size_t used_slots(pic_handle *h, int s, const BinMeta &m) {
 }
 
 std::vector<Blob> store_columns(pic_handle *h, const Store &S, size_t used) {
-  const size_t e = h->esz * used;
-  return {{S.fr, e}, {S.fz, e}, {S.vr, e}, {S.vt, e}, {S.vz, e}, {S.ar, e}, {S.at, e}, {S.az, e},
-          {S.id, sizeof(unsigned long long) * used}, {S.cell, sizeof(int) * used}};
+  const size_t e = 4 * h->esz * used;
+  return {{S.pa, e}, {S.pb, e}, {S.id, sizeof(unsigned long long) * used}, {S.cell, sizeof(int) * used}};
 }
 
 }  // namespace

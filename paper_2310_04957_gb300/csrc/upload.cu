@@ -52,14 +52,8 @@ __global__ void k_upload_scatter(UploadParams<T> U) {
     const int2 br = U.bin_rank[k];
     const int d = U.start[br.x] + br.y;
     const StoreView<T> &S = U.out;
-    S.fr[d] = U.fr_tmp[k];
-    S.fz[d] = U.fz_tmp[k];
-    S.vr[d] = (T)U.vr[k];
-    S.vt[d] = (T)U.vt[k];
-    S.vz[d] = (T)U.vz[k];
-    S.ar[d] = (T)U.ar[k];
-    S.at[d] = (T)U.at[k];
-    S.az[d] = (T)U.az[k];
+    S.pa[d] = Vec4<T>{U.fr_tmp[k], U.fz_tmp[k], (T)U.vr[k], (T)U.vt[k]};
+    S.pb[d] = Vec4<T>{(T)U.vz[k], (T)U.ar[k], (T)U.at[k], (T)U.az[k]};
     S.id[d] = U.id[k];
   }
 }

@@ -26,6 +26,7 @@ DIAG = {"phi": 0, "Er": 1, "Ez": 2, "chi": 3, "dep_e": 4, "dep_i": 5, "sigma": 6
 DIAG_SCALARS = 100
 DIAG_STORE = 101
 DIAG_SOLVER = 102
+DIAG_CIRCUIT = 103
 NSCALARS = 47
 SCALARS = ["step", "t", "U_E", "Q_E", "C_eq", "I_conv", "I_ccp", "y0", "y1", "y2", "y3", "y4", "y5", "pcg_iters",
            "pcg_relres", "numax_e", "numax_i", "pcoll_e", "pcoll_i", "absq_e_pow", "absq_e_gnd", "absq_e_surf",
@@ -254,6 +255,15 @@ class Discharge:
         _check(lib().pic_diag(self.h, DIAG_STORE, _p(o), o.nbytes), "pic_diag(store)")
         keys = ("in_bins", "overflow", "capacity", "overflow_start")
         return [dict(zip(keys, o[4 * s:4 * s + 4].astype(np.int64).tolist())) for s in (0, 1)]
+
+    def circuit_diag(self):
+        """Circuit post-processing of the last RF window (Eqs. 11-14) as a dict."""
+        o = np.zeros(18)
+        _check(lib().pic_diag(self.h, DIAG_CIRCUIT, _p(o), o.nbytes), "pic_diag(circuit)")
+        return {"z_ccp": complex(o[0], o[1]), "z_load": complex(o[2], o[3]), "gamma": complex(o[4], o[5]),
+                "gamma_abs": o[6], "p_source": o[7], "p_rs": o[8], "p_series": o[9], "p_stray": o[10],
+                "p_ccp": o[11], "p_forward": o[12], "p_ref": o[13], "u1": complex(o[14], o[15]),
+                "u_dc": o[16], "i_dc": o[17]}
 
     def solver_state(self):
         """Multigrid solves counter, rebuild period, last iterations, outer steps, status."""

@@ -1,10 +1,13 @@
 """The batched sweep (independent discharges stepped by one graph per step with
 one field-solve launch for all of them) against the same discharges stepped
 one at a time, through the C ABI."""
+import dataclasses
+
 import numpy as np
 import pytest
 
-from gpu_common import compare_particles, pic
+from gpu_common import compare_particles, make_pair, pic
+from parity_tools import StepParity
 from paper_2310_04957_gb300 import sweep
 from paper_2310_04957_gb300 import workloads as W
 from util import rel_l2
@@ -47,6 +50,33 @@ def test_batch_matches_discharges_stepped_alone():
             assert c["bad"] <= max(2, 1e-4 * c["common"]), c
         assert d.status() == 0
         assert d.scalars()["step"] == e.scalars()["step"] == 3
+
+
+def test_batch_discharges_match_the_oracle():
+    """Every discharge of an uneven batch (grids 64x32 to 256x128, field solves on
+    clusters of 1 to 8 CTAs) stepped side by side with its own FP64 oracle for
+    3 steps, the last one ending an RF window: per particle, in the surface
+    charge, deposits, circuit, C_eq refresh and phi, with the checks and
+    tolerances of the single-discharge parity test (FP32 particle kernel)."""
+    P = pic()
+    wls = [dataclasses.replace(wl, steps_per_rf=3) for wl in _cases()]
+    pairs = [make_pair(wl, 0, solver=MIXED, tile=(4, 2)) for wl in wls]
+    for d, o in pairs:
+        d.start()
+        o.init_fields()
+    b = P.Batch([d for d, _ in pairs])
+    sps = [StepParity(wl, d, o, True) for wl, (d, o) in zip(wls, pairs)]
+    for _ in range(3):
+        for sp in sps:
+            sp.begin()
+        b.step(1)
+        b.sync()
+        for sp in sps:
+            sp.finish()
+    for sp, (d, _) in zip(sps, pairs):
+        assert d.status() == 0
+        assert d.scalars()["windows"] == 1
+        print(f"{sp.wl.nr}x{sp.wl.nz}: flips {sp.flips} of {sp.seen}, phi end to end {sp.phi_e2e}")
 
 
 def test_batch_crosses_an_rf_window():

@@ -907,3 +907,30 @@ def test_circuit_postprocessing_matches_phasor_solution_of_the_vacuum_match():
     assert b["p_source"] == pytest.approx(b["p_rs"] + b["p_series"] + b["p_stray"] + b["p_ccp"], rel=1e-6, abs=0)
     assert abs(b["u1"]) == pytest.approx(abs(ref["Ub"]), rel=1e-6, abs=0)
     assert abs(b["u1"]) == pytest.approx(g["U_electrode_amplitude"], rel=5e-3, abs=0)
+
+
+def test_blocking_capacitor_charges_at_the_closed_form_rate():
+    """Circuit I (Eq. 9: source, R_b, L_b and the blocking capacitor C_b in series with the
+    electrode's C_eq, Sec. 3's values) with a constant net convective current I0 into the
+    electrode (Eq. 8): at DC the inductor and resistor drop nothing, so the blocking capacitor
+    and the electrode charge together (Q_b = -C_b U_E): the electrode's window-mean potential --
+    the DC self-bias -- rises by I0 T / (C_eq + C_b) per RF period T, the loop carries the mean
+    current -I0 C_b / (C_eq + C_b), and the fundamental stays periodic.  The trapezoidal rule is
+    exact on this linear drift."""
+    base = W.small_cylinder(n_per_species=16)
+    Rb, Lb, Cb, Ceq, I0 = 0.5, 0.01e-6, 5e-9, 892.07e-12, 0.37
+    wl = dataclasses.replace(with_particles(base), circuit=W.CIRCUIT_RLC, circ=(Rb, Lb, Cb, 0.0, 0.0, 0.0, 0.0, 0.0), V_src=150.0,
+                             phase_src=0.0, ceq_refresh=0)
+    o = orc.Oracle(wl)
+    o.set_ceq(Ceq)
+    o.set_circuit_state(np.zeros(6))
+    o.set_conv_current(I0)
+    o.set_step(0)
+    o.circuit_run(wl.steps_per_rf * 12)
+    a = o.circuit_diag()
+    o.circuit_run(wl.steps_per_rf)
+    b = o.circuit_diag()
+    T = wl.steps_per_rf * wl.dt
+    assert b["u_dc"] - a["u_dc"] == pytest.approx(I0 * T / (Ceq + Cb), rel=1e-9, abs=0)
+    assert b["i_dc"] == pytest.approx(-I0 * Cb / (Ceq + Cb), rel=1e-9, abs=0)
+    assert abs(b["u1"] - a["u1"]) <= 1e-9 * abs(b["u1"])
