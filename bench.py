@@ -393,7 +393,9 @@ def run_selfbias(args):
     rows, t_all = [], 0.0
     for V in (50.0, 100.0, 150.0, 200.0, 250.0, 300.0):
         wl = W.gec_case(128, 64, 100.0, V, n_per_species=200_000, seed_index=31)
-        wl = dataclasses.replace(wl, circuit=W.CIRCUIT_RLC, circ=(0.5, 0.01e-6, 5e-9, 0, 0, 0, 0, 0))
+        # ionization grows the population over the run: room for 3x the initial count
+        wl = dataclasses.replace(wl, circuit=W.CIRCUIT_RLC, circ=(0.5, 0.01e-6, 5e-9, 0, 0, 0, 0, 0),
+                                 capacity=(600_000, 600_000))
         d = pic.Discharge(wl, solver=pic.PIC_SOLVER_MG)
         d.start()
         torch.cuda.synchronize()

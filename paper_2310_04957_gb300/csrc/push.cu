@@ -663,6 +663,94 @@ __device__ __forceinline__ void emit(const PushParams<T> &P, int s, bool alive, 
   }
 }
 
+// ---- FP32: warps process whole chunks of one bin -------------------------------------
+// A warp's 32 particles come from one cell (its "home"), and in a step most of
+// them stay there.  Those claim their slots in the home bin with one ballot and
+// one atomic, and add their four node weights to per-lane registers; the warp
+// reduces the registers into the shared node tile once per bin (flush_home).
+// Particles that leave the home cell claim by match_any groups and deposit
+// directly.  Warp-collective.
+template <int TX, int TY>
+__device__ __forceinline__ void emit_home(const PushParams<float> &P, int s, bool alive, const Part<float> &p,
+                                          const TileCtx &tc, int hci, int hcj, int hkey, unsigned acc[4]) {
+  constexpr int TW = TX + 1 + 2 * kHalo;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const StoreView<float> &S = P.out[s];
+  const bool home = alive && p.ci == hci && p.cj == hcj;
+  const unsigned hm = __ballot_sync(FULL, home);
+  int key = -1, pos = 0;
+  if (hm) {
+    const int hl = __ffs(hm) - 1;
+    int hbase = 0;
+    if (lane == hl) hbase = atomicAdd(S.fill + hkey, __popc(hm));
+    hbase = __shfl_sync(FULL, hbase, hl);
+    if (home) {
+      key = hkey;
+      pos = hbase + __popc(hm & lt);
+    }
+  }
+  const bool other = alive && !home;
+  if (__any_sync(FULL, other)) {
+    const int okey = other ? bin_key<TX, TY>(p.ci, p.cj, P.map.ntx) : -1;
+    const unsigned peers = __match_any_sync(FULL, okey);
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (okey >= 0 && lane == leader) base = atomicAdd(S.fill + okey, __popc(peers));
+    base = __shfl_sync(FULL, base, leader);
+    if (other) {
+      key = okey;
+      pos = base + __popc(peers & lt);
+    }
+  }
+  if (key >= 0) {
+    const bool ovf = !(pos < __ldg(S.cap + key));
+    const int slot = ovf ? overflow_slot(P, S) : __ldg(S.start + key) + pos;
+    if (slot >= 0) store_particle(S, slot, p, p.cj * P.nr + p.ci, ovf);
+  }
+  if (!alive) return;
+  unsigned long long W[4];
+  node_weights_q(P, p, W);
+  if (home) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] += (unsigned)W[k];
+    return;
+  }
+  const int li = p.ci - tc.ci0 + kHalo, lj = p.cj - tc.cj0 + kHalo;
+  const bool in_tile = tc.tile != nullptr && li >= 0 && lj >= 0 && li < TX + 2 * kHalo && lj < TY + 2 * kHalo;
+  const int n00 = p.cj * (P.nr + 1) + p.ci;
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    const int dx = n & 1, dy = n >> 1;
+    if (!W[n]) continue;
+    if (in_tile) add_shared64(tc.tile + (lj + dy) * TW + li + dx, (unsigned)W[n]);
+    else atomicAdd(P.dep[s] + n00 + dy * (P.nr + 1) + dx, W[n]);
+  }
+}
+
+// Add the warp's home-cell node weights (per-lane sums below 2^32) to the
+// shared node tile: each sum split into 16-bit halves, so the warp totals of
+// the halves fit 32 bits and one redux.sync each forms them.  Warp-collective.
+template <int TX, int TY>
+__device__ __forceinline__ void flush_home(const TileCtx &tc, int hci, int hcj, unsigned acc[4]) {
+  constexpr int TW = TX + 1 + 2 * kHalo;
+  const unsigned FULL = 0xffffffffu;
+  unsigned long long t[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const unsigned lo = __reduce_add_sync(FULL, acc[k] & 0xffffu), hi = __reduce_add_sync(FULL, acc[k] >> 16);
+    t[k] = ((unsigned long long)hi << 16) + lo;
+    acc[k] = 0u;
+  }
+  const int lane = threadIdx.x & 31;
+  if (lane < 4) {
+    const unsigned long long v = lane == 0 ? t[0] : (lane == 1 ? t[1] : (lane == 2 ? t[2] : t[3]));
+    const int li = hci - tc.ci0 + kHalo + (lane & 1), lj = hcj - tc.cj0 + kHalo + (lane >> 1);
+    if (v) atomicAdd(tc.tile + lj * TW + li, v);
+  }
+}
+
 // A newborn ion from an electron CTA: predictor, absorption, write, deposit
 // (per lane: births are rare).
 template <typename T, int TX, int TY>
@@ -755,6 +843,19 @@ __device__ __forceinline__ void process(const PushParams<T> &P, int s, bool acti
   emit_births<T, TX, TY>(P, active && o.birth, be, bi, tc);
 }
 
+// process() for an FP32 warp whose particles all start in its home cell.
+template <int TX, int TY>
+__device__ __forceinline__ void process_home(const PushParams<float> &P, int s, bool active, Part<float> &p,
+                                             const TileCtx &tc, const float2 en[4], int hci, int hcj, int hkey,
+                                             unsigned acc[4]) {
+  Part<float> be, bi;
+  Outcome o{0, -1, 0, -1, 0};
+  if (active) o = advance(P, s, p, be, bi, en);
+  tally(P, s, o, active);
+  emit_home<TX, TY>(P, s, active && o.alive, p, tc, hci, hcj, hkey, acc);
+  emit_births<float, TX, TY>(P, active && o.birth, be, bi, tc);
+}
+
 // One species' CTA (species known at compile time: its store views, charge
 // to mass ratio and deposit array are fixed kernel-parameter operands, and only
 // its own collision code is compiled in).
@@ -763,13 +864,13 @@ __device__ __forceinline__ void process(const PushParams<T> &P, int s, bool acti
 // offsets, and (FP32) the double-buffered next-round particle state.
 template <typename T, int TX, int TY>
 struct ParticleSmem {
-  static constexpr int kPf = sizeof(T) == 4 ? kThreads : 1;
+  static constexpr int kW = sizeof(T) == 4 ? kThreads / 32 : 1;
   unsigned long long tile[(TX + 1 + 2 * kHalo) * (TY + 1 + 2 * kHalo)];
   int pre[TX * TY + 1];
+  int cpre[TX * TY + 1];  // prefix of the bins' 32-particle chunk counts
   int off[TX * TY];
-  Vec4<float> pa[2][kPf], pb[2][kPf];
-  unsigned long long pid[2][kPf];
-  int plo[2][kPf];
+  Vec4<float> wa[kW][2][32], wb[kW][2][32];  // per-warp staging of the next chunk
+  unsigned long long wid[kW][2][32];
 };
 
 template <typename T, int TX, int TY, int s>
@@ -791,8 +892,8 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
     tc.cj0 = tyi * TY;
     for (int k = threadIdx.x; k < TW * TH; k += blockDim.x) smem[k] = 0ull;
     if (threadIdx.x < 32) {
-      // prefix of the tile's in-bin counts
-      int carry = 0;
+      // prefix of the tile's in-bin counts and chunk counts
+      int carry = 0, ccarry = 0;
 #pragma unroll
       for (int c0 = 0; c0 < per; c0 += 32) {
         int b = c0 + threadIdx.x;
@@ -802,72 +903,85 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
           n = f < cp ? f : cp;
           off = A.start[b0 + b];
         }
-        int incl = n;
+        const int nc = (n + 31) >> 5;
+        int incl = n, cincl = nc;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-          int y = __shfl_up_sync(0xffffffffu, incl, d);
-          if ((int)threadIdx.x >= d) incl += y;
+          int y = __shfl_up_sync(0xffffffffu, incl, d), yc = __shfl_up_sync(0xffffffffu, cincl, d);
+          if ((int)threadIdx.x >= d) { incl += y; cincl += yc; }
         }
-        if (b < per) { s_pre[b] = carry + incl - n; s_off[b] = off; }
+        if (b < per) { s_pre[b] = carry + incl - n; s_off[b] = off; sh.cpre[b] = ccarry + cincl - nc; }
         carry += __shfl_sync(0xffffffffu, incl, 31);
+        ccarry += __shfl_sync(0xffffffffu, cincl, 31);
       }
-      if (threadIdx.x == 0) s_pre[per] = carry;
+      if (threadIdx.x == 0) { s_pre[per] = carry; sh.cpre[per] = ccarry; }
     }
     __syncthreads();
     const int ntot = s_pre[per];
     if constexpr (sizeof(T) == 4) {
-      // Software pipeline: while a round of blockDim.x particles is processed,
-      // the state of each thread's particle of the next round streams from HBM
-      // into shared memory with cp.async (two 16-byte copies and the id).  A thread only reads back what it
-      // fetched itself, so no block barrier is needed.  (The E field at the
-      // cell's nodes is read directly: it is small and L1-resident, and staging
-      // it as well measured slower.)
-      auto &spa = sh.pa;
-      auto &spb = sh.pb;
-      auto &pid = sh.pid;
-      auto &plo = sh.plo;
-      const int tid = threadIdx.x;
-      auto issue = [&](int base, int b) {
-        const int k = base + tid;
-        if (k < ntot) {
-          int lo = 0;  // largest bin with s_pre[lo] <= k
+      // Warp w takes the w-th of eight equal runs of the tile's chunks (32
+      // particles of one bin each, in bin order), so a warp stays in one bin
+      // for a run of chunks.  While a chunk is processed the next one streams
+      // from HBM into the warp's shared staging with cp.async (two 16-byte
+      // copies and the id per lane; each lane reads back only its own copy).
+      const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      const int *s_cpre = sh.cpre;
+      const int nch = s_cpre[per];
+      const int c0 = (int)((long long)nch * w / ParticleSmem<T, TX, TY>::kW);
+      const int c1 = (int)((long long)nch * (w + 1) / ParticleSmem<T, TX, TY>::kW);
+      auto bin_of = [&](int c) {  // largest bin with s_cpre[bin] <= c
+        int lo = 0;
 #pragma unroll
-          for (int step = per / 2; step >= 1; step >>= 1)
-            if (lo + step < per && s_pre[lo + step] <= k) lo += step;
-          const int slot = s_off[lo] + (k - s_pre[lo]);
-          cp_async16(&spa[b][tid], A.pa + slot);
-          cp_async16(&spb[b][tid], A.pb + slot);
-          cp_async8(&pid[b][tid], A.id + slot);
-          plo[b][tid] = lo;
+        for (int step = per / 2; step >= 1; step >>= 1)
+          if (lo + step < per && s_cpre[lo + step] <= c) lo += step;
+        return lo;
+      };
+      auto issue = [&](int c, int buf) {
+        if (c < c1) {
+          const int bb = bin_of(c);
+          const int k = (c - s_cpre[bb]) * 32 + lane;
+          if (k < s_pre[bb + 1] - s_pre[bb]) {
+            const int slot = s_off[bb] + k;
+            cp_async16(&sh.wa[w][buf][lane], A.pa + slot);
+            cp_async16(&sh.wb[w][buf][lane], A.pb + slot);
+            cp_async8(&sh.wid[w][buf][lane], A.id + slot);
+          }
         }
         cp_async_commit_group();
       };
-      issue(0, 0);
-      for (int base = 0, it = 0; base < ntot; base += blockDim.x, ++it) {
-        const int b = it & 1;
-        if (base + (int)blockDim.x < ntot) {
-          issue(base + blockDim.x, b ^ 1);
-          cp_async_wait_group<1>();
-        } else {
-          cp_async_wait_group<0>();
+      int home = -1, hci = 0, hcj = 0, nin = 0;
+      unsigned acc[4] = {0u, 0u, 0u, 0u};
+      issue(c0, 0);
+      for (int c = c0, it = 0; c < c1; ++c, ++it) {
+        const int buf = it & 1;
+        issue(c + 1, buf ^ 1);
+        cp_async_wait_group<1>();
+        const int bb = bin_of(c);
+        if (bb != home || nin == 63) {  // a lane's sum holds at most 63 quantised weights
+          if (home >= 0) flush_home<TX, TY>(tc, hci, hcj, acc);
+          home = bb;
+          hci = tc.ci0 + (bb & (TX - 1));
+          hcj = tc.cj0 + bb / TX;
+          nin = 0;
         }
-        const int k = base + tid;
-        const bool active = k < ntot;
+        ++nin;
+        const int k = (c - s_cpre[bb]) * 32 + lane;
+        const bool active = k < s_pre[bb + 1] - s_pre[bb];
         Part<T> p;
-        p.ci = 0; p.cj = 0;
+        p.ci = hci;
+        p.cj = hcj;
         float2 en[4];
         if (active) {
-          const Vec4<float> va = spa[b][tid], vb = spb[b][tid];
+          const Vec4<float> va = sh.wa[w][buf][lane], vb = sh.wb[w][buf][lane];
           p.fr = va.x; p.fz = va.y; p.vr = va.z; p.vt = va.w;
           p.vz = vb.x; p.ar = vb.y; p.at = vb.z; p.az = vb.w;
-          p.id = pid[b][tid];
-          const int lo = plo[b][tid];
-          p.ci = tc.ci0 + (lo & (TX - 1));
-          p.cj = tc.cj0 + (lo / TX);
-          gather_nodes(P, p.ci, p.cj, en);  // E is small and L1/L2-resident
+          p.id = sh.wid[w][buf][lane];
+          gather_nodes(P, hci, hcj, en);  // E is small and L1/L2-resident
         }
-        process<T, TX, TY>(P, s, active, p, tc, en);
+        process_home<TX, TY>(P, s, active, p, tc, en, hci, hcj, b0 + bb, acc);
       }
+      cp_async_wait_group<0>();
+      if (home >= 0) flush_home<TX, TY>(tc, hci, hcj, acc);
     } else {
       for (int base = 0; base < ntot; base += blockDim.x) {
         int k = base + threadIdx.x;

@@ -23,10 +23,19 @@ pytestmark = pytest.mark.gpu
 
 
 def close(a, b, tol):
+    """Each quantity within tol of its own size, or of the size of what it is a small part
+    of: Gamma of 1, the reflected and plasma powers of the source power, the DC means of the
+    fundamental's amplitude."""
     for k, v in b.items():
         scale = max(abs(v), 1e-30)
-        if k in ("gamma", "gamma_abs", "p_ref", "p_ccp"):
-            scale = max(scale, 1.0 if k.startswith("gamma") else abs(b["p_source"]))
+        if k in ("gamma", "gamma_abs"):
+            scale = max(scale, 1.0)
+        elif k in ("p_ref", "p_ccp"):
+            scale = max(scale, abs(b["p_source"]))
+        elif k == "u_dc":
+            scale = max(scale, abs(b["u1"]))
+        elif k == "i_dc":
+            scale = max(scale, abs(b["u1"] / b["z_ccp"]))
         assert abs(a[k] - v) <= tol * scale, (k, a[k], v)
 
 
