@@ -49,7 +49,7 @@ class Setup(ctypes.Structure):
         ("V_src", ctypes.c_double), ("f_src", ctypes.c_double), ("phase_src", ctypes.c_double),
         ("n_sub", ctypes.c_int32), ("steps_per_rf", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
         ("pcg_maxit", ctypes.c_int32), ("ceq_refresh", ctypes.c_int32), ("seed", ctypes.c_uint32),
-        ("capacity", ctypes.c_int64 * 2),
+        ("capacity", ctypes.c_int64 * 2), ("split_cells", ctypes.c_int32),
     ]
 
 
@@ -61,10 +61,10 @@ def lib():
         P = ctypes.c_void_p
         L.orc_create.argtypes = [ctypes.POINTER(Setup), ctypes.POINTER(P)]
         L.orc_destroy.argtypes = [P]
-        L.orc_set_particles.argtypes = [P, ctypes.c_int, ctypes.c_int64] + [P] * 9
+        L.orc_set_particles.argtypes = [P, ctypes.c_int, ctypes.c_int64] + [P] * 10
         L.orc_count.argtypes = [P, ctypes.c_int]
         L.orc_count.restype = ctypes.c_int64
-        L.orc_get_particles.argtypes = [P, ctypes.c_int] + [P] * 10
+        L.orc_get_particles.argtypes = [P, ctypes.c_int] + [P] * 11
         for name in ("orc_get_field", "orc_set_field", "orc_get_operator"):
             getattr(L, name).argtypes = [P, ctypes.c_int, P]
         L.orc_set_step.argtypes = [P, ctypes.c_uint32]
@@ -89,6 +89,7 @@ def lib():
         L.orc_trace.argtypes = [P, ctypes.c_int, P]
         L.orc_circuit_diag.argtypes = [P, P]
         L.orc_child_ids.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, P, P]
+        L.orc_split_ids.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, P, P]
         _lib = L
     return _lib
 
@@ -102,7 +103,7 @@ SCALARS = ["step", "t", "U_E", "Q_E", "C_eq", "I_conv", "I_ccp", "y0", "y1", "y2
            "absq_i_pow", "absq_i_gnd", "absq_i_surf", "absn_e_pow", "absn_e_gnd", "absn_e_surf", "absn_i_pow",
            "absn_i_gnd", "absn_i_surf", "coll_e_el", "coll_e_ex", "coll_e_iz", "coll_i_iso", "coll_i_cx",
            "coll_i_none", "born_e", "born_i", "ioncur_pow", "ioncur_gnd", "ioncur_surf", "i1_re", "i1_im",
-           "windows", "ceq_gauss", "pcg_status"]
+           "windows", "ceq_gauss", "pcg_status", "splits_e", "splits_i"]
 
 
 def philox(ctr, key):
@@ -128,6 +129,14 @@ def child_ids(step, seed, parents):
     p = np.ascontiguousarray(parents, np.uint64)
     out = np.zeros((len(p), 2), np.uint64)
     lib().orc_child_ids(step, seed, len(p), _p(p), _p(out))
+    return out
+
+
+def split_ids(step, seed, parents):
+    """Id of the second half of each parent if it splits in `step`."""
+    p = np.ascontiguousarray(parents, np.uint64)
+    out = np.zeros(len(p), np.uint64)
+    lib().orc_split_ids(step, seed, len(p), _p(p), _p(out))
     return out
 
 
@@ -165,6 +174,7 @@ class Oracle:
         s.pcg_tol, s.pcg_maxit, s.ceq_refresh, s.seed = wl.pcg_tol, wl.pcg_maxit, wl.ceq_refresh, wl.seed
         cap = capacity if capacity is not None else wl.capacity
         s.capacity[:] = [int(cap[0]), int(cap[1])]
+        s.split_cells = int(getattr(wl, "split_cells", 0))
         h = ctypes.c_void_p()
         st = L.orc_create(ctypes.byref(s), ctypes.byref(h))
         if st != 0:
@@ -188,7 +198,9 @@ class Oracle:
     def set_particles(self, spc, P):
         a = [np.ascontiguousarray(getattr(P, k), np.float64) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az")]
         ids = np.ascontiguousarray(P.id, np.uint64)
-        st = lib().orc_set_particles(self.h, spc, P.n, *[_p(x) for x in a], _p(ids))
+        w = getattr(P, "w", None)
+        w = None if w is None else np.ascontiguousarray(w, np.float64)
+        st = lib().orc_set_particles(self.h, spc, P.n, *[_p(x) for x in a], _p(ids), None if w is None else _p(w))
         if st != 0:
             raise RuntimeError(f"orc_set_particles failed: {st}")
 
@@ -200,7 +212,8 @@ class Oracle:
         out = {k: np.zeros(n) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az")}
         out["id"] = np.zeros(n, np.uint64)
         out["cell"] = np.zeros(n, np.int32)
-        keys = ("r", "z", "vr", "vt", "vz", "ar", "at", "az", "id", "cell")
+        out["w"] = np.zeros(n)
+        keys = ("r", "z", "vr", "vt", "vz", "ar", "at", "az", "id", "cell", "w")
         lib().orc_get_particles(self.h, spc, *[_p(out[k]) for k in keys])
         return out
 

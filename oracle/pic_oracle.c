@@ -91,12 +91,14 @@ static void box_muller(double ua, double ub, double *na, double *nb) {
 typedef struct {
   int64_t n, cap;
   double *r, *z, *vr, *vt, *vz, *ar, *at, *az; /* x~, v, a-bar */
+  double *w;                                   /* weight ratio: macro weight w_p = w * cfg.w[species] */
   uint64_t *id;
   int32_t *cell;
 } orc_species;
 
 typedef struct {
   double r, z, vr, vt, vz, ar, at, az;
+  double w;
   uint64_t id;
 } orc_particle;
 
@@ -117,6 +119,9 @@ struct orc_sim {
   /* births created during one particle phase */
   orc_particle *born[2];
   int64_t n_born[2], cap_born[2];
+  /* second halves of particles split during one particle phase */
+  orc_particle *split[2];
+  int64_t n_split[2], cap_split[2];
   /* per-step tallies: [species][0 powered,1 grounded,2 surface] */
   double abs_q[2][3];
   int64_t abs_n[2][3];
@@ -276,7 +281,7 @@ static void node_weights(const orc_sim *s, double r, double z, int i, int j, dou
  * the plasma (position clamped into the domain): a powered node adds to the
  * electrode's convective charge (Eq. 8), a grounded node is only counted, a
  * free node (dielectric surface) keeps it as surface charge. */
-static void credit(orc_sim *s, int spc, double r, double z) {
+static void credit(orc_sim *s, int spc, double r, double z, double w) {
   double R = s->cfg.nr * s->cfg.dr, Z = s->cfg.nz * s->cfg.dz;
   double rc = r < 0 ? 0 : (r > R ? R : r);
   double zc = z < 0 ? 0 : (z > Z ? Z : z);
@@ -285,21 +290,22 @@ static void credit(orc_sim *s, int spc, double r, double z) {
   if (i > s->cfg.nr) i = s->cfg.nr;
   if (j > s->cfg.nz) j = s->cfg.nz;
   int node = nidx(s, i, j);
-  double qw = s->cfg.q[spc] * s->cfg.w[spc];
+  double qw = s->cfg.q[spc] * s->cfg.w[spc] * w;
   int kind = s->node_kind[node];
   if (kind == ORC_POWERED) { s->abs_q[spc][0] += qw; s->abs_n[spc][0] += 1; }
   else if (kind == ORC_GROUNDED) { s->abs_q[spc][1] += qw; s->abs_n[spc][1] += 1; }
   else { s->sigma[node] += qw; s->abs_q[spc][2] += qw; s->abs_n[spc][2] += 1; }
 }
 
-static void deposit(orc_sim *s, int spc, double r, double z, int i, int j) {
+/* Node counts of a particle of weight ratio pw: its four node weights times pw. */
+static void deposit(orc_sim *s, int spc, double r, double z, int i, int j, double pw) {
   double w[4];
   node_weights(s, r, z, i, j, w);
   double *d = s->dep[spc];
-  d[nidx(s, i, j)] += w[0];
-  d[nidx(s, i + 1, j)] += w[1];
-  d[nidx(s, i, j + 1)] += w[2];
-  d[nidx(s, i + 1, j + 1)] += w[3];
+  d[nidx(s, i, j)] += pw * w[0];
+  d[nidx(s, i + 1, j)] += pw * w[1];
+  d[nidx(s, i, j + 1)] += pw * w[2];
+  d[nidx(s, i + 1, j + 1)] += pw * w[3];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -411,13 +417,13 @@ static void mcc_electron(orc_sim *s, orc_particle *p, double r, double z) {
     double ssc = sqrt(2.0 * Esc * QE_C / c->m[0]);
     double sej = sqrt(2.0 * Eej * QE_C / c->m[0]);
     p->vr = ssc * dsc[0]; p->vt = ssc * dsc[1]; p->vz = ssc * dsc[2];
-    orc_particle e = {r, z, sej * dej[0], sej * dej[1], sej * dej[2], 0, 0, 0,
+    orc_particle e = {r, z, sej * dej[0], sej * dej[1], sej * dej[2], 0, 0, 0, p->w,
                       child_id(p->id, s->step, 0, c->seed)};
     double n0, n1, n2, n3;
     box_muller(u2[0], u2[1], &n0, &n1);
     box_muller(u2[2], u2[3], &n2, &n3);
     double vth = sqrt(KB * c->T_gas / c->m_gas);
-    orc_particle ion = {r, z, vth * n0, vth * n1, vth * n2, 0, 0, 0,
+    orc_particle ion = {r, z, vth * n0, vth * n1, vth * n2, 0, 0, 0, p->w,
                         child_id(p->id, s->step, 1, c->seed)};
     push_birth(s, 0, &e);
     push_birth(s, 1, &ion);
@@ -493,28 +499,64 @@ static void predict(orc_sim *s, orc_particle *p, double r, double z) {
   p->z = z + dt * uz;
 }
 
+/* Particle splitting near the axis (Sec. 2: unequal weights make the few
+ * particles of the small axial cells heavy and noisy; splitting restores their
+ * number).  Radial cell i has the target weight ratio (2i+1)/(2 i_s + 1),
+ * proportional to its volume, within the first i_s = split_cells cells and 1
+ * beyond; a particle heavier than twice the target of the cell it enters splits
+ * into two halves.  The second half has the id split_id(parent, step). */
+static double split_target(const orc_sim *s, int i) {
+  int is = s->cfg.split_cells;
+  if (is <= 0 || i >= is) return 1.0;
+  return (2.0 * i + 1.0) / (2.0 * is + 1.0);
+}
+
+static uint64_t split_id(uint64_t id, uint32_t step, uint32_t seed) {
+  uint32_t ctr[4] = {step, 0x5B17u, 0u, seed};
+  uint32_t key[2] = {(uint32_t)id, (uint32_t)(id >> 32)};
+  uint32_t x[4];
+  philox4x32_10(ctr, key, x);
+  return ((uint64_t)x[0] | ((uint64_t)x[1] << 32)) | (1ull << 63);
+}
+
+static void push_split(orc_sim *s, int spc, const orc_particle *p) {
+  if (s->n_split[spc] == s->cap_split[spc]) {
+    int64_t nc = s->cap_split[spc] ? 2 * s->cap_split[spc] : 1024;
+    orc_particle *nb = (orc_particle *)realloc(s->split[spc], (size_t)nc * sizeof(orc_particle));
+    if (!nb) { fprintf(stderr, "oracle: out of memory for splits\n"); abort(); }
+    s->split[spc] = nb; s->cap_split[spc] = nc;
+  }
+  s->split[spc][s->n_split[spc]++] = *p;
+}
+
 /* Finish a particle at x_n (after correction and MCC): predictor, absorption
- * test at x~_{n+1}, deposit.  Returns 1 if it stays. */
+ * test at x~_{n+1}, deposit, split.  Returns 1 if it stays. */
 static int finish_particle(orc_sim *s, int spc, orc_particle *p, double r, double z, int32_t *cell) {
   predict(s, p, r, z);
   note_margin(s, 1, face_margin(s, p->r, p->z));
   int i, j;
   if (!inside_plasma(s, p->r, p->z, &i, &j)) {
-    credit(s, spc, p->r, p->z);
+    credit(s, spc, p->r, p->z, p->w);
     return 0;
   }
-  deposit(s, spc, p->r, p->z, i, j);
+  deposit(s, spc, p->r, p->z, i, j, p->w);
   *cell = j * s->cfg.nr + i;
+  if (s->cfg.split_cells > 0 && p->w > 2.0 * split_target(s, i)) {
+    p->w *= 0.5;
+    orc_particle half = *p;
+    half.id = split_id(p->id, s->step, s->cfg.seed);
+    push_split(s, spc, &half);
+  }
   return 1;
 }
 
 static void sp_store(orc_species *S, int64_t k, const orc_particle *p, int32_t cell) {
   S->r[k] = p->r; S->z[k] = p->z; S->vr[k] = p->vr; S->vt[k] = p->vt; S->vz[k] = p->vz;
-  S->ar[k] = p->ar; S->at[k] = p->at; S->az[k] = p->az; S->id[k] = p->id; S->cell[k] = cell;
+  S->ar[k] = p->ar; S->at[k] = p->at; S->az[k] = p->az; S->w[k] = p->w; S->id[k] = p->id; S->cell[k] = cell;
 }
 
 static orc_particle sp_load(const orc_species *S, int64_t k) {
-  orc_particle p = {S->r[k], S->z[k], S->vr[k], S->vt[k], S->vz[k], S->ar[k], S->at[k], S->az[k], S->id[k]};
+  orc_particle p = {S->r[k], S->z[k], S->vr[k], S->vt[k], S->vz[k], S->ar[k], S->at[k], S->az[k], S->w[k], S->id[k]};
   return p;
 }
 
@@ -549,6 +591,7 @@ static int particle_phase(orc_sim *s) {
   for (int spc = 0; spc < 2; ++spc) {
     memset(s->dep[spc], 0, sizeof(double) * s->nn);
     s->n_born[spc] = 0;
+    s->n_split[spc] = 0;
     for (int k = 0; k < 3; ++k) { s->abs_q[spc][k] = 0; s->abs_n[spc][k] = 0; s->coll[spc][k] = 0; }
   }
   for (int spc = 0; spc < 2; ++spc) {
@@ -558,7 +601,7 @@ static int particle_phase(orc_sim *s) {
     for (int64_t k = 0; k < S->n; ++k) {
       orc_particle p = sp_load(S, k);
       int i, j;
-      if (!inside_plasma(s, p.r, p.z, &i, &j)) { credit(s, spc, p.r, p.z); continue; }
+      if (!inside_plasma(s, p.r, p.z, &i, &j)) { credit(s, spc, p.r, p.z, p.w); continue; }
       double w[4];
       node_weights(s, p.r, p.z, i, j, w);
       int nd[4] = {nidx(s, i, j), nidx(s, i + 1, j), nidx(s, i, j + 1), nidx(s, i + 1, j + 1)};
@@ -574,7 +617,7 @@ static int particle_phase(orc_sim *s) {
       note_margin(s, 1, fabs(r) / s->cfg.dr);
       if (r < 0.0) { r = -r; p.vr = -p.vr; p.vt = -p.vt; p.ar = -p.ar; p.at = -p.at; }
       note_margin(s, 1, face_margin(s, r, z));
-      if (!inside_plasma(s, r, z, &i, &j)) { credit(s, spc, r, z); continue; }
+      if (!inside_plasma(s, r, z, &i, &j)) { credit(s, spc, r, z, p.w); continue; }
       if (spc == 0) mcc_electron(s, &p, r, z); else mcc_ion(s, &p);
       int32_t cell;
       if (finish_particle(s, spc, &p, r, z, &cell)) sp_store(S, kept++, &p, cell);
@@ -591,6 +634,14 @@ static int particle_phase(orc_sim *s) {
         if (S->n >= S->cap) return ORC_EOVERFLOW;
         sp_store(S, S->n++, &p, cell);
       }
+    }
+    /* second halves of this phase's splits (already pushed and deposited) */
+    for (int64_t b = 0; b < s->n_split[spc]; ++b) {
+      orc_particle p = s->split[spc][b];
+      int i, j;
+      inside_plasma(s, p.r, p.z, &i, &j);
+      if (S->n >= S->cap) return ORC_EOVERFLOW;
+      sp_store(S, S->n++, &p, j * s->cfg.nr + i);
     }
     int st = rebin(s, spc);
     if (st) return st;
@@ -1111,7 +1162,7 @@ static int one_step(orc_sim *s) {
 /* ------------------------------------------------------------------------ */
 static void free_species(orc_species *S) {
   free(S->r); free(S->z); free(S->vr); free(S->vt); free(S->vz);
-  free(S->ar); free(S->at); free(S->az); free(S->id); free(S->cell);
+  free(S->ar); free(S->at); free(S->az); free(S->w); free(S->id); free(S->cell);
 }
 
 void orc_destroy(orc_sim *s) {
@@ -1120,7 +1171,8 @@ void orc_destroy(orc_sim *s) {
   free(s->vnode); free(s->Gr); free(s->Gz); free(s->sigma); free(s->chi); free(s->qrhs);
   free(s->phi); free(s->Er); free(s->Ez);
   for (int k = 0; k < 2; ++k) {
-    free(s->dep[k]); free_species(&s->sp[k]); free(s->born[k]); free(s->dens_sum[k]); free(s->dens_avg[k]);
+    free(s->dep[k]); free_species(&s->sp[k]); free(s->born[k]); free(s->split[k]); free(s->dens_sum[k]);
+    free(s->dens_avg[k]);
   }
   free(s);
 }
@@ -1161,9 +1213,10 @@ int orc_create(const orc_setup *cfg, orc_sim **out) {
     S->vr = (double *)malloc(sizeof(double) * cap); S->vt = (double *)malloc(sizeof(double) * cap);
     S->vz = (double *)malloc(sizeof(double) * cap); S->ar = (double *)malloc(sizeof(double) * cap);
     S->at = (double *)malloc(sizeof(double) * cap); S->az = (double *)malloc(sizeof(double) * cap);
+    S->w = (double *)malloc(sizeof(double) * cap);
     S->id = (uint64_t *)malloc(sizeof(uint64_t) * cap); S->cell = (int32_t *)malloc(sizeof(int32_t) * cap);
     ok = s->dep[k] && s->dens_sum[k] && s->dens_avg[k] && S->r && S->z && S->vr && S->vt && S->vz && S->ar &&
-         S->at && S->az && S->id && S->cell;
+         S->at && S->az && S->w && S->id && S->cell;
   }
   if (!ok) { orc_destroy(s); return ORC_ENOMEM; }
   memcpy(s->node_kind, cfg->node_kind, s->nn);
@@ -1180,17 +1233,20 @@ int orc_create(const orc_setup *cfg, orc_sim **out) {
   return ORC_OK;
 }
 
+/* w: weight ratios in (0, 1] (NULL: all 1). */
 int orc_set_particles(orc_sim *s, int spc, int64_t n, const double *r, const double *z, const double *vr,
                       const double *vt, const double *vz, const double *ar, const double *at, const double *az,
-                      const uint64_t *id) {
+                      const uint64_t *id, const double *w) {
   if (!s || spc < 0 || spc > 1 || n < 0) return ORC_EINVAL;
   orc_species *S = &s->sp[spc];
   if (n > S->cap) return ORC_EOVERFLOW;
   for (int64_t k = 0; k < n; ++k) {
     int i, j;
     if (!inside_plasma(s, r[k], z[k], &i, &j)) return ORC_EINVAL;
+    if (w && !(w[k] > 0.0 && w[k] <= 1.0)) return ORC_EINVAL;
     S->r[k] = r[k]; S->z[k] = z[k]; S->vr[k] = vr[k]; S->vt[k] = vt[k]; S->vz[k] = vz[k];
     S->ar[k] = ar[k]; S->at[k] = at[k]; S->az[k] = az[k]; S->id[k] = id[k];
+    S->w[k] = w ? w[k] : 1.0;
     S->cell[k] = j * s->cfg.nr + i;
   }
   S->n = n;
@@ -1200,11 +1256,12 @@ int orc_set_particles(orc_sim *s, int spc, int64_t n, const double *r, const dou
 int64_t orc_count(const orc_sim *s, int spc) { return s->sp[spc].n; }
 
 int orc_get_particles(const orc_sim *s, int spc, double *r, double *z, double *vr, double *vt, double *vz,
-                      double *ar, double *at, double *az, uint64_t *id, int32_t *cell) {
+                      double *ar, double *at, double *az, uint64_t *id, int32_t *cell, double *w) {
   const orc_species *S = &s->sp[spc];
   for (int64_t k = 0; k < S->n; ++k) {
     r[k] = S->r[k]; z[k] = S->z[k]; vr[k] = S->vr[k]; vt[k] = S->vt[k]; vz[k] = S->vz[k];
     ar[k] = S->ar[k]; at[k] = S->at[k]; az[k] = S->az[k]; id[k] = S->id[k]; cell[k] = S->cell[k];
+    if (w) w[k] = S->w[k];
   }
   return ORC_OK;
 }
@@ -1255,7 +1312,7 @@ int orc_deposit_only(orc_sim *s) {
     for (int64_t k = 0; k < S->n; ++k) {
       int i, j;
       if (!inside_plasma(s, S->r[k], S->z[k], &i, &j)) return ORC_EINVAL;
-      deposit(s, spc, S->r[k], S->z[k], i, j);
+      deposit(s, spc, S->r[k], S->z[k], i, j, S->w[k]);
     }
   }
   return ORC_OK;
@@ -1331,9 +1388,10 @@ int orc_step(orc_sim *s, int nsteps) {
  * (e: elastic, excitation, ionization; i: isotropic, charge exchange, -),
  * [37] births e, [38] births i, [39..41] ion current of the last window
  * (powered, grounded, surface), [42] Re I1, [43] Im I1, [44] windows done,
- * [45] C_eq Gauss route, [46] pcg status. */
+ * [45] C_eq Gauss route, [46] pcg status, [47..48] splits of the last
+ * particle phase (e, i). */
 int orc_scalars(const orc_sim *s, double *o, int n) {
-  double v[47];
+  double v[49];
   v[0] = s->step; v[1] = s->step * s->cfg.dt; v[2] = s->U_E; v[3] = s->Q_E; v[4] = s->ceq;
   v[5] = s->I_conv; v[6] = s->I_ccp;
   for (int k = 0; k < 6; ++k) v[7 + k] = s->y[k];
@@ -1348,7 +1406,8 @@ int orc_scalars(const orc_sim *s, double *o, int n) {
   v[37] = (double)s->n_born[0]; v[38] = (double)s->n_born[1];
   for (int k = 0; k < 3; ++k) v[39 + k] = s->ion_cur_avg[k];
   v[42] = s->i1_re; v[43] = s->i1_im; v[44] = s->windows_done; v[45] = s->ceq_gauss; v[46] = s->pcg_status;
-  for (int k = 0; k < n && k < 47; ++k) o[k] = v[k];
+  v[47] = (double)s->n_split[0]; v[48] = (double)s->n_split[1];
+  for (int k = 0; k < n && k < 49; ++k) o[k] = v[k];
   return ORC_OK;
 }
 
@@ -1378,6 +1437,11 @@ void orc_child_ids(uint32_t step, uint32_t seed, int64_t n, const uint64_t *pare
     out[2 * k] = child_id(parents[k], step, 0, seed);
     out[2 * k + 1] = child_id(parents[k], step, 1, seed);
   }
+}
+
+/* Id of the second half of parents[k] if it splits in `step` (test hook). */
+void orc_split_ids(uint32_t step, uint32_t seed, int64_t n, const uint64_t *parents, uint64_t *out) {
+  for (int64_t k = 0; k < n; ++k) out[k] = split_id(parents[k], step, seed);
 }
 
 /* Circuit post-processing of the last closed window (Sec. 3, Eqs. 11-14):

@@ -54,6 +54,8 @@ typedef struct orc_setup {
   int32_t ceq_refresh;       /* recompute C_eq with chi once per window           */
   uint32_t seed;             /* fourth Philox counter word                       */
   int64_t capacity[2];       /* particle capacity per species                    */
+  int32_t split_cells;       /* particle splitting in the first split_cells radial
+                                cells (0: off); see split_target() */
 } orc_setup;
 
 typedef struct orc_sim orc_sim;

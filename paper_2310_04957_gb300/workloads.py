@@ -53,13 +53,15 @@ class Particles:
     at: np.ndarray
     az: np.ndarray
     id: np.ndarray
+    w: np.ndarray = None  # weight ratios in (0, 1] (macro weight w * Workload.w); None: all 1
 
     @property
     def n(self) -> int:
         return int(self.r.shape[0])
 
     def take(self, idx) -> "Particles":
-        return Particles(*(getattr(self, f.name)[idx] for f in dataclasses.fields(self)))
+        return Particles(*(None if getattr(self, f.name) is None else getattr(self, f.name)[idx]
+                           for f in dataclasses.fields(self)))
 
 
 @dataclasses.dataclass
@@ -97,6 +99,7 @@ class Workload:
     seed: int
     particles: tuple  # (electrons, ions)
     capacity: tuple
+    split_cells: int = 0  # particle splitting in the first split_cells radial cells (0: off)
 
     @property
     def n_nodes(self) -> int:
@@ -196,21 +199,34 @@ def plasma_volume(cell_kind, dr, dz):
 # --------------------------------------------------------------------------
 # Particle loading: uniform in volume over plasma cells, Maxwellian velocities
 # --------------------------------------------------------------------------
-def load_particles(cell_kind, dr, dz, n, T_eV, mass, rng, co_located=None, edge_margin=1e-3):
-    """n particles uniform in volume over the plasma cells.
+def radial_weight(i, split_cells):
+    """Weight ratio of a particle loaded in radial cell i: (2i+1)/(2 i_s + 1), the
+    cell's volume relative to that of cell i_s, within the first i_s = split_cells
+    cells, and 1 beyond (the target the splitting rule keeps particles near)."""
+    i = np.asarray(i)
+    return np.where(i < split_cells, (2.0 * i + 1.0) / (2.0 * split_cells + 1.0), 1.0)
 
-    A cell is picked with probability proportional to its volume; inside it
-    r^2 is uniform in [r_i^2, r_{i+1}^2] and z uniform, kept a relative
-    `edge_margin` away from the cell faces so that FP32 and FP64 agree on the
-    containing cell.  If `co_located` is given the positions are copied from
-    it (ions placed on their electrons, so the initial charge density is zero).
+
+def load_particles(cell_kind, dr, dz, n, T_eV, mass, rng, co_located=None, edge_margin=1e-3, split_cells=0):
+    """n particles over the plasma cells, uniform in volume (in density).
+
+    A cell is picked with probability proportional to its volume divided by its
+    weight ratio (radial_weight; 1 everywhere when split_cells is 0), so each
+    cell's total weight is proportional to its volume; inside it r^2 is uniform
+    in [r_i^2, r_{i+1}^2] and z uniform, kept a relative `edge_margin` away from
+    the cell faces so that FP32 and FP64 agree on the containing cell.  If
+    `co_located` is given the positions and ratios are copied from it (ions
+    placed on their electrons, so the initial charge density is zero).
     """
     nz, nr = cell_kind.shape
+    w = None
     if co_located is not None:
         r, z = co_located.r.copy(), co_located.z.copy()
+        w = None if co_located.w is None else co_located.w.copy()
     else:
         i = np.arange(nr)
-        vol = ((cell_kind == CELL_PLASMA) * (((i + 1) ** 2 - i**2).astype(np.float64))[None, :]).ravel()
+        vol = ((cell_kind == CELL_PLASMA) * ((((i + 1) ** 2 - i**2).astype(np.float64)) /
+                                               radial_weight(i, split_cells))[None, :]).ravel()
         p = vol / vol.sum()
         cells = rng.choice(nr * nz, size=n, p=p)
         ci, cj = cells % nr, cells // nr
@@ -220,10 +236,13 @@ def load_particles(cell_kind, dr, dz, n, T_eV, mass, rng, co_located=None, edge_
         z = (cj + u2) * dz
         r = r.astype(np.float32).astype(np.float64)
         z = z.astype(np.float32).astype(np.float64)
+        if split_cells > 0:
+            w = radial_weight(ci, split_cells).astype(np.float32).astype(np.float64)
     sig = math.sqrt(T_eV * ELEMENTARY_CHARGE / mass)
     v = (sig * rng.standard_normal((3, n))).astype(np.float32).astype(np.float64)
     zeros = np.zeros(n)
-    return Particles(r, z, v[0], v[1], v[2], zeros.copy(), zeros.copy(), zeros.copy(), np.arange(n, dtype=np.uint64))
+    return Particles(r, z, v[0], v[1], v[2], zeros.copy(), zeros.copy(), zeros.copy(), np.arange(n, dtype=np.uint64),
+                     w)
 
 
 # --------------------------------------------------------------------------
@@ -233,7 +252,8 @@ F_RF = 13.56e6
 
 
 def _make(name, nr, nz, R, Z, geometry, pressure_mtorr, n_per_species, steps_per_rf, circuit, circ, V_src,
-          seed_index, n0=1e15, Te=2.0, Ti=0.026, T_gas=300.0, capacity_factor=1.5, n_particles_override=None):
+          seed_index, n0=1e15, Te=2.0, Ti=0.026, T_gas=300.0, capacity_factor=1.5, n_particles_override=None,
+          split_cells=0):
     dr, dz = R / nr, Z / nz
     if geometry == "cylinder":
         node, cell, eps = cylinder_geometry(nr, nz, R, Z)
@@ -243,9 +263,9 @@ def _make(name, nr, nz, R, Z, geometry, pressure_mtorr, n_per_species, steps_per
     seed = SEED_BASE + seed_index
     rng = np.random.default_rng(seed)
     vp = plasma_volume(cell, dr, dz)
-    w = n0 * vp / n
-    el = load_particles(cell, dr, dz, n, Te, ELECTRON_MASS, rng)
+    el = load_particles(cell, dr, dz, n, Te, ELECTRON_MASS, rng, split_cells=split_cells)
     io = load_particles(cell, dr, dz, n, Ti, ARGON_MASS, rng, co_located=el)
+    w = n0 * vp / (n if el.w is None else float(el.w.sum()))  # macro weight of ratio 1
     E, sig = xs_table()
     cap = int(capacity_factor * n) + 4096
     return Workload(
@@ -255,7 +275,7 @@ def _make(name, nr, nz, R, Z, geometry, pressure_mtorr, n_per_species, steps_per
         xs_energy=E, xs_sigma=sig, thr_ex=THR_EXC, thr_iz=THR_ION, B_ej=B_EJECT, circuit=circuit,
         circ=tuple(circ) + (0.0,) * (8 - len(circ)), V_src=V_src, f_src=F_RF, phase_src=0.0, n_sub=16,
         steps_per_rf=steps_per_rf, pcg_tol=1e-10, pcg_maxit=20000, ceq_refresh=1, seed=seed & 0xFFFFFFFF,
-        particles=(el, io), capacity=(cap, cap))
+        particles=(el, io), capacity=(cap, cap), split_cells=split_cells)
 
 
 # L-network of the 150 V GEC-like case: Rs, Cm1 (shunt), Lm, Cm2 (series), Rm, Cstray, Rstray, Lstray.
@@ -280,14 +300,16 @@ def gec_512(n_per_species=32_000_000, **kw):
                  CIRCUIT_IMN, IMN_GEC, 150.0, 2, n_particles_override=n_per_species, **kw)
 
 
-def gec_case(nr, nz, pressure_mtorr, V_src, cm2=200e-12, n_per_species=1_000_000, seed_index=16, name=None):
+def gec_case(nr, nz, pressure_mtorr, V_src, cm2=200e-12, n_per_species=1_000_000, seed_index=16, name=None,
+             split_cells=0):
     """GEC-like cell on an nr x nz grid at a given pressure, source amplitude and
-    series matching capacitor (the L-network of IMN_GEC otherwise)."""
+    series matching capacitor (the L-network of IMN_GEC otherwise); split_cells
+    > 0 loads radially weighted particles and enables splitting."""
     circ = list(IMN_GEC)
     circ[3] = cm2
     nm = name or f"gec-{nr}x{nz}-{pressure_mtorr:g}mT-{V_src:g}V"
     return _make(nm, nr, nz, 0.10, 0.06, "gec", pressure_mtorr, n_per_species, 200, CIRCUIT_IMN, tuple(circ), V_src,
-                 seed_index, n_particles_override=n_per_species)
+                 seed_index, n_particles_override=n_per_species, split_cells=split_cells)
 
 
 PRESETS = {"c1": small_cylinder, "c2": gec_256, "c3": gec_512}

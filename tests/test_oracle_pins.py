@@ -934,3 +934,88 @@ def test_blocking_capacitor_charges_at_the_closed_form_rate():
     assert b["u_dc"] - a["u_dc"] == pytest.approx(I0 * T / (Ceq + Cb), rel=1e-9, abs=0)
     assert b["i_dc"] == pytest.approx(-I0 * Cb / (Ceq + Cb), rel=1e-9, abs=0)
     assert abs(b["u1"] - a["u1"]) <= 1e-9 * abs(b["u1"])
+
+
+# ---------------------------------------------------------------- unequal weights and splitting
+def test_weight_ratio_scales_deposit_and_credit_linearly():
+    """A macroparticle of weight ratio w deposits w times the node weights of one of ratio 1 at
+    the same place (the deposit is linear in the weight), and an absorbed one credits q w_s w."""
+    base = W.small_cylinder(n_per_species=16)
+    n = 2000
+    rng = np.random.default_rng(3)
+    r = np.sqrt(rng.uniform(0.01**2, 0.04**2, n))
+    z = rng.uniform(0.003, 0.02, n)
+    z0 = np.zeros(n)
+    mk = lambda w: W.Particles(r, z, z0, z0, z0, z0, z0, z0, np.arange(n, dtype=np.uint64), w)
+    deps = []
+    for w in (None, np.full(n, 0.25)):
+        o = orc.Oracle(with_particles(base, electrons=mk(w)))
+        o.deposit_only()
+        deps.append(o.field("dep_e"))
+    np.testing.assert_allclose(deps[1], 0.25 * deps[0], rtol=1e-15, atol=0)
+    assert deps[1].sum() == pytest.approx(0.25 * n, rel=1e-13, abs=0)
+    # an electron of ratio 0.375 flying into the powered plate at z = 0
+    e = beam(1, 0.02, 0.3 * base.dz, (0.0, 0.0, -0.5 * base.dz / base.dt))
+    e.w = np.array([0.375])
+    wl = dataclasses.replace(with_particles(base, electrons=e), n_gas=0.0, V_src=0.0)
+    o = orc.Oracle(wl)
+    o.set_field("Er", np.zeros(o.n_nodes))
+    o.set_field("Ez", np.zeros(o.n_nodes))
+    o.particle_phase()
+    s = o.scalars()
+    assert s["absn_e_pow"] == 1 and s["absq_e_pow"] == pytest.approx(0.375 * wl.q[0] * wl.w[0], rel=1e-15, abs=0)
+
+
+def test_splitting_halves_heavy_particles_entering_small_axial_cells():
+    """The splitting rule (Sec. 2's noise fix for unequal weights): radial cell i < i_s has the
+    target ratio (2i+1)/(2 i_s + 1); an electron of ratio 1 moving inward from cell 3 to cell 2
+    (i_s = 8: target 5/17, twice that 10/17 < 1) becomes two halves of ratio 1/2 with identical
+    state, the second with the split id; one cell further in (target 3/17, 6/17 < 1/2) each half
+    splits again; at cell 0 (2/17 < 1/4) again.  Weight and deposited count are conserved at
+    every step, and a particle moving outward never splits."""
+    base = W.small_cylinder(n_per_species=16)
+    dr, dt = base.dr, base.dt
+    e = W.Particles(np.array([3.5 * dr, 5.5 * dr]), np.array([0.0127, 0.0127]), np.array([-dr / dt, dr / dt]),
+                    np.zeros(2), np.zeros(2), np.zeros(2), np.zeros(2), np.zeros(2), np.array([7, 8], np.uint64),
+                    np.ones(2))
+    wl = dataclasses.replace(with_particles(base, electrons=e), n_gas=0.0, V_src=0.0, split_cells=8)
+    o = orc.Oracle(wl)
+    o.set_field("Er", np.zeros(o.n_nodes))
+    o.set_field("Ez", np.zeros(o.n_nodes))
+    counts, splits = [], []
+    for step in range(3):
+        o.set_step(step)
+        o.particle_phase()
+        g = o.get_particles(0)
+        counts.append(len(g["id"]))
+        splits.append(o.scalars()["splits_e"])
+        assert g["w"].sum() == pytest.approx(2.0, rel=1e-15, abs=0)
+        assert o.field("dep_e").sum() == pytest.approx(2.0, rel=1e-13, abs=0)
+        inward = g["vr"] < 0
+        assert np.all(g["w"][~inward] == 1.0)  # the outward electron keeps its ratio
+        np.testing.assert_allclose(g["w"][inward], 0.5 ** (step + 1), rtol=0, atol=0)
+        assert np.ptp(g["r"][inward]) == 0.0 and np.ptp(g["vr"][inward]) == 0.0  # halves are copies
+    assert counts == [3, 5, 9] and splits == [1, 2, 4]
+    # the second halves carry the split ids of their parents in the step they split
+    g = o.get_particles(0)
+    first = orc.split_ids(0, wl.seed, [7])[0]
+    assert first in set(g["id"].tolist())
+
+
+def test_radially_weighted_loading_samples_the_uniform_density():
+    """Radially weighted loading (ratio (2i+1)/(2 i_s + 1) near the axis, uniform counts there)
+    still samples the uniform density n0: the deposited density averaged over the inner nodes
+    is n0 within a few per cent, near the axis as far out."""
+    wl = W.gec_case(64, 32, 30.0, 150.0, n_per_species=400_000, split_cells=16)
+    o = orc.Oracle(wl)
+    o.deposit_only()
+    dens = wl.w[0] * o.field("dep_e") / np.where(o.field("vnode") > 0, o.field("vnode"), np.inf)
+    cell = np.asarray(wl.cell_kind).reshape(wl.nz, wl.nr)
+    rows = slice(10, 20)  # the gap between the electrodes
+    assert (cell[10:20, :50] == 0).all()
+    near, far = dens[rows, 1:8].mean(), dens[rows, 30:50].mean()
+    assert near == pytest.approx(1e15, rel=0.03, abs=0)
+    assert far == pytest.approx(1e15, rel=0.03, abs=0)
+    e = wl.particles[0]
+    i = np.floor(e.r / wl.dr).astype(int)
+    np.testing.assert_array_equal(e.w, W.radial_weight(i, 16).astype(np.float32).astype(np.float64))
