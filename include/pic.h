@@ -116,6 +116,21 @@ typedef struct pic_config {
   int64_t spin_limit;          /* clock cycles a field-solve grid barrier may wait
                                   for the other blocks before the solve gives up
                                   with PIC_ETIMEOUT (0 = default, 4e9: ~2 s)     */
+  int32_t weighted;            /* 1: unequal macroparticle weights (Sec. 2) -- each
+                                  particle carries a weight ratio w in (0, 1]
+                                  (macro weight w * w[species]) that scales its
+                                  deposit and absorbed charge; newborn particles
+                                  take their parent's ratio.  0: all ratios 1  */
+  int32_t split_cells;         /* particle splitting near the axis (Sec. 2;
+                                  requires weighted = 1; 0 = off, at most nr):
+                                  radial cell i < split_cells has the target
+                                  ratio (2i+1)/(2 split_cells + 1), 1 beyond; a
+                                  particle that enters a cell with a ratio above
+                                  twice its target is split into two halves of
+                                  the same state, the second with the id
+                                  Philox4x32-10(key = parent id, counter = (step,
+                                  0x5B17, 0, seed)) with bit 63 set; both halves
+                                  count as deposited by the parent's deposit   */
 } pic_config;
 
 /* Particle arrays of one species in FP64 host memory (caller-owned).  Position
@@ -127,6 +142,9 @@ typedef struct pic_particles {
   double *r, *z, *vr, *vt, *vz, *ar, *at, *az;
   uint64_t *id;
   int32_t *cell;
+  double *w;  /* weight ratios in (0, 1]: input of weighted handles (NULL = all 1;
+                 must be NULL for unweighted ones), output if not NULL (all 1
+                 for unweighted handles) */
 } pic_particles;
 
 typedef struct pic_handle pic_handle;
@@ -221,7 +239,7 @@ int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss);
                                 reuses it; a failed solve resets it to 0),
                                 rebuild period, last solve's iterations,
                                 outer refinement steps, status */
-#define PIC_NSCALARS 47
+#define PIC_NSCALARS 49
 /* Scalars: [0] step, [1] t, [2] U_E, [3] Q_E, [4] C_eq, [5] I_conv, [6] I_ccp,
  * [7..12] circuit state (RLC: Qb, Ib, QE; IMN: Q1, Q2, I2, Qccp, Istray, QE),
  * [13] field-solve iterations, [14] relative residual, [15..16] nu_max e/i,
@@ -231,7 +249,9 @@ int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss);
  * i: isotropic, charge exchange, 0), [37..38] births e/i, [39..41] ion
  * current of the last window (powered, grounded, surface), [42..43] first
  * harmonic of I_ccp over the last window (Re, Im), [44] windows completed,
- * [45] C_eq by the Gauss route, [46] field-solve status. */
+ * [45] C_eq by the Gauss route, [46] field-solve status, [47..48] particles
+ * split near the axis in the last step e/i.  The absorbed charge of weighted
+ * handles sums the particles' weight ratios (to 2^-32 of a macro weight). */
 
 /* pic_diag -- copy one diagnostic to a host buffer of `bytes` bytes
  * (synchronises).  Errors: PIC_EINVAL for an unknown selector or short buffer. */

@@ -128,7 +128,7 @@ StoreView<T> view(pic_handle *h, int buf, int s) {
   Store &S = h->st[buf][s];
   StoreView<T> v;
   v.pa = (Vec4<T> *)S.pa; v.pb = (Vec4<T> *)S.pb;
-  v.id = S.id; v.cell = S.cell; v.start = S.start; v.cap = S.cap; v.fill = S.fill; v.meta = S.meta;
+  v.id = S.id; v.w = (T *)S.w; v.cell = S.cell; v.start = S.start; v.cap = S.cap; v.fill = S.fill; v.meta = S.meta;
   v.capacity = (int)h->capacity[s];
   return v;
 }
@@ -172,6 +172,8 @@ PushParams<T> push_params(pic_handle *h, int in_buf) {
   P.dep_scale = (T)(h->prec == PIC_FP32 ? 67108864.0 : 1099511627776.0);
   P.dep_one = h->prec == PIC_FP32 ? (1ull << 26) : (1ull << 40);
   P.flags = h->d_flags;
+  P.weighted = h->weighted ? 1 : 0;
+  P.split_cells = c.split_cells;
   return P;
 }
 
@@ -192,6 +194,7 @@ FieldParams field_params(pic_handle *h, const double *chi, double *Gr, double *G
     F.chi_coef[s] = c.dt * c.dt / (2.0 * kEps0) * c.q[s] * c.q[s] / c.m[s] * c.w[s];
   }
   F.dep_inv_scale = dep_inv_scale(h);
+  F.surf_scale = h->weighted ? 1.0 / kCreditOne : 1.0;
   F.chi = const_cast<double *>(chi);
   F.qrhs = h->d_qrhs; F.phi = h->d_phi; F.Gr = Gr; F.Gz = Gz; F.dinv = dinv;
   F.scalars = h->d_scalars;
@@ -237,6 +240,7 @@ CircuitParams circuit_params(pic_handle *h, int n_run, double *U_hist, uint32_t 
   C.V = c.V_src; C.f = c.f_src; C.phase = c.phase_src; C.dt = c.dt;
   C.qw[0] = c.q[0] * c.w[0]; C.qw[1] = c.q[1] * c.w[1];
   C.counters = h->d_counters;
+  C.weighted = h->weighted ? 1 : 0;
   C.step_ptr = h->d_step;
   C.scalars = h->d_scalars;
   C.n_run = n_run; C.U_hist = U_hist; C.step_inc = step_inc;
@@ -258,6 +262,7 @@ DiagParams diag_params(pic_handle *h) {
   D.qw_ion = c.q[1] * c.w[1];
   D.f = c.f_src; D.dt = c.dt; D.window = c.steps_per_rf;
   D.counters = h->d_counters;
+  D.weighted = h->weighted ? 1 : 0;
   D.step_ptr = h->d_step; D.step_mut = h->d_step;
   for (int s = 0; s < 2; ++s) { D.dens_sum[s] = h->d_dens_sum[s]; D.dens_avg[s] = h->d_dens_avg[s]; }
   D.scalars = h->d_scalars;
@@ -468,6 +473,8 @@ bool check_config(const pic_config *c) {
   if (c->capacity[0] < 1 || c->capacity[1] < 1 || c->capacity[0] > 2000000000ll || c->capacity[1] > 2000000000ll)
     return false;
   if (c->spin_limit < 0) return false;
+  if (c->weighted != 0 && c->weighted != 1) return false;
+  if (c->split_cells < 0 || c->split_cells > c->nr || (c->split_cells > 0 && !c->weighted)) return false;
   if (!(c->m[0] > 0) || !(c->m[1] > 0) || !(c->m_gas > 0)) return false;
   for (int k = 0; k + 1 < c->n_xs; ++k)
     if (!(c->xs_energy[k + 1] > c->xs_energy[k]) || !(c->xs_energy[k] > 0)) return false;
@@ -495,7 +502,8 @@ int upload_species(pic_handle *h, int s, int64_t n, const pic_particles *p) {
       ~DevTmp() { if (p) cudaFree(p); }
     } raw, work, bins;
     const size_t m = (size_t)n;
-    CK(cudaMalloc(&raw.p, 9 * sizeof(double) * m));
+    const bool has_w = h->weighted && p->w;
+    CK(cudaMalloc(&raw.p, (has_w ? 10 : 9) * sizeof(double) * m));
     CK(cudaMalloc(&work.p, (sizeof(int2) + 2 * sizeof(T)) * m));
     CK(cudaMalloc(&bins.p, sizeof(int) * (2 * (size_t)nb + 1)));
     double *d_raw = static_cast<double *>(raw.p);
@@ -504,6 +512,7 @@ int upload_species(pic_handle *h, int s, int64_t n, const pic_particles *p) {
       CK(cudaMemcpyAsync(d_raw + k * m, cols[k], sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
     auto *d_id = reinterpret_cast<unsigned long long *>(d_raw + 8 * m);
     CK(cudaMemcpyAsync(d_id, p->id, sizeof(unsigned long long) * m, cudaMemcpyHostToDevice, h->stream));
+    if (has_w) CK(cudaMemcpyAsync(d_raw + 9 * m, p->w, sizeof(double) * m, cudaMemcpyHostToDevice, h->stream));
     int *d_count = static_cast<int *>(bins.p), *d_start = d_count + nb;
     unsigned *d_err = reinterpret_cast<unsigned *>(d_start + nb);
     CK(cudaMemsetAsync(d_count, 0, sizeof(int) * ((size_t)nb + 0), h->stream));
@@ -513,6 +522,7 @@ int upload_species(pic_handle *h, int s, int64_t n, const pic_particles *p) {
     U.r = d_raw; U.z = d_raw + m; U.vr = d_raw + 2 * m; U.vt = d_raw + 3 * m; U.vz = d_raw + 4 * m;
     U.ar = d_raw + 5 * m; U.at = d_raw + 6 * m; U.az = d_raw + 7 * m;
     U.id = d_id;
+    U.w = has_w ? d_raw + 9 * m : nullptr;
     U.dr = c.dr; U.dz = c.dz;
     U.map = h->map;
     U.cell_kind = h->d_cell_kind;
@@ -528,7 +538,7 @@ int upload_species(pic_handle *h, int s, int64_t n, const pic_particles *p) {
     CK(cudaMemcpyAsync(fill.data(), d_count, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(&err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
     if (sync(h)) return PIC_ECUDA;
-    if (err) return PIC_EINVAL;  // a particle outside the plasma: the store is untouched
+    if (err) return PIC_EINVAL;  // a particle outside the plasma or a bad ratio: the store is untouched
     int run = 0;
     for (int b = 0; b < nb; ++b) { start[b] = run; run += fill[b]; }
     CK(cudaMemcpyAsync(d_start, start.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, h->stream));
@@ -566,6 +576,8 @@ int download_species(pic_handle *h, int s, pic_particles *out, int64_t capn, int
   std::vector<Vec4<T>> va(used), vb(used);
   std::vector<unsigned long long> id(used);
   std::vector<int> cell(used);
+  std::vector<T> wr(h->weighted ? used : 0);
+  if (h->weighted) CK(cudaMemcpy(wr.data(), S.w, sizeof(T) * used, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(va.data(), S.pa, sizeof(Vec4<T>) * used, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(vb.data(), S.pb, sizeof(Vec4<T>) * used, cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(id.data(), S.id, sizeof(unsigned long long) * used, cudaMemcpyDeviceToHost));
@@ -580,6 +592,7 @@ int download_species(pic_handle *h, int s, pic_particles *out, int64_t capn, int
     out->ar[k] = b.y; out->at[k] = b.z; out->az[k] = b.w;
     out->id[k] = id[slot];
     if (out->cell) out->cell[k] = j * h->nr + i;
+    if (out->w) out->w[k] = h->weighted ? (double)wr[slot] : 1.0;
     ++k;
   };
   for (int b = 0; b < h->nbins; ++b) {
@@ -710,6 +723,7 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
   h->slack = cfg->bin_slack > 0 ? (float)cfg->bin_slack : 0.25f;
   h->capacity[0] = cfg->capacity[0];
   h->capacity[1] = cfg->capacity[1];
+  h->weighted = cfg->weighted != 0;
   int TX = cfg->tile_r > 0 ? cfg->tile_r : 4, TY = cfg->tile_z > 0 ? cfg->tile_z : 4;
   h->map.nr = h->nr; h->map.nz = h->nz; h->map.TX = TX; h->map.TY = TY;
   h->map.ntx = (h->nr + TX - 1) / TX; h->map.nty = (h->nz + TY - 1) / TY;
@@ -789,6 +803,7 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
         DA(S.pa, 4 * h->esz * cap);
         DA(S.pb, 4 * h->esz * cap);
         DA(S.id, sizeof(unsigned long long) * cap);
+        if (h->weighted) DA(S.w, h->esz * cap);
         DA(S.cell, sizeof(int) * cap);
         DA(S.start, sizeof(int) * h->nbins);
         DA(S.cap, sizeof(int) * h->nbins);
@@ -853,6 +868,7 @@ int pic_set_particles(pic_handle *h, int species, int64_t n, const pic_particles
   if (!h || species < 0 || species > 1 || n < 0 || (n > 0 && (!p || !p->r || !p->z || !p->vr || !p->vt || !p->vz ||
                                                                 !p->ar || !p->at || !p->az || !p->id)))
     return PIC_EINVAL;
+  if (n > 0 && p->w && !h->weighted) return PIC_EINVAL;  // ratios need a weighted handle
   if (n > h->capacity[species]) return PIC_EOVERFLOW;
   if (sync(h)) return PIC_ECUDA;
   return h->prec == PIC_FP32 ? upload_species<float>(h, species, n, p) : upload_species<double>(h, species, n, p);
@@ -1227,7 +1243,8 @@ int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
     o[15] = h->numax[0]; o[16] = h->numax[1]; o[17] = h->pcoll[0]; o[18] = h->pcoll[1];
     for (int s = 0; s < 2; ++s)
       for (int k = 0; k < 3; ++k) {
-        o[19 + 3 * s + k] = c.q[s] * c.w[s] * (double)cnt[CNT_ABS + 3 * s + k];
+        o[19 + 3 * s + k] = c.q[s] * c.w[s] *
+                            (h->weighted ? (double)cnt[CNT_ABSW + 3 * s + k] / kCreditOne : (double)cnt[CNT_ABS + 3 * s + k]);
         o[25 + 3 * s + k] = (double)cnt[CNT_ABS + 3 * s + k];
         o[31 + 3 * s + k] = (double)cnt[CNT_COLL + 3 * s + k];
       }
@@ -1236,6 +1253,7 @@ int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
     for (int k = 0; k < 3; ++k) o[39 + k] = sc[SC_IONCUR + k];
     o[42] = sc[SC_I1_RE]; o[43] = sc[SC_I1_IM]; o[44] = sc[SC_WINDOWS]; o[45] = sc[SC_CEQ_GAUSS];
     o[46] = pcg[2];
+    o[47] = (double)cnt[CNT_SPLIT + 0]; o[48] = (double)cnt[CNT_SPLIT + 1];
     return PIC_OK;
   }
   if (what == PIC_DIAG_CIRCUIT) {
@@ -1302,7 +1320,9 @@ int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
       CK(cudaMemcpy(u0.data(), h->d_surf[0], sizeof(unsigned long long) * h->nn, cudaMemcpyDeviceToHost));
       CK(cudaMemcpy(u1.data(), h->d_surf[1], sizeof(unsigned long long) * h->nn, cudaMemcpyDeviceToHost));
       const pic_config &c = h->cfg;
-      for (int a = 0; a < h->nn; ++a) o[a] = c.q[0] * c.w[0] * (double)u0[a] + c.q[1] * c.w[1] * (double)u1[a];
+      const double us = h->weighted ? 1.0 / kCreditOne : 1.0;
+      for (int a = 0; a < h->nn; ++a)
+        o[a] = c.q[0] * c.w[0] * ((double)u0[a] * us) + c.q[1] * c.w[1] * ((double)u1[a] * us);
       return PIC_OK;
     }
     default: return PIC_EINVAL;
@@ -1384,8 +1404,13 @@ int pic_set_conv_current(pic_handle *h, double I_conv) {
   double per = c.q[0] * c.w[0] / c.dt;
   if (I_conv != 0.0) {
     double k = I_conv / per;
-    if (!(k >= 0) || std::fabs(k - std::llround(k)) > 1e-9 * (1 + std::fabs(k))) return PIC_EINVAL;
-    cnt[CNT_ABS + 0] = (unsigned long long)std::llround(k);
+    if (h->weighted) {  // weighted tallies hold macro weights to 2^-32
+      if (!(k >= 0) || !(k < 1e9)) return PIC_EINVAL;
+      cnt[CNT_ABSW + 0] = (unsigned long long)std::llround(k * kCreditOne);
+    } else {
+      if (!(k >= 0) || std::fabs(k - std::llround(k)) > 1e-9 * (1 + std::fabs(k))) return PIC_EINVAL;
+      cnt[CNT_ABS + 0] = (unsigned long long)std::llround(k);
+    }
   }
   CK(cudaMemcpy(h->d_counters, cnt, sizeof(cnt), cudaMemcpyHostToDevice));
   return PIC_OK;

@@ -15,6 +15,12 @@
 
 namespace pic {
 
+// Macro particles absorbed in the last step in tally slot k (species*3 + kind):
+// the count, or for weighted particles the sum of their weight ratios.
+__device__ __forceinline__ double absorbed(const unsigned long long *counters, int weighted, int k) {
+  return weighted ? (double)counters[CNT_ABSW + k] * (1.0 / kCreditOne) : (double)counters[CNT_ABS + k];
+}
+
 // ---- assembly ---------------------------------------------------------------
 // Node pass: chi (D1 susceptibility dt^2/(2 eps0) sum_s q_s^2 n_s/m_s), node
 // charge (particles + surface), Dirichlet values.
@@ -25,7 +31,8 @@ __global__ void k_assemble_nodes(const FieldParams F) {
     double Qi = (double)F.dep[1][a] * F.dep_inv_scale;
     double v = F.vnode[a];
     F.chi[a] = v > 0.0 ? (F.chi_coef[0] * Qe + F.chi_coef[1] * Qi) / v : 0.0;
-    F.qrhs[a] = F.qw[0] * (Qe + (double)F.surf[0][a]) + F.qw[1] * (Qi + (double)F.surf[1][a]);
+    F.qrhs[a] = F.qw[0] * (Qe + (double)F.surf[0][a] * F.surf_scale) +
+                F.qw[1] * (Qi + (double)F.surf[1][a] * F.surf_scale);
     int k = F.node_kind[a];
     if (k == 1) F.phi[a] = UE;
     else if (k == 2) F.phi[a] = 0.0;
@@ -324,7 +331,7 @@ __global__ void k_circuit(const CircuitParams C) {
   double *S = C.scalars;
   const double two_pi = 6.283185307179586476925286766559;
   double ceq = S[SC_CEQ];
-  double Iconv = (C.qw[0] * (double)C.counters[CNT_ABS + 0] + C.qw[1] * (double)C.counters[CNT_ABS + 3]) / C.dt;
+  double Iconv = (C.qw[0] * absorbed(C.counters, C.weighted, 0) + C.qw[1] * absorbed(C.counters, C.weighted, 3)) / C.dt;
   S[SC_ICONV] = Iconv;
   uint32_t step = *C.step_ptr;
   if (C.kind == 0) {
@@ -448,7 +455,7 @@ __global__ void k_diag(const DiagParams D) {
     for (int k = 0; k < 6; ++k) S[SC_CP + k] += p[k];
     S[SC_CDC + 0] += w[3];
     S[SC_CDC + 1] += w[4];
-    for (int k = 0; k < 3; ++k) S[SC_IONQ + k] += D.qw_ion * (double)D.counters[CNT_ABS + 3 + k];
+    for (int k = 0; k < 3; ++k) S[SC_IONQ + k] += D.qw_ion * absorbed(D.counters, D.weighted, 3 + k);
     S[SC_WINCOUNT] += 1.0;
     *D.step_mut = step + 1;
   }

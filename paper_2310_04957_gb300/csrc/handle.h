@@ -18,6 +18,7 @@ namespace pic {
 struct Store {
   void *pa = nullptr, *pb = nullptr;  // Vec4 (fr, fz, vr, vt) and (vz, ar, at, az)
   unsigned long long *id = nullptr;
+  void *w = nullptr;                  // weight ratios (weighted handles only)
   int *cell = nullptr, *start = nullptr, *cap = nullptr, *fill = nullptr;
   BinMeta *meta = nullptr;
 };
@@ -37,6 +38,7 @@ struct pic_handle {
   int nbins = 0, ntiles = 0;
   float slack = 0.25f;
   int64_t capacity[2] = {0, 0};
+  bool weighted = false;  // particles carry weight ratios (cfg.weighted)
   // device: geometry, operator, fields
   int8_t *d_node_kind = nullptr, *d_cell_kind = nullptr, *d_bin_plasma = nullptr;
   double *d_Gvac_r = nullptr, *d_Gpl_r = nullptr, *d_Gvac_z = nullptr, *d_Gpl_z = nullptr, *d_vnode = nullptr;

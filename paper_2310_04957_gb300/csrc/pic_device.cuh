@@ -28,8 +28,14 @@ enum Counter : int {
   CNT_BORN = 12,      // [species]
   CNT_OVERFLOW = 14,  // particles dropped because the overflow region was full
   CNT_OUTSIDE = 15,   // particles read from the store outside the plasma
-  CNT_N = 16
+  CNT_ABSW = 16,      // weighted particles: absorbed macro weight [species*3 + kind],
+                      // in units of 2^-32 of the species' macro weight
+  CNT_SPLIT = 22,     // [species] particles split near the axis
+  CNT_N = 24
 };
+
+// Fixed-point unit of weighted absorption tallies (CNT_ABSW, surface charge).
+constexpr double kCreditOne = 4294967296.0;  // 2^32
 
 // Scalars (double) shared by the circuit, assembly and diagnostics kernels.
 enum Scalar : int {
@@ -64,6 +70,7 @@ struct StoreView {
   Vec4<T> *pa;    // (fr, fz, vr, vt)
   Vec4<T> *pb;    // (vz, ar, at, az)
   unsigned long long *id;
+  T *w;           // weight ratios in (0, 1] (weighted handles only)
   int *cell;      // only meaningful in the overflow region
   int *start;     // [nbins] first slot of each bin
   int *cap;       // [nbins] room of each bin

@@ -40,6 +40,8 @@ struct PushParams {
   T dep_scale;
   unsigned long long dep_one;
   uint32_t *flags;
+  int weighted;             // particles carry weight ratios (store column w)
+  int split_cells;          // split heavy particles in the first split_cells radial cells (0: off)
 };
 
 struct FieldParams {
@@ -49,6 +51,7 @@ struct FieldParams {
   const double *vnode;
   const unsigned long long *dep[2];
   const unsigned long long *surf[2];
+  double surf_scale;        // macro particles per surface-tally unit (1, or 2^-32 weighted)
   double dep_inv_scale;
   double qw[2];             // q_s w_s
   double chi_coef[2];       // dt^2/(2 eps0) q_s^2/m_s w_s
@@ -93,6 +96,7 @@ struct CircuitParams {
   double V, f, phase, dt;
   double qw[2];
   const unsigned long long *counters;
+  int weighted;             // absorbed charge from the weighted tallies
   const uint32_t *step_ptr;
   double *scalars;
   int n_run;                // steps to advance (1 inside the step graph)
@@ -114,6 +118,7 @@ struct DiagParams {
   double f, dt;
   int window;
   const unsigned long long *counters;
+  int weighted;             // absorbed charge from the weighted tallies
   const uint32_t *step_ptr;
   uint32_t *step_mut;
   double *dens_sum[2], *dens_avg[2];
@@ -121,6 +126,7 @@ struct DiagParams {
 };
 
 template <typename T> cudaError_t launch_particles(const PushParams<T> &P, cudaStream_t st);
+template <typename T> cudaError_t launch_particles_weighted(const PushParams<T> &P, cudaStream_t st);
 bool tile_supported(int tx, int ty);
 template <typename T> cudaError_t launch_deposit_only(const PushParams<T> &P, cudaStream_t st);
 struct LayoutParams {
@@ -143,6 +149,7 @@ struct UploadParams {
   int64_t n;
   const double *r, *z, *vr, *vt, *vz, *ar, *at, *az;
   const unsigned long long *id;
+  const double *w;   // weight ratios (weighted stores; nullptr: all 1)
   double dr, dz;
   BinMap map;
   const int8_t *cell_kind;
@@ -150,7 +157,7 @@ struct UploadParams {
   const int *start;  // [nbins] first slot of each bin (pass 2)
   int2 *bin_rank;    // [n] bin and rank within it
   T *fr_tmp, *fz_tmp;
-  unsigned *err;     // set to 1 if any particle is outside the plasma
+  unsigned *err;     // set to 1 if any particle is outside the plasma or has a ratio outside (0, 1]
   StoreView<T> out;
 };
 template <typename T> cudaError_t launch_upload_bin(const UploadParams<T> &U, cudaStream_t st);

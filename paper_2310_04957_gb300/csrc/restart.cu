@@ -6,7 +6,8 @@
 // host step counter, then the device state as blobs, each prefixed by its
 // byte count and checked against what the restored handle expects.  The
 // particle store is written as stored (cell-relative positions, bins,
-// overflow region); only the slots in use are written.
+// overflow region, weight ratios of weighted handles); only the slots in use
+// are written.
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -19,7 +20,7 @@ using namespace pic;
 namespace {
 
 const char kMagic[8] = {'P', 'I', 'C', 'R', 'S', 'T', 'G', 'B'};
-const uint32_t kVersion = 1;
+const uint32_t kVersion = 2;
 const size_t kChunk = size_t(64) << 20;  // host bounce buffer
 
 struct File {
@@ -129,7 +130,9 @@ size_t used_slots(pic_handle *h, int s, const BinMeta &m) {
 
 std::vector<Blob> store_columns(pic_handle *h, const Store &S, size_t used) {
   const size_t e = 4 * h->esz * used;
-  return {{S.pa, e}, {S.pb, e}, {S.id, sizeof(unsigned long long) * used}, {S.cell, sizeof(int) * used}};
+  std::vector<Blob> b = {{S.pa, e}, {S.pb, e}, {S.id, sizeof(unsigned long long) * used}, {S.cell, sizeof(int) * used}};
+  if (h->weighted) b.push_back({S.w, h->esz * used});
+  return b;
 }
 
 }  // namespace

@@ -9,7 +9,8 @@
 //   up(b)|e2: 384->128, 128->128 (d2)   up(d2)|e1: 192->64, 64->64 (d1)
 //   up(d1)|e0: 96->32, 32->32 (d0)      out = 1x1 32->1
 // Concatenation is free: encoders write into the channel slice of the
-// decoder's input buffer.  Input channels: 0 = rho~, 1 = chi, 2 = mask, 3..15 = 0.
+// decoder's input buffer.  Input channels: 0 = the scaled Jacobi value D^-1 r / s
+// of the residual it is applied to, 1 = chi, 2 = Dirichlet mask, 3..15 = 0.
 #include <cmath>
 #include <cstdio>
 #include <cstring>

@@ -9,7 +9,8 @@ namespace pic {
 // ---------------------------------------------------------------------------
 // Upload of one species from its raw FP64 columns (already on the device).
 // Pass 1: each particle's cell (checked: r, z >= 0, inside the grid, a plasma
-// cell), its cell-relative offsets in the store's precision (below 1) and its
+// cell; a weight ratio in (0, 1]), its cell-relative offsets in the store's
+// precision (below 1) and its
 // rank within its bin (one atomic per particle: the order inside a bin is
 // arbitrary, which nothing downstream depends on).  Pass 2, after the bins'
 // starts are known: the scatter into the binned store.
@@ -20,7 +21,8 @@ __global__ void k_upload_bin(UploadParams<T> U) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < U.n; k += stride) {
     const double r = U.r[k], z = U.z[k];
     int bin = -1;
-    if (r >= 0.0 && z >= 0.0) {
+    const bool w_ok = !U.w || (U.w[k] > 0.0 && U.w[k] <= 1.0);
+    if (w_ok && r >= 0.0 && z >= 0.0) {
       const double x = r / U.dr, y = z / U.dz;
       const double fx = floor(x), fy = floor(y);
       const int i = fx < 2.0e9 ? (int)fx : U.map.nr, j = fy < 2.0e9 ? (int)fy : U.map.nz;
@@ -55,6 +57,7 @@ __global__ void k_upload_scatter(UploadParams<T> U) {
     S.pa[d] = Vec4<T>{U.fr_tmp[k], U.fz_tmp[k], (T)U.vr[k], (T)U.vt[k]};
     S.pb[d] = Vec4<T>{(T)U.vz[k], (T)U.ar[k], (T)U.at[k], (T)U.az[k]};
     S.id[d] = U.id[k];
+    if (S.w) S.w[d] = U.w ? (T)U.w[k] : (T)1;
   }
 }
 

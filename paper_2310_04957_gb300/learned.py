@@ -180,23 +180,3 @@ def train_on_discharge(wl, warm_pairs=300, iterate_pairs=200, steps=1500, seed=0
             "loss_pass1": h1[-1], "loss_pass2": h2[-1], "seconds": time.perf_counter() - t0}
     del store
     return net, d, info
-
-
-def profile_forward(H=256, W=512, seed=1):
-    """One U-Net forward inside a cudaProfilerStart/Stop range, after creation
-    (tiling autotune), parameters and three warm-up forwards: the range a
-    profiler started with profiling off (ncu --profile-from-start off) captures."""
-    import torch
-
-    net = pic.UNet(H, W)
-    net.set_params(init_params(seed))
-    inp = torch.randn(3, H * W, device="cuda")
-    out = torch.zeros(H * W, device="cuda")
-    for _ in range(3):
-        net.forward(inp.data_ptr(), out.data_ptr())
-    torch.cuda.synchronize()
-    torch.cuda.profiler.start()
-    net.forward(inp.data_ptr(), out.data_ptr())
-    torch.cuda.synchronize()
-    torch.cuda.profiler.stop()
-    return net.status()

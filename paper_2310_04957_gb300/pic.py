@@ -27,13 +27,13 @@ DIAG_SCALARS = 100
 DIAG_STORE = 101
 DIAG_SOLVER = 102
 DIAG_CIRCUIT = 103
-NSCALARS = 47
+NSCALARS = 49
 SCALARS = ["step", "t", "U_E", "Q_E", "C_eq", "I_conv", "I_ccp", "y0", "y1", "y2", "y3", "y4", "y5", "pcg_iters",
            "pcg_relres", "numax_e", "numax_i", "pcoll_e", "pcoll_i", "absq_e_pow", "absq_e_gnd", "absq_e_surf",
            "absq_i_pow", "absq_i_gnd", "absq_i_surf", "absn_e_pow", "absn_e_gnd", "absn_e_surf", "absn_i_pow",
            "absn_i_gnd", "absn_i_surf", "coll_e_el", "coll_e_ex", "coll_e_iz", "coll_i_iso", "coll_i_cx",
            "coll_i_none", "born_e", "born_i", "ioncur_pow", "ioncur_gnd", "ioncur_surf", "i1_re", "i1_im",
-           "windows", "ceq_gauss", "pcg_status"]
+           "windows", "ceq_gauss", "pcg_status", "splits_e", "splits_i"]
 EXPORTS = ["pic_init", "pic_set_particles", "pic_count", "pic_get_particles", "pic_start", "pic_step",
            "pic_particle_phase", "pic_field_solve", "pic_ceq", "pic_diag", "pic_set_field", "pic_set_step",
            "pic_set_ceq", "pic_set_circuit_state", "pic_set_conv_current", "pic_circuit_run", "pic_status",
@@ -68,12 +68,12 @@ class Config(ctypes.Structure):
         ("pcg_maxit", ctypes.c_int32), ("ceq_refresh", ctypes.c_int32), ("seed", ctypes.c_uint32),
         ("capacity", ctypes.c_int64 * 2), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
         ("tile_r", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("bin_slack", ctypes.c_double),
-        ("spin_limit", ctypes.c_int64),
+        ("spin_limit", ctypes.c_int64), ("weighted", ctypes.c_int32), ("split_cells", ctypes.c_int32),
     ]
 
 
 class Particles(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_void_p) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az", "id", "cell")]
+    _fields_ = [(k, ctypes.c_void_p) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az", "id", "cell", "w")]
 
 
 _lib = None
@@ -142,9 +142,10 @@ class Discharge:
     """One discharge on the current CUDA device (wraps a pic_handle)."""
 
     def __init__(self, wl, precision=PIC_FP32, solver=PIC_SOLVER_PLAIN, stream=None, tile=(0, 0), bin_slack=0.0,
-                 capacity=None, load=True, spin_limit=0):
+                 capacity=None, load=True, spin_limit=0, weighted=None):
         L = lib()
         self.wl = wl
+        self.weighted = bool(wl.weighted if weighted is None else weighted)
         self.nr, self.nz = wl.nr, wl.nz
         keep = []
 
@@ -175,6 +176,8 @@ class Discharge:
         c.tile_r, c.tile_z = tile
         c.bin_slack = bin_slack
         c.spin_limit = spin_limit
+        c.weighted = int(self.weighted)
+        c.split_cells = int(wl.split_cells)
         h = ctypes.c_void_p()
         _check(L.pic_init(ctypes.byref(c), _stream(stream), ctypes.byref(h)), "pic_init")
         self.h = h
@@ -199,7 +202,8 @@ class Discharge:
     def set_particles(self, s, P):
         cols = [np.ascontiguousarray(getattr(P, k), np.float64) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az")]
         ids = np.ascontiguousarray(P.id, np.uint64)
-        v = Particles(*[_p(x) for x in cols], _p(ids), None)
+        w = None if getattr(P, "w", None) is None else np.ascontiguousarray(P.w, np.float64)
+        v = Particles(*[_p(x) for x in cols], _p(ids), None, None if w is None else _p(w))
         _check(lib().pic_set_particles(self.h, s, P.n, ctypes.byref(v)), "pic_set_particles")
 
     def count(self, s):
@@ -212,7 +216,8 @@ class Discharge:
         out = {k: np.zeros(n) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az")}
         out["id"] = np.zeros(n, np.uint64)
         out["cell"] = np.zeros(n, np.int32)
-        v = Particles(*[_p(out[k]) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az", "id", "cell")])
+        out["w"] = np.zeros(n)
+        v = Particles(*[_p(out[k]) for k in ("r", "z", "vr", "vt", "vz", "ar", "at", "az", "id", "cell", "w")])
         got = ctypes.c_int64()
         _check(lib().pic_get_particles(self.h, s, ctypes.byref(v), n, ctypes.byref(got)), "pic_get_particles")
         assert got.value == n
@@ -318,6 +323,7 @@ class Discharge:
         d = cls.__new__(cls)
         d.wl, d.nr, d.nz, d.h = wl, wl.nr, wl.nz, h
         d.capacity = tuple(wl.capacity)
+        d.weighted = bool(wl.weighted)
         return d
 
     def philox(self, ctr, key):

@@ -105,6 +105,11 @@ class Workload:
     def n_nodes(self) -> int:
         return (self.nr + 1) * (self.nz + 1)
 
+    @property
+    def weighted(self) -> bool:
+        """Particles carry weight ratios: splitting is on or a species has ratios."""
+        return self.split_cells > 0 or any(p.w is not None for p in self.particles)
+
 
 # --------------------------------------------------------------------------
 # Cross sections (synthetic, analytic; m^2 vs eV).  Argon's real data are not

@@ -16,7 +16,7 @@ def pic():
 
 
 def particles_from(g):
-    return W.Particles(g["r"], g["z"], g["vr"], g["vt"], g["vz"], g["ar"], g["at"], g["az"], g["id"])
+    return W.Particles(g["r"], g["z"], g["vr"], g["vt"], g["vz"], g["ar"], g["at"], g["az"], g["id"], g.get("w"))
 
 
 def make_pair(wl, precision, **kw):

@@ -62,7 +62,8 @@ def divergence(gd, go, rtol):
 
 
 def _particles(g, idx):
-    return W.Particles(*(np.ascontiguousarray(g[k][idx]) for k in KEYS), np.ascontiguousarray(g["id"][idx]))
+    w = np.ascontiguousarray(g["w"][idx]) if g.get("w") is not None else None
+    return W.Particles(*(np.ascontiguousarray(g[k][idx]) for k in KEYS), np.ascontiguousarray(g["id"][idx]), w)
 
 
 def _empty():
@@ -104,6 +105,16 @@ def classify(wl, E_pre, step, pre, post_dev, post_orc, rtol):
     pre_ids = [set(pre[s]["id"].tolist()) for s in (0, 1)]
     kids = orc.child_ids(step, wl.seed, pre[0]["id"])  # [n_e, 2]: children of every electron
     parent_of = {int(c): int(p) for p, pair in zip(pre[0]["id"].tolist(), kids) for c in pair}
+    # second halves of split particles (Sec. 2): of an old particle (explained by
+    # itself) or of a newborn one (explained by the newborn's parent)
+    split_of = [{}, {}]
+    if wl.split_cells > 0:
+        for s in (0, 1):
+            split_of[s] = dict(zip(orc.split_ids(step, wl.seed, pre[s]["id"]).tolist(), pre[s]["id"].tolist()))
+        for c in (0, 1):
+            born = np.ascontiguousarray(kids[:, c]) if len(kids) else np.zeros(0, np.uint64)
+            for sid, b in zip(orc.split_ids(step, wl.seed, born).tolist(), born.tolist()):
+                split_of[c][sid] = parent_of[b]
     explained = {}
 
     def check(s, pid):
@@ -121,17 +132,25 @@ def classify(wl, E_pre, step, pre, post_dev, post_orc, rtol):
             if pid in pre_ids[s]:
                 check(s, pid)
                 flipped[s].add(pid)
+            elif pid in split_of[s] and split_of[s][pid] in pre_ids[s]:
+                check(s, split_of[s][pid])
+                flipped[s].add(split_of[s][pid])
             else:
-                parent = parent_of.get(pid)
+                parent = parent_of.get(pid, split_of[s].get(pid))
                 assert parent is not None, f"species {s}: divergent particle {pid} is neither old nor a newborn"
                 check(0, parent)
                 flipped[0].add(parent)
-    # every child of a flipped electron leaves the deposit comparison too
+    # every child of a flipped electron leaves the deposit comparison too, and
+    # so does the second half of every flipped particle that split
     for pid in list(flipped[0]):
         if pid in pre_ids[0]:
             c = kids[int(np.searchsorted(pre[0]["id"], np.uint64(pid)))]
             flipped[0].add(int(c[0]))
             flipped[1].add(int(c[1]))
+    if wl.split_cells > 0:
+        for s in (0, 1):
+            ids = np.fromiter(flipped[s], np.uint64, len(flipped[s]))
+            flipped[s].update(orc.split_ids(step, wl.seed, ids).tolist())
     stats["n"] = sum(1 for s in (0, 1) for p in flipped[s] if p in pre_ids[s])
     return flipped, stats
 
@@ -158,7 +177,10 @@ def clean_deposits(wl, d, o, post_dev, post_orc, flipped):
 
 E_CHARGE = 1.602176634e-19
 COUNTERS = ("absn_e_pow", "absn_e_gnd", "absn_e_surf", "absn_i_pow", "absn_i_gnd", "absn_i_surf",
-            "coll_e_el", "coll_e_ex", "coll_e_iz", "coll_i_iso", "coll_i_cx", "born_e", "born_i")
+            "coll_e_el", "coll_e_ex", "coll_e_iz", "coll_i_iso", "coll_i_cx", "born_e", "born_i",
+            "splits_e", "splits_i")
+# Weighted tallies (absorbed charge, surface charge) hold macro weights to 2^-32.
+CREDIT_UNIT = 2.0 ** -32
 
 
 def rel_l2(a, b):
@@ -191,6 +213,7 @@ class StepParity:
         self.seen = 0
         self.surf_hits = 0
         self.overflow = 0
+        self.splits = 0
         self.phi_e2e = []
 
     def step(self, advance):
@@ -232,11 +255,16 @@ class StepParity:
         for key in COUNTERS:
             assert abs(sd[key] - so[key]) <= nflip, (key, sd[key], so[key], nflip)
         self.surf_hits += so["absn_e_surf"] + so["absn_i_surf"]
+        self.splits += so["splits_e"] + so["splits_i"]
         # surface charge node by node, in units of one macroparticle's charge
         qw = E_CHARGE * wl.w[0]
         dsig = (d.field("sigma") - o.field("sigma")) / qw
-        assert np.allclose(dsig, np.round(dsig), atol=1e-6)
-        assert np.abs(np.round(dsig)).sum() <= 2 * nflip, np.abs(np.round(dsig)).sum()
+        hits = so["absn_e_surf"] + so["absn_i_surf"]
+        if not wl.weighted:
+            assert np.allclose(dsig, np.round(dsig), atol=1e-6)
+            assert np.abs(np.round(dsig)).sum() <= 2 * nflip, np.abs(np.round(dsig)).sum()
+        else:  # a flipped particle carries a ratio <= 1; each credit is rounded to 2^-32
+            assert np.abs(dsig).sum() <= 2 * nflip + (hits + 1) * CREDIT_UNIT, np.abs(dsig).sum()
         # deposits and node charge without the flipped particles
         (de_d, di_d), (de_o, di_o) = clean_deposits(wl, d, o, post_d, post_o, flipped)
         assert rel_l2(de_d, de_o) <= self.tol_dep
@@ -248,7 +276,8 @@ class StepParity:
         # circuit (Eqs. 5, 8-10): I_conv differs only by flipped absorptions at the
         # powered electrode; U_E and Q_E are compared on the state scale C_eq V_src
         dI = sd["I_conv"] - so["I_conv"]
-        assert abs(dI) <= (nflip * qw / wl.dt) * (1 + 1e-9) + 1e-12 * abs(so["I_conv"])
+        quant = (so["absn_e_pow"] + so["absn_i_pow"]) * CREDIT_UNIT * qw / wl.dt if wl.weighted else 0.0
+        assert abs(dI) <= (nflip * qw / wl.dt) * (1 + 1e-9) + 1e-12 * abs(so["I_conv"]) + quant
         assert abs(sd["U_E"] - so["U_E"]) <= 1e-10 * max(wl.V_src, 1.0) + 2 * abs(dI) * wl.dt / so["C_eq"], \
             (sd["U_E"], so["U_E"])
         assert abs(sd["Q_E"] - so["Q_E"]) <= 1e-10 * so["C_eq"] * max(wl.V_src, 1.0) + 2 * abs(dI) * wl.dt, \

@@ -53,3 +53,30 @@ def test_load_rejects_missing_and_foreign_files(tmp_path):
     (tmp_path / "junk").write_bytes(b"not a restart file" * 10)
     assert L.pic_load(str(tmp_path / "junk").encode(), None, ctypes.byref(h)) == pic.PIC_EIO
     assert L.pic_strerror(pic.PIC_EIO).startswith(b"restart file")
+
+
+@pytest.mark.parametrize("struct", ["Config", "Particles"])
+def test_binding_structs_match_the_header(struct, tmp_path):
+    """The binding's ctypes mirrors of pic_config and pic_particles have the
+    header's field offsets and size (checked by compiling the header with the
+    host C compiler)."""
+    import shutil
+    import subprocess
+
+    from paper_2310_04957_gb300 import pic
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    py = getattr(pic, struct)
+    cname = {"Config": "pic_config", "Particles": "pic_particles"}[struct]
+    fields = [f[0] for f in py._fields_]
+    lines = [f'  printf("%zu\\n", offsetof({cname}, {f}));' for f in fields]
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stddef.h>\n#include <stdio.h>\n#include "pic.h"\nint main(void) {\n' + "\n".join(lines) +
+                   f'\n  printf("%zu\\n", sizeof({cname}));\n  return 0;\n}}\n')
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [getattr(py, f).offset for f in fields] + [ctypes.sizeof(py)]
+    assert got == want, list(zip(fields + ["sizeof"], got, want))

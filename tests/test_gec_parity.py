@@ -47,10 +47,10 @@ MG, PLAIN = 3, 0
 RLC = (0.5, 0.01e-6, 5e-9, 0.0, 0.0, 0.0, 0.0, 0.0)
 
 
-def gec_small(n=200_000, circuit="imn"):
+def gec_small(n=200_000, circuit="imn", split_cells=0):
     # 128x64 is the coarsest grid on which the 1 mm dielectric ring survives
     # snapping (2 cells); a 3-step RF window makes the third step end a window
-    wl = W.gec_case(128, 64, 30.0, 150.0, n_per_species=n, seed_index=21)
+    wl = W.gec_case(128, 64, 30.0, 150.0, n_per_species=n, seed_index=21, split_cells=split_cells)
     wl = dataclasses.replace(wl, steps_per_rf=3, phase_src=0.9)
     if circuit == "rlc":
         wl = dataclasses.replace(wl, circuit=W.CIRCUIT_RLC, circ=RLC)
@@ -67,12 +67,18 @@ CASES = [
     pytest.param(FP64, MG, (4, 2), 0.0, "imn", id="fp64-mg-4x2"),
     pytest.param(FP64, PLAIN, (4, 4), 1e-6, "imn", id="fp64-plain-4x4-overflow"),
     pytest.param(FP64, MG, (4, 4), 0.0, "rlc", id="fp64-mg-4x4-rlc"),
+    # unequal weights and splitting near the axis (Sec. 2): radially weighted
+    # loading in the first 8 radial cells, split on entering a smaller cell
+    pytest.param(FP32, MG, (4, 4), 0.0, "imn-split", id="fp32-mg-4x4-split"),
+    pytest.param(FP32, MG, (4, 4), 1e-6, "imn-split", id="fp32-mg-4x4-split-overflow"),
+    pytest.param(FP64, MG, (4, 2), 0.0, "imn-split", id="fp64-mg-4x2-split"),
 ]
 
 
 @pytest.mark.parametrize("precision,solver,tile,slack,circuit", CASES)
 def test_gec_full_steps_match_oracle(precision, solver, tile, slack, circuit):
-    wl = gec_small(circuit=circuit)
+    split = circuit.endswith("-split")
+    wl = gec_small(circuit=circuit.removesuffix("-split"), split_cells=8 if split else 0)
     d, o = make_pair(wl, precision, solver=solver, tile=tile, bin_slack=slack)
     o.init_fields()
     d.start()
@@ -90,5 +96,7 @@ def test_gec_full_steps_match_oracle(precision, solver, tile, slack, circuit):
     assert sp.surf_hits > 0, "no particle reached the dielectric surface: the surface-charge path went unchecked"
     if slack > 0:
         assert sp.overflow > 0, "the overflow region was never used"
+    if split:
+        assert sp.splits > 0, "no particle split: the splitting path went unchecked"
     print(f"{precision=} {tile=} flips {sp.flips} of {sp.seen} particle-steps, surface hits {sp.surf_hits}, "
-          f"overflow-region particles {sp.overflow}, phi end to end (flips, rel L2) {sp.phi_e2e}")
+          f"overflow-region particles {sp.overflow}, splits {sp.splits}, phi end to end (flips, rel L2) {sp.phi_e2e}")
