@@ -21,7 +21,7 @@ _lock = threading.Lock()
 _lib = None
 
 FIELD = {"phi": 0, "Er": 1, "Ez": 2, "chi": 3, "dep_e": 4, "dep_i": 5, "sigma": 6, "vnode": 7, "rho": 8,
-         "ne_avg": 9, "ni_avg": 10}
+         "ne_avg": 9, "ni_avg": 10, "phiP": 11, "phiL0": 12, "phiL1": 13, "phiL2": 14, "phiL3": 15}
 
 
 def build(force: bool = False) -> str:
@@ -50,6 +50,8 @@ class Setup(ctypes.Structure):
         ("n_sub", ctypes.c_int32), ("steps_per_rf", ctypes.c_int32), ("pcg_tol", ctypes.c_double),
         ("pcg_maxit", ctypes.c_int32), ("ceq_refresh", ctypes.c_int32), ("seed", ctypes.c_uint32),
         ("capacity", ctypes.c_int64 * 2), ("split_cells", ctypes.c_int32),
+        ("n_drive", ctypes.c_int32), ("drive_V", ctypes.c_double * 3), ("drive_f", ctypes.c_double * 3),
+        ("drive_phase", ctypes.c_double * 3), ("field_mode", ctypes.c_int32),
     ]
 
 
@@ -175,6 +177,11 @@ class Oracle:
         cap = capacity if capacity is not None else wl.capacity
         s.capacity[:] = [int(cap[0]), int(cap[1])]
         s.split_cells = int(getattr(wl, "split_cells", 0))
+        drive = tuple(getattr(wl, "drive", ()))
+        s.n_drive = len(drive)
+        for k, (V, f, ph) in enumerate(drive):
+            s.drive_V[k], s.drive_f[k], s.drive_phase[k] = V, f, ph
+        s.field_mode = int(getattr(wl, "field_mode", 0))
         h = ctypes.c_void_p()
         st = L.orc_create(ctypes.byref(s), ctypes.byref(h))
         if st != 0:

@@ -114,6 +114,11 @@ struct orc_sim {
   double *dep[2];    /* deposited counts per species */
   double *sigma;     /* surface charge on free boundary nodes */
   double *chi, *qrhs, *phi, *Er, *Ez;
+  /* Vahedi decomposition (Eqs. 2-4): phi_P of the last solve (its warm start)
+   * and the unit-voltage Laplace solutions of the powered electrode (0) and of
+   * the driven electrodes (1..n_drive) */
+  double *phiP, *phiL[1 + ORC_MAX_DRIVE];
+  double t_field;    /* time of the field being assembled and solved */
   double numax[2], pcoll[2];
   orc_species sp[2];
   /* births created during one particle phase */
@@ -293,7 +298,7 @@ static void credit(orc_sim *s, int spc, double r, double z, double w) {
   double qw = s->cfg.q[spc] * s->cfg.w[spc] * w;
   int kind = s->node_kind[node];
   if (kind == ORC_POWERED) { s->abs_q[spc][0] += qw; s->abs_n[spc][0] += 1; }
-  else if (kind == ORC_GROUNDED) { s->abs_q[spc][1] += qw; s->abs_n[spc][1] += 1; }
+  else if (kind != ORC_FREE) { s->abs_q[spc][1] += qw; s->abs_n[spc][1] += 1; } /* grounded or driven metal */
   else { s->sigma[node] += qw; s->abs_q[spc][2] += qw; s->abs_n[spc][2] += 1; }
 }
 
@@ -740,12 +745,29 @@ static void build_operator(orc_sim *s, double *Gr, double *Gz, const double *chi
     if ((j) < nz_) { int NB = nidx((s), (i), (j) + 1); double G = (Gz)[(j) * (nr_ + 1) + (i)]; BODY } \
   } while (0)
 
-/* Set Dirichlet values: powered metal at U, grounded metal at 0. */
-static void apply_dirichlet(orc_sim *s, double *phi, double U) {
+/* Voltage of driven electrode k (0-based) at time t. */
+static double drive_voltage(const orc_setup *c, int k, double t) {
+  return c->drive_V[k] * sin(TWO_PI * c->drive_f[k] * t + c->drive_phase[k]);
+}
+
+/* Set Dirichlet values: powered metal at U, grounded metal at 0, driven
+ * electrode k at Ud[k] (Ud = NULL: all driven electrodes at 0). */
+static void apply_dirichlet_all(orc_sim *s, double *phi, double U, const double *Ud) {
   for (int a = 0; a < s->nn; ++a) {
-    if (s->node_kind[a] == ORC_POWERED) phi[a] = U;
-    else if (s->node_kind[a] == ORC_GROUNDED) phi[a] = 0.0;
+    int k = s->node_kind[a];
+    if (k == ORC_POWERED) phi[a] = U;
+    else if (k == ORC_GROUNDED) phi[a] = 0.0;
+    else if (k >= ORC_DRIVEN) phi[a] = Ud ? Ud[k - ORC_DRIVEN] : 0.0;
   }
+}
+
+/* The C_eq problem's boundary: the powered electrode at U, every other metal at 0. */
+static void apply_dirichlet(orc_sim *s, double *phi, double U) { apply_dirichlet_all(s, phi, U, NULL); }
+
+/* Unit-voltage boundary of electrode `e` (a node kind): 1 on it, 0 on all other metal. */
+static void apply_dirichlet_unit(orc_sim *s, double *phi, int e) {
+  for (int a = 0; a < s->nn; ++a)
+    if (s->node_kind[a] != ORC_FREE) phi[a] = s->node_kind[a] == e ? 1.0 : 0.0;
 }
 
 /* Jacobi-preconditioned conjugate gradients on the free nodes of
@@ -908,7 +930,31 @@ static int compute_ceq(orc_sim *s, int with_chi, double *ceq, double *gauss) {
     }
   *ceq = energy2; /* 2 * (1/2 sum G dphi^2) / U^2 with U = 1 */
   *gauss = q;
+  /* the same solution is the powered electrode's unit Laplace solution phi_L0 */
+  if (s->cfg.field_mode == ORC_FIELD_VAHEDI && st == ORC_OK) memcpy(s->phiL[0], phiL, sizeof(double) * nn);
   free(Gr); free(Gz); free(phiL); free(q0);
+  return st;
+}
+
+/* Unit-voltage Laplace solutions of the driven electrodes (Eq. 4 with the
+ * implicit operator of Eq. 1: phi_Lk = 1 on electrode k, 0 on all other
+ * metal, no charge), with the current chi or in vacuum.  Solved to the C_eq
+ * solve's tolerance, each from its previous solution. */
+static int refresh_laplace(orc_sim *s, int with_chi) {
+  int nn = s->nn, nr = s->cfg.nr, nz = s->cfg.nz;
+  double *Gr = (double *)malloc(sizeof(double) * (size_t)(nz + 1) * nr);
+  double *Gz = (double *)malloc(sizeof(double) * (size_t)nz * (nr + 1));
+  double *q0 = (double *)calloc(nn, sizeof(double));
+  if (!Gr || !Gz || !q0) { free(Gr); free(Gz); free(q0); return ORC_ENOMEM; }
+  build_operator(s, Gr, Gz, with_chi ? s->chi : NULL);
+  double tol = s->cfg.pcg_tol < 1e-12 ? s->cfg.pcg_tol : 1e-12;
+  int st = ORC_OK;
+  for (int k = 0; k < s->cfg.n_drive && st == ORC_OK; ++k) {
+    int it; double rel;
+    apply_dirichlet_unit(s, s->phiL[k + 1], ORC_DRIVEN + k);
+    st = pcg_solve(s, Gr, Gz, s->phiL[k + 1], q0, tol, s->cfg.pcg_maxit, &it, &rel);
+  }
+  free(Gr); free(Gz); free(q0);
   return st;
 }
 
@@ -1025,12 +1071,33 @@ static void assemble(orc_sim *s) {
     s->qrhs[a] = q;
   }
   build_operator(s, s->Gr, s->Gz, s->chi);
-  apply_dirichlet(s, s->phi, s->U_E);
+  if (c->field_mode == ORC_FIELD_VAHEDI) {
+    apply_dirichlet_all(s, s->phiP, 0.0, NULL);  /* Eq. 3: zero on every electrode */
+  } else {
+    double Ud[ORC_MAX_DRIVE];
+    for (int k = 0; k < c->n_drive; ++k) Ud[k] = drive_voltage(c, k, s->t_field);
+    apply_dirichlet_all(s, s->phi, s->U_E, Ud);
+  }
 }
 
+/* Direct mode: one solve of Eq. 1 with every electrode at its voltage.
+ * Vahedi mode: the zero-boundary solve phi_P (Eq. 3), then Eq. 2,
+ * phi = phi_P + U_E phi_L0 + sum_k U_k phi_Lk, with the Laplace solutions of
+ * the last refresh. */
 static int field_solve(orc_sim *s) {
-  int st = pcg_solve(s, s->Gr, s->Gz, s->phi, s->qrhs, s->cfg.pcg_tol, s->cfg.pcg_maxit, &s->pcg_iters, &s->pcg_relres);
+  const orc_setup *c = &s->cfg;
+  double *target = c->field_mode == ORC_FIELD_VAHEDI ? s->phiP : s->phi;
+  int st = pcg_solve(s, s->Gr, s->Gz, target, s->qrhs, c->pcg_tol, c->pcg_maxit, &s->pcg_iters, &s->pcg_relres);
   s->pcg_status = st;
+  if (c->field_mode == ORC_FIELD_VAHEDI) {
+    double Ud[ORC_MAX_DRIVE];
+    for (int k = 0; k < c->n_drive; ++k) Ud[k] = drive_voltage(c, k, s->t_field);
+    for (int a = 0; a < s->nn; ++a) {
+      double v = s->phiP[a] + s->U_E * s->phiL[0][a];
+      for (int k = 0; k < c->n_drive; ++k) v += Ud[k] * s->phiL[k + 1][a];
+      s->phi[a] = v;
+    }
+  }
   compute_efield(s);
   return st;
 }
@@ -1144,6 +1211,7 @@ static int one_step(orc_sim *s) {
   if (st) return st;
   s->I_conv = (s->abs_q[0][0] + s->abs_q[1][0]) / s->cfg.dt;
   circuit_advance(s);
+  s->t_field = (double)(s->step + 1) * s->cfg.dt;
   assemble(s);
   st = field_solve(s);
   diag_accumulate(s);
@@ -1152,6 +1220,8 @@ static int one_step(orc_sim *s) {
     double cq, g;
     int st2 = compute_ceq(s, 1, &cq, &g);
     if (st2 == ORC_OK) { s->ceq = cq; s->ceq_gauss = g; }
+    if (st2 == ORC_OK && s->cfg.field_mode == ORC_FIELD_VAHEDI) st2 = refresh_laplace(s, 1);
+    if (st2 != ORC_OK && st == ORC_OK) st = st2;
     if (s->cfg.circuit != ORC_CIRCUIT_DIRECT) s->U_E = s->Q_E / s->ceq;
   }
   return st;
@@ -1169,7 +1239,8 @@ void orc_destroy(orc_sim *s) {
   if (!s) return;
   free(s->node_kind); free(s->cell_kind); free(s->cell_eps); free(s->xs_energy); free(s->xs_sigma);
   free(s->vnode); free(s->Gr); free(s->Gz); free(s->sigma); free(s->chi); free(s->qrhs);
-  free(s->phi); free(s->Er); free(s->Ez);
+  free(s->phi); free(s->Er); free(s->Ez); free(s->phiP);
+  for (int k = 0; k <= ORC_MAX_DRIVE; ++k) free(s->phiL[k]);
   for (int k = 0; k < 2; ++k) {
     free(s->dep[k]); free_species(&s->sp[k]); free(s->born[k]); free(s->split[k]); free(s->dens_sum[k]);
     free(s->dens_avg[k]);
@@ -1180,6 +1251,10 @@ void orc_destroy(orc_sim *s) {
 int orc_create(const orc_setup *cfg, orc_sim **out) {
   if (!cfg || !out || cfg->nr < 1 || cfg->nz < 1 || cfg->n_xs < 2 || cfg->dt <= 0) return ORC_EINVAL;
   if (cfg->circuit < 0 || cfg->circuit > 2 || cfg->steps_per_rf < 1 || cfg->n_sub < 1) return ORC_EINVAL;
+  if (cfg->n_drive < 0 || cfg->n_drive > ORC_MAX_DRIVE) return ORC_EINVAL;
+  if (cfg->field_mode != ORC_FIELD_DIRECT && cfg->field_mode != ORC_FIELD_VAHEDI) return ORC_EINVAL;
+  for (int a = 0; a < (cfg->nr + 1) * (cfg->nz + 1); ++a)
+    if (cfg->node_kind[a] < 0 || cfg->node_kind[a] > ORC_GROUNDED + cfg->n_drive) return ORC_EINVAL;
   orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
   if (!s) return ORC_ENOMEM;
   s->cfg = *cfg;
@@ -1200,8 +1275,13 @@ int orc_create(const orc_setup *cfg, orc_sim **out) {
   s->phi = (double *)calloc(s->nn, sizeof(double));
   s->Er = (double *)calloc(s->nn, sizeof(double));
   s->Ez = (double *)calloc(s->nn, sizeof(double));
+  s->phiP = (double *)calloc(s->nn, sizeof(double));
   int ok = s->node_kind && s->cell_kind && s->cell_eps && s->xs_energy && s->xs_sigma && s->vnode && s->Gr &&
-           s->Gz && s->sigma && s->chi && s->qrhs && s->phi && s->Er && s->Ez;
+           s->Gz && s->sigma && s->chi && s->qrhs && s->phi && s->Er && s->Ez && s->phiP;
+  for (int k = 0; k <= cfg->n_drive && ok; ++k) {
+    s->phiL[k] = (double *)calloc(s->nn, sizeof(double));
+    ok = s->phiL[k] != NULL;
+  }
   for (int k = 0; k < 2 && ok; ++k) {
     s->dep[k] = (double *)calloc(s->nn, sizeof(double));
     s->dens_sum[k] = (double *)calloc(s->nn, sizeof(double));
@@ -1274,6 +1354,8 @@ static double *field_ptr(orc_sim *s, int which) {
     case 0: return s->phi; case 1: return s->Er; case 2: return s->Ez; case 3: return s->chi;
     case 4: return s->dep[0]; case 5: return s->dep[1]; case 6: return s->sigma; case 7: return s->vnode;
     case 8: return s->qrhs; case 9: return s->dens_avg[0]; case 10: return s->dens_avg[1];
+    case 11: return s->phiP;
+    case 12: case 13: case 14: case 15: return s->phiL[which - 12];  /* NULL beyond n_drive */
     default: return NULL;
   }
 }
@@ -1360,6 +1442,7 @@ int orc_init_fields(orc_sim *s) {
   st = compute_ceq(s, 0, &cq, &g);
   if (st) return st;
   s->ceq = cq; s->ceq_gauss = g;
+  if (s->cfg.field_mode == ORC_FIELD_VAHEDI && (st = refresh_laplace(s, 0))) return st;
   if (s->cfg.circuit == ORC_CIRCUIT_DIRECT) {
     s->U_E = source_voltage(&s->cfg, (double)s->step * s->cfg.dt);
     s->Q_E = s->ceq * s->U_E;
@@ -1368,6 +1451,7 @@ int orc_init_fields(orc_sim *s) {
     s->Q_E = s->y[n - 1];
     s->U_E = s->Q_E / s->ceq;
   }
+  s->t_field = (double)s->step * s->cfg.dt;
   assemble(s);
   return field_solve(s);
 }

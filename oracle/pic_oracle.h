@@ -19,6 +19,11 @@
 #define ORC_FREE 0
 #define ORC_POWERED 1
 #define ORC_GROUNDED 2
+#define ORC_DRIVEN 3   /* first of up to three voltage-driven electrodes: 3, 4, 5 */
+#define ORC_MAX_DRIVE 3
+
+#define ORC_FIELD_DIRECT 0  /* one solve with every electrode at its voltage   */
+#define ORC_FIELD_VAHEDI 1  /* phi = phi_P + sum_i U_Ei phi_Li (Eqs. 2-4)      */
 
 #define ORC_CELL_PLASMA 0
 #define ORC_CELL_POWERED 1
@@ -56,6 +61,10 @@ typedef struct orc_setup {
   int64_t capacity[2];       /* particle capacity per species                    */
   int32_t split_cells;       /* particle splitting in the first split_cells radial
                                 cells (0: off); see split_target() */
+  int32_t n_drive;           /* voltage-driven electrodes (node kinds 3 .. 2+n_drive) */
+  double drive_V[ORC_MAX_DRIVE], drive_f[ORC_MAX_DRIVE], drive_phase[ORC_MAX_DRIVE];
+                             /* U_k(t) = V sin(2 pi f t + phase)                  */
+  int32_t field_mode;        /* ORC_FIELD_DIRECT or ORC_FIELD_VAHEDI              */
 } orc_setup;
 
 typedef struct orc_sim orc_sim;

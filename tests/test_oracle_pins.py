@@ -1019,3 +1019,127 @@ def test_radially_weighted_loading_samples_the_uniform_density():
     e = wl.particles[0]
     i = np.floor(e.r / wl.dr).astype(int)
     np.testing.assert_array_equal(e.w, W.radial_weight(i, 16).astype(np.float32).astype(np.float64))
+
+
+# ---------------------------------------------------------------- Vahedi decomposition (Eqs. 2-4)
+def _planar_two_electrodes(nr=8, nz=20, R=0.03, L=0.02, mode=W.FIELD_VAHEDI, drive=((40.0, 2e6, 0.7),)):
+    """Powered plate at z = 0 (direct drive, 100 V at phase 1.1), a voltage-driven plate at
+    z = L (node kind 3), free outer wall and axis, vacuum, no particles."""
+    node, cell, eps = grounded_box(nr, nz, R, L, neumann_wall=True, powered_bottom=True)
+    node[nz, :] = W.NODE_DRIVEN
+    wl = field_only(nr, nz, R, L, node, cell, eps, V=100.0, phase=1.1)
+    return dataclasses.replace(wl, drive=drive, field_mode=mode, ceq_refresh=0)
+
+
+def test_vahedi_decomposition_of_a_planar_gap_is_the_closed_form():
+    """Two plates, a uniform volume charge rho0 between them (node charges rho0 A_a dz, A_a the
+    node's axial face area, so the discrete problem is r-independent), no chi: the unit Laplace solutions are phi_L0 = 1 - z/L (powered plate) and
+    phi_L1 = z/L (driven plate), the zero-boundary Poisson solution is
+    phi_P = rho0 z (L - z) / (2 eps0), and phi = phi_P + U_E phi_L0 + U_1 phi_L1 (Eq. 2) with
+    U_E = 100 sin(1.1) V and U_1 = 40 sin(0.7) V; the direct solve gives the same phi."""
+    nr, nz, L = 8, 20, 0.02
+    rho0 = 3e-6  # C / m^3
+    z = (np.arange(nz + 1) * L / nz)[:, None]
+    UE, U1 = 100.0 * math.sin(1.1), 40.0 * math.sin(0.7)
+    want_P = rho0 * z * (L - z) / (2 * EPS0)
+    want = want_P + UE * (1 - z / L) + U1 * z / L
+    phis = {}
+    for mode in (W.FIELD_VAHEDI, W.FIELD_DIRECT):
+        wl = _planar_two_electrodes(nr, nz, L=L, mode=mode)
+        o = orc.Oracle(wl, set_particles=False)
+        o.assemble()
+        _, Gz = o.operator()
+        dz = L / nz
+        o.set_field("sigma", np.broadcast_to(rho0 * Gz[0] * dz * dz / EPS0, (nz + 1, nr + 1)))
+        o.init_fields()
+        phi = o.field("phi")
+        np.testing.assert_allclose(phi, np.broadcast_to(want, phi.shape), rtol=0, atol=1e-9 * np.abs(want).max())
+        phis[mode] = phi
+        if mode == W.FIELD_VAHEDI:
+            np.testing.assert_allclose(o.field("phiL0"), np.broadcast_to(1 - z / L, phi.shape), atol=1e-11)
+            np.testing.assert_allclose(o.field("phiL1"), np.broadcast_to(z / L, phi.shape), atol=1e-11)
+            np.testing.assert_allclose(o.field("phiP"), np.broadcast_to(want_P, phi.shape), rtol=0,
+                                       atol=1e-9 * want_P.max())
+    # both solves stop at the workload's relative residual (1e-10), the closed form above holds to 1e-9
+    assert rel_l2(phis[W.FIELD_VAHEDI], phis[W.FIELD_DIRECT]) <= 1e-9
+
+
+def test_vahedi_laplace_solutions_see_a_dielectric_layer():
+    """A dielectric layer eps_r = 4 over the powered plate (rows below k): phi_L1 of the driven
+    plate is the series-capacitor profile, linear in each layer with continuous D; and with two
+    driven electrodes side by side (inner and outer halves of the top plate) the unit solutions
+    of the three electrodes sum to 1 everywhere (superposition of the all-ones boundary)."""
+    nr, nz, R, L, k, er = 12, 24, 0.03, 0.024, 9, 4.0
+    wl = _planar_two_electrodes(nr, nz, R, L)
+    cell = wl.cell_kind.copy()
+    eps = wl.cell_eps.copy()
+    cell[:k, :] = W.CELL_DIELECTRIC
+    eps[:k, :] = er
+    wl = dataclasses.replace(wl, cell_kind=cell, cell_eps=eps)
+    o = orc.Oracle(wl, set_particles=False)
+    o.init_fields()
+    z = (np.arange(nz + 1) * L / nz)[:, None]
+    d1, d2 = k * L / nz, (nz - k) * L / nz
+    Dn = 1.0 / (d1 / er + d2)
+    want = np.where(z <= d1, Dn * z / er, Dn * d1 / er + Dn * (z - d1))
+    np.testing.assert_allclose(o.field("phiL1"), np.broadcast_to(want, (nz + 1, nr + 1)), atol=1e-11)
+    # split the top plate into two driven electrodes
+    node = wl.node_kind.copy()
+    node[nz, nr // 2:] = W.NODE_DRIVEN + 1
+    wl2 = dataclasses.replace(wl, node_kind=node, drive=((40.0, 2e6, 0.7), (-15.0, 1e6, 0.2)))
+    o2 = orc.Oracle(wl2, set_particles=False)
+    o2.init_fields()
+    total = o2.field("phiL0") + o2.field("phiL1") + o2.field("phiL2")
+    np.testing.assert_allclose(total, 1.0, atol=1e-10)
+    assert o2.field("phiL2")[nz, nr] == 1.0 and o2.field("phiL2")[nz, 0] == 0.0
+
+
+def _eq1_residual(o, phi):
+    """Relative residual of Eq. 1's finite-volume form at the free nodes:
+    ||sum_b G_ab (phi_a - phi_b) - Q_a|| / ||(Q + Dirichlet lift)_free||."""
+    Gr, Gz = o.operator()
+    q = o.field("rho")
+    kind = o.kind
+    Ap = np.zeros_like(phi)
+    lift = np.zeros_like(phi)
+    d = phi[:, :-1] - phi[:, 1:]
+    Ap[:, :-1] += Gr * d
+    Ap[:, 1:] -= Gr * d
+    d = phi[:-1, :] - phi[1:, :]
+    Ap[:-1, :] += Gz * d
+    Ap[1:, :] -= Gz * d
+    metal = kind != W.NODE_FREE
+    pm = np.where(metal, phi, 0.0)
+    lift[:, :-1] += Gr * pm[:, 1:]
+    lift[:, 1:] += Gr * pm[:, :-1]
+    lift[:-1, :] += Gz * pm[1:, :]
+    lift[1:, :] += Gz * pm[:-1, :]
+    free = ~metal
+    return float(np.linalg.norm((Ap - q)[free]) / np.linalg.norm((q + lift)[free]))
+
+
+def test_vahedi_laplace_parts_refresh_with_chi_once_per_window():
+    """With particles (chi > 0) the Laplace parts stay the vacuum ones until the first RF window
+    ends, then are re-solved with that step's chi.  phi = phi_P + sum U phi_L solves Eq. 1 only
+    when the parts carry the solve's chi: the window's last step (formed with the vacuum parts)
+    leaves a residual, the same step re-solved after the refresh does not."""
+    wl = W.small_cylinder(n_per_species=4000)
+    node = wl.node_kind.copy()
+    top = node.shape[0] - 1
+    node[top, :] = np.where(node[top, :] == W.NODE_GROUNDED, W.NODE_DRIVEN, node[top, :])
+    wl = dataclasses.replace(wl, node_kind=node, drive=((30.0, 4e6, 0.3),), field_mode=W.FIELD_VAHEDI,
+                             steps_per_rf=3, ceq_refresh=1)
+    o = orc.Oracle(wl)
+    o.kind = node
+    o.init_fields()
+    L1_vac = o.field("phiL1")
+    o.step(2)
+    np.testing.assert_array_equal(o.field("phiL1"), L1_vac)  # no window has ended
+    o.step(1)  # the third step ends the window
+    assert rel_l2(o.field("phiL1"), L1_vac) > 1e-6
+    o.assemble()  # the same step's charge and chi again
+    before = _eq1_residual(o, o.field("phi"))
+    st, _, _ = o.field_solve()
+    assert st == 0
+    after = _eq1_residual(o, o.field("phi"))
+    assert after <= 1e-9 < before, (after, before)
