@@ -73,12 +73,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+KERNEL_SOURCES = ("push_kernels.cuh", "push.cu")
+
+
 def kernel_traffic():
     """DRAM bytes per particle-kernel launch from the committed ncu summary, scaled to
     the bench's particle count, if the summary was taken on the current kernel source;
     else None."""
     p = os.path.join(ROOT, "profiles", "k_particles_gec256.md")
-    src = os.path.join(ROOT, "paper_2310_04957_gb300", "csrc", "push.cu")
+    csrc = os.path.join(ROOT, "paper_2310_04957_gb300", "csrc")
     if not os.path.exists(p):
         return None
     kv = {}
@@ -87,7 +90,10 @@ def kernel_traffic():
         if ":" in line and line.split(":")[0] in ("traffic_bytes_per_launch", "particles_in_launch", "source_sha256"):
             k, v = line.split(":", 1)
             kv[k] = v.strip()
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:  # the particle kernel and its unweighted instance
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    sha = h.hexdigest()
     if kv.get("source_sha256") != sha:
         return None
     return {"bytes": float(kv["traffic_bytes_per_launch"]), "particles": float(kv["particles_in_launch"])}

@@ -50,6 +50,9 @@ extern "C" {
 #define PIC_NODE_FREE 0
 #define PIC_NODE_POWERED 1
 #define PIC_NODE_GROUNDED 2
+#define PIC_NODE_DRIVEN 3   /* first voltage-driven electrode: kinds 3, 4, 5 are
+                               electrodes 1..3 of pic_config.drive_* (a particle
+                               absorbed there counts as a grounded-type exit) */
 
 #define PIC_CELL_PLASMA 0
 #define PIC_CELL_POWERED 1
@@ -64,6 +67,17 @@ extern "C" {
 
 #define PIC_FP32 0 /* particle state and push in FP32; FP64 reductions, field, circuit */
 #define PIC_FP64 1 /* everything in FP64 (the plain method)                          */
+
+/* Field composition (Sec. 2, Eqs. 2-4). */
+#define PIC_FIELD_DIRECT 0 /* one solve of Eq. 1 with every electrode at its voltage */
+#define PIC_FIELD_VAHEDI 1 /* phi = phi_P + U_E phi_L0 + sum_k U_k phi_Lk (Eq. 2):
+                              phi_P solves Eq. 1 with every electrode at 0 (Eq. 3)
+                              each step; phi_L0 / phi_Lk are the unit-voltage
+                              solutions of the powered / driven electrodes (Eq. 4,
+                              the implicit operator with the chi of their last
+                              refresh), re-solved together with C_eq: in vacuum
+                              at start and with chi at every RF-window end when
+                              ceq_refresh is set                                 */
 
 #define PIC_SOLVER_PLAIN 0 /* FP64 Jacobi-preconditioned CG                        */
 #define PIC_SOLVER_MIXED 1 /* FP32 Jacobi-preconditioned inner CG, FP64
@@ -131,6 +145,13 @@ typedef struct pic_config {
                                   Philox4x32-10(key = parent id, counter = (step,
                                   0x5B17, 0, seed)) with bit 63 set; both halves
                                   count as deposited by the parent's deposit   */
+  int32_t n_drive;             /* voltage-driven electrodes (0..3): node kinds 3 ..
+                                  2 + n_drive, electrode k at
+                                  drive_V[k] sin(2 pi drive_f[k] t + drive_phase[k])
+                                  (V, Hz, rad) -- an ideal source, no circuit  */
+  double drive_V[3], drive_f[3], drive_phase[3];
+  int32_t field_mode;          /* PIC_FIELD_DIRECT or PIC_FIELD_VAHEDI (not with
+                                  PIC_SOLVER_LEARNED)                            */
 } pic_config;
 
 /* Particle arrays of one species in FP64 host memory (caller-owned).  Position
@@ -210,6 +231,10 @@ int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss);
 #define PIC_DIAG_NI_AVG 10 /* last window's mean n_i, m^-3     [nodes] */
 #define PIC_DIAG_PHI_WARM 11 /* warm start of the last solve, V (kept by
                                 pic_keep_warm or the learned solver) [nodes] */
+#define PIC_DIAG_PHI_P 12    /* PIC_FIELD_VAHEDI: zero-boundary part phi_P, V [nodes] */
+#define PIC_DIAG_PHI_L0 13   /* PIC_FIELD_VAHEDI: unit Laplace solution of the powered
+                                electrode; 14..16 those of driven electrodes 1..3
+                                (dimensionless) [nodes] */
 #define PIC_DIAG_SCALARS 100 /* PIC_NSCALARS doubles, see below  */
 #define PIC_DIAG_STORE 101   /* 8 doubles: per species (electrons, then ions)
                                 particles in their cell bins, particles in the

@@ -177,6 +177,21 @@ PushParams<T> push_params(pic_handle *h, int in_buf) {
   return P;
 }
 
+Drive drive_of(const pic_config &c) {
+  Drive d;
+  memset(&d, 0, sizeof(d));
+  d.n = c.n_drive;
+  for (int k = 0; k < c.n_drive && k < 3; ++k) {
+    d.V[k] = c.drive_V[k];
+    d.f[k] = c.drive_f[k];
+    d.phase[k] = c.drive_phase[k];
+  }
+  return d;
+}
+
+// The array the field solve works on: phi itself, or phi_P in the Vahedi composition.
+double *field_target(pic_handle *h) { return h->vahedi ? h->d_phiP : h->d_phi; }
+
 double dep_inv_scale(const pic_handle *h) { return h->prec == PIC_FP32 ? 1.0 / 67108864.0 : 1.0 / 1099511627776.0; }
 
 FieldParams field_params(pic_handle *h, const double *chi, double *Gr, double *Gz, double *dinv) {
@@ -196,9 +211,25 @@ FieldParams field_params(pic_handle *h, const double *chi, double *Gr, double *G
   F.dep_inv_scale = dep_inv_scale(h);
   F.surf_scale = h->weighted ? 1.0 / kCreditOne : 1.0;
   F.chi = const_cast<double *>(chi);
-  F.qrhs = h->d_qrhs; F.phi = h->d_phi; F.Gr = Gr; F.Gz = Gz; F.dinv = dinv;
+  F.qrhs = h->d_qrhs; F.phi = field_target(h); F.Gr = Gr; F.Gz = Gz; F.dinv = dinv;
   F.scalars = h->d_scalars;
+  F.vahedi = h->vahedi ? 1 : 0;
+  F.drive = drive_of(c);
   return F;
+}
+
+// Eq. 2 from the last solve's phi_P and the Laplace parts of the last refresh.
+VahediParams vahedi_params(pic_handle *h) {
+  VahediParams V;
+  memset(&V, 0, sizeof(V));
+  V.nn = h->nn;
+  V.phiP = h->d_phiP;
+  V.phiL[0] = h->d_phiL;
+  for (int k = 0; k < 3; ++k) V.phiL[k + 1] = h->d_phiLd[k];
+  V.phi = h->d_phi;
+  V.scalars = h->d_scalars;
+  V.drive = drive_of(h->cfg);
+  return V;
 }
 
 PcgParams pcg_params(pic_handle *h, const double *Gr, const double *Gz, const double *dinv, const double *qrhs, double *phi,
@@ -315,7 +346,7 @@ __global__ void k_restore_warm(int nn, const int8_t *kind, const double *stats, 
 
 int enqueue_solve(pic_handle *h, int mode) {
   if (h->keep_warm || mode == PIC_SOLVER_LEARNED)
-    CK(cudaMemcpyAsync(h->d_phi_warm, h->d_phi, sizeof(double) * h->nn, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->d_phi_warm, field_target(h), sizeof(double) * h->nn, cudaMemcpyDeviceToDevice, h->stream));
   if (mode == PIC_SOLVER_LEARNED) {
     // flexible CG with the network; the plain PCG below then confirms the
     // residual in FP64 (zero iterations when it holds) or finishes the solve
@@ -325,7 +356,7 @@ int enqueue_solve(pic_handle *h, int mode) {
     CK(cudaGetLastError());
   }
   CK(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
-  PcgParams P = pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, h->d_phi, h->cfg.pcg_tol, h->d_pcg_out);
+  PcgParams P = pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, field_target(h), h->cfg.pcg_tol, h->d_pcg_out);
   const int finisher = mode == PIC_SOLVER_LEARNED ? h->learned_finish : mode;
   if (finisher == PIC_SOLVER_MIXED) CK(launch_pcg_mixed(P, h->pcg_grid, h->stream));
   else if (finisher == PIC_SOLVER_MG) CK(launch_pcg_mg(P, h->mg, h->pcg_grid, h->stream));
@@ -370,6 +401,7 @@ int enqueue_step_pre(pic_handle *h, int in_buf, cudaEvent_t *ev) {
 
 // Step after the field solve: node E field and diagnostics (advances the device step).
 int enqueue_step_post(pic_handle *h, cudaEvent_t *ev) {
+  if (h->vahedi) CK(launch_vahedi_combine(vahedi_params(h), h->stream));
   CK(launch_efield(efield_params(h), h->stream));
   if (ev) CK(cudaEventRecord(ev[6], h->stream));
   CK(launch_diag(diag_params(h), h->stream));
@@ -398,6 +430,20 @@ int enqueue_ceq(pic_handle *h, bool with_chi) {
   PcgParams P = pcg_params(h, h->d_Grc, h->d_Gzc, h->d_dinvc, h->d_zero, h->d_phiL, tol, h->d_pcg_out + 4);
   CK(launch_pcg(P, h->pcg_grid, h->stream));
   CK(launch_energy(h->nr, h->nz, h->d_node_kind, h->d_Grc, h->d_Gzc, h->d_phiL, h->d_ceq_out, h->stream));
+  return PIC_OK;
+}
+
+// Unit Laplace solutions of the driven electrodes (Eq. 4) on the operator the
+// last enqueue_ceq built (vacuum or with chi), each from its previous solution,
+// to the C_eq solve's tolerance.  The powered electrode's is that C_eq solve's.
+int enqueue_laplace(pic_handle *h) {
+  double tol = h->cfg.pcg_tol < 1e-12 ? h->cfg.pcg_tol : 1e-12;
+  for (int k = 0; k < h->cfg.n_drive; ++k) {
+    CK(launch_set_dirichlet_unit(h->nn, h->d_node_kind, h->d_phiLd[k], PIC_NODE_DRIVEN + k, h->stream));
+    CK(cudaMemsetAsync(h->d_bar, 0, 2 * sizeof(unsigned), h->stream));
+    PcgParams P = pcg_params(h, h->d_Grc, h->d_Gzc, h->d_dinvc, h->d_zero, h->d_phiLd[k], tol, h->d_pcg_out + 4);
+    CK(launch_pcg(P, h->pcg_grid, h->stream));
+  }
   return PIC_OK;
 }
 
@@ -458,6 +504,7 @@ int window_end(pic_handle *h) {
     CK(cudaMemcpyAsync(h->d_scalars + SC_CEQ_GAUSS, h->d_ceq_out + 1, sizeof(double), cudaMemcpyDeviceToDevice,
                        h->stream));
     CK(launch_circuit_prepare(circuit_params(h, 1, nullptr, nullptr), h->stream));
+    if (h->vahedi && (st = enqueue_laplace(h))) return st;
   }
   return PIC_OK;
 }
@@ -475,6 +522,12 @@ bool check_config(const pic_config *c) {
   if (c->spin_limit < 0) return false;
   if (c->weighted != 0 && c->weighted != 1) return false;
   if (c->split_cells < 0 || c->split_cells > c->nr || (c->split_cells > 0 && !c->weighted)) return false;
+  if (c->n_drive < 0 || c->n_drive > 3) return false;
+  for (int k = 0; k < c->n_drive; ++k)
+    if (!std::isfinite(c->drive_V[k]) || !std::isfinite(c->drive_f[k]) || !std::isfinite(c->drive_phase[k]))
+      return false;
+  if (c->field_mode != PIC_FIELD_DIRECT && c->field_mode != PIC_FIELD_VAHEDI) return false;
+  if (c->field_mode == PIC_FIELD_VAHEDI && c->solver == PIC_SOLVER_LEARNED) return false;
   if (!(c->m[0] > 0) || !(c->m[1] > 0) || !(c->m_gas > 0)) return false;
   for (int k = 0; k + 1 < c->n_xs; ++k)
     if (!(c->xs_energy[k + 1] > c->xs_energy[k]) || !(c->xs_energy[k] > 0)) return false;
@@ -650,7 +703,8 @@ cudaError_t batch_build(pic_batch *b, int parity) {
                   [&](pic_handle *h) { return enqueue_step_pre(h, parity, nullptr); });
     if (e != cudaSuccess) break;
     e = add_child(G, b->hs[i], b->stream, &pre[i], 1, &solve[i], [&](pic_handle *h) {
-      const PcgParams P = pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, h->d_phi, h->cfg.pcg_tol, h->d_pcg_out);
+      const PcgParams P =
+          pcg_params(h, h->d_Gr, h->d_Gz, h->d_dinv, h->d_qrhs, field_target(h), h->cfg.pcg_tol, h->d_pcg_out);
       return launch_pcg_mg_cluster(P, h->mg, mg_cluster_size(h->nn), h->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
     });
     if (e != cudaSuccess) break;
@@ -712,7 +766,7 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
   h->xs_E.assign(cfg->xs_energy, cfg->xs_energy + cfg->n_xs);
   h->xs_S.assign(cfg->xs_sigma, cfg->xs_sigma + 5 * (size_t)cfg->n_xs);
   for (int a = 0; a < h->nn; ++a)
-    if (h->node_kind[a] < 0 || h->node_kind[a] > 2) { delete h; return PIC_EINVAL; }
+    if (h->node_kind[a] < 0 || h->node_kind[a] > 2 + cfg->n_drive) { delete h; return PIC_EINVAL; }
   for (int c = 0; c < h->nc; ++c)
     if (h->cell_kind[c] < 0 || h->cell_kind[c] > 3 || !(h->cell_eps[c] > 0)) { delete h; return PIC_EINVAL; }
   h->cfg.node_kind = h->node_kind.data();
@@ -724,6 +778,7 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
   h->capacity[0] = cfg->capacity[0];
   h->capacity[1] = cfg->capacity[1];
   h->weighted = cfg->weighted != 0;
+  h->vahedi = cfg->field_mode == PIC_FIELD_VAHEDI;
   int TX = cfg->tile_r > 0 ? cfg->tile_r : 4, TY = cfg->tile_z > 0 ? cfg->tile_z : 4;
   h->map.nr = h->nr; h->map.nz = h->nz; h->map.TX = TX; h->map.TY = TY;
   h->map.ntx = (h->nr + TX - 1) / TX; h->map.nty = (h->nz + TY - 1) / TY;
@@ -773,6 +828,10 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
     DA(h->d_bar, 4 * sizeof(unsigned));
     DA(h->d_pcg_out, sizeof(double) * 8);
     DA(h->d_phi_warm, sizeof(double) * nn);
+    if (h->vahedi) {
+      DA(h->d_phiP, sizeof(double) * nn);
+      for (int k = 0; k < cfg->n_drive; ++k) DA(h->d_phiLd[k], sizeof(double) * nn);
+    }
     DA(h->d_lstats, sizeof(double) * 4);
     DA(h->d_pair_s2, sizeof(double) * 2);
     DA(h->d_energy, sizeof(double) * 2);
@@ -921,8 +980,10 @@ int pic_start(pic_handle *h) {
   CK(cudaMemcpyAsync(h->d_scalars, sc, sizeof(sc), cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, h->stream));
   CK(launch_circuit_prepare(circuit_params(h, 1, nullptr, nullptr), h->stream));
+  if (h->vahedi && (st = enqueue_laplace(h))) return st;  // vacuum, like C_eq
   CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
   if ((st = enqueue_solve(h, h->cfg.solver))) return st;
+  if (h->vahedi) CK(launch_vahedi_combine(vahedi_params(h), h->stream));
   CK(launch_efield(efield_params(h), h->stream));
   if (sync(h)) return PIC_ECUDA;
   h->started = true;
@@ -1008,6 +1069,7 @@ int pic_field_solve(pic_handle *h, int mode, int *iters, double *rel_resid) {
   CK(launch_assemble(field_params(h, h->d_chi, h->d_Gr, h->d_Gz, h->d_dinv), h->stream));
   int st = enqueue_solve(h, mode);
   if (st) return st;
+  if (h->vahedi) CK(launch_vahedi_combine(vahedi_params(h), h->stream));
   CK(launch_efield(efield_params(h), h->stream));
   double out[3];
   CK(cudaMemcpyAsync(out, h->d_pcg_out, sizeof(out), cudaMemcpyDeviceToHost, h->stream));
@@ -1150,6 +1212,7 @@ int pic_set_solver(pic_handle *h, int solver) {
   if (!h || (solver != PIC_SOLVER_PLAIN && solver != PIC_SOLVER_MIXED && solver != PIC_SOLVER_LEARNED &&
              solver != PIC_SOLVER_MG))
     return PIC_EINVAL;
+  if (solver == PIC_SOLVER_LEARNED && h->vahedi) return PIC_EINVAL;
   if (sync(h)) return PIC_ECUDA;
   if (h->cfg.solver != solver) {
     for (int k = 0; k < 2; ++k)
@@ -1306,6 +1369,22 @@ int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
     case PIC_DIAG_NE_AVG: CK(cudaMemcpy(o, h->d_dens_avg[0], nb, cudaMemcpyDeviceToHost)); return PIC_OK;
     case PIC_DIAG_NI_AVG: CK(cudaMemcpy(o, h->d_dens_avg[1], nb, cudaMemcpyDeviceToHost)); return PIC_OK;
     case PIC_DIAG_PHI_WARM: CK(cudaMemcpy(o, h->d_phi_warm, nb, cudaMemcpyDeviceToHost)); return PIC_OK;
+    case PIC_DIAG_PHI_P:
+      if (!h->vahedi) return PIC_EINVAL;
+      CK(cudaMemcpy(o, h->d_phiP, nb, cudaMemcpyDeviceToHost));
+      return PIC_OK;
+    case PIC_DIAG_PHI_L0:
+      if (!h->vahedi) return PIC_EINVAL;
+      CK(cudaMemcpy(o, h->d_phiL, nb, cudaMemcpyDeviceToHost));
+      return PIC_OK;
+    case PIC_DIAG_PHI_L0 + 1:
+    case PIC_DIAG_PHI_L0 + 2:
+    case PIC_DIAG_PHI_L0 + 3: {
+      const int k = what - PIC_DIAG_PHI_L0 - 1;
+      if (!h->vahedi || k >= h->cfg.n_drive) return PIC_EINVAL;
+      CK(cudaMemcpy(o, h->d_phiLd[k], nb, cudaMemcpyDeviceToHost));
+      return PIC_OK;
+    }
     case PIC_DIAG_DEP_E:
     case PIC_DIAG_DEP_I: {
       std::vector<unsigned long long> u(h->nn);

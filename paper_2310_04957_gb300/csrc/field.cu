@@ -34,8 +34,15 @@ __global__ void k_assemble_nodes(const FieldParams F) {
     F.qrhs[a] = F.qw[0] * (Qe + (double)F.surf[0][a] * F.surf_scale) +
                 F.qw[1] * (Qi + (double)F.surf[1][a] * F.surf_scale);
     int k = F.node_kind[a];
-    if (k == 1) F.phi[a] = UE;
-    else if (k == 2) F.phi[a] = 0.0;
+    if (F.vahedi) {
+      if (k != 0) F.phi[a] = 0.0;  // phi_P: every electrode at 0 (Eq. 3)
+    } else if (k == 1) {
+      F.phi[a] = UE;
+    } else if (k == 2) {
+      F.phi[a] = 0.0;
+    } else if (k >= 3) {
+      F.phi[a] = F.drive.voltage(k - 3, F.scalars[SC_T]);
+    }
   }
 }
 
@@ -81,7 +88,7 @@ cudaError_t launch_assemble_edges_only(const FieldParams &F, cudaStream_t st) {
 __global__ void k_set_dirichlet(int nn, const int8_t *kind, double *phi, double U) {
   for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nn; a += gridDim.x * blockDim.x) {
     if (kind[a] == 1) phi[a] = U;
-    else if (kind[a] == 2) phi[a] = 0.0;
+    else if (kind[a] >= 2) phi[a] = 0.0;  // grounded and driven metal
   }
 }
 
@@ -89,6 +96,38 @@ cudaError_t launch_set_dirichlet(int nn, const int8_t *kind, double *phi, double
   int blocks = (nn + 255) / 256;
   if (blocks > 2048) blocks = 2048;
   k_set_dirichlet<<<blocks, 256, 0, st>>>(nn, kind, phi, U);
+  return cudaGetLastError();
+}
+
+__global__ void k_set_dirichlet_unit(int nn, const int8_t *kind, double *phi, int e) {
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < nn; a += gridDim.x * blockDim.x)
+    if (kind[a] != 0) phi[a] = kind[a] == e ? 1.0 : 0.0;
+}
+
+cudaError_t launch_set_dirichlet_unit(int nn, const int8_t *kind, double *phi, int e, cudaStream_t st) {
+  int blocks = (nn + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  k_set_dirichlet_unit<<<blocks, 256, 0, st>>>(nn, kind, phi, e);
+  return cudaGetLastError();
+}
+
+// Eq. 2 at the time of the field (scalars[SC_T]); at metal nodes it gives each
+// electrode's voltage exactly (phi_P = 0 there, phi_L one-hot).
+__global__ void k_vahedi_combine(const VahediParams V) {
+  const double t = V.scalars[SC_T], UE = V.scalars[SC_UE];
+  double U[3] = {0.0, 0.0, 0.0};
+  for (int k = 0; k < V.drive.n; ++k) U[k] = V.drive.voltage(k, t);
+  for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < V.nn; a += gridDim.x * blockDim.x) {
+    double v = V.phiP[a] + UE * V.phiL[0][a];
+    for (int k = 0; k < V.drive.n; ++k) v += U[k] * V.phiL[k + 1][a];
+    V.phi[a] = v;
+  }
+}
+
+cudaError_t launch_vahedi_combine(const VahediParams &V, cudaStream_t st) {
+  int blocks = (V.nn + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  k_vahedi_combine<<<blocks, 256, 0, st>>>(V);
   return cudaGetLastError();
 }
 

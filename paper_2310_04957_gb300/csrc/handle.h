@@ -39,6 +39,9 @@ struct pic_handle {
   float slack = 0.25f;
   int64_t capacity[2] = {0, 0};
   bool weighted = false;  // particles carry weight ratios (cfg.weighted)
+  bool vahedi = false;    // field composed by Eq. 2 (cfg.field_mode)
+  double *d_phiP = nullptr;                            // phi_P, the zero-boundary part
+  double *d_phiLd[3] = {nullptr, nullptr, nullptr};    // unit Laplace solutions of the driven electrodes
   // device: geometry, operator, fields
   int8_t *d_node_kind = nullptr, *d_cell_kind = nullptr, *d_bin_plasma = nullptr;
   double *d_Gvac_r = nullptr, *d_Gpl_r = nullptr, *d_Gvac_z = nullptr, *d_Gpl_z = nullptr, *d_vnode = nullptr;

@@ -9,6 +9,15 @@ namespace pic {
 
 constexpr int kMaxTileCells = 256;
 
+// Voltage-driven electrodes: electrode k (node kind 3 + k) at V[k] sin(2 pi f[k] t + phase[k]).
+struct Drive {
+  int n;
+  double V[3], f[3], phase[3];
+  __device__ __forceinline__ double voltage(int k, double t) const {
+    return V[k] * sin(6.283185307179586476925286766559 * f[k] * t + phase[k]);
+  }
+};
+
 template <typename T>
 struct PushParams {
   BinMap map;
@@ -57,7 +66,21 @@ struct FieldParams {
   double chi_coef[2];       // dt^2/(2 eps0) q_s^2/m_s w_s
   double *chi, *qrhs, *phi, *Gr, *Gz, *dinv;
   double *scalars;
+  int vahedi;               // phi is phi_P: every electrode at 0
+  Drive drive;              // voltage-driven electrodes (node kinds 3..)
 };
+
+// Unit-voltage boundary of electrode kind `e`: 1 on it, 0 on every other metal node.
+cudaError_t launch_set_dirichlet_unit(int nn, const int8_t *kind, double *phi, int e, cudaStream_t st);
+// Eq. 2: phi = phi_P + U_E phi_L0 + sum_k U_k phi_Lk (U_E and t from the scalars).
+struct VahediParams {
+  int nn;
+  const double *phiP, *phiL[4];
+  double *phi;
+  const double *scalars;
+  Drive drive;
+};
+cudaError_t launch_vahedi_combine(const VahediParams &V, cudaStream_t st);
 
 // Field solve on the free nodes of sum_b G_ab (phi_a - phi_b) = qrhs_a.
 // work: [8*nn] doubles (plain) -- r[2], w[2], s[2], p, spare;

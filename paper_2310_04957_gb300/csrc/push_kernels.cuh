@@ -107,6 +107,11 @@ __device__ __forceinline__ bool in_plasma(const PushParams<T> &P, int ci, int cj
   return __ldg(P.cell_kind + cj * P.nr + ci) == 0;
 }
 
+// Tally slot of an exit through a node of kind k: 0 the powered electrode,
+// 2 a free node (dielectric surface charge), 1 any other metal (grounded or
+// voltage-driven).
+__device__ __forceinline__ int tally_kind(int k) { return k == 1 ? 0 : (k == 0 ? 2 : 1); }
+
 // Node nearest to an exit point given in cell units (position clamped into the domain).
 template <typename T>
 __device__ __forceinline__ int exit_node(const PushParams<T> &P, int ci, T fr, int cj, T fz) {
@@ -329,20 +334,23 @@ struct Outcome {
   int birth;      // 1 -> electron + ion born at x_n (electrons only)
 };
 
-// Electron null-collision test (Sec. 2, Vahedi's method): -1 for a null
-// collision, else the process (0 elastic, 1 excitation, 2 ionization).  Returns
-// the energy E (eV) and the uniforms u2, u3 its kinematics use.
+// Electron null-collision method (Sec. 2, Vahedi's method).  The test: the
+// step's four uniforms u of the particle, a candidate if u0 < P_null.
 template <typename T>
-__device__ __forceinline__ int mcc_electron_choose(const PushParams<T> &P, const Part<T> &p, T &E, T &u2, T &u3) {
-  T u[4];
+__device__ __forceinline__ bool electron_candidate(const PushParams<T> &P, const Part<T> &p, T u[4]) {
   draw4(P, p.id, 0u, 0u, u);
-  if (!(u[0] < P.pcoll[0])) return -1;
+  return u[0] < P.pcoll[0];
+}
+
+// The process of a candidate, from u1 against the cumulative collision
+// frequencies at its energy E (eV, returned): -1 null, else 0 elastic,
+// 1 excitation, 2 ionization.  Its kinematics use u2 and u3.
+template <typename T>
+__device__ __forceinline__ int mcc_electron_select(const PushParams<T> &P, const Part<T> &p, const T u[4], T &E) {
   T v2 = p.vr * p.vr + p.vt * p.vt + p.vz * p.vz;
   T speed = m_sqrt(v2);
   if (!(speed > (T)0)) return -1;
   E = P.e_per_v2[0] * v2;
-  u2 = u[2];
-  u3 = u[3];
   T ng_v = P.n_gas * speed;
   T sg[3];
   xs_electron(P, E, sg);
@@ -412,9 +420,11 @@ __device__ __forceinline__ void mcc_electron_apply(const PushParams<T> &P, Part<
 // Electron collision: test, then kinematics when one occurs.
 template <typename T>
 __device__ __forceinline__ int mcc_electron(const PushParams<T> &P, Part<T> &p, Part<T> &be, Part<T> &bi) {
-  T E = (T)0, u2 = (T)0, u3 = (T)0;
-  const int c = mcc_electron_choose(P, p, E, u2, u3);
-  if (c >= 0) mcc_electron_apply(P, p, c, E, u2, u3, be, bi);
+  T u[4];
+  if (!electron_candidate(P, p, u)) return -1;
+  T E = (T)0;
+  const int c = mcc_electron_select(P, p, u, E);
+  if (c >= 0) mcc_electron_apply(P, p, c, E, u[2], u[3], be, bi);
   return c;
 }
 
@@ -473,10 +483,11 @@ __device__ __forceinline__ void gather_nodes(const PushParams<T> &P, int ci, int
   e[3] = E[n00 + P.nr + 2];
 }
 
+// Gather, correction, D1 filter and velocity update, axis, absorption test at
+// x_n.  Returns false (with the absorption in o) if the particle left the plasma.
 template <typename T>
-__device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T> &p, Part<T> &be, Part<T> &bi,
-                                           const typename V2<T>::type en[4]) {
-  Outcome o{0, -1, 0, -1, 0};
+__device__ __forceinline__ bool to_xn(const PushParams<T> &P, int s, Part<T> &p, const typename V2<T>::type en[4],
+                                      Outcome &o) {
   // gather E at x~_n with the deposit weights: linear in z, by annulus area in r
   T ir = (T)p.ci;
   T a = p.fr * ((T)2 * ir + p.fr) * rcp((T)2 * ir + (T)1);
@@ -508,9 +519,31 @@ __device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T
   if (!in_plasma(P, p.ci, p.cj)) {
     o.abs_node = exit_node(P, p.ci, p.fr, p.cj, p.fz);
     o.abs_kind = (int)__ldg(P.node_kind + o.abs_node);
-    o.abs_kind = o.abs_kind == 1 ? 0 : (o.abs_kind == 2 ? 1 : 2);
-    return o;
+    o.abs_kind = tally_kind(o.abs_kind);
+    return false;
   }
+  return true;
+}
+
+// Predictor to x~_{n+1} and the absorption test there.
+template <typename T>
+__device__ __forceinline__ void finish_push(const PushParams<T> &P, Part<T> &p, Outcome &o) {
+  predict(P, p);
+  if (!in_plasma(P, p.ci, p.cj)) {
+    o.abs_node = exit_node(P, p.ci, p.fr, p.cj, p.fz);
+    o.abs_kind = (int)__ldg(P.node_kind + o.abs_node);
+    o.abs_kind = tally_kind(o.abs_kind);
+    return;
+  }
+  o.alive = 1;
+}
+
+// The whole push of one particle with its collision in line.
+template <typename T>
+__device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T> &p, Part<T> &be, Part<T> &bi,
+                                           const typename V2<T>::type en[4]) {
+  Outcome o{0, -1, 0, -1, 0};
+  if (!to_xn(P, s, p, en, o)) return o;
   // MCC at x_n on v_{n-1/2}
   if (s == 0) {
     o.coll = mcc_electron(P, p, be, bi);
@@ -518,14 +551,7 @@ __device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T
   } else {
     o.coll = mcc_ion(P, p);
   }
-  predict(P, p);
-  if (!in_plasma(P, p.ci, p.cj)) {
-    o.abs_node = exit_node(P, p.ci, p.fr, p.cj, p.fz);
-    o.abs_kind = (int)__ldg(P.node_kind + o.abs_node);
-    o.abs_kind = o.abs_kind == 1 ? 0 : (o.abs_kind == 2 ? 1 : 2);
-    return o;
-  }
-  o.alive = 1;
+  finish_push(P, p, o);
   return o;
 }
 
@@ -883,7 +909,7 @@ template <typename T>
 __device__ __forceinline__ int exit_kind(const PushParams<T> &P, const Part<T> &p, int &node) {
   node = exit_node(P, p.ci, p.fr, p.cj, p.fz);
   const int k = (int)__ldg(P.node_kind + node);
-  return k == 1 ? 0 : (k == 2 ? 1 : 2);
+  return tally_kind(k);
 }
 
 // A newborn ion from an electron CTA: predictor, absorption, write (and split),
@@ -996,7 +1022,7 @@ __device__ __forceinline__ void process_home(const PushParams<float> &P, int s, 
 // Shared memory of a particle CTA (declared once in the kernel, shared by both
 // species' code): the node tile of the deposit, the tile's bin prefix and
 // offsets, and (FP32) the double-buffered next-chunk particle state.
-template <typename T, int TX, int TY>
+template <typename T, int TX, int TY, bool WT>
 struct ParticleSmem {
   static constexpr int kW = sizeof(T) == 4 ? kThreads / 32 : 1;
   unsigned long long tile[(TX + 1 + 2 * kHalo) * (TY + 1 + 2 * kHalo)];
@@ -1005,8 +1031,7 @@ struct ParticleSmem {
   int off[TX * TY];
   Vec4<float> wa[kW][2][32], wb[kW][2][32];  // per-warp staging of the next chunk
   unsigned long long wid[kW][2][32];
-  float ww[kW][2][32];   // weight ratios (weighted particles)
-  int wcell[kW][2][32];  // cells of overflow-region particles
+  float ww[WT ? kW : 1][2][32];  // weight ratios (weighted particles)
   unsigned cnt[CNT_N];   // the CTA's tallies
   unsigned long long cntw[6];  // and its weighted absorption tallies
 };
@@ -1020,7 +1045,7 @@ struct ParticleSmem {
 // code whichever region it was stored in (which region that is depends on the
 // order of the slot claims of the previous step).
 template <typename T, int TX, int TY, int s, bool WT>
-__device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSmem<T, TX, TY> &sh) {
+__device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSmem<T, TX, TY, WT> &sh) {
   constexpr int per = TX * TY;
   constexpr int TW = TX + 1 + 2 * kHalo, TH = TY + 1 + 2 * kHalo;
   const StoreView<T> &A = P.in[s];
@@ -1078,8 +1103,8 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
     // overflow CTA's warps take every (overflow warps)-th chunk of the region.
     // While a chunk is processed the next one streams from HBM into the warp's
     // shared staging with cp.async (two 16-byte copies and the id per lane, and
-    // the cell in the overflow region; each lane reads back only its own copy).
-    constexpr int kW = ParticleSmem<T, TX, TY>::kW;
+    // the ratio of weighted particles; each lane reads back only its own copy).
+    constexpr int kW = ParticleSmem<T, TX, TY, WT>::kW;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int *s_cpre = sh.cpre;
     int c0, c1, cstep;
@@ -1119,7 +1144,6 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
           cp_async16(&sh.wb[w][buf][lane], A.pb + slot);
           cp_async8(&sh.wid[w][buf][lane], A.id + slot);
           if (WT) cp_async4(&sh.ww[w][buf][lane], A.w + slot);
-          if (ovf_cta) sh.wcell[w][buf][lane] = __ldg(A.cell + slot);
         }
       }
       cp_async_commit_group();
@@ -1156,7 +1180,7 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
         p.id = sh.wid[w][buf][lane];
         p.w = WT ? sh.ww[w][buf][lane] : 1.0f;
         if (ovf_cta) {
-          const int cl = sh.wcell[w][buf][lane];
+          const int cl = __ldg(A.cell + slot);
           p.cj = cl / P.nr;
           p.ci = cl - p.cj * P.nr;
         } else {
@@ -1218,7 +1242,7 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
 
 template <typename T, int TX, int TY, bool WT>
 __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 4 : 2) k_particles(const PushParams<T> P) {
-  __shared__ ParticleSmem<T, TX, TY> sh;
+  __shared__ ParticleSmem<T, TX, TY, WT> sh;
   if (blockIdx.y == 0) particles_cta<T, TX, TY, 0, WT>(P, sh);
   else particles_cta<T, TX, TY, 1, WT>(P, sh);
 }

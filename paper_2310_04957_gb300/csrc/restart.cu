@@ -20,7 +20,7 @@ using namespace pic;
 namespace {
 
 const char kMagic[8] = {'P', 'I', 'C', 'R', 'S', 'T', 'G', 'B'};
-const uint32_t kVersion = 2;
+const uint32_t kVersion = 3;
 const size_t kChunk = size_t(64) << 20;  // host bounce buffer
 
 struct File {
@@ -111,6 +111,10 @@ std::vector<Blob> state_blobs(pic_handle *h) {
       {h->mg.persist, sizeof(float) * (size_t)(h->mg.smem_floats > 0 ? h->mg.smem_floats : 1)},
       {h->mg.solves, sizeof(int)},
   };
+  if (h->vahedi) {  // the Vahedi parts: phi_P (warm start) and the driven electrodes' Laplace solutions
+    b.push_back({h->d_phiP, d8 * nn});
+    for (int k = 0; k < h->cfg.n_drive; ++k) b.push_back({h->d_phiLd[k], d8 * nn});
+  }
   for (int s = 0; s < 2; ++s) {
     b.push_back({h->d_dep[s], u8 * nn});
     b.push_back({h->d_surf[s], u8 * nn});

@@ -21,8 +21,9 @@ PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ENOCONV, PIC_ETIMEOUT, PIC_EOVERFLOW, PIC
 PIC_FLAG_OVERFLOW, PIC_FLAG_TIMEOUT, PIC_FLAG_NOCONV, PIC_FLAG_NAN = 0x1, 0x2, 0x4, 0x8
 PIC_FP32, PIC_FP64 = 0, 1
 PIC_SOLVER_PLAIN, PIC_SOLVER_MIXED, PIC_SOLVER_LEARNED, PIC_SOLVER_MG = 0, 1, 2, 3
+PIC_FIELD_DIRECT, PIC_FIELD_VAHEDI = 0, 1
 DIAG = {"phi": 0, "Er": 1, "Ez": 2, "chi": 3, "dep_e": 4, "dep_i": 5, "sigma": 6, "vnode": 7, "rho": 8,
-        "ne_avg": 9, "ni_avg": 10, "phi_warm": 11}
+        "ne_avg": 9, "ni_avg": 10, "phi_warm": 11, "phiP": 12, "phiL0": 13, "phiL1": 14, "phiL2": 15, "phiL3": 16}
 DIAG_SCALARS = 100
 DIAG_STORE = 101
 DIAG_SOLVER = 102
@@ -69,6 +70,8 @@ class Config(ctypes.Structure):
         ("capacity", ctypes.c_int64 * 2), ("precision", ctypes.c_int32), ("solver", ctypes.c_int32),
         ("tile_r", ctypes.c_int32), ("tile_z", ctypes.c_int32), ("bin_slack", ctypes.c_double),
         ("spin_limit", ctypes.c_int64), ("weighted", ctypes.c_int32), ("split_cells", ctypes.c_int32),
+        ("n_drive", ctypes.c_int32), ("drive_V", ctypes.c_double * 3), ("drive_f", ctypes.c_double * 3),
+        ("drive_phase", ctypes.c_double * 3), ("field_mode", ctypes.c_int32),
     ]
 
 
@@ -178,6 +181,11 @@ class Discharge:
         c.spin_limit = spin_limit
         c.weighted = int(self.weighted)
         c.split_cells = int(wl.split_cells)
+        drive = tuple(wl.drive)
+        c.n_drive = len(drive)
+        for k, (V, f, ph) in enumerate(drive):
+            c.drive_V[k], c.drive_f[k], c.drive_phase[k] = V, f, ph
+        c.field_mode = int(wl.field_mode)
         h = ctypes.c_void_p()
         _check(L.pic_init(ctypes.byref(c), _stream(stream), ctypes.byref(h)), "pic_init")
         self.h = h

@@ -30,6 +30,8 @@ BOLTZMANN = 1.380649e-23
 MILLITORR = 0.13332236842105263  # Pa
 
 NODE_FREE, NODE_POWERED, NODE_GROUNDED = 0, 1, 2
+NODE_DRIVEN = 3  # first voltage-driven electrode (3, 4, 5)
+FIELD_DIRECT, FIELD_VAHEDI = 0, 1
 CELL_PLASMA, CELL_POWERED, CELL_GROUNDED, CELL_DIELECTRIC = 0, 1, 2, 3
 CIRCUIT_DIRECT, CIRCUIT_RLC, CIRCUIT_IMN = 0, 1, 2
 SEED_BASE = 0x5EED0000
@@ -100,6 +102,8 @@ class Workload:
     particles: tuple  # (electrons, ions)
     capacity: tuple
     split_cells: int = 0  # particle splitting in the first split_cells radial cells (0: off)
+    drive: tuple = ()  # voltage-driven electrodes (node kinds 3, 4, 5): (V, f, phase) each, V sin(2 pi f t + phase)
+    field_mode: int = 0  # FIELD_DIRECT or FIELD_VAHEDI
 
     @property
     def n_nodes(self) -> int:

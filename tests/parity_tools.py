@@ -312,11 +312,15 @@ class StepParity:
         if wl.circuit != 0:
             o.set_ceq(ceq_solve)
             o.set_circuit_state(y)
-        o.assemble()
-        st_o, _, _ = o.field_solve()
-        assert st_o == 0
-        assert phi_err(d.field("phi"), o.field("phi"), wl.V_src) <= 1e-8
-        assert rel_l2(d.field("Ez"), o.field("Ez")) <= 1e-8
+        # (in the Vahedi composition a window end has since re-solved the Laplace
+        # parts, which the step's solve did not use: no re-solve to compare then)
+        refreshed = wl.field_mode == W.FIELD_VAHEDI and wl.ceq_refresh and sd["step"] % wl.steps_per_rf == 0
+        if not refreshed:
+            o.assemble()
+            st_o, _, _ = o.field_solve()
+            assert st_o == 0
+            assert phi_err(d.field("phi"), o.field("phi"), wl.V_src) <= 1e-8
+            assert rel_l2(d.field("Ez"), o.field("Ez")) <= 1e-8
         # carry the device's state into the next step
         for s in (0, 1):
             o.set_particles(s, _particles(post_d[s], np.arange(len(post_d[s]["id"]))))
