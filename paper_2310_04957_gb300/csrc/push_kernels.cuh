@@ -47,10 +47,13 @@ __device__ __forceinline__ void m_sincospi(float x, float *s, float *c) { sincos
 __device__ __forceinline__ void m_sincospi(double x, double *s, double *c) { sincospi(x, s, c); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
 __device__ __forceinline__ double m_floor(double x) { return floor(x); }
-// Reciprocal and reciprocal square root: FP32 uses the correctly rounded
-// reciprocal and one Newton step on the hardware rsqrt estimate (error ~1 ulp,
-// unbiased); FP64 keeps IEEE division and square root.
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// Reciprocal and reciprocal square root: FP32 uses the hardware reciprocal
+// approximation (__fdividef, at most 2 ulp; the arguments here are normal
+// numbers of order 1..1e3) and one Newton step on the hardware rsqrt estimate
+// (~1 ulp, unbiased); FP64 keeps IEEE division and square root.  The FP32
+// path's tolerances (1e-5 per particle, FLIP_MARGIN in the parity proofs) are
+// far above these errors.
+__device__ __forceinline__ float rcp(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rsq(float q) {
   float y = rsqrtf(q);
@@ -483,11 +486,19 @@ __device__ __forceinline__ void gather_nodes(const PushParams<T> &P, int ci, int
   e[3] = E[n00 + P.nr + 2];
 }
 
+// Cell (i, j) is in the plasma: (kci, kcj) is a cell known to be (the warp's
+// home cell: particles are only stored in plasma cells), else the cell map decides.
+template <typename T>
+__device__ __forceinline__ bool in_plasma_k(const PushParams<T> &P, int ci, int cj, int kci, int kcj) {
+  return (ci == kci && cj == kcj) || in_plasma(P, ci, cj);
+}
+
 // Gather, correction, D1 filter and velocity update, axis, absorption test at
 // x_n.  Returns false (with the absorption in o) if the particle left the plasma.
+// (kci, kcj): a cell known to be plasma (-1: none).
 template <typename T>
 __device__ __forceinline__ bool to_xn(const PushParams<T> &P, int s, Part<T> &p, const typename V2<T>::type en[4],
-                                      Outcome &o) {
+                                      Outcome &o, int kci = -1, int kcj = -1) {
   // gather E at x~_n with the deposit weights: linear in z, by annulus area in r
   T ir = (T)p.ci;
   T a = p.fr * ((T)2 * ir + p.fr) * rcp((T)2 * ir + (T)1);
@@ -516,7 +527,7 @@ __device__ __forceinline__ bool to_xn(const PushParams<T> &P, int s, Part<T> &p,
   }
   renorm(p.ci, p.fr);
   renorm(p.cj, p.fz);
-  if (!in_plasma(P, p.ci, p.cj)) {
+  if (!in_plasma_k(P, p.ci, p.cj, kci, kcj)) {
     o.abs_node = exit_node(P, p.ci, p.fr, p.cj, p.fz);
     o.abs_kind = (int)__ldg(P.node_kind + o.abs_node);
     o.abs_kind = tally_kind(o.abs_kind);
@@ -527,9 +538,10 @@ __device__ __forceinline__ bool to_xn(const PushParams<T> &P, int s, Part<T> &p,
 
 // Predictor to x~_{n+1} and the absorption test there.
 template <typename T>
-__device__ __forceinline__ void finish_push(const PushParams<T> &P, Part<T> &p, Outcome &o) {
+__device__ __forceinline__ void finish_push(const PushParams<T> &P, Part<T> &p, Outcome &o, int kci = -1,
+                                            int kcj = -1) {
   predict(P, p);
-  if (!in_plasma(P, p.ci, p.cj)) {
+  if (!in_plasma_k(P, p.ci, p.cj, kci, kcj)) {
     o.abs_node = exit_node(P, p.ci, p.fr, p.cj, p.fz);
     o.abs_kind = (int)__ldg(P.node_kind + o.abs_node);
     o.abs_kind = tally_kind(o.abs_kind);
@@ -541,9 +553,9 @@ __device__ __forceinline__ void finish_push(const PushParams<T> &P, Part<T> &p, 
 // The whole push of one particle with its collision in line.
 template <typename T>
 __device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T> &p, Part<T> &be, Part<T> &bi,
-                                           const typename V2<T>::type en[4]) {
+                                           const typename V2<T>::type en[4], int kci = -1, int kcj = -1) {
   Outcome o{0, -1, 0, -1, 0};
-  if (!to_xn(P, s, p, en, o)) return o;
+  if (!to_xn(P, s, p, en, o, kci, kcj)) return o;
   // MCC at x_n on v_{n-1/2}
   if (s == 0) {
     o.coll = mcc_electron(P, p, be, bi);
@@ -551,7 +563,7 @@ __device__ __forceinline__ Outcome advance(const PushParams<T> &P, int s, Part<T
   } else {
     o.coll = mcc_ion(P, p);
   }
-  finish_push(P, p, o);
+  finish_push(P, p, o, kci, kcj);
   return o;
 }
 
@@ -945,13 +957,19 @@ template <typename T, bool WT>
 __device__ __forceinline__ void tally(const PushParams<T> &P, int s, const Outcome &o, bool active, const Part<T> &p,
                                       const TileCtx &tc) {
   if (!__any_sync(0xffffffffu, active && (o.abs_kind >= 0 || o.coll >= 0))) return;
-  count_warp(tc.cnt + CNT_ABS + 3 * s + 0, active && o.abs_kind == 0);
-  count_warp(tc.cnt + CNT_ABS + 3 * s + 1, active && o.abs_kind == 1);
-  count_warp(tc.cnt + CNT_ABS + 3 * s + 2, active && o.abs_kind == 2);
+  // each lane sets bit 10k of its absorption word for kind k and of its collision word
+  // for process k; one redux.sync per word sums the warp's counts into three 10-bit
+  // fields (at most 32 each), which lanes 0..5 add to the CTA's tallies
+  const unsigned pa = (active && o.abs_kind >= 0) ? 1u << (10 * o.abs_kind) : 0u;
+  const unsigned pc = (active && o.coll >= 0) ? 1u << (10 * o.coll) : 0u;
+  const unsigned sa = __reduce_add_sync(0xffffffffu, pa), scl = __reduce_add_sync(0xffffffffu, pc);
+  const int lane = threadIdx.x & 31;
+  if (lane < 6) {
+    const int k = lane < 3 ? lane : lane - 3;
+    const unsigned v = ((lane < 3 ? sa : scl) >> (10 * k)) & 1023u;
+    if (v) atomicAdd(tc.cnt + (lane < 3 ? CNT_ABS : CNT_COLL) + 3 * s + k, v);
+  }
   if (active && o.abs_kind >= 0) credit<WT>(P, tc, s, o.abs_kind, o.abs_node, p.w);
-  count_warp(tc.cnt + CNT_COLL + 3 * s + 0, active && o.coll == 0);
-  count_warp(tc.cnt + CNT_COLL + 3 * s + 1, active && o.coll == 1);
-  count_warp(tc.cnt + CNT_COLL + 3 * s + 2, active && o.coll == 2);
 }
 
 template <bool WT, typename T>
@@ -1013,7 +1031,7 @@ __device__ __forceinline__ void process_home(const PushParams<float> &P, int s, 
                                              unsigned acc[4]) {
   Part<float> be, bi;
   Outcome o{0, -1, 0, -1, 0};
-  if (active) o = advance(P, s, p, be, bi, en);
+  if (active) o = advance(P, s, p, be, bi, en, hci, hcj);
   tally<float, WT>(P, s, o, active, p, tc);
   emit_home<TX, TY, WT>(P, s, active && o.alive, p, tc, hci, hcj, hkey, acc);
   emit_births<float, TX, TY, WT>(P, active && o.birth, be, bi, tc);
