@@ -8,14 +8,17 @@
 // electrons and Ar+ in argon, deposition of charge and of the implicit
 // susceptibility (both from the same per-species node counts).
 //
-// One CTA = one tile of TX x TY cells of one species.  It reads the tile's bins
-// (contiguous slots), pushes every particle in registers, claims a slot in the
-// particle's new bin of the write store (warp-aggregated: lanes with the same
-// new bin share one atomicAdd on the bin's fill counter), and deposits the
-// four node weights as 2^-26 fixed-point integers: summed over lanes of the
-// same new cell with redux.sync, added to a shared-memory node tile (tile +
-// halo), and flushed with one 64-bit global add per tile node.  Integer sums
-// are exact and order-independent.
+// One CTA = one tile of TX x TY cells of one species (plus a few CTAs for the
+// overflow region).  It reads the tile's bins (contiguous slots); in FP32 each
+// warp takes whole 32-particle chunks of one bin, staged by cp.async.  Every
+// particle is pushed in registers and claims a slot in its new bin of the write
+// store: one ballot and one atomic for the lanes that stay in the warp's home
+// cell, match_any groups for the others.  The four node weights are 2^-26
+// fixed-point integers (2^-40 in FP64): home-cell weights are summed in
+// registers and reduced once per bin, the others added to a shared-memory node
+// tile (tile + halo), which is flushed with one 64-bit global add per node.
+// Integer sums are exact and order-independent.  Weighted particles (ratios,
+// splitting) are a separate template instance (WT).
 #pragma once
 #include <cstdint>
 
@@ -983,11 +986,23 @@ __device__ __forceinline__ void load_particle(const StoreView<T> &S, int slot, P
 
 // The pair an ionization created (lanes with `birth`, both with the parent's
 // weight ratio): predictor and absorption test of the newborn electron,
-// warp-wide emit, then the newborn ion.  Warp-collective.
+// warp-wide emit, then the newborn ion.  Warp-collective.  Out of line: few
+// warps have a birth in a step, and the inlined body costs the common path
+// registers and instruction-cache room (measured 2.6 % of the kernel).
+template <typename T, int TX, int TY, bool WT>
+__device__ __noinline__ void emit_births_body(const PushParams<T> &P, bool birth, Part<T> &be, Part<T> &bi,
+                                              const TileCtx &tc);
+
 template <typename T, int TX, int TY, bool WT>
 __device__ __forceinline__ void emit_births(const PushParams<T> &P, bool birth, Part<T> &be, Part<T> &bi,
                                             const TileCtx &tc) {
   if (!__any_sync(0xffffffffu, birth)) return;
+  emit_births_body<T, TX, TY, WT>(P, birth, be, bi, tc);
+}
+
+template <typename T, int TX, int TY, bool WT>
+__device__ __noinline__ void emit_births_body(const PushParams<T> &P, bool birth, Part<T> &be, Part<T> &bi,
+                                              const TileCtx &tc) {
   count_warp(tc.cnt + CNT_BORN + 0, birth);
   count_warp(tc.cnt + CNT_BORN + 1, birth);
   bool e_alive = false;
