@@ -107,3 +107,43 @@ def test_autotuner_picks_a_measured_tile():
     cls = sweep.tile_class(wls[0])
     assert choice[cls] in ((2, 2), (4, 4), (8, 8))
     assert t[cls][choice[cls]] == min(t[cls].values())
+
+
+def _driven_top(wl):
+    """The GEC-like cell with its upper electrode voltage-driven (2 MHz, 60 V), Vahedi mode."""
+    node = wl.node_kind.copy()
+    ish, jt = int(round(0.055 / wl.dr)), int(round(0.0404 / wl.dz))
+    block = node[jt:wl.nz, 0:ish + 1]
+    node[jt:wl.nz, 0:ish + 1] = np.where(block == W.NODE_GROUNDED, W.NODE_DRIVEN, block)
+    return dataclasses.replace(wl, node_kind=node, drive=((60.0, 2e6, 0.4),), field_mode=W.FIELD_VAHEDI)
+
+
+def test_batch_of_weighted_and_vahedi_discharges_matches_the_oracle():
+    """A batch mixing the optional paths: radially weighted particles with splitting in the
+    first 6 radial cells (the weighted kernel instance), the Vahedi composition with a
+    voltage-driven upper electrode (phi_P solved on the discharge's cluster, then Eq. 2),
+    and a plain discharge; each stepped side by side with its oracle for 3 steps across a
+    window end, with the single-discharge checks (FP32 particle kernel)."""
+    P = pic()
+    wls = [W.gec_case(64, 32, 20.0, 120.0, cm2=150e-12, n_per_species=30_000, seed_index=77, split_cells=6),
+           _driven_top(W.gec_case(96, 48, 30.0, 150.0, n_per_species=40_000, seed_index=78)),
+           W.gec_case(128, 64, 8.0, 80.0, n_per_species=20_000, seed_index=79)]
+    wls = [dataclasses.replace(wl, steps_per_rf=3) for wl in wls]
+    pairs = [make_pair(wl, 0, solver=MIXED, tile=(4, 2)) for wl in wls]
+    for d, o in pairs:
+        d.start()
+        o.init_fields()
+    b = P.Batch([d for d, _ in pairs])
+    sps = [StepParity(wl, d, o, True) for wl, (d, o) in zip(wls, pairs)]
+    for _ in range(3):
+        for sp in sps:
+            sp.begin()
+        b.step(1)
+        b.sync()
+        for sp in sps:
+            sp.finish()
+    for sp, (d, _) in zip(sps, pairs):
+        assert d.status() == 0
+        assert d.scalars()["windows"] == 1
+    assert sps[0].splits > 0
+    assert rel_l2(pairs[1][0].field("phiL1"), pairs[1][1].field("phiL1")) <= 1e-6

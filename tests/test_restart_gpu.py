@@ -28,10 +28,11 @@ def snapshot(d):
     return out
 
 
-@pytest.mark.parametrize("precision", [1, 0], ids=["fp64", "fp32"])
-def test_save_load_continues_bit_for_bit(precision, tmp_path):
+@pytest.mark.parametrize("precision,split", [(1, 0), (0, 0), (0, 8)], ids=["fp64", "fp32", "fp32-weighted"])
+def test_save_load_continues_bit_for_bit(precision, split, tmp_path):
     P = pic()
-    wl = dataclasses.replace(W.gec_case(128, 64, 30.0, 150.0, n_per_species=100_000, seed_index=22),
+    wl = dataclasses.replace(W.gec_case(128, 64, 30.0, 150.0, n_per_species=100_000, seed_index=22,
+                                        split_cells=split),
                              steps_per_rf=5, phase_src=0.4)
     d = P.Discharge(wl, precision=precision, solver=P.PIC_SOLVER_MG, bin_slack=0.05)
     d.start()
