@@ -327,7 +327,8 @@ def run_sweep(args):
     t_setup = time.perf_counter() - t_setup
     K, Wm = args.steps, args.warmup
     seq_s, ps = 0.0, 0.0
-    for d in ds:
+    flagged = []  # (phase, discharge, status bits) of every discharge that reported a failure
+    for i, d in enumerate(ds):
         d.step(Wm)
         torch.cuda.synchronize()
         n = d.count(0) + d.count(1)
@@ -336,6 +337,9 @@ def run_sweep(args):
         torch.cuda.synchronize()
         seq_s += time.perf_counter() - t0
         ps += n * K
+        f = d.status()
+        if f:
+            flagged.append(("alone", mine[i], f))
     b = pic.Batch(ds)
     b.step(Wm)
     b.sync()
@@ -348,8 +352,12 @@ def run_sweep(args):
         b.sync()
         t_b = time.perf_counter() - t0
     flags = 0
-    for d in ds:
-        flags |= d.status()
+    for i, d in enumerate(ds):
+        f = d.status()
+        if f:
+            flagged.append(("batch", mine[i], f))
+    for _, _, f in flagged:
+        flags |= f
     t_b, n_all = across_ranks(t_b, float(n), dist)
     seq_s, ps = across_ranks(seq_s, ps, dist)
     value = n_all * K / t_b
@@ -371,7 +379,7 @@ def run_sweep(args):
             "autotuned_tiles": {f"{c[0]}x{c[1]}": list(t) for c, t in choice.items()},
             "autotune_ms": {f"{c[0]}x{c[1]}": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in tv.items()}
                             for c, tv in timings.items()},
-            "setup_s": t_setup, "status_flags": flags, "clocks": clk.summary(),
+            "setup_s": t_setup, "status_flags": flags, "flagged": flagged, "clocks": clk.summary(),
             "gpu_launches": None, "e2e": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
     if dist is not None:
