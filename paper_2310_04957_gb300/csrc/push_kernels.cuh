@@ -10,7 +10,8 @@
 //
 // One CTA = one tile of TX x TY cells of one species (plus a few CTAs for the
 // overflow region).  It reads the tile's bins (contiguous slots); in FP32 each
-// warp takes whole 32-particle chunks of one bin, staged by cp.async.  Every
+// warp takes whole 32-particle chunks of one bin, staged by cp.async, and
+// gathers E from a shared-memory copy of the tile's nodes.  Every
 // particle is pushed in registers and claims a slot in its new bin of the write
 // store: one ballot and one atomic for the lanes that stay in the warp's home
 // cell, match_any groups for the others.  The four node weights are 2^-26
@@ -833,7 +834,9 @@ __device__ __forceinline__ void emit(const PushParams<T> &P, int s, bool alive, 
 // one atomic, and add their four node weights to per-lane registers; the warp
 // reduces the registers into the shared node tile once per bin (flush_home).
 // Particles that leave the home cell claim by match_any groups and deposit
-// directly.  Warp-collective.
+// directly.  Both claim atomics are issued before the deposit and their results
+// read after it, so the deposit arithmetic covers the atomics' latency.
+// Warp-collective.
 template <int TX, int TY, bool WT>
 __device__ __forceinline__ void emit_home(const PushParams<float> &P, int s, bool alive, const Part<float> &p,
                                           const TileCtx &tc, int hci, int hcj, int hkey, unsigned acc[4]) {
@@ -846,24 +849,56 @@ __device__ __forceinline__ void emit_home(const PushParams<float> &P, int s, boo
   bool split = false;
   if constexpr (WT) split = alive && splits(P, p.ci, p.w);
   const unsigned hm = __ballot_sync(FULL, home);
+  const bool other = alive && !home;
+  const unsigned om = __ballot_sync(FULL, other);
+  int hbase = 0, hl = 0;
+  if (hm) {
+    hl = __ffs(hm) - 1;
+    if (lane == hl) hbase = atomicAdd(S.fill + hkey, __popc(hm));
+  }
+  int okey = -1, base = 0, leader = 0;
+  unsigned peers = 0u;
+  if (om) {
+    okey = other ? bin_key<TX, TY>(p.ci, p.cj, P.map.ntx) : -1;
+    peers = __match_any_sync(FULL, okey);
+    leader = __ffs(peers) - 1;
+    if (okey >= 0 && lane == leader) base = atomicAdd(S.fill + okey, __popc(peers));
+  }
+  // the claimed bin's capacity and start, loaded ahead of the deposit as well
+  const int k0 = home ? hkey : okey;
+  int cap0 = 0, start0 = 0;
+  if (k0 >= 0) {
+    cap0 = __ldg(S.cap + k0);
+    start0 = __ldg(S.start + k0);
+  }
+  if (alive) {
+    unsigned long long W[4];
+    node_weights_q<WT>(P, p, W);
+    if (home) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[k] += (unsigned)W[k];
+    } else {
+      const int li = p.ci - tc.ci0 + kHalo, lj = p.cj - tc.cj0 + kHalo;
+      const bool in_tile = tc.tile != nullptr && li >= 0 && lj >= 0 && li < TX + 2 * kHalo && lj < TY + 2 * kHalo;
+      const int n00 = p.cj * (P.nr + 1) + p.ci;
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        const int dx = n & 1, dy = n >> 1;
+        if (!W[n]) continue;
+        if (in_tile) add_shared64(tc.tile + (lj + dy) * TW + li + dx, (unsigned)W[n]);
+        else atomicAdd(P.dep[s] + n00 + dy * (P.nr + 1) + dx, W[n]);
+      }
+    }
+  }
   int key = -1, pos = 0;
   if (hm) {
-    const int hl = __ffs(hm) - 1;
-    int hbase = 0;
-    if (lane == hl) hbase = atomicAdd(S.fill + hkey, __popc(hm));
     hbase = __shfl_sync(FULL, hbase, hl);
     if (home) {
       key = hkey;
       pos = hbase + __popc(hm & lt);
     }
   }
-  const bool other = alive && !home;
-  if (__any_sync(FULL, other)) {
-    const int okey = other ? bin_key<TX, TY>(p.ci, p.cj, P.map.ntx) : -1;
-    const unsigned peers = __match_any_sync(FULL, okey);
-    const int leader = __ffs(peers) - 1;
-    int base = 0;
-    if (okey >= 0 && lane == leader) base = atomicAdd(S.fill + okey, __popc(peers));
+  if (om) {
     base = __shfl_sync(FULL, base, leader);
     if (other) {
       key = okey;
@@ -871,29 +906,11 @@ __device__ __forceinline__ void emit_home(const PushParams<float> &P, int s, boo
     }
   }
   if (key >= 0) {
-    const bool ovf = !(pos < __ldg(S.cap + key));
-    const int slot = ovf ? overflow_slot(P, S) : __ldg(S.start + key) + pos;
+    const bool ovf = !(pos < cap0);
+    const int slot = ovf ? overflow_slot(P, S) : start0 + pos;
     if (slot >= 0) store_particle<WT>(S, slot, p, p.cj * P.nr + p.ci, ovf, p.id, split ? p.w * 0.5f : p.w);
   }
   emit_split<WT, float, TX, TY>(P, s, split, p, tc);
-  if (!alive) return;
-  unsigned long long W[4];
-  node_weights_q<WT>(P, p, W);
-  if (home) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc[k] += (unsigned)W[k];
-    return;
-  }
-  const int li = p.ci - tc.ci0 + kHalo, lj = p.cj - tc.cj0 + kHalo;
-  const bool in_tile = tc.tile != nullptr && li >= 0 && lj >= 0 && li < TX + 2 * kHalo && lj < TY + 2 * kHalo;
-  const int n00 = p.cj * (P.nr + 1) + p.ci;
-#pragma unroll
-  for (int n = 0; n < 4; ++n) {
-    const int dx = n & 1, dy = n >> 1;
-    if (!W[n]) continue;
-    if (in_tile) add_shared64(tc.tile + (lj + dy) * TW + li + dx, (unsigned)W[n]);
-    else atomicAdd(P.dep[s] + n00 + dy * (P.nr + 1) + dx, W[n]);
-  }
 }
 
 // Add the warp's home-cell node weights (per-lane sums below 2^32) to the
@@ -1065,6 +1082,7 @@ struct ParticleSmem {
   Vec4<float> wa[kW][2][32], wb[kW][2][32];  // per-warp staging of the next chunk
   unsigned long long wid[kW][2][32];
   float ww[WT ? kW : 1][2][32];  // weight ratios (weighted particles)
+  float2 et[(TX + 1) * (TY + 1)];  // E at the tile's nodes (FP32 tile CTAs)
   unsigned cnt[CNT_N];   // the CTA's tallies
   unsigned long long cntw[6];  // and its weighted absorption tallies
 };
@@ -1098,6 +1116,14 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
     tc.ci0 = txi * TX;
     tc.cj0 = tyi * TY;
     for (int k = threadIdx.x; k < TW * TH; k += blockDim.x) smem[k] = 0ull;
+    if constexpr (sizeof(T) == 4) {
+      for (int k = threadIdx.x; k < (TX + 1) * (TY + 1); k += blockDim.x) {
+        const int ni = tc.ci0 + k % (TX + 1), nj = tc.cj0 + k / (TX + 1);
+        float2 v = make_float2(0.f, 0.f);
+        if (ni <= P.nr && nj <= P.nz) v = reinterpret_cast<const float2 *>(P.E)[nj * (P.nr + 1) + ni];
+        sh.et[k] = v;
+      }
+    }
     if (threadIdx.x < 32) {
       // prefix of the tile's in-bin counts and chunk counts
       int carry = 0, ccarry = 0;
@@ -1220,7 +1246,15 @@ __device__ __forceinline__ void particles_cta(const PushParams<T> &P, ParticleSm
           p.ci = hci;
           p.cj = hcj;
         }
-        gather_nodes(P, p.ci, p.cj, en);  // E is small and L1/L2-resident
+        if (ovf_cta) {
+          gather_nodes(P, p.ci, p.cj, en);
+        } else {  // the home cell's nodes, from the tile's copy of E
+          const int e00 = (p.cj - tc.cj0) * (TX + 1) + p.ci - tc.ci0;
+          en[0] = sh.et[e00];
+          en[1] = sh.et[e00 + 1];
+          en[2] = sh.et[e00 + TX + 1];
+          en[3] = sh.et[e00 + TX + 2];
+        }
       }
       // overflow chunks have no home (hci = -1): their lanes claim and deposit by groups
       process_home<TX, TY, WT>(P, s, active, p, tc, en, hci, hcj, b0 + bb, acc);
