@@ -282,6 +282,22 @@ int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss);
  * (synchronises).  Errors: PIC_EINVAL for an unknown selector or short buffer. */
 int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes);
 
+/* pic_diag_async -- enqueue, on the handle's stream, the read of the scalars
+ * (what = PIC_DIAG_SCALARS only; PIC_NSCALARS doubles, the values pic_diag
+ * gives at the same point of the stream) into host_buf, and return without
+ * waiting.  host_buf is the caller's and must stay valid until the copy has
+ * run: after pic_sync, or any call that synchronises, it holds the scalars of
+ * the step the read followed.  In page-locked memory (cudaHostAlloc, a pinned
+ * tensor) the copy is asynchronous; from pageable memory the CUDA runtime may
+ * make it wait.  A run can so log every step's scalars while the host keeps
+ * enqueuing steps ahead of the device.  Errors: PIC_EINVAL for another
+ * selector, a NULL buffer or fewer than PIC_NSCALARS doubles. */
+int pic_diag_async(pic_handle *h, int what, void *host_buf, size_t bytes);
+
+/* pic_sync -- wait until everything enqueued on the handle's stream has run.
+ * Errors: PIC_ECUDA if a launch or copy failed. */
+int pic_sync(pic_handle *h);
+
 /* pic_set_field -- overwrite a node array (PIC_DIAG_PHI, _ER, _EZ, _DEP_E,
  * _DEP_I, _SIGMA or _RHO) from a host buffer: test and restart hook.
  * Setting _ER/_EZ updates the copy the particle gather reads. */

@@ -720,6 +720,66 @@ cudaError_t batch_build(pic_batch *b, int parity) {
   return e;
 }
 
+// The PIC_NSCALARS scalars of pic_diag(PIC_DIAG_SCALARS), assembled by one
+// thread from the device scalars, the last solve's result and the step's
+// counters, with the host-side values (step, nu_max, collision probabilities,
+// q w per species) passed in.  Both the synchronous and the enqueued read use
+// it, so their values agree bit for bit.
+struct ScalarPack {
+  const double *sc, *pcg;
+  const unsigned long long *cnt;
+  double step, t, numax[2], pcoll[2], qw[2];
+  int weighted;
+  double *out;
+};
+
+__global__ void k_pack_scalars(const ScalarPack K) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const double *sc = K.sc;
+  const unsigned long long *cnt = K.cnt;
+  double *o = K.out;
+  o[0] = K.step; o[1] = K.t; o[2] = sc[SC_UE]; o[3] = sc[SC_QE]; o[4] = sc[SC_CEQ];
+  o[5] = sc[SC_ICONV]; o[6] = sc[SC_ICCP];
+  for (int k = 0; k < 6; ++k) o[7 + k] = sc[SC_Y0 + k];
+  o[13] = K.pcg[0]; o[14] = K.pcg[1];
+  o[15] = K.numax[0]; o[16] = K.numax[1]; o[17] = K.pcoll[0]; o[18] = K.pcoll[1];
+  for (int s = 0; s < 2; ++s)
+    for (int k = 0; k < 3; ++k) {
+      o[19 + 3 * s + k] = K.qw[s] * (K.weighted ? (double)cnt[CNT_ABSW + 3 * s + k] / kCreditOne
+                                                : (double)cnt[CNT_ABS + 3 * s + k]);
+      o[25 + 3 * s + k] = (double)cnt[CNT_ABS + 3 * s + k];
+      o[31 + 3 * s + k] = (double)cnt[CNT_COLL + 3 * s + k];
+    }
+  o[36] = 0.0;
+  o[37] = (double)cnt[CNT_BORN + 0]; o[38] = (double)cnt[CNT_BORN + 1];
+  for (int k = 0; k < 3; ++k) o[39 + k] = sc[SC_IONCUR + k];
+  o[42] = sc[SC_I1_RE]; o[43] = sc[SC_I1_IM]; o[44] = sc[SC_WINDOWS]; o[45] = sc[SC_CEQ_GAUSS];
+  o[46] = K.pcg[2];
+  o[47] = (double)cnt[CNT_SPLIT + 0]; o[48] = (double)cnt[CNT_SPLIT + 1];
+}
+
+// Enqueue the scalars' assembly and their copy into host_buf on the handle's stream.
+int enqueue_scalars(pic_handle *h, double *host_buf) {
+  const pic_config &c = h->cfg;
+  ScalarPack K;
+  K.sc = h->d_scalars;
+  K.pcg = h->d_pcg_out;
+  K.cnt = h->d_counters;
+  K.step = h->step;
+  K.t = h->step * c.dt;
+  for (int s = 0; s < 2; ++s) {
+    K.numax[s] = h->numax[s];
+    K.pcoll[s] = h->pcoll[s];
+    K.qw[s] = c.q[s] * c.w[s];
+  }
+  K.weighted = h->weighted ? 1 : 0;
+  K.out = h->d_scal_pack;
+  k_pack_scalars<<<1, 32, 0, h->stream>>>(K);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(host_buf, h->d_scal_pack, sizeof(double) * PIC_NSCALARS, cudaMemcpyDeviceToHost, h->stream));
+  return PIC_OK;
+}
+
 }  // namespace
 
 // =============================================================================
@@ -838,6 +898,7 @@ int pic_init(const pic_config *cfg, void *cuda_stream, pic_handle **out) {
     DA(h->d_ceq_out, sizeof(double) * 2);
     DA(h->d_counters, sizeof(unsigned long long) * CNT_N);
     DA(h->d_scalars, sizeof(double) * SC_N);
+    DA(h->d_scal_pack, sizeof(double) * PIC_NSCALARS);
     DA(h->d_prop, sizeof(double) * 64);
     {
       int nblk = (h->nbins + 1023) / 1024;
@@ -1286,6 +1347,16 @@ int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss) {
   return PIC_OK;
 }
 
+int pic_diag_async(pic_handle *h, int what, void *host_buf, size_t bytes) {
+  if (!h || !host_buf || what != PIC_DIAG_SCALARS || bytes < sizeof(double) * PIC_NSCALARS) return PIC_EINVAL;
+  return enqueue_scalars(h, static_cast<double *>(host_buf));
+}
+
+int pic_sync(pic_handle *h) {
+  if (!h) return PIC_EINVAL;
+  return sync(h);
+}
+
 int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
   if (!h || !host_buf) return PIC_EINVAL;
   const size_t nb = sizeof(double) * h->nn;
@@ -1293,31 +1364,9 @@ int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
   double *o = (double *)host_buf;
   if (what == PIC_DIAG_SCALARS) {
     if (bytes < sizeof(double) * PIC_NSCALARS) return PIC_EINVAL;
-    double sc[SC_N], pcg[3];
-    unsigned long long cnt[CNT_N];
-    CK(cudaMemcpy(sc, h->d_scalars, sizeof(sc), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(pcg, h->d_pcg_out, sizeof(pcg), cudaMemcpyDeviceToHost));
-    CK(cudaMemcpy(cnt, h->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost));
-    const pic_config &c = h->cfg;
-    o[0] = h->step; o[1] = h->step * c.dt; o[2] = sc[SC_UE]; o[3] = sc[SC_QE]; o[4] = sc[SC_CEQ];
-    o[5] = sc[SC_ICONV]; o[6] = sc[SC_ICCP];
-    for (int k = 0; k < 6; ++k) o[7 + k] = sc[SC_Y0 + k];
-    o[13] = pcg[0]; o[14] = pcg[1];
-    o[15] = h->numax[0]; o[16] = h->numax[1]; o[17] = h->pcoll[0]; o[18] = h->pcoll[1];
-    for (int s = 0; s < 2; ++s)
-      for (int k = 0; k < 3; ++k) {
-        o[19 + 3 * s + k] = c.q[s] * c.w[s] *
-                            (h->weighted ? (double)cnt[CNT_ABSW + 3 * s + k] / kCreditOne : (double)cnt[CNT_ABS + 3 * s + k]);
-        o[25 + 3 * s + k] = (double)cnt[CNT_ABS + 3 * s + k];
-        o[31 + 3 * s + k] = (double)cnt[CNT_COLL + 3 * s + k];
-      }
-    o[36] = 0.0;
-    o[37] = (double)cnt[CNT_BORN + 0]; o[38] = (double)cnt[CNT_BORN + 1];
-    for (int k = 0; k < 3; ++k) o[39 + k] = sc[SC_IONCUR + k];
-    o[42] = sc[SC_I1_RE]; o[43] = sc[SC_I1_IM]; o[44] = sc[SC_WINDOWS]; o[45] = sc[SC_CEQ_GAUSS];
-    o[46] = pcg[2];
-    o[47] = (double)cnt[CNT_SPLIT + 0]; o[48] = (double)cnt[CNT_SPLIT + 1];
-    return PIC_OK;
+    int st = enqueue_scalars(h, o);
+    if (st) return st;
+    return sync(h);
   }
   if (what == PIC_DIAG_CIRCUIT) {
     if (bytes < sizeof(double) * 18) return PIC_EINVAL;

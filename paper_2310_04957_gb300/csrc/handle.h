@@ -55,6 +55,7 @@ struct pic_handle {
   // C_eq solve
   double *d_phiL = nullptr, *d_Grc = nullptr, *d_Gzc = nullptr, *d_dinvc = nullptr, *d_energy = nullptr,
          *d_ceq_out = nullptr;
+  double *d_scal_pack = nullptr;  // the PIC_NSCALARS scalars of pic_diag, packed on the device
   // particles, deposits, counters
   unsigned long long *d_dep[2] = {nullptr, nullptr}, *d_surf[2] = {nullptr, nullptr}, *d_counters = nullptr;
   pic::Store st[2][2];  // [buffer][species]

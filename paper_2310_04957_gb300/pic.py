@@ -45,7 +45,7 @@ EXPORTS = ["pic_init", "pic_set_particles", "pic_count", "pic_get_particles", "p
            "pic_conv3x3_op_ex", "pic_attach_unet", "pic_keep_warm", "pic_learned_pair", "pic_learned_stats",
            "pic_unet_loss_backward", "pic_learned_snapshot", "pic_batch_create", "pic_batch_step", "pic_batch_sync",
            "pic_batch_destroy", "pic_set_solver", "pic_check", "pic_set_spin_limit", "pic_save", "pic_load",
-           "pic_pcg_static_result"]
+           "pic_pcg_static_result", "pic_diag_async", "pic_sync"]
 STATIC_MAX_NODES = 139264
 
 
@@ -100,6 +100,8 @@ def lib():
         L.pic_field_solve.argtypes = [P, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(D)]
         L.pic_ceq.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]
         L.pic_diag.argtypes = [P, I, P, ctypes.c_size_t]
+        L.pic_diag_async.argtypes = [P, I, P, ctypes.c_size_t]
+        L.pic_sync.argtypes = [P]
         L.pic_set_field.argtypes = [P, I, P, ctypes.c_size_t]
         L.pic_set_step.argtypes = [P, ctypes.c_uint32]
         L.pic_set_ceq.argtypes = [P, D]
@@ -288,6 +290,18 @@ class Discharge:
         o = np.zeros(NSCALARS)
         _check(lib().pic_diag(self.h, DIAG_SCALARS, _p(o), o.nbytes), "pic_diag(scalars)")
         return dict(zip(SCALARS, o.tolist()))
+
+    def scalars_async(self, out):
+        """Enqueue the read of the scalars at this point of the stream into `out` (a
+        C-contiguous float64 array of at least NSCALARS values, kept alive by the
+        caller; page-locked memory for a copy that does not wait). The values are
+        there after sync() or any synchronising call."""
+        if out.dtype != np.float64 or out.size < NSCALARS or not out.flags.c_contiguous:
+            raise ValueError("scalars_async needs a C-contiguous float64 array of NSCALARS values")
+        _check(lib().pic_diag_async(self.h, DIAG_SCALARS, _p(out), out.nbytes), "pic_diag_async")
+
+    def sync(self):
+        _check(lib().pic_sync(self.h), "pic_sync")
 
     def set_step(self, n):
         _check(lib().pic_set_step(self.h, n), "pic_set_step")
