@@ -47,10 +47,10 @@ MG, PLAIN = 3, 0
 RLC = (0.5, 0.01e-6, 5e-9, 0.0, 0.0, 0.0, 0.0, 0.0)
 
 
-def gec_small(n=200_000, circuit="imn", split_cells=0):
+def gec_small(n=200_000, circuit="imn", split_cells=0, nr=128, nz=64):
     # 128x64 is the coarsest grid on which the 1 mm dielectric ring survives
     # snapping (2 cells); a 3-step RF window makes the third step end a window
-    wl = W.gec_case(128, 64, 30.0, 150.0, n_per_species=n, seed_index=21, split_cells=split_cells)
+    wl = W.gec_case(nr, nz, 30.0, 150.0, n_per_species=n, seed_index=21, split_cells=split_cells)
     wl = dataclasses.replace(wl, steps_per_rf=3, phase_src=0.9)
     if circuit == "rlc":
         wl = dataclasses.replace(wl, circuit=W.CIRCUIT_RLC, circ=RLC)
@@ -72,13 +72,21 @@ CASES = [
     pytest.param(FP32, MG, (4, 4), 0.0, "imn-split", id="fp32-mg-4x4-split"),
     pytest.param(FP32, MG, (4, 4), 1e-6, "imn-split", id="fp32-mg-4x4-split-overflow"),
     pytest.param(FP64, MG, (4, 2), 0.0, "imn-split", id="fp64-mg-4x2-split"),
+    # a 130x66 grid: the last tile of every row and column is ragged (2 of 4 or
+    # 8 cells), and the multigrid levels have odd node counts
+    pytest.param(FP32, MG, (4, 4), 0.0, "imn-ragged", id="fp32-mg-4x4-ragged"),
+    pytest.param(FP32, MG, (8, 4), 1e-6, "imn-ragged", id="fp32-mg-8x4-ragged-overflow"),
+    pytest.param(FP64, MG, (4, 4), 0.0, "imn-ragged", id="fp64-mg-4x4-ragged"),
 ]
 
 
 @pytest.mark.parametrize("precision,solver,tile,slack,circuit", CASES)
 def test_gec_full_steps_match_oracle(precision, solver, tile, slack, circuit):
-    split = circuit.endswith("-split")
-    wl = gec_small(circuit=circuit.removesuffix("-split"), split_cells=8 if split else 0)
+    split, ragged = circuit.endswith("-split"), circuit.endswith("-ragged")
+    grid = dict(nr=130, nz=66) if ragged else {}
+    wl = gec_small(circuit=circuit.split("-")[0], split_cells=8 if split else 0, **grid)
+    if ragged:
+        assert wl.nr % tile[0] and wl.nz % tile[1]
     d, o = make_pair(wl, precision, solver=solver, tile=tile, bin_slack=slack)
     o.init_fields()
     d.start()
