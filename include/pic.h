@@ -504,6 +504,8 @@ int pic_learned_stats(pic_handle *h, double *out4);
  * must outlive the batch.  Unstarted handles are started.
  * pic_batch_step advances all of them by nsteps (asynchronous, except at RF
  * window ends, which run per handle as in pic_step); pic_batch_sync waits.
+ * Each handle's own stream waits for the batch's steps, so a later call on a
+ * handle (pic_diag, pic_diag_async, pic_step) sees their result.
  * Errors: PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA. */
 typedef struct pic_batch pic_batch;
 int pic_batch_create(pic_handle *const *hs, int n, pic_batch **out);

@@ -667,6 +667,7 @@ int download_species(pic_handle *h, int s, pic_particles *out, int64_t capn, int
 void batch_free(pic_batch *b) {
   for (int k = 0; k < 2; ++k)
     if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+  if (b->done) cudaEventDestroy(b->done);
   if (b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -1159,7 +1160,8 @@ int pic_batch_create(pic_handle *const *hs, int n, pic_batch **out) {
     }
     if (sync(h)) { delete b; return PIC_ECUDA; }
   }
-  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     batch_free(b);
     delete b;
@@ -1200,8 +1202,20 @@ int pic_batch_step(pic_batch *b, int nsteps) {
           int st = window_end(h);
           if (st) return st;
         }
+      // the window ends run on the handles' own streams (concurrently): the next
+      // step waits for them, since they rewrite C_eq, the circuit propagator and
+      // the solver scratch that the step's own solve uses
+      for (pic_handle *h : b->hs)
+        if (h->step % (uint32_t)h->cfg.steps_per_rf == 0) {
+          CK(cudaEventRecord(b->done, h->stream));
+          CK(cudaStreamWaitEvent(b->stream, b->done, 0));
+        }
     }
   }
+  // whatever is enqueued on a handle's own stream next (a read, a step) runs
+  // after the batch's steps
+  CK(cudaEventRecord(b->done, b->stream));
+  for (pic_handle *h : b->hs) CK(cudaStreamWaitEvent(h->stream, b->done, 0));
   return PIC_OK;
 }
 

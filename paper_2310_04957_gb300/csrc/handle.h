@@ -95,5 +95,6 @@ struct pic_handle {
 struct pic_batch {
   std::vector<pic_handle *> hs;
   cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;  // recorded after each pic_batch_step; the handles' streams wait on it
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
 };

@@ -14,7 +14,8 @@ from util import rel_l2
 
 pytestmark = pytest.mark.gpu
 
-MIXED = 1
+FP64 = 1
+MIXED, MG = 1, 3
 
 
 def _cases():
@@ -98,6 +99,35 @@ def test_batch_crosses_an_rf_window():
         assert sc["step"] == wls[0].steps_per_rf + 2
         assert np.isfinite(d.field("ne_avg")).all() and d.field("ne_avg").max() > 0
         assert d.status() == 0
+
+
+def test_one_batch_call_across_window_ends_matches_stepping_alone():
+    """One pic_batch_step call that crosses two RF-window ends.  Each window end's
+    C_eq refresh and circuit propagator run on the discharge's own stream and use
+    its solver scratch; the batch's next step must wait for them.  In FP64 (no
+    branch flips) the run then agrees with the same discharges stepped alone by
+    the grid-wide multigrid solve: every particle within 1e-9, C_eq (refreshed
+    with chi) to 1e-9, phi to 1e-8 (the two solve arrangements each meet a 1e-10
+    residual), and no status bits."""
+    P = pic()
+    wls = [dataclasses.replace(wl, steps_per_rf=3) for wl in _cases()[:3]]
+    n = 8
+    solo = [P.Discharge(wl, precision=FP64, solver=MG) for wl in wls]
+    for e in solo:
+        e.step(n)
+    both = [P.Discharge(wl, precision=FP64, solver=MG) for wl in wls]
+    b = P.Batch(both)
+    b.step(n)
+    b.sync()
+    for d, e in zip(both, solo):
+        sd, se = d.scalars(), e.scalars()
+        assert d.status() == 0 and e.status() == 0
+        assert sd["step"] == se["step"] == n and sd["windows"] == se["windows"] == 2
+        assert sd["C_eq"] == pytest.approx(se["C_eq"], rel=1e-9, abs=0)
+        assert rel_l2(d.field("phi"), e.field("phi")) <= 1e-8
+        for s in (0, 1):
+            c = compare_particles(d.get_particles(s), e.get_particles(s), 1e-9)
+            assert c["only_dev"] == 0 and c["only_orc"] == 0 and c["bad"] == 0, c
 
 
 def test_autotuner_picks_a_measured_tile():
