@@ -37,6 +37,7 @@ METRIC = "particle-steps/s (push+MCC+deposit); field-solve ms to 1e-10 residual,
 BYTES_PER_PARTICLE_STEP = {"fp32": 88, "fp64": 152}
 STORED_BYTES_PER_PARTICLE_STEP = {"fp32": 80, "fp64": 144}
 KERNELS_PER_STEP = 10  # layout x3, particles, circuit, assemble x2, solve, efield, diag
+# (plus one per pic_step call: the step counter set on the device)
 KERNELS_PER_WINDOW = 6  # diag window, C_eq refresh (edges, dirichlet, solve, energy), circuit propagator
 
 
@@ -598,7 +599,7 @@ def main():
                                "unit": "particle-steps/s"},
             "field_solve": {"ms": phases[4] / args.steps, "solver": args.solver, "iters": sc["pcg_iters"] if e2e else None,
                             "tol": wl.pcg_tol, "comparison": learned_cmp},
-            "gpu_launches": KERNELS_PER_STEP * args.steps + KERNELS_PER_WINDOW * windows,
+            "gpu_launches": 1 + KERNELS_PER_STEP * args.steps + KERNELS_PER_WINDOW * windows,
             "status_flags": flags,
             "clocks": clk.summary(),
             "e2e": e2e,

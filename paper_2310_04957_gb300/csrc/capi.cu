@@ -337,6 +337,12 @@ int enqueue_particle_phase(pic_handle *h, int in_buf) {
   return launch_push(h, in_buf);
 }
 
+// The device step counter (the Philox counter's first word) set to the host's
+// value, passed as a kernel argument: ordered on the stream like a copy, but
+// with no pageable host buffer to stage (staging may make the host wait for the
+// stream, which would idle the device between calls of pic_step).
+__global__ void k_set_step(uint32_t *d_step, uint32_t v) { *d_step = v; }
+
 // If the learned solve ended on a non-finite value, restart from the warm start.
 __global__ void k_restore_warm(int nn, const int8_t *kind, const double *stats, const double *warm, double *phi) {
   if (stats[2] != -7.0) return;
@@ -1054,8 +1060,8 @@ int pic_start(pic_handle *h) {
 
 int pic_particle_phase(pic_handle *h) {
   if (!h) return PIC_EINVAL;
-  uint32_t step = h->step;
-  CK(cudaMemcpyAsync(h->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, h->stream));
+  k_set_step<<<1, 1, 0, h->stream>>>(h->d_step, h->step);
+  CK(cudaGetLastError());
   int st = enqueue_particle_phase(h, h->cur);
   if (st) return st;
   h->cur ^= 1;
@@ -1068,8 +1074,8 @@ int pic_step(pic_handle *h, int nsteps) {
     int st = pic_start(h);
     if (st) return st;
   }
-  uint32_t step = h->step;
-  CK(cudaMemcpyAsync(h->d_step, &step, sizeof(step), cudaMemcpyHostToDevice, h->stream));
+  k_set_step<<<1, 1, 0, h->stream>>>(h->d_step, h->step);
+  CK(cudaGetLastError());
   for (int k = 0; k < nsteps; ++k) {
     int buf = h->cur;
     if (h->timing) {
