@@ -279,7 +279,14 @@ int pic_ceq(pic_handle *h, int with_chi, double *ceq, double *gauss);
  * handles sums the particles' weight ratios (to 2^-32 of a macro weight). */
 
 /* pic_diag -- copy one diagnostic to a host buffer of `bytes` bytes
- * (synchronises).  Errors: PIC_EINVAL for an unknown selector or short buffer. */
+ * (synchronises).  With PIC_DIAG_DEVICE or'ed into `what`, the buffer is device
+ * memory on the handle's device (a CUDA tensor, say) and the copy is enqueued on
+ * the handle's stream without waiting; work on another stream that reads the
+ * buffer must wait for that stream.  The device form serves the node arrays and
+ * PIC_DIAG_SCALARS, with the values of the host form bit for bit; the other
+ * selectors are host-only.  Errors: PIC_EINVAL for an unknown selector, a
+ * host-only selector with PIC_DIAG_DEVICE, or a short buffer. */
+#define PIC_DIAG_DEVICE 0x10000
 int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes);
 
 /* pic_diag_async -- enqueue, on the handle's stream, the read of the scalars

@@ -765,7 +765,8 @@ __global__ void k_pack_scalars(const ScalarPack K) {
   o[47] = (double)cnt[CNT_SPLIT + 0]; o[48] = (double)cnt[CNT_SPLIT + 1];
 }
 
-// Enqueue the scalars' assembly and their copy into host_buf on the handle's stream.
+// Enqueue the scalars' assembly and (host_buf not NULL) their copy into host_buf on
+// the handle's stream.
 int enqueue_scalars(pic_handle *h, double *host_buf) {
   const pic_config &c = h->cfg;
   ScalarPack K;
@@ -783,7 +784,78 @@ int enqueue_scalars(pic_handle *h, double *host_buf) {
   K.out = h->d_scal_pack;
   k_pack_scalars<<<1, 32, 0, h->stream>>>(K);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(host_buf, h->d_scal_pack, sizeof(double) * PIC_NSCALARS, cudaMemcpyDeviceToHost, h->stream));
+  if (host_buf)
+    CK(cudaMemcpyAsync(host_buf, h->d_scal_pack, sizeof(double) * PIC_NSCALARS, cudaMemcpyDeviceToHost, h->stream));
+  return PIC_OK;
+}
+
+// Fixed-point node counts to doubles on the device, with the host path's
+// arithmetic and rounding: out = sa * (double)a (deposits), or
+// qa * (a * us) + qb * (b * us) (surface charge of both species).  No fused
+// multiply-add, so the values equal pic_diag's host conversion bit for bit.
+__global__ void k_counts_to_f64(int n, const unsigned long long *a, const unsigned long long *b, double sa,
+                                double qa, double qb, double us, double *out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    if (b == nullptr) {
+      out[k] = __dmul_rn((double)a[k], sa);
+    } else {
+      out[k] = __dadd_rn(__dmul_rn(qa, __dmul_rn((double)a[k], us)), __dmul_rn(qb, __dmul_rn((double)b[k], us)));
+    }
+  }
+}
+
+// Enqueue the conversion of PIC_DIAG_DEP_E, _DEP_I or _SIGMA into dst (device).
+int enqueue_counts(pic_handle *h, int what, double *dst) {
+  if (what == PIC_DIAG_SIGMA) {
+    const pic_config &c = h->cfg;
+    k_counts_to_f64<<<256, 256, 0, h->stream>>>(h->nn, h->d_surf[0], h->d_surf[1], 0.0, c.q[0] * c.w[0],
+                                               c.q[1] * c.w[1], h->weighted ? 1.0 / kCreditOne : 1.0, dst);
+  } else {
+    k_counts_to_f64<<<256, 256, 0, h->stream>>>(h->nn, h->d_dep[what - PIC_DIAG_DEP_E], nullptr, dep_inv_scale(h),
+                                               0.0, 0.0, 0.0, dst);
+  }
+  CK(cudaGetLastError());
+  return PIC_OK;
+}
+
+// pic_diag into a device buffer: enqueued on the handle's stream, no host wait.
+int diag_to_device(pic_handle *h, int what, double *dst, size_t bytes) {
+  const size_t nb = sizeof(double) * h->nn;
+  if (what == PIC_DIAG_SCALARS) {
+    if (bytes < sizeof(double) * PIC_NSCALARS) return PIC_EINVAL;
+    int st = enqueue_scalars(h, nullptr);
+    if (st) return st;
+    CK(cudaMemcpyAsync(dst, h->d_scal_pack, sizeof(double) * PIC_NSCALARS, cudaMemcpyDeviceToDevice, h->stream));
+    return PIC_OK;
+  }
+  if (bytes < nb) return PIC_EINVAL;
+  const double *src = nullptr;
+  switch (what) {
+    case PIC_DIAG_PHI: src = h->d_phi; break;
+    case PIC_DIAG_ER: src = h->d_Er; break;
+    case PIC_DIAG_EZ: src = h->d_Ez; break;
+    case PIC_DIAG_CHI: src = h->d_chi; break;
+    case PIC_DIAG_VNODE: src = h->d_vnode; break;
+    case PIC_DIAG_RHO: src = h->d_qrhs; break;
+    case PIC_DIAG_NE_AVG: src = h->d_dens_avg[0]; break;
+    case PIC_DIAG_NI_AVG: src = h->d_dens_avg[1]; break;
+    case PIC_DIAG_PHI_WARM: src = h->d_phi_warm; break;
+    case PIC_DIAG_PHI_P: src = h->vahedi ? h->d_phiP : nullptr; break;
+    case PIC_DIAG_PHI_L0: src = h->vahedi ? h->d_phiL : nullptr; break;
+    case PIC_DIAG_PHI_L0 + 1:
+    case PIC_DIAG_PHI_L0 + 2:
+    case PIC_DIAG_PHI_L0 + 3: {
+      const int k = what - PIC_DIAG_PHI_L0 - 1;
+      src = (h->vahedi && k < h->cfg.n_drive) ? h->d_phiLd[k] : nullptr;
+      break;
+    }
+    case PIC_DIAG_DEP_E:
+    case PIC_DIAG_DEP_I:
+    case PIC_DIAG_SIGMA: return enqueue_counts(h, what, dst);
+    default: return PIC_EINVAL;
+  }
+  if (src == nullptr) return PIC_EINVAL;
+  CK(cudaMemcpyAsync(dst, src, nb, cudaMemcpyDeviceToDevice, h->stream));
   return PIC_OK;
 }
 
@@ -1379,6 +1451,7 @@ int pic_sync(pic_handle *h) {
 
 int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
   if (!h || !host_buf) return PIC_EINVAL;
+  if (what & PIC_DIAG_DEVICE) return diag_to_device(h, what & ~PIC_DIAG_DEVICE, static_cast<double *>(host_buf), bytes);
   const size_t nb = sizeof(double) * h->nn;
   if (sync(h)) return PIC_ECUDA;
   double *o = (double *)host_buf;
@@ -1455,23 +1528,14 @@ int pic_diag(pic_handle *h, int what, void *host_buf, size_t bytes) {
       return PIC_OK;
     }
     case PIC_DIAG_DEP_E:
-    case PIC_DIAG_DEP_I: {
-      std::vector<unsigned long long> u(h->nn);
-      CK(cudaMemcpy(u.data(), h->d_dep[what - PIC_DIAG_DEP_E], sizeof(unsigned long long) * h->nn,
-                    cudaMemcpyDeviceToHost));
-      double sc = dep_inv_scale(h);
-      for (int a = 0; a < h->nn; ++a) o[a] = (double)u[a] * sc;
-      return PIC_OK;
-    }
+    case PIC_DIAG_DEP_I:
     case PIC_DIAG_SIGMA: {
-      std::vector<unsigned long long> u0(h->nn), u1(h->nn);
-      CK(cudaMemcpy(u0.data(), h->d_surf[0], sizeof(unsigned long long) * h->nn, cudaMemcpyDeviceToHost));
-      CK(cudaMemcpy(u1.data(), h->d_surf[1], sizeof(unsigned long long) * h->nn, cudaMemcpyDeviceToHost));
-      const pic_config &c = h->cfg;
-      const double us = h->weighted ? 1.0 / kCreditOne : 1.0;
-      for (int a = 0; a < h->nn; ++a)
-        o[a] = c.q[0] * c.w[0] * ((double)u0[a] * us) + c.q[1] * c.w[1] * ((double)u1[a] * us);
-      return PIC_OK;
+      // converted on the device (the solver's scratch vector holds them), as in
+      // the device form, then copied
+      int st = enqueue_counts(h, what, h->d_work);
+      if (st) return st;
+      CK(cudaMemcpyAsync(o, h->d_work, nb, cudaMemcpyDeviceToHost, h->stream));
+      return sync(h);
     }
     default: return PIC_EINVAL;
   }

@@ -28,6 +28,7 @@ DIAG_SCALARS = 100
 DIAG_STORE = 101
 DIAG_SOLVER = 102
 DIAG_CIRCUIT = 103
+DIAG_DEVICE = 0x10000  # or'ed into a selector: the buffer is device memory
 NSCALARS = 49
 SCALARS = ["step", "t", "U_E", "Q_E", "C_eq", "I_conv", "I_ccp", "y0", "y1", "y2", "y3", "y4", "y5", "pcg_iters",
            "pcg_relres", "numax_e", "numax_i", "pcoll_e", "pcoll_i", "absq_e_pow", "absq_e_gnd", "absq_e_surf",
@@ -133,6 +134,13 @@ def _p(a):
 def _check(code, what):
     if code != PIC_OK:
         raise PicError(code, what)
+
+
+def _check_device_out(out, n):
+    import torch
+
+    if not (out.is_cuda and out.dtype == torch.float64 and out.is_contiguous() and out.numel() >= n):
+        raise ValueError(f"needs a contiguous float64 CUDA tensor of at least {n} values")
 
 
 def _stream(stream):
@@ -259,6 +267,21 @@ class Discharge:
         o = np.zeros(self.n_nodes)
         _check(lib().pic_diag(self.h, DIAG[name], _p(o), o.nbytes), f"pic_diag({name})")
         return o.reshape(self.nz + 1, self.nr + 1)
+
+    def field_to(self, name, out):
+        """Enqueue the copy of a node array into `out`, a contiguous float64 CUDA tensor of
+        at least n_nodes values on the handle's device (no host round trip; the copy runs
+        on the handle's stream)."""
+        _check_device_out(out, self.n_nodes)
+        _check(lib().pic_diag(self.h, DIAG[name] | DIAG_DEVICE, ctypes.c_void_p(out.data_ptr()),
+                              out.numel() * 8), f"pic_diag({name}, device)")
+
+    def scalars_to(self, out):
+        """Enqueue the scalars' copy into `out`, a contiguous float64 CUDA tensor of at least
+        NSCALARS values (the handle's stream)."""
+        _check_device_out(out, NSCALARS)
+        _check(lib().pic_diag(self.h, DIAG_SCALARS | DIAG_DEVICE, ctypes.c_void_p(out.data_ptr()),
+                              out.numel() * 8), "pic_diag(scalars, device)")
 
     def set_field(self, name, values):
         v = np.ascontiguousarray(values, np.float64).ravel()

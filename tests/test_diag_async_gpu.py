@@ -1,5 +1,5 @@
-"""The enqueued scalar read (pic_diag_async) against the synchronising one
-(pic_diag), through the C ABI.
+"""The enqueued scalar read (pic_diag_async) and device-buffer reads
+(PIC_DIAG_DEVICE) against the synchronising host read (pic_diag), through the C ABI.
 
 - At the same point of the stream both give the same PIC_NSCALARS doubles, bit
   for bit (one device-side assembly serves both).
@@ -8,6 +8,8 @@
   values: the log of a pipelined run equals the synchronous reads of the same
   run stepped again from the same start (the step is deterministic).
 - Another selector, a short or NULL buffer are rejected with PIC_EINVAL.
+- Into CUDA tensors, every node array and the scalars equal the host read bit
+  for bit; host-only selectors and short buffers are rejected.
 """
 import ctypes
 
@@ -89,4 +91,53 @@ def test_async_read_rejects_other_selectors_and_short_buffers():
     assert L.pic_diag_async(d.h, P.DIAG_SCALARS, p, buf.nbytes) == P.PIC_OK
     assert L.pic_sync(d.h) == P.PIC_OK
     assert buf[0] == 0.0  # step 0 after start
+    d.close()
+
+
+NODE_FIELDS = ("phi", "Er", "Ez", "chi", "dep_e", "dep_i", "sigma", "vnode", "rho", "ne_avg", "ni_avg",
+               "phi_warm")
+
+
+@pytest.mark.parametrize("precision,solver", [(0, 3), (1, 0)])
+def test_device_buffers_receive_the_host_values(precision, solver):
+    """pic_diag with PIC_DIAG_DEVICE into CUDA tensors: every node array and the
+    scalars equal the host form bit for bit (one device-side conversion serves
+    both), after steps that end an RF window (so the window averages are set)."""
+    import dataclasses
+
+    import torch
+
+    P = pic()
+    wl = dataclasses.replace(small(20_000), steps_per_rf=3)
+    d = P.Discharge(wl, precision=precision, solver=solver)
+    d.start()
+    d.step(4)
+    n = d.n_nodes
+    for name in NODE_FIELDS:
+        t = torch.full((n,), float("nan"), dtype=torch.float64, device="cuda")
+        d.field_to(name, t)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(t.cpu().numpy(), d.field(name).ravel(), err_msg=name)
+    t = torch.full((P.NSCALARS,), float("nan"), dtype=torch.float64, device="cuda")
+    d.scalars_to(t)
+    torch.cuda.synchronize()
+    sc = d.scalars()
+    np.testing.assert_array_equal(t.cpu().numpy(), np.array([sc[k] for k in P.SCALARS]))
+    d.close()
+
+
+def test_device_buffers_reject_host_only_selectors_and_short_buffers():
+    import torch
+
+    P = pic()
+    d = P.Discharge(small(5_000))
+    d.start()
+    L = P.lib()
+    t = torch.zeros(d.n_nodes, dtype=torch.float64, device="cuda")
+    ptr = ctypes.c_void_p(t.data_ptr())
+    for sel in (P.DIAG_CIRCUIT, P.DIAG_SOLVER, P.DIAG_STORE, P.DIAG["phiP"]):  # phiP: not a Vahedi handle
+        assert L.pic_diag(d.h, sel | P.DIAG_DEVICE, ptr, t.numel() * 8) == P.PIC_EINVAL, sel
+    assert L.pic_diag(d.h, P.DIAG["phi"] | P.DIAG_DEVICE, ptr, t.numel() * 8 - 8) == P.PIC_EINVAL
+    with pytest.raises(ValueError):
+        d.field_to("phi", torch.zeros(d.n_nodes, dtype=torch.float32, device="cuda"))
     d.close()
