@@ -35,7 +35,6 @@ import pytest
 from gpu_common import make_pair
 from parity_tools import StepParity, phi_err
 from paper_2310_04957_gb300 import workloads as W
-from util import rel_l2
 
 pytestmark = pytest.mark.gpu
 

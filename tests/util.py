@@ -1,6 +1,5 @@
 """Small workload builders and comparison helpers shared by the tests."""
 import dataclasses
-import math
 
 import numpy as np
 
