@@ -25,7 +25,13 @@ step) and compares, per step:
   particle flipped in the step (measured 2e-9 to 4e-9; a flip moves one
   macroparticle's charge and is accounted for by the deposit check);
 - U_E, Q_E and I_conv of the circuit (Eqs. 5, 8, 10), and after the RF window
-  the chi-inclusive C_eq refresh (Eqs. 6-7) and the window averages.
+  the chi-inclusive C_eq refresh (Eqs. 6-7) and the window averages;
+- the window's circuit post-processing (Eqs. 11-14: impedances, powers, Gamma)
+  to 1e-6 (FP32) or 1e-9 (FP64) while no particle has flipped: a flipped
+  absorption at the powered electrode changes that step's I_conv by one
+  macroparticle's charge over dt, which the per-step I_conv bound checks.
+Whatever flipped, every step also compares phi with the oracle's solve of the
+device's own charge (1e-8), so no FP32 step leaves phi unchecked.
 """
 import dataclasses
 
